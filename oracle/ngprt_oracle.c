@@ -1,0 +1,868 @@
+/*
+ * ngprt_oracle.c -- plain CPU oracle of the NGP-RT render path (arXiv 2407.10482).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the package smoke check and the
+ * benchmark's CPU-baseline / reference arm load this library.  It shares no code,
+ * header or constant table with the CUDA library; both sides receive the same
+ * seeded input arrays and nothing else.
+ *
+ * Precision.  Every feature, attention, compositing, MLP and gradient value is
+ * computed in FP64.  The march itself (ray set-up, sample positions t, the
+ * contraction, occupancy voxel choice, empty-space steps) is a recurrence whose
+ * results are integers (which voxel, which sample), so it is evaluated in FP32,
+ * one IEEE-rounded operation at a time with no fused multiply-add (compile with
+ * -ffp-contract=off): the kernel takes the same decisions in the same precision.
+ * The grid cell of a trilinear lookup (an integer) is chosen the same way from the
+ * FP32 position; its interpolation weights are FP64.
+ *
+ * Where each function comes from:
+ *   volume rendering quadrature ........ Eq. 2 (Sec. 3, Preliminaries)
+ *   deferred shading C = C_d + MLP ..... Eq. 5
+ *   hash-grid encoding ................. Eq. 3 and Sec. S2.1 (the spatial hash of
+ *                                         Instant-NGP, which the paper builds on)
+ *   feature construction f = f~ + f^ ... Eq. 6
+ *   attention a = [w1,b1,...] .......... Eq. 7;  Att(...) weighted sums ..... Eq. 8
+ *   occupancy distance step ............ Eq. 9 (Sec. 3.3)
+ *   5-level occupancy pyramid, T<2e-3 .. Sec. S2.5 (Real-time Rendering)
+ *   activations (exp, sigmoid) ......... Sec. S2.1 (Activation Layers)
+ *   SH16 view embedding ................ Sec. S2.1 (Forward Pass)
+ * Readings of passages the paper leaves open are listed with the build's design
+ * notes (hash function, distance metric of G, delta_i, background, contraction).
+ */
+#define _DEFAULT_SOURCE
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_MAXL 32
+#define OR_NFEAT 8
+#define OR_MLP_IN 32
+
+typedef struct {
+    int L;
+    int T_log2;
+    int N[OR_MAXL];
+    const double* tables;  /* [n_entries][8] */
+    int R_C;
+    const double* coarse;  /* [R_C^3][8 + 2L] */
+    int mlp_layers;
+    int mlp_width;
+    const double* mlp_w;   /* layer k: [out_k][in_k] row-major, concatenated */
+    int bounded;
+} or_scene;
+
+typedef struct {
+    int R_O;
+    int n_levels;
+    const uint32_t* bits;  /* pyramid, finest level first */
+    const uint8_t* dist;   /* R_O^3 occupancy distance grid, or NULL */
+} or_occ;
+
+typedef struct {
+    float step_base;
+    float step_gamma;
+    float t_min;
+    float r_far;
+    float t_term;
+    double bg[3];
+    int max_march;
+    int max_samples;
+    int use_dist;
+    int lattice_snap;
+    int attn_mode;  /* 0 separate (w, b per level), 1 SUM (w = b = 1), 2 shared (b = w) */
+    int dist_rule;  /* 0: Eq. 9 as printed (v G when G > 0); 1: max(v G, s_O) */
+} or_opts;
+
+/* ------------------------------------------------------------------ hashing */
+
+/* Spatial hash of Instant-NGP: XOR of the coordinates times large primes,
+ * uint32 wrap-around, modulo the power-of-two table size. */
+uint32_t or_hash(uint32_t x, uint32_t y, uint32_t z, uint32_t T) {
+    uint32_t h = (x * 1u) ^ (y * 2654435761u) ^ (z * 805459861u);
+    return h % T;
+}
+
+/* Entry of vertex (x, y, z) inside one level: dense row-major (x fastest) when
+ * the level's N^3 vertices fit in T entries, else the spatial hash. */
+uint64_t or_level_entry(int N, uint32_t T, int x, int y, int z) {
+    uint64_t n = (uint64_t)N;
+    if (n * n * n <= (uint64_t)T)
+        return (uint64_t)x + n * ((uint64_t)y + n * (uint64_t)z);
+    return (uint64_t)or_hash((uint32_t)x, (uint32_t)y, (uint32_t)z, T);
+}
+
+void or_hash_batch(const uint32_t* xyz, int n, uint32_t T, uint32_t* out) {
+    for (int i = 0; i < n; ++i) out[i] = or_hash(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], T);
+}
+
+uint64_t or_level_offset(const int* N, int L, int T_log2, int l) {
+    uint64_t T = 1ull << T_log2, off = 0;
+    for (int j = 0; j < l && j < L; ++j) {
+        uint64_t n = (uint64_t)N[j];
+        uint64_t e = n * n * n;
+        off += e < T ? e : T;
+    }
+    return off;
+}
+
+/* Trilinear cell of a vertex grid of N vertices per axis covering u in [0, 1]:
+ * p = u (N - 1).  The integer cell is chosen in FP32 (as the kernel chooses it),
+ * clamped to [0, N-2]; the fractional weights are FP64. */
+static void or_cell(const float u[3], int N, int base[3], double w[3]) {
+    for (int a = 0; a < 3; ++a) {
+        float pf = u[a] * (float)(N - 1);
+        float bf = floorf(pf);
+        bf = fminf(fmaxf(bf, 0.0f), (float)(N - 2));
+        base[a] = (int)bf;
+        w[a] = (double)u[a] * (double)(N - 1) - (double)bf;
+    }
+}
+
+/* For tests: per position, per level, the 8 corner entry indices (absolute row in
+ * the concatenated tables) and the 3 FP64 weights.  Corner c takes +1 on x if bit0,
+ * on y if bit1, on z if bit2. */
+void or_grid_indices(const int* N, int L, int T_log2, const float* u, int n,
+                     uint64_t* idx_out, double* w_out) {
+    uint32_t T = 1u << T_log2;
+    for (int i = 0; i < n; ++i) {
+        for (int l = 0; l < L; ++l) {
+            int base[3];
+            double w[3];
+            or_cell(u + 3 * i, N[l], base, w);
+            uint64_t off = or_level_offset(N, L, T_log2, l);
+            for (int c = 0; c < 8; ++c) {
+                int x = base[0] + (c & 1), y = base[1] + ((c >> 1) & 1), z = base[2] + ((c >> 2) & 1);
+                idx_out[((size_t)i * L + l) * 8 + c] = off + or_level_entry(N[l], T, x, y, z);
+            }
+            for (int a = 0; a < 3; ++a) w_out[((size_t)i * L + l) * 3 + a] = w[a];
+        }
+    }
+}
+
+/* --------------------------------------------------- occupancy and distance */
+
+static size_t or_words(size_t bits) { return (bits + 31) / 32; }
+
+size_t or_pyramid_words(int R, int n_levels) {
+    size_t total = 0;
+    for (int k = 0; k < n_levels; ++k) {
+        size_t r = (size_t)(R >> k);
+        total += or_words(r * r * r);
+    }
+    return total;
+}
+
+static int or_bit(const uint32_t* w, size_t i) { return (int)((w[i >> 5] >> (i & 31)) & 1u); }
+
+/* Occupancy pyramid, finest first; a coarser voxel is occupied iff any of its
+ * 8 children is (Sec. S2.5: the grid is down-sampled to coarser levels). */
+void or_build_pyramid(const uint8_t* occ, int R, int n_levels, uint32_t* bits) {
+    memset(bits, 0, or_pyramid_words(R, n_levels) * 4);
+    size_t R3 = (size_t)R * R * R;
+    for (size_t i = 0; i < R3; ++i)
+        if (occ[i]) bits[i >> 5] |= 1u << (i & 31);
+    size_t off_prev = 0, off = or_words(R3);
+    for (int k = 1; k < n_levels; ++k) {
+        int rp = R >> (k - 1), r = R >> k;
+        for (int z = 0; z < r; ++z)
+            for (int y = 0; y < r; ++y)
+                for (int x = 0; x < r; ++x) {
+                    int any = 0;
+                    for (int c = 0; c < 8; ++c) {
+                        size_t cx = 2 * x + (c & 1), cy = 2 * y + ((c >> 1) & 1), cz = 2 * z + ((c >> 2) & 1);
+                        any |= or_bit(bits + off_prev, cx + (size_t)rp * (cy + (size_t)rp * cz));
+                    }
+                    size_t i = (size_t)x + (size_t)r * ((size_t)y + (size_t)r * z);
+                    if (any) bits[off + (i >> 5)] |= 1u << (i & 31);
+                }
+        off_prev = off;
+        off += or_words((size_t)r * r * r);
+    }
+}
+
+static int64_t or_isqrt(int64_t v) {
+    int64_t s = (int64_t)sqrt((double)v);
+    while (s * s > v) --s;
+    while ((s + 1) * (s + 1) <= v) ++s;
+    return s;
+}
+
+/* Squared box-to-box gap along one axis between voxel p and voxel q, in voxels:
+ * max(|p - q| - 1, 0)^2.  Summed over the axes it is the squared Euclidean distance
+ * between the two closed voxel boxes. */
+static int64_t or_gap2(int k) {
+    int64_t g = (k < 0 ? -k : k) - 1;
+    return g > 0 ? g * g : 0;
+}
+
+/* Occupancy distance grid G by brute force (Sec. 3.3: distance to the nearest
+ * occupied voxel, rounded down, in voxel units, stored as uint8).  Distance is
+ * between voxel boxes; G = min(255, floor(sqrt(D^2))); 255 when nothing is
+ * occupied.  O(R^3 x occupied): for small grids. */
+void or_occ_dist_brute(const uint8_t* occ, int R, uint8_t* dist) {
+    size_t R3 = (size_t)R * R * R;
+    for (size_t p = 0; p < R3; ++p) {
+        int px = (int)(p % R), py = (int)((p / R) % R), pz = (int)(p / ((size_t)R * R));
+        int64_t best = -1;
+        for (size_t q = 0; q < R3; ++q) {
+            if (!occ[q]) continue;
+            int qx = (int)(q % R), qy = (int)((q / R) % R), qz = (int)(q / ((size_t)R * R));
+            int64_t d2 = or_gap2(px - qx) + or_gap2(py - qy) + or_gap2(pz - qz);
+            if (best < 0 || d2 < best) best = d2;
+        }
+        dist[p] = (uint8_t)(best < 0 ? 255 : (or_isqrt(best) < 255 ? or_isqrt(best) : 255));
+    }
+}
+
+/* Same quantity by three exact 1-D minimisations: the squared box distance is a sum
+ * of per-axis terms, so min over q of the sum = nested minima axis by axis.
+ * O(R^4); used for grids too large for brute force. */
+void or_occ_dist(const uint8_t* occ, int R, uint8_t* dist) {
+    size_t R3 = (size_t)R * R * R;
+    const int64_t INF = (int64_t)1 << 40;
+    int64_t* a = (int64_t*)malloc(R3 * sizeof(int64_t));
+    int64_t* b = (int64_t*)malloc(R3 * sizeof(int64_t));
+    for (int z = 0; z < R; ++z)
+        for (int y = 0; y < R; ++y)
+            for (int x = 0; x < R; ++x) {
+                int64_t best = INF;
+                for (int q = 0; q < R; ++q)
+                    if (occ[(size_t)q + (size_t)R * (y + (size_t)R * z)]) {
+                        int64_t v = or_gap2(x - q);
+                        if (v < best) best = v;
+                    }
+                a[(size_t)x + (size_t)R * (y + (size_t)R * z)] = best;
+            }
+    for (int z = 0; z < R; ++z)
+        for (int y = 0; y < R; ++y)
+            for (int x = 0; x < R; ++x) {
+                int64_t best = INF;
+                for (int q = 0; q < R; ++q) {
+                    int64_t v = a[(size_t)x + (size_t)R * (q + (size_t)R * z)];
+                    if (v < INF && v + or_gap2(y - q) < best) best = v + or_gap2(y - q);
+                }
+                b[(size_t)x + (size_t)R * (y + (size_t)R * z)] = best;
+            }
+    for (int z = 0; z < R; ++z)
+        for (int y = 0; y < R; ++y)
+            for (int x = 0; x < R; ++x) {
+                int64_t best = INF;
+                for (int q = 0; q < R; ++q) {
+                    int64_t v = b[(size_t)x + (size_t)R * (y + (size_t)R * q)];
+                    if (v < INF && v + or_gap2(z - q) < best) best = v + or_gap2(z - q);
+                }
+                int64_t g = best >= INF ? 255 : or_isqrt(best);
+                dist[(size_t)x + (size_t)R * (y + (size_t)R * z)] = (uint8_t)(g < 255 ? g : 255);
+            }
+    free(a);
+    free(b);
+}
+
+/* --------------------------------------------------------- view embedding */
+
+/* Real spherical harmonics of bands 0..3 (16 values) of the unit direction d, in
+ * the order l^2 + l + m, m = -l..l; Y_l^m = sqrt(2) K_l^|m| P_l^|m|(cos th) times
+ * cos(m phi) (m > 0) or sin(|m| phi) (m < 0), K_l^m = sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!),
+ * associated Legendre functions without the Condon-Shortley phase.  Evaluated from
+ * the definition by the three-term recurrence, in FP64 (Sec. S2.1). */
+void or_sh16(const double d[3], double out[16]) {
+    double x = d[2];                       /* cos(theta) */
+    double s = sqrt(fmax(0.0, 1.0 - x * x));
+    double phi = atan2(d[1], d[0]);
+    double P[4][4];
+    memset(P, 0, sizeof P);
+    for (int m = 0; m <= 3; ++m) {
+        double pmm = 1.0;
+        for (int k = 1; k <= m; ++k) pmm *= (2.0 * k - 1.0) * s;
+        P[m][m] = pmm;
+        if (m + 1 <= 3) P[m + 1][m] = x * (2.0 * m + 1.0) * pmm;
+        for (int l = m + 2; l <= 3; ++l)
+            P[l][m] = (x * (2.0 * l - 1.0) * P[l - 1][m] - (l + m - 1.0) * P[l - 2][m]) / (l - m);
+    }
+    for (int l = 0; l <= 3; ++l)
+        for (int m = -l; m <= l; ++m) {
+            int am = m < 0 ? -m : m;
+            double fr = 1.0;  /* (l-|m|)!/(l+|m|)! */
+            for (int k = l - am + 1; k <= l + am; ++k) fr /= (double)k;
+            double K = sqrt((2.0 * l + 1.0) / (4.0 * 3.14159265358979323846) * fr);
+            double v;
+            if (m == 0) v = K * P[l][0];
+            else if (m > 0) v = sqrt(2.0) * K * cos(m * phi) * P[l][am];
+            else v = sqrt(2.0) * K * sin(am * phi) * P[l][am];
+            out[l * l + l + m] = v;
+        }
+}
+
+void or_sh16_batch(const double* d, int n, double* out) {
+    for (int i = 0; i < n; ++i) or_sh16(d + 3 * i, out + 16 * i);
+}
+
+/* ----------------------------------------------------------- deferred MLP */
+
+static int or_mlp_out(const or_scene* s, int k) { return k == s->mlp_layers - 1 ? 3 : s->mlp_width; }
+static int or_mlp_in(const or_scene* s, int k) { return k == 0 ? OR_MLP_IN : s->mlp_width; }
+
+/* MLP_psi of Eq. 5: dense layers without bias, ReLU on hidden layers, linear
+ * output of 3.  Stores every layer's pre-activation in acts (for the reverse pass). */
+static void or_mlp_forward(const or_scene* s, const double* x, double* y, double* acts) {
+    double h[256], g[256];
+    memcpy(h, x, OR_MLP_IN * sizeof(double));
+    const double* w = s->mlp_w;
+    size_t ao = 0;
+    for (int k = 0; k < s->mlp_layers; ++k) {
+        int no = or_mlp_out(s, k), ni = or_mlp_in(s, k);
+        for (int o = 0; o < no; ++o) {
+            double acc = 0.0;
+            for (int i = 0; i < ni; ++i) acc += w[(size_t)o * ni + i] * h[i];
+            g[o] = acc;
+            if (acts) acts[ao + o] = acc;
+        }
+        ao += no;
+        w += (size_t)no * ni;
+        for (int o = 0; o < no; ++o) h[o] = (k == s->mlp_layers - 1) ? g[o] : (g[o] > 0.0 ? g[o] : 0.0);
+    }
+    memcpy(y, h, 3 * sizeof(double));
+}
+
+void or_mlp_batch(const or_scene* s, const double* x, int n, double* y) {
+    for (int i = 0; i < n; ++i) or_mlp_forward(s, x + (size_t)OR_MLP_IN * i, y + 3 * i, NULL);
+}
+
+/* ----------------------------------------------------- feature construction */
+
+static double or_sigmoid(double v) { return 1.0 / (1.0 + exp(-v)); }
+
+/* Per-sample quantities the reverse pass needs again. */
+typedef struct {
+    float t, delta, u[3];
+    double sigma_raw, sigma, alpha, T_before;
+    double f[OR_NFEAT];          /* fused deferred feature [sigma_raw, c_d, v_s] */
+} or_sample;
+
+/* Trilinear interpolation over one grid: 8 corners, weight prod(w or 1-w). */
+static double or_corner_weight(const double w[3], int c) {
+    double wx = (c & 1) ? w[0] : 1.0 - w[0];
+    double wy = (c & 2) ? w[1] : 1.0 - w[1];
+    double wz = (c & 4) ? w[2] : 1.0 - w[2];
+    return wx * wy * wz;
+}
+
+/* Eq. 6-8: f = f~ + Att(f^1..f^L; a), f~ and a trilinear in the coarse grid, a
+ * squashed by a sigmoid after interpolation (Sec. S2.1), f^l trilinear in level l. */
+static void or_features(const or_scene* s, const or_opts* op, const float u[3], double f[OR_NFEAT]) {
+    int nch = OR_NFEAT + 2 * s->L;
+    double coarse[OR_NFEAT + 2 * OR_MAXL];
+    int base[3];
+    double w[3];
+    memset(coarse, 0, sizeof coarse);
+    or_cell(u, s->R_C, base, w);
+    for (int c = 0; c < 8; ++c) {
+        int x = base[0] + (c & 1), y = base[1] + ((c >> 1) & 1), z = base[2] + ((c >> 2) & 1);
+        size_t v = (size_t)x + (size_t)s->R_C * ((size_t)y + (size_t)s->R_C * z);
+        double cw = or_corner_weight(w, c);
+        for (int ch = 0; ch < nch; ++ch) coarse[ch] += cw * s->coarse[v * nch + ch];
+    }
+    for (int ch = 0; ch < OR_NFEAT; ++ch) f[ch] = coarse[ch];
+    uint32_t T = 1u << s->T_log2;
+    for (int l = 0; l < s->L; ++l) {
+        double om, be;
+        if (op->attn_mode == 1) { om = 1.0; be = 1.0; }
+        else if (op->attn_mode == 2) { om = or_sigmoid(coarse[OR_NFEAT + 2 * l]); be = om; }
+        else { om = or_sigmoid(coarse[OR_NFEAT + 2 * l]); be = or_sigmoid(coarse[OR_NFEAT + 2 * l + 1]); }
+        double fl[OR_NFEAT];
+        memset(fl, 0, sizeof fl);
+        or_cell(u, s->N[l], base, w);
+        uint64_t off = or_level_offset(s->N, s->L, s->T_log2, l);
+        for (int c = 0; c < 8; ++c) {
+            int x = base[0] + (c & 1), y = base[1] + ((c >> 1) & 1), z = base[2] + ((c >> 2) & 1);
+            uint64_t e = off + or_level_entry(s->N[l], T, x, y, z);
+            double cw = or_corner_weight(w, c);
+            for (int ch = 0; ch < OR_NFEAT; ++ch) fl[ch] += cw * s->tables[e * OR_NFEAT + ch];
+        }
+        f[0] += om * fl[0];
+        for (int ch = 1; ch < OR_NFEAT; ++ch) f[ch] += be * fl[ch];
+    }
+}
+
+/* ------------------------------------------------------------- FP32 march */
+
+/* Contraction of mip-NeRF 360 (the unbounded configuration): identity inside the
+ * unit ball, else (2 - 1/r) x / r.  FP32, one rounding per operation. */
+static void or_point(const or_scene* s, const float o[3], const float d[3], float t,
+                     float x[3], float y[3], float u[3], float* r_out) {
+    for (int a = 0; a < 3; ++a) x[a] = o[a] + t * d[a];
+    float r2 = (x[0] * x[0] + x[1] * x[1]) + x[2] * x[2];
+    float r = sqrtf(r2);
+    *r_out = r;
+    float B = s->bounded ? 1.0f : 2.0f, hB = s->bounded ? 0.5f : 0.25f;
+    if (!s->bounded && r > 1.0f) {
+        float k = (2.0f - 1.0f / r) / r;
+        for (int a = 0; a < 3; ++a) y[a] = x[a] * k;
+    } else {
+        for (int a = 0; a < 3; ++a) y[a] = x[a];
+    }
+    for (int a = 0; a < 3; ++a) u[a] = (y[a] + B) * hB;
+}
+
+/* For tests: the FP32 contraction and unit-cube position of world points x. */
+void or_contract_batch(int bounded, const float* x, int n, float* y_out, float* u_out) {
+    or_scene s;
+    memset(&s, 0, sizeof s);
+    s.bounded = bounded;
+    float o[3] = {0.0f, 0.0f, 0.0f};
+    for (int i = 0; i < n; ++i) {
+        float xx[3], r;
+        or_point(&s, o, x + 3 * i, 1.0f, xx, y_out + 3 * i, u_out + 3 * i, &r);
+    }
+}
+
+static int or_vox(float u, int Rk) {
+    float c = floorf(u * (float)Rk);
+    c = fminf(fmaxf(c, 0.0f), (float)(Rk - 1));
+    return (int)c;
+}
+
+typedef struct {
+    int n_march, n_samples, ambiguous, hit;
+    double C_d[3], F[4], A, depth;
+    double T;
+} or_ray_out;
+
+/* March one ray and composite (Eq. 2, Eq. 5 before the MLP).  The step rule is
+ * Eq. 9 with the multi-level occupancy check of Sec. 3.3.  If samples != NULL the
+ * per-sample records are written there (capacity max_samples). */
+static void or_march(const or_scene* s, const or_occ* oc, const or_opts* op,
+                     const float o[3], const float din[3], float t_lo, float t_hi,
+                     or_ray_out* res, or_sample* samples, float d_out[3]) {
+    memset(res, 0, sizeof *res);
+    res->T = 1.0;
+    float n2 = (din[0] * din[0] + din[1] * din[1]) + din[2] * din[2];
+    float nn = sqrtf(n2);
+    float d[3] = {din[0] / nn, din[1] / nn, din[2] / nn};
+    if (d_out) { d_out[0] = d[0]; d_out[1] = d[1]; d_out[2] = d[2]; }
+    float t_in, t_out;
+    float B = s->bounded ? 1.0f : 2.0f;
+    if (s->bounded) {
+        float lo[3], hi[3];
+        for (int a = 0; a < 3; ++a) {
+            float ia = 1.0f / d[a];
+            float t0 = (-1.0f - o[a]) * ia, t1 = (1.0f - o[a]) * ia;
+            lo[a] = fminf(t0, t1);
+            hi[a] = fmaxf(t0, t1);
+        }
+        t_in = fmaxf(fmaxf(lo[0], lo[1]), lo[2]);
+        t_out = fminf(fminf(hi[0], hi[1]), hi[2]);
+    } else {
+        float b = (o[0] * d[0] + o[1] * d[1]) + o[2] * d[2];
+        float c = ((o[0] * o[0] + o[1] * o[1]) + o[2] * o[2]) - op->r_far * op->r_far;
+        float disc = b * b - c;
+        if (!(disc >= 0.0f)) return;
+        float sq = sqrtf(disc);
+        t_in = -b - sq;
+        t_out = -b + sq;
+    }
+    float t = fmaxf(t_in, op->t_min);
+    /* optional interval [t_lo, t_hi] from the learned proposal */
+    t = fmaxf(t, t_lo);
+    t_out = fminf(t_out, t_hi);
+    if (!(t < t_out)) return;
+    res->hit = 1;
+    const float dt0 = op->step_base * op->step_gamma;
+    const float t_start = t;
+    int lat_k = 0;
+    const int R_O = oc->R_O;
+    const float vG = (2.0f * B) / (float)R_O;
+    double T = 1.0;
+    while (t < t_out && res->n_march < op->max_march && res->n_samples < op->max_samples) {
+        res->n_march++;
+        float x[3], y[3], u[3], r;
+        or_point(s, o, d, t, x, y, u, &r);
+        /* coarse-to-fine occupancy check; empty_level = coarsest level reporting empty */
+        int empty_level = -1, ev[3] = {0, 0, 0};
+        size_t woff = 0;
+        size_t offs[16];
+        for (int k = 0; k < oc->n_levels; ++k) {
+            offs[k] = woff;
+            size_t rk = (size_t)(R_O >> k);
+            woff += or_words(rk * rk * rk);
+        }
+        for (int k = oc->n_levels - 1; k >= 0; --k) {
+            int Rk = R_O >> k;
+            int c[3] = {or_vox(u[0], Rk), or_vox(u[1], Rk), or_vox(u[2], Rk)};
+            size_t bi = (size_t)c[0] + (size_t)Rk * ((size_t)c[1] + (size_t)Rk * c[2]);
+            if (!or_bit(oc->bits + offs[k], bi)) {
+                empty_level = k;
+                ev[0] = c[0]; ev[1] = c[1]; ev[2] = c[2];
+                break;
+            }
+        }
+        float step;
+        int sampled = 0;
+        if (empty_level < 0) {
+            /* occupied at every level: take a sample */
+            float dt = s->bounded ? dt0 : dt0 * fmaxf(1.0f, r);
+            float delta = fminf(dt, t_out - t);
+            double f[OR_NFEAT];
+            or_features(s, op, u, f);
+            double sr = f[0];
+            double sigma = exp(sr);
+            double alpha = 1.0 - exp(-sigma * (double)delta);
+            double w = T * alpha;
+            if (samples) {
+                or_sample* sp = samples + res->n_samples;
+                sp->t = t; sp->delta = delta;
+                sp->u[0] = u[0]; sp->u[1] = u[1]; sp->u[2] = u[2];
+                sp->sigma_raw = sr; sp->sigma = sigma; sp->alpha = alpha; sp->T_before = T;
+                memcpy(sp->f, f, sizeof f);
+            }
+            for (int k = 0; k < 3; ++k) res->C_d[k] += w * f[1 + k];
+            for (int k = 0; k < 4; ++k) res->F[k] += w * f[4 + k];
+            res->A += w;
+            res->depth += w * (double)t;
+            T *= 1.0 - alpha;
+            res->n_samples++;
+            sampled = 1;
+            step = dt;
+            double rel = fabs(T - (double)op->t_term) / (double)op->t_term;
+            if (rel < 3e-5) res->ambiguous = 1;
+            if (T < (double)op->t_term) break;
+        } else {
+            /* s_O: leave the empty voxel of level empty_level along the ray (its
+             * local direction in contracted space), plus a small guard distance */
+            int Rk = R_O >> empty_level;
+            float vk = (2.0f * B) / (float)Rk;
+            float v[3];
+            if (s->bounded || !(r > 1.0f)) {
+                v[0] = d[0]; v[1] = d[1]; v[2] = d[2];
+            } else {
+                float k = (2.0f - 1.0f / r) / r;
+                float px = (x[0] * d[0] + x[1] * d[1]) + x[2] * d[2];
+                float r2 = r * r;
+                float m = (px * (2.0f * (1.0f - r))) / (r2 * r2);
+                for (int a = 0; a < 3; ++a) v[a] = k * d[a] + m * x[a];
+            }
+            float se = INFINITY;
+            for (int a = 0; a < 3; ++a) {
+                float lo = (float)ev[a] * vk - B;
+                float hi = lo + vk;
+                float ta = INFINITY;
+                if (v[a] > 0.0f) ta = (hi - y[a]) / v[a];
+                else if (v[a] < 0.0f) ta = (lo - y[a]) / v[a];
+                se = fminf(se, ta);
+            }
+            float s_O = fmaxf(se, 0.0f) + 1e-5f * fmaxf(1.0f, t);
+            step = s_O;
+            /* Eq. 9: read G only when the empty level is coarser than G's grid */
+            if (op->use_dist && oc->dist && empty_level >= 1) {
+                int c0[3] = {or_vox(u[0], R_O), or_vox(u[1], R_O), or_vox(u[2], R_O)};
+                int g = oc->dist[(size_t)c0[0] + (size_t)R_O * ((size_t)c0[1] + (size_t)R_O * c0[2])];
+                if (g > 0) {
+                    float rho = (float)g * vG;
+                    float sg = rho;
+                    if (!s->bounded && r > 1.0f) {
+                        float a = ((r + 1.0f) * (r + 1.0f) * rho) / (4.0f * r);
+                        float cap = (r - 1.0f) * 0.5f;
+                        sg = fmaxf(rho, fminf(a, cap));
+                    }
+                    step = op->dist_rule == 1 ? fmaxf(sg, s_O) : sg;
+                }
+            }
+        }
+        if (op->lattice_snap && s->bounded) {
+            if (sampled) lat_k += 1;
+            else {
+                int kk = (int)floorf(((t + step) - t_start) / dt0);
+                lat_k = kk > lat_k + 1 ? kk : lat_k + 1;
+            }
+            t = t_start + (float)lat_k * dt0;
+        } else {
+            t = t + step;
+        }
+    }
+    res->T = T;
+}
+
+/* Pinhole ray of pixel (col, row) of a camera [c2w(3x4) fx fy cx cy] through the
+ * pixel centre; OpenCV axes (x right, y down, z forward).  FP32. */
+static void or_camera_ray(const float* cam, int col, int row, float o[3], float d[3]) {
+    float px = (((float)col + 0.5f) - cam[14]) / cam[12];
+    float py = (((float)row + 0.5f) - cam[15]) / cam[13];
+    for (int r = 0; r < 3; ++r) {
+        d[r] = (cam[4 * r + 0] * px + cam[4 * r + 1] * py) + cam[4 * r + 2];
+        o[r] = cam[4 * r + 3];
+    }
+}
+
+/* Ray i of a batch: pixel i (or pix[i]) of the cameras, view-major then row-major,
+ * or the i-th explicit ray. */
+static void or_ray_input(const float* cams, int n_cams, int W, int H, const int32_t* pix,
+                         const float* rays_o, const float* rays_d, int i, float o[3], float d[3]) {
+    if (cams) {
+        int64_t id = pix ? pix[i] : i;
+        int64_t v = id / ((int64_t)W * H), rem = id % ((int64_t)W * H);
+        if (v >= n_cams) v = n_cams - 1;
+        or_camera_ray(cams + 16 * v, (int)(rem % W), (int)(rem / W), o, d);
+    } else {
+        for (int a = 0; a < 3; ++a) { o[a] = rays_o[3 * i + a]; d[a] = rays_d[3 * i + a]; }
+    }
+}
+
+void or_camera_rays(const float* cams, int n_cams, int W, int H, const int32_t* pix, int n,
+                    float* o_out, float* d_out) {
+    for (int i = 0; i < n; ++i) {
+        int64_t id = pix ? pix[i] : i;
+        int64_t v = id / ((int64_t)W * H), rem = id % ((int64_t)W * H);
+        if (v >= n_cams) v = n_cams - 1;
+        or_camera_ray(cams + 16 * v, (int)(rem % W), (int)(rem / W), o_out + 3 * i, d_out + 3 * i);
+    }
+}
+
+/* Final colour: sigmoid(C_d + MLP_psi(C_d, F, SH(d))) (Eq. 5 then the colour
+ * sigmoid of Sec. S2.1), composited over the background with the accumulated
+ * opacity A (the paper's C when A = 1). */
+static void or_shade(const or_scene* s, const or_opts* op, const or_ray_out* rr, const float d[3],
+                     double rgb[3], double x_out[OR_MLP_IN], double acts[256], double z_out[3]) {
+    double x[OR_MLP_IN];
+    memset(x, 0, sizeof x);
+    for (int k = 0; k < 3; ++k) x[k] = rr->C_d[k];
+    for (int k = 0; k < 4; ++k) x[3 + k] = rr->F[k];
+    double dd[3] = {d[0], d[1], d[2]};
+    or_sh16(dd, x + 7);
+    double y[3];
+    or_mlp_forward(s, x, y, acts);
+    for (int k = 0; k < 3; ++k) {
+        double z = rr->C_d[k] + y[k];
+        if (z_out) z_out[k] = z;
+        rgb[k] = rr->A * or_sigmoid(z) + (1.0 - rr->A) * op->bg[k];
+    }
+    if (x_out) memcpy(x_out, x, sizeof x);
+}
+
+/* Render n rays (explicit rays, or camera pixels when cams != NULL).  Outputs:
+ * rgb [n][3], depth [n] (= sum w_i t_i), opacity [n] (= sum w_i), stats [n][2]
+ * (marching points, samples), ambiguous [n] (1 when a termination test came
+ * within 3e-5 relative of the threshold, so FP32 may decide it otherwise), state
+ * [n][9] = C_d(3), F(4), A, depth. */
+void or_render(const or_scene* s, const or_occ* oc, const or_opts* op,
+               const float* cams, int n_cams, int W, int H, const int32_t* pix,
+               const float* rays_o, const float* rays_d, int n, const float* interval,
+               double* rgb, double* depth, double* opacity, int32_t* stats,
+               int32_t* ambiguous, double* state) {
+    /* rays are independent: one ray per loop iteration, spread over host threads */
+    #pragma omp parallel for schedule(dynamic, 16)
+    for (int i = 0; i < n; ++i) {
+        float o[3], dv[3], d[3];
+        or_ray_input(cams, n_cams, W, H, pix, rays_o, rays_d, i, o, dv);
+        float tlo = interval ? interval[2 * i] : -INFINITY, thi = interval ? interval[2 * i + 1] : INFINITY;
+        or_ray_out rr;
+        or_march(s, oc, op, o, dv, tlo, thi, &rr, NULL, d);
+        double c[3];
+        if (rr.hit) or_shade(s, op, &rr, d, c, NULL, NULL, NULL);
+        else { c[0] = op->bg[0]; c[1] = op->bg[1]; c[2] = op->bg[2]; }
+        for (int k = 0; k < 3; ++k) rgb[3 * i + k] = c[k];
+        depth[i] = rr.depth;
+        opacity[i] = rr.A;
+        if (stats) { stats[2 * i] = rr.n_march; stats[2 * i + 1] = rr.n_samples; }
+        if (ambiguous) ambiguous[i] = rr.ambiguous;
+        if (state) {
+            for (int k = 0; k < 3; ++k) state[9 * i + k] = rr.C_d[k];
+            for (int k = 0; k < 4; ++k) state[9 * i + 3 + k] = rr.F[k];
+            state[9 * i + 7] = rr.A;
+            state[9 * i + 8] = rr.depth;
+        }
+    }
+}
+
+/* Per-sample dump of one ray: t, delta, u, sigma, weight (for tests). */
+int or_ray_samples(const or_scene* s, const or_occ* oc, const or_opts* op, const float o[3],
+                   const float d[3], int cap, double* out /* [cap][7] */) {
+    or_sample* sm = (or_sample*)malloc(sizeof(or_sample) * (size_t)(op->max_samples > 0 ? op->max_samples : 1));
+    or_ray_out rr;
+    or_march(s, oc, op, o, d, -INFINITY, INFINITY, &rr, sm, NULL);
+    int n = rr.n_samples < cap ? rr.n_samples : cap;
+    for (int i = 0; i < n; ++i) {
+        out[7 * i + 0] = sm[i].t;
+        out[7 * i + 1] = sm[i].delta;
+        out[7 * i + 2] = sm[i].u[0];
+        out[7 * i + 3] = sm[i].u[1];
+        out[7 * i + 4] = sm[i].u[2];
+        out[7 * i + 5] = sm[i].sigma;
+        out[7 * i + 6] = sm[i].T_before * sm[i].alpha;
+    }
+    free(sm);
+    return rr.n_samples;
+}
+
+/* ------------------------------------------------------------ reverse pass */
+
+/* Reverse-mode derivative of or_render with respect to the fine tables, the coarse
+ * grid and the MLP weights, accumulated (+=) into g_tables, g_coarse, g_mlp.
+ *
+ * Compositing (Eq. 2 and Eq. 5): Q = sum_i w_i q_i with w_i = T_i alpha_i,
+ * alpha_i = 1 - exp(-sigma_i delta_i), T_i = prod_{j<i} (1 - alpha_j), so
+ *   dQ/dq_i     = w_i
+ *   dQ/dsigma_i = delta_i (T_{i+1} q_i - sum_{j>i} w_j q_j),
+ * the second sum written out over the later samples of the ray.  The density
+ * activation exp has the truncated derivative exp(min(sigma_raw, 15))
+ * (Sec. S2.1, following Instant-NGP).  The sample set itself does not depend on
+ * the parameters except through the termination test, whose derivative is zero. */
+void or_render_backward(const or_scene* s, const or_occ* oc, const or_opts* op,
+                        const float* cams, int n_cams, int W, int H, const int32_t* pix,
+                        const float* rays_o, const float* rays_d, int n,
+                        const double* d_rgb, const double* d_depth, const double* d_opacity,
+                        double* g_tables, double* g_coarse, double* g_mlp) {
+    int cap = op->max_samples > 0 ? op->max_samples : 1;
+    or_sample* sm = (or_sample*)malloc(sizeof(or_sample) * (size_t)cap);
+    double* qg = (double*)malloc(sizeof(double) * (size_t)cap);
+    int nch = OR_NFEAT + 2 * s->L;
+    uint32_t T = 1u << s->T_log2;
+    for (int i = 0; i < n; ++i) {
+        float o[3], dv[3], d[3];
+        or_ray_input(cams, n_cams, W, H, pix, rays_o, rays_d, i, o, dv);
+        or_ray_out rr;
+        or_march(s, oc, op, o, dv, -INFINITY, INFINITY, &rr, sm, d);
+        if (!rr.hit) continue;
+        double x[OR_MLP_IN], acts[256], z[3], rgb[3];
+        or_shade(s, op, &rr, d, rgb, x, acts, z);
+        double g_z[3], g_A = d_opacity ? d_opacity[i] : 0.0;
+        for (int k = 0; k < 3; ++k) {
+            double sg = or_sigmoid(z[k]);
+            double gr = d_rgb ? d_rgb[3 * i + k] : 0.0;
+            g_z[k] = gr * rr.A * sg * (1.0 - sg);
+            g_A += gr * (sg - op->bg[k]);
+        }
+        /* MLP reverse pass: layer inputs are x, then relu of the previous pre-activation */
+        double g_cur[256], g_in[256];
+        memcpy(g_cur, g_z, sizeof g_z);
+        size_t woff[16], aoff[16];
+        size_t wo = 0, ao = 0;
+        for (int k = 0; k < s->mlp_layers; ++k) {
+            woff[k] = wo; aoff[k] = ao;
+            wo += (size_t)or_mlp_out(s, k) * or_mlp_in(s, k);
+            ao += or_mlp_out(s, k);
+        }
+        for (int k = s->mlp_layers - 1; k >= 0; --k) {
+            int no = or_mlp_out(s, k), ni = or_mlp_in(s, k);
+            const double* Wk = s->mlp_w + woff[k];
+            double hin[256];
+            for (int j = 0; j < ni; ++j) {
+                if (k == 0) hin[j] = x[j];
+                else { double pa = acts[aoff[k - 1] + j]; hin[j] = pa > 0.0 ? pa : 0.0; }
+            }
+            for (int oo = 0; oo < no; ++oo)
+                for (int j = 0; j < ni; ++j) g_mlp[woff[k] + (size_t)oo * ni + j] += g_cur[oo] * hin[j];
+            for (int j = 0; j < ni; ++j) {
+                double acc = 0.0;
+                for (int oo = 0; oo < no; ++oo) acc += Wk[(size_t)oo * ni + j] * g_cur[oo];
+                g_in[j] = acc;
+            }
+            if (k > 0)
+                for (int j = 0; j < ni; ++j) g_cur[j] = acts[aoff[k - 1] + j] > 0.0 ? g_in[j] : 0.0;
+        }
+        double g_Cd[3], g_F[4], g_D = d_depth ? d_depth[i] : 0.0;
+        for (int k = 0; k < 3; ++k) g_Cd[k] = g_z[k] + g_in[k];
+        for (int k = 0; k < 4; ++k) g_F[k] = g_in[3 + k];
+        /* per-sample scalar q_i . g (the gradient-weighted quantity composited) */
+        int ns = rr.n_samples;
+        for (int a = 0; a < ns; ++a) {
+            double q = g_A + g_D * (double)sm[a].t;
+            for (int k = 0; k < 3; ++k) q += g_Cd[k] * sm[a].f[1 + k];
+            for (int k = 0; k < 4; ++k) q += g_F[k] * sm[a].f[4 + k];
+            qg[a] = q;
+        }
+        for (int a = 0; a < ns; ++a) {
+            const or_sample* sp = sm + a;
+            double w = sp->T_before * sp->alpha;
+            double T_next = sp->T_before * (1.0 - sp->alpha);
+            double later = 0.0;
+            for (int b = a + 1; b < ns; ++b) later += sm[b].T_before * sm[b].alpha * qg[b];
+            double g_sigma = (double)sp->delta * (T_next * qg[a] - later);
+            double g_f[OR_NFEAT];
+            g_f[0] = g_sigma * exp(fmin(sp->sigma_raw, 15.0));
+            for (int k = 0; k < 3; ++k) g_f[1 + k] = w * g_Cd[k];
+            for (int k = 0; k < 4; ++k) g_f[4 + k] = w * g_F[k];
+            /* Eq. 6-8 reverse: coarse part, attention logits, fine levels */
+            double coarse[OR_NFEAT + 2 * OR_MAXL], g_coarse_v[OR_NFEAT + 2 * OR_MAXL];
+            int base[3];
+            double wc[3];
+            memset(coarse, 0, sizeof coarse);
+            memset(g_coarse_v, 0, sizeof g_coarse_v);
+            or_cell(sp->u, s->R_C, base, wc);
+            size_t cv[8];
+            double cwt[8];
+            for (int c = 0; c < 8; ++c) {
+                int xx = base[0] + (c & 1), yy = base[1] + ((c >> 1) & 1), zz = base[2] + ((c >> 2) & 1);
+                cv[c] = (size_t)xx + (size_t)s->R_C * ((size_t)yy + (size_t)s->R_C * zz);
+                cwt[c] = or_corner_weight(wc, c);
+                for (int ch = 0; ch < nch; ++ch) coarse[ch] += cwt[c] * s->coarse[cv[c] * nch + ch];
+            }
+            for (int ch = 0; ch < OR_NFEAT; ++ch) g_coarse_v[ch] = g_f[ch];
+            for (int l = 0; l < s->L; ++l) {
+                double om, be;
+                double lo = coarse[OR_NFEAT + 2 * l], lb = coarse[OR_NFEAT + 2 * l + 1];
+                if (op->attn_mode == 1) { om = 1.0; be = 1.0; }
+                else if (op->attn_mode == 2) { om = or_sigmoid(lo); be = om; }
+                else { om = or_sigmoid(lo); be = or_sigmoid(lb); }
+                int bl[3];
+                double wl[3];
+                or_cell(sp->u, s->N[l], bl, wl);
+                uint64_t off = or_level_offset(s->N, s->L, s->T_log2, l);
+                double fl[OR_NFEAT];
+                memset(fl, 0, sizeof fl);
+                uint64_t ent[8];
+                double ew[8];
+                for (int c = 0; c < 8; ++c) {
+                    int xx = bl[0] + (c & 1), yy = bl[1] + ((c >> 1) & 1), zz = bl[2] + ((c >> 2) & 1);
+                    ent[c] = off + or_level_entry(s->N[l], T, xx, yy, zz);
+                    ew[c] = or_corner_weight(wl, c);
+                    for (int ch = 0; ch < OR_NFEAT; ++ch) fl[ch] += ew[c] * s->tables[ent[c] * OR_NFEAT + ch];
+                }
+                double g_om = fl[0] * g_f[0], g_be = 0.0;
+                for (int ch = 1; ch < OR_NFEAT; ++ch) g_be += fl[ch] * g_f[ch];
+                if (op->attn_mode == 0) {
+                    g_coarse_v[OR_NFEAT + 2 * l] += g_om * om * (1.0 - om);
+                    g_coarse_v[OR_NFEAT + 2 * l + 1] += g_be * be * (1.0 - be);
+                } else if (op->attn_mode == 2) {
+                    g_coarse_v[OR_NFEAT + 2 * l] += (g_om + g_be) * om * (1.0 - om);
+                }
+                for (int c = 0; c < 8; ++c) {
+                    g_tables[ent[c] * OR_NFEAT + 0] += ew[c] * om * g_f[0];
+                    for (int ch = 1; ch < OR_NFEAT; ++ch) g_tables[ent[c] * OR_NFEAT + ch] += ew[c] * be * g_f[ch];
+                }
+            }
+            for (int c = 0; c < 8; ++c)
+                for (int ch = 0; ch < nch; ++ch) g_coarse[cv[c] * nch + ch] += cwt[c] * g_coarse_v[ch];
+        }
+    }
+    free(sm);
+    free(qg);
+}
+
+/* Scalar loss used by the gradient tests: sum of the rendered outputs weighted by
+ * fixed cotangents, L = <d_rgb, rgb> + <d_depth, depth> + <d_opacity, A>. */
+double or_render_dot(const or_scene* s, const or_occ* oc, const or_opts* op,
+                     const float* cams, int n_cams, int W, int H, const int32_t* pix,
+                     const float* rays_o, const float* rays_d, int n,
+                     const double* d_rgb, const double* d_depth, const double* d_opacity) {
+    double* rgb = (double*)malloc(sizeof(double) * 3 * (size_t)n);
+    double* dep = (double*)malloc(sizeof(double) * (size_t)n);
+    double* opa = (double*)malloc(sizeof(double) * (size_t)n);
+    or_render(s, oc, op, cams, n_cams, W, H, pix, rays_o, rays_d, n, NULL, rgb, dep, opa, NULL, NULL, NULL);
+    double L = 0.0;
+    for (int i = 0; i < n; ++i) {
+        for (int k = 0; k < 3; ++k) L += (d_rgb ? d_rgb[3 * i + k] : 0.0) * rgb[3 * i + k];
+        L += (d_depth ? d_depth[i] : 0.0) * dep[i] + (d_opacity ? d_opacity[i] : 0.0) * opa[i];
+    }
+    free(rgb); free(dep); free(opa);
+    return L;
+}
+
+#ifdef _OPENMP
+#include <omp.h>
+void or_set_threads(int n) { omp_set_num_threads(n); }
+int or_max_threads(void) { return omp_get_max_threads(); }
+#else
+void or_set_threads(int n) { (void)n; }
+int or_max_threads(void) { return 1; }
+#endif

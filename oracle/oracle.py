@@ -1,0 +1,306 @@
+"""Python bindings of the CPU oracle of the NGP-RT render path.
+
+TEST INFRASTRUCTURE ONLY: the test-suite, the package smoke check and the
+benchmark's CPU-baseline / reference arm call it; the CUDA library never does.
+The arithmetic lives in ``ngprt_oracle.c`` (FP64 values, FP32 march decisions);
+this module only builds that file with gcc, marshals numpy arrays and converts
+every table to FP64 before the call.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ngprt_oracle.c")
+_LIBDIR = os.path.join(_HERE, "lib")
+_LIB = os.path.join(_LIBDIR, "libngprt_oracle.so")
+MAXL = 32
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (FP contraction off, OpenMP over rays)."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    os.makedirs(_LIBDIR, exist_ok=True)
+    tmp = _LIB + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
+           "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"]
+    subprocess.check_call(cmd)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+class OrScene(C.Structure):
+    _fields_ = [("L", C.c_int), ("T_log2", C.c_int), ("N", C.c_int * MAXL),
+                ("tables", C.c_void_p), ("R_C", C.c_int), ("coarse", C.c_void_p),
+                ("mlp_layers", C.c_int), ("mlp_width", C.c_int), ("mlp_w", C.c_void_p),
+                ("bounded", C.c_int)]
+
+
+class OrOcc(C.Structure):
+    _fields_ = [("R_O", C.c_int), ("n_levels", C.c_int), ("bits", C.c_void_p), ("dist", C.c_void_p)]
+
+
+class OrOpts(C.Structure):
+    _fields_ = [("step_base", C.c_float), ("step_gamma", C.c_float), ("t_min", C.c_float),
+                ("r_far", C.c_float), ("t_term", C.c_float), ("bg", C.c_double * 3),
+                ("max_march", C.c_int), ("max_samples", C.c_int), ("use_dist", C.c_int),
+                ("lattice_snap", C.c_int), ("attn_mode", C.c_int), ("dist_rule", C.c_int)]
+
+
+_lib_handle = None
+
+
+def lib():
+    global _lib_handle
+    if _lib_handle is None:
+        _lib_handle = C.CDLL(build())
+        _lib_handle.or_hash.restype = C.c_uint32
+        _lib_handle.or_hash.argtypes = [C.c_uint32] * 4
+        _lib_handle.or_pyramid_words.restype = C.c_size_t
+        _lib_handle.or_pyramid_words.argtypes = [C.c_int, C.c_int]
+        _lib_handle.or_level_offset.restype = C.c_uint64
+        _lib_handle.or_render_dot.restype = C.c_double
+        _lib_handle.or_ray_samples.restype = C.c_int
+        _lib_handle.or_max_threads.restype = C.c_int
+    return _lib_handle
+
+
+def _p(a):
+    return C.c_void_p(a.ctypes.data) if a is not None else None
+
+
+def _c(a, dtype):
+    return None if a is None else np.ascontiguousarray(a, dtype=dtype)
+
+
+def set_threads(n: int) -> None:
+    lib().or_set_threads(int(n))
+
+
+def max_threads() -> int:
+    return int(lib().or_max_threads())
+
+
+# ----------------------------------------------------------------- primitives
+
+def hash3(xyz: np.ndarray, T: int) -> np.ndarray:
+    xyz = _c(xyz, np.uint32).reshape(-1, 3)
+    out = np.empty(len(xyz), np.uint32)
+    lib().or_hash_batch(_p(xyz), C.c_int(len(xyz)), C.c_uint32(T), _p(out))
+    return out
+
+
+def level_offset(N, T_log2: int, l: int) -> int:
+    arr = (C.c_int * MAXL)(*N)
+    return int(lib().or_level_offset(arr, C.c_int(len(N)), C.c_int(T_log2), C.c_int(l)))
+
+
+def grid_indices(N, T_log2: int, u: np.ndarray):
+    """Corner entry rows [n, L, 8] (uint64) and FP64 weights [n, L, 3] of positions u."""
+    u = _c(u, np.float32).reshape(-1, 3)
+    L = len(N)
+    idx = np.empty((len(u), L, 8), np.uint64)
+    w = np.empty((len(u), L, 3), np.float64)
+    arr = (C.c_int * MAXL)(*N)
+    lib().or_grid_indices(arr, C.c_int(L), C.c_int(T_log2), _p(u), C.c_int(len(u)), _p(idx), _p(w))
+    return idx, w
+
+
+def pyramid_words(R: int, n_levels: int) -> int:
+    return int(lib().or_pyramid_words(R, n_levels))
+
+
+def build_pyramid(occ: np.ndarray, R: int, n_levels: int) -> np.ndarray:
+    occ = _c(occ, np.uint8).reshape(-1)
+    out = np.empty(pyramid_words(R, n_levels), np.uint32)
+    lib().or_build_pyramid(_p(occ), C.c_int(R), C.c_int(n_levels), _p(out))
+    return out
+
+
+def occ_dist_brute(occ: np.ndarray, R: int) -> np.ndarray:
+    occ = _c(occ, np.uint8).reshape(-1)
+    out = np.empty(R ** 3, np.uint8)
+    lib().or_occ_dist_brute(_p(occ), C.c_int(R), _p(out))
+    return out
+
+
+def occ_dist(occ: np.ndarray, R: int) -> np.ndarray:
+    occ = _c(occ, np.uint8).reshape(-1)
+    out = np.empty(R ** 3, np.uint8)
+    lib().or_occ_dist(_p(occ), C.c_int(R), _p(out))
+    return out
+
+
+def sh16(d: np.ndarray) -> np.ndarray:
+    d = _c(d, np.float64).reshape(-1, 3)
+    out = np.empty((len(d), 16), np.float64)
+    lib().or_sh16_batch(_p(d), C.c_int(len(d)), _p(out))
+    return out
+
+
+def camera_rays(cams: np.ndarray, W: int, H: int, pix=None, n=None):
+    cams = _c(cams, np.float32).reshape(-1, 16)
+    pix = _c(pix, np.int32)
+    if n is None:
+        n = len(pix) if pix is not None else len(cams) * W * H
+    o = np.empty((n, 3), np.float32)
+    d = np.empty((n, 3), np.float32)
+    lib().or_camera_rays(_p(cams), C.c_int(len(cams)), C.c_int(W), C.c_int(H), _p(pix), C.c_int(n),
+                         _p(o), _p(d))
+    return o, d
+
+
+# ----------------------------------------------------------------- the oracle
+
+class Oracle:
+    """FP64 renderer over one scene.  ``tables``/``coarse``/``mlp_w`` may be FP32 or
+    FP16/BF16-rounded copies (pass them as float arrays); they are widened to FP64."""
+
+    def __init__(self, cfg, tables, coarse, mlp_w, occ_bits, dist=None):
+        self.cfg = cfg
+        self.tables = _c(np.asarray(tables, np.float64), np.float64)
+        self.coarse = _c(np.asarray(coarse, np.float64), np.float64)
+        self.mlp_w = _c(np.asarray(mlp_w, np.float64), np.float64)
+        self.bits = _c(occ_bits, np.uint32)
+        self.dist = _c(dist, np.uint8)
+        s = OrScene()
+        s.L = cfg.L
+        s.T_log2 = cfg.T_log2
+        for i, n in enumerate(cfg.N):
+            s.N[i] = int(n)
+        s.tables = self.tables.ctypes.data
+        s.R_C = cfg.R_C
+        s.coarse = self.coarse.ctypes.data
+        s.mlp_layers = cfg.mlp_layers
+        s.mlp_width = cfg.mlp_width
+        s.mlp_w = self.mlp_w.ctypes.data
+        s.bounded = 1 if cfg.bounded else 0
+        self._s = s
+        o = OrOcc()
+        o.R_O = cfg.R_O
+        o.n_levels = cfg.n_occ_levels
+        o.bits = self.bits.ctypes.data
+        o.dist = self.dist.ctypes.data if self.dist is not None else None
+        self._o = o
+
+    @staticmethod
+    def _opts(opts) -> OrOpts:
+        p = OrOpts()
+        p.step_base = opts.step_base
+        p.step_gamma = opts.step_gamma
+        p.t_min = opts.t_min
+        p.r_far = opts.r_far
+        p.t_term = opts.t_term
+        for k in range(3):
+            p.bg[k] = float(opts.bg[k])
+        p.max_march = int(opts.max_march)
+        p.max_samples = int(opts.max_samples)
+        p.use_dist = 1 if opts.use_dist else 0
+        p.lattice_snap = 1 if opts.lattice_snap else 0
+        p.attn_mode = int(opts.attn_mode)
+        p.dist_rule = int(opts.dist_rule)
+        return p
+
+    def _rays(self, cams, pix, rays_o, rays_d):
+        cams = _c(cams, np.float32)
+        pix = _c(pix, np.int32)
+        ro = _c(rays_o, np.float32)
+        rd = _c(rays_d, np.float32)
+        if cams is not None:
+            cams = cams.reshape(-1, 16)
+            n = len(pix) if pix is not None else len(cams) * self.cfg.W * self.cfg.H
+        else:
+            n = len(ro.reshape(-1, 3))
+        return cams, pix, ro, rd, n
+
+    def render(self, opts, cams=None, pix=None, rays_o=None, rays_d=None, interval=None,
+               W=None, H=None):
+        W = W or self.cfg.W
+        H = H or self.cfg.H
+        cams, pix, ro, rd, n = self._rays(cams, pix, rays_o, rays_d)
+        iv = _c(interval, np.float32)
+        rgb = np.empty((n, 3), np.float64)
+        depth = np.empty(n, np.float64)
+        opac = np.empty(n, np.float64)
+        stats = np.empty((n, 2), np.int32)
+        amb = np.empty(n, np.int32)
+        state = np.empty((n, 9), np.float64)
+        op = self._opts(opts)
+        lib().or_render(C.byref(self._s), C.byref(self._o), C.byref(op), _p(cams),
+                        C.c_int(0 if cams is None else len(cams)), C.c_int(W), C.c_int(H), _p(pix),
+                        _p(ro), _p(rd), C.c_int(n), _p(iv), _p(rgb), _p(depth), _p(opac), _p(stats),
+                        _p(amb), _p(state))
+        return dict(rgb=rgb, depth=depth, opacity=opac, stats=stats, ambiguous=amb.astype(bool),
+                    state=state)
+
+    def render_backward(self, opts, d_rgb=None, d_depth=None, d_opacity=None, cams=None, pix=None,
+                        rays_o=None, rays_d=None, W=None, H=None):
+        W = W or self.cfg.W
+        H = H or self.cfg.H
+        cams, pix, ro, rd, n = self._rays(cams, pix, rays_o, rays_d)
+        g_t = np.zeros_like(self.tables)
+        g_c = np.zeros_like(self.coarse)
+        g_m = np.zeros_like(self.mlp_w)
+        op = self._opts(opts)
+        lib().or_render_backward(C.byref(self._s), C.byref(self._o), C.byref(op), _p(cams),
+                                 C.c_int(0 if cams is None else len(cams)), C.c_int(W), C.c_int(H),
+                                 _p(pix), _p(ro), _p(rd), C.c_int(n), _p(_c(d_rgb, np.float64)),
+                                 _p(_c(d_depth, np.float64)), _p(_c(d_opacity, np.float64)),
+                                 _p(g_t), _p(g_c), _p(g_m))
+        return dict(tables=g_t, coarse=g_c, mlp_w=g_m)
+
+    def render_dot(self, opts, d_rgb=None, d_depth=None, d_opacity=None, cams=None, pix=None,
+                   rays_o=None, rays_d=None, W=None, H=None) -> float:
+        W = W or self.cfg.W
+        H = H or self.cfg.H
+        cams, pix, ro, rd, n = self._rays(cams, pix, rays_o, rays_d)
+        op = self._opts(opts)
+        return float(lib().or_render_dot(
+            C.byref(self._s), C.byref(self._o), C.byref(op), _p(cams),
+            C.c_int(0 if cams is None else len(cams)), C.c_int(W), C.c_int(H), _p(pix), _p(ro), _p(rd),
+            C.c_int(n), _p(_c(d_rgb, np.float64)), _p(_c(d_depth, np.float64)),
+            _p(_c(d_opacity, np.float64))))
+
+    def ray_samples(self, opts, o, d, cap=4096) -> np.ndarray:
+        """Per-sample records [n, 7] = t, delta, u(3), sigma, weight of one ray."""
+        o = _c(o, np.float32).reshape(3)
+        d = _c(d, np.float32).reshape(3)
+        out = np.empty((cap, 7), np.float64)
+        op = self._opts(opts)
+        n = lib().or_ray_samples(C.byref(self._s), C.byref(self._o), C.byref(op), _p(o), _p(d),
+                                 C.c_int(cap), _p(out))
+        return out[:min(n, cap)]
+
+    def mlp(self, x: np.ndarray) -> np.ndarray:
+        x = _c(x, np.float64).reshape(-1, 32)
+        y = np.empty((len(x), 3), np.float64)
+        lib().or_mlp_batch(C.byref(self._s), _p(x), C.c_int(len(x)), _p(y))
+        return y
+
+
+def oracle_for_scene(scene, tables=None, coarse=None, use_dist=True) -> Oracle:
+    """Oracle over a generated scene: builds the pyramid and distance grid itself."""
+    cfg = scene.cfg
+    bits = build_pyramid(scene.occ, cfg.R_O, cfg.n_occ_levels)
+    dist = occ_dist(scene.occ, cfg.R_O) if use_dist else None
+    return Oracle(cfg, scene.tables if tables is None else tables,
+                  scene.coarse if coarse is None else coarse, scene.mlp_w, bits, dist)
+
+
+def contract(x: np.ndarray, bounded: bool = False):
+    """FP32 contraction y and unit-cube position u of world points x [n, 3]."""
+    x = _c(x, np.float32).reshape(-1, 3)
+    y = np.empty_like(x)
+    u = np.empty_like(x)
+    lib().or_contract_batch(C.c_int(1 if bounded else 0), _p(x), C.c_int(len(x)), _p(y), _p(u))
+    return y, u
+
+
+def coarse_channels(L: int) -> int:
+    """Channels per coarse-grid vertex: deferred feature (8) plus omega, beta per level."""
+    return 8 + 2 * L

@@ -1,0 +1,71 @@
+"""Pins of the oracle's reverse pass: central finite differences of its own FP64
+forward (h = 1e-3), per coordinate and along random directions.  Termination is
+switched off (t_term = 0) so the sample set cannot change under perturbation, and
+densities stay below the exp truncation (sigma_raw < 15)."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2407_10482_gb300 import scenes as S
+
+H = 1e-3
+
+
+def _setup(attn_mode=0, bounded=True):
+    if bounded:
+        cfg = S.small_config(blob_std=(0.05, 0.15))
+        o, d = S.random_rays(12, 11, True)
+        kw = {}
+    else:
+        cfg = S.small_config(blob_std=(0.05, 0.15), bounded=False, R_O=32, n_occ_levels=3,
+                             t_min=0.05, r_far=16.0, shell=True, mlp_layers=3, mlp_width=16)
+        o, d = S.random_rays(12, 12, False)
+        kw = {}
+    sc = S.make_scene(cfg)
+    sc.coarse[:, 8:] *= 10.0   # spread the attention gates away from 1/2
+    orc = O.oracle_for_scene(sc)
+    opts = S.default_options(cfg, t_term=0.0, attn_mode=attn_mode, **kw)
+    rng = np.random.default_rng(5)
+    cot = dict(d_rgb=rng.normal(size=(len(o), 3)), d_depth=rng.normal(size=len(o)) * 0.3,
+               d_opacity=rng.normal(size=len(o)))
+    return sc, orc, opts, o, d, cot
+
+
+def _fd(orc, opts, o, d, cot, arr, flat_idx, direction=None):
+    base = arr.reshape(-1)
+    keep = base.copy()
+    if direction is None:
+        base[flat_idx] = keep[flat_idx] + H
+        fp = orc.render_dot(opts, rays_o=o, rays_d=d, **cot)
+        base[flat_idx] = keep[flat_idx] - H
+        fm = orc.render_dot(opts, rays_o=o, rays_d=d, **cot)
+    else:
+        base[:] = keep + H * direction
+        fp = orc.render_dot(opts, rays_o=o, rays_d=d, **cot)
+        base[:] = keep - H * direction
+        fm = orc.render_dot(opts, rays_o=o, rays_d=d, **cot)
+    base[:] = keep
+    return (fp - fm) / (2 * H)
+
+
+@pytest.mark.parametrize("attn_mode,bounded", [(0, True), (2, True), (0, False)])
+def test_reverse_pass_matches_central_differences(attn_mode, bounded):
+    sc, orc, opts, o, d, cot = _setup(attn_mode, bounded)
+    g = orc.render_backward(opts, rays_o=o, rays_d=d, **cot)
+    rng = np.random.default_rng(9)
+    checked = 0
+    for name, arr in (("tables", orc.tables), ("coarse", orc.coarse), ("mlp_w", orc.mlp_w)):
+        gr = g[name].reshape(-1)
+        nz = np.nonzero(np.abs(gr) > 1e-8)[0]
+        assert len(nz) > 0, name
+        for k in rng.choice(nz, min(24, len(nz)), replace=False):
+            fd = _fd(orc, opts, o, d, cot, arr, k)
+            assert abs(fd - gr[k]) <= 1e-6 + 1e-4 * abs(gr[k]), (name, k, fd, gr[k])
+            checked += 1
+        for _ in range(2):
+            v = rng.normal(size=arr.size)
+            v /= np.linalg.norm(v)
+            fd = _fd(orc, opts, o, d, cot, arr, None, v)
+            an = float(gr @ v)
+            assert abs(fd - an) <= 1e-6 + 1e-4 * abs(an), (name, fd, an)
+    assert checked > 40

@@ -1,0 +1,418 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Every test here checks the oracle against something other than itself: values the
+paper prints (Table S4, Eq. S1), closed forms of the volume-rendering sum (Eq. 2,
+Eq. 5), brute force on tiny inputs, a different algorithm for the same quantity,
+or geometric invariants.  No GPU is needed.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2407_10482_gb300 import scenes as S
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+P2, P3 = 2654435761, 805459861  # spatial-hash primes of Instant-NGP (x uses 1)
+
+
+# ------------------------------------------------------------------ hashing
+
+def test_hash_axis_values_and_xor_structure():
+    T = 1 << 19
+    rng = np.random.default_rng(0)
+    xyz = rng.integers(0, 1 << 13, (2000, 3)).astype(np.uint32)
+    h = O.hash3(xyz, T)
+    assert h.max() < T
+    hx = O.hash3(np.stack([xyz[:, 0], 0 * xyz[:, 0], 0 * xyz[:, 0]], 1), T)
+    hy = O.hash3(np.stack([0 * xyz[:, 0], xyz[:, 1], 0 * xyz[:, 0]], 1), T)
+    hz = O.hash3(np.stack([0 * xyz[:, 0], 0 * xyz[:, 0], xyz[:, 2]], 1), T)
+    # x has prime 1: identity modulo T
+    assert np.array_equal(hx, xyz[:, 0] % T)
+    # unit steps reproduce the primes, with 32-bit wrap-around for larger multiples
+    assert O.hash3(np.array([0, 1, 0]), T)[0] == P2 % T
+    assert O.hash3(np.array([0, 0, 1]), T)[0] == P3 % T
+    assert O.hash3(np.array([0, 3, 0]), 1 << 31)[0] == (3 * P2) % (1 << 32) % (1 << 31)
+    # for a power-of-two T the modulus distributes over XOR
+    assert np.array_equal(h, hx ^ hy ^ hz)
+
+
+def test_dense_levels_are_a_bijection_and_offsets_add_up():
+    cfg = S.hd_config()
+    T = 1 << cfg.T_log2
+    assert cfg.N == [16, 23, 33, 48, 70, 101, 147, 212, 307, 445, 645, 933, 1351, 1955, 2830, 4096]
+    dense = [n for n in cfg.N if n ** 3 <= T]
+    assert dense == [16, 23, 33, 48, 70]
+    total = O.level_offset(cfg.N, cfg.T_log2, cfg.L)
+    assert total == S.table_entries(cfg) == 6272960
+    # every vertex of a dense level gets its own row, rows fill [offset, offset + N^3)
+    N = cfg.N[1]
+    g = (np.arange(N, dtype=np.float32)) / np.float32(N - 1)
+    zz, yy, xx = np.meshgrid(g, g, g, indexing="ij")
+    u = np.stack([xx, yy, zz], -1).reshape(-1, 3)
+    idx, w = O.grid_indices(cfg.N[:2], cfg.T_log2, u)
+    rows = idx[:, 1, :].reshape(-1)
+    off = O.level_offset(cfg.N, cfg.T_log2, 1)
+    assert rows.min() >= off and rows.max() < off + N ** 3
+    assert len(np.unique(rows)) == N ** 3
+
+
+def test_trilinear_reproduces_affine_functions():
+    """Weights and corner order: interpolating an affine function of the vertex
+    coordinates must return that function at p = u (N - 1) (dense level)."""
+    N = [16]
+    rng = np.random.default_rng(1)
+    u = rng.uniform(0, 1, (500, 3)).astype(np.float32)
+    u[:5] = [[0, 0, 0], [1, 1, 1], [1, 0, 0.5], [0.999999, 0.5, 0], [0.5, 0.5, 0.5]]
+    idx, w = O.grid_indices(N, 12, u)
+    a = np.array([0.7, -1.3, 2.1])
+    e = idx[:, 0, :].astype(np.int64)
+    vx, vy, vz = e % 16, (e // 16) % 16, e // 256
+    fval = a[0] * vx + a[1] * vy + a[2] * vz + 0.25
+    cw = np.ones((len(u), 8))
+    for c in range(8):
+        for ax in range(3):
+            bit = (c >> ax) & 1
+            cw[:, c] *= np.where(bit, w[:, 0, ax], 1.0 - w[:, 0, ax])
+    interp = (cw * fval).sum(1)
+    p = u.astype(np.float64) * 15.0
+    want = p @ a + 0.25
+    np.testing.assert_allclose(interp, want, atol=1e-12)
+    assert np.all(w >= -1e-6) and np.all(w <= 1 + 1e-6)
+
+
+# ------------------------------------------------------- occupancy / distance
+
+def _grid(R, frac, seed):
+    rng = np.random.default_rng(seed)
+    return (rng.uniform(size=R ** 3) < frac).astype(np.uint8)
+
+
+def test_distance_grid_single_voxel_geometry():
+    R = 11
+    occ = np.zeros(R ** 3, np.uint8)
+    c = 5
+    occ[c + R * (c + R * c)] = 1
+    g = O.occ_dist_brute(occ, R).reshape(R, R, R)  # [z, y, x]
+    # the occupied voxel and its 26 neighbours touch it: distance 0
+    assert np.all(g[4:7, 4:7, 4:7] == 0)
+    # along an axis, k voxels away leaves a gap of k - 1 voxels
+    for k in range(1, 6):
+        assert g[c, c, c + k] == k - 1
+        assert g[c - k, c, c] == k - 1
+    # along a face diagonal the gap is sqrt(2)(k-1), along the body diagonal sqrt(3)(k-1)
+    for k in range(1, 6):
+        assert g[c, c + k, c + k] == math.floor(math.sqrt(2) * (k - 1) + 1e-12)
+        assert g[c + k, c + k, c + k] == math.floor(math.sqrt(3) * (k - 1) + 1e-12)
+
+
+def test_distance_grid_empty_and_full():
+    R = 8
+    assert np.all(O.occ_dist_brute(np.zeros(R ** 3, np.uint8), R) == 255)
+    assert np.all(O.occ_dist(np.zeros(R ** 3, np.uint8), R) == 255)
+    assert np.all(O.occ_dist(np.ones(R ** 3, np.uint8), R) == 0)
+
+
+@pytest.mark.parametrize("R,frac,seed", [(6, 0.02, 0), (9, 0.01, 1), (12, 0.003, 2), (12, 0.05, 3)])
+def test_separable_distance_equals_brute_force(R, frac, seed):
+    occ = _grid(R, frac, seed)
+    assert np.array_equal(O.occ_dist(occ, R), O.occ_dist_brute(occ, R))
+
+
+def test_distance_grid_caps_at_255():
+    R = 40
+    occ = np.zeros(R ** 3, np.uint8)
+    occ[0] = 1
+    g = O.occ_dist(occ, R).reshape(R, R, R)
+    assert g[R - 1, R - 1, R - 1] == math.floor(math.sqrt(3) * (R - 2))
+    assert g.max() < 255
+
+
+def test_distance_step_never_enters_an_occupied_voxel():
+    """Safety of Eq. 9's step v * G: from any point of an empty voxel, a straight move
+    of length G voxels in any direction stays out of every occupied voxel."""
+    R = 24
+    occ = _grid(R, 0.004, 7)
+    g = O.occ_dist(occ, R)
+    occ3 = occ.reshape(R, R, R)
+    rng = np.random.default_rng(3)
+    empty = np.nonzero(g > 0)[0]
+    for p in rng.choice(empty, 300, replace=False):
+        vx, vy, vz = p % R, (p // R) % R, p // (R * R)
+        x0 = np.array([vx, vy, vz]) + rng.uniform(0, 1, 3)
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        for s in np.linspace(0, g[p] * (1 - 1e-9), 64):
+            q = np.floor(x0 + s * d).astype(int)
+            if np.all(q >= 0) and np.all(q < R):
+                assert occ3[q[2], q[1], q[0]] == 0
+
+
+def test_pyramid_is_block_or():
+    R, n_levels = 16, 4
+    occ = _grid(R, 0.01, 5)
+    bits = O.build_pyramid(occ, R, n_levels)
+    off = 0
+    cur = occ.reshape(R, R, R).astype(bool)
+    for k in range(n_levels):
+        r = R >> k
+        words = (r ** 3 + 31) // 32
+        lvl = np.unpackbits(bits[off:off + words].view(np.uint8), bitorder="little")[:r ** 3]
+        assert np.array_equal(lvl.reshape(r, r, r).astype(bool), cur)
+        cur = cur.reshape(r // 2, 2, r // 2, 2, r // 2, 2).any(axis=(1, 3, 5)) if r > 1 else cur
+        off += words
+
+
+# ------------------------------------------------------------ view embedding
+
+def test_sh16_orthonormal_on_the_sphere():
+    nt, nphi = 24, 48
+    x, wx = np.polynomial.legendre.leggauss(nt)      # cos(theta) nodes
+    phi = (np.arange(nphi) + 0.5) * 2 * np.pi / nphi
+    ct, ph = np.meshgrid(x, phi, indexing="ij")
+    st = np.sqrt(1 - ct ** 2)
+    d = np.stack([st * np.cos(ph), st * np.sin(ph), ct], -1).reshape(-1, 3)
+    wts = (wx[:, None] * np.full(nphi, 2 * np.pi / nphi)[None, :]).reshape(-1)
+    Y = O.sh16(d)
+    G = (Y * wts[:, None]).T @ Y
+    np.testing.assert_allclose(G, np.eye(16), atol=1e-10)
+
+
+def test_sh16_low_bands():
+    d = np.array([[0.0, 0.0, 1.0], [1.0, 0.0, 0.0], [0.0, 1.0, 0.0]])
+    Y = O.sh16(d)
+    np.testing.assert_allclose(Y[:, 0], 0.5 / math.sqrt(math.pi), rtol=1e-14)
+    k1 = math.sqrt(3 / (4 * math.pi))
+    # band 1 is proportional to (y, z, x)
+    np.testing.assert_allclose(Y[:, 1:4], k1 * d[:, [1, 2, 0]], atol=1e-14)
+
+
+# -------------------------------------------------------------- contraction
+
+def test_contraction_identity_inside_and_bounded_outside():
+    rng = np.random.default_rng(2)
+    x = rng.normal(size=(4000, 3)).astype(np.float32) * np.float32(3)
+    y, u = O.contract(x, bounded=False)
+    r = np.linalg.norm(x.astype(np.float64), axis=1)
+    inside = r <= 0.999
+    np.testing.assert_array_equal(y[inside], x[inside])
+    ry = np.linalg.norm(y.astype(np.float64), axis=1)
+    assert ry.max() < 2.0
+    np.testing.assert_allclose(ry[~inside & (r > 1.001)], (2 - 1 / r)[~inside & (r > 1.001)], rtol=1e-6)
+    assert np.all((u >= 0) & (u <= 1))
+    # 1-Lipschitz: contracted distances never exceed world distances
+    a, b = x[:2000], x[2000:]
+    ya, yb = y[:2000], y[2000:]
+    dw = np.linalg.norm((a - b).astype(np.float64), axis=1)
+    dc = np.linalg.norm((ya - yb).astype(np.float64), axis=1)
+    assert np.all(dc <= dw * (1 + 1e-5) + 1e-6)
+
+
+# ------------------------------------------------------------------ cameras
+
+def test_camera_rays_project_back_to_pixel_centres():
+    cfg = S.small_config(W=40, H=30)
+    cam = S.orbit_cameras(cfg, 1, azimuth0=33.0)[0]
+    o, d = O.camera_rays(cam[None], 40, 30)
+    c2w = cam[:12].reshape(3, 4).astype(np.float64)
+    fx, fy, cx, cy = cam[12:].astype(np.float64)
+    R, t = c2w[:, :3], c2w[:, 3]
+    pts = o.astype(np.float64) + 2.5 * d.astype(np.float64)
+    pc = (pts - t) @ R  # world -> camera (R orthonormal)
+    col = fx * pc[:, 0] / pc[:, 2] + cx
+    row = fy * pc[:, 1] / pc[:, 2] + cy
+    ii = np.arange(40 * 30)
+    np.testing.assert_allclose(col, ii % 40 + 0.5, atol=1e-4)
+    np.testing.assert_allclose(row, ii // 40 + 0.5, atol=1e-4)
+
+
+# ------------------------------------------------------ rendering closed forms
+
+def _full_scene(cfg, sigma_table=0.0, coarse_sigma=0.0, att_logit=0.0, color=0.0, occ_full=True):
+    sc = S.make_scene(cfg)
+    sc.tables[:] = 0.0
+    sc.tables[:, 0] = sigma_table
+    sc.tables[:, 1:] = color
+    sc.coarse[:] = att_logit
+    sc.coarse[:, 0] = coarse_sigma
+    sc.coarse[:, 1:8] = color
+    sc.mlp_w[:] = 0.0
+    if occ_full:
+        sc.occ[:] = 1
+    return sc
+
+
+def test_empty_scene_renders_background():
+    cfg = S.small_config()
+    sc = S.make_scene(cfg)
+    sc.occ[:] = 0
+    orc = O.oracle_for_scene(sc)
+    opts = S.default_options(cfg, bg=(0.25, 0.5, 0.75))
+    r = orc.render(opts, cams=S.orbit_cameras(cfg, 1))
+    assert np.all(r["rgb"] == np.array([0.25, 0.5, 0.75]))
+    assert np.all(r["opacity"] == 0) and np.all(r["depth"] == 0)
+    assert np.all(r["stats"][:, 1] == 0)
+
+
+@pytest.mark.parametrize("s_raw", [-1.0, 0.2, 0.9])
+def test_homogeneous_slab_opacity_and_depth(s_raw):
+    """A medium of constant density sigma crossed over length 2 has opacity
+    1 - exp(-2 sigma) (Eq. 2), and the discrete depth sum is a geometric series.
+    The step 1/64 and entry at t = 2 keep every FP32 position exact."""
+    cfg = S.small_config()
+    L = cfg.L
+    logit = float(np.float32(0.3))     # table values are FP32: use the stored numbers
+    s_raw = float(np.float32(s_raw))
+    om = 1 / (1 + math.exp(-logit))
+    sc = _full_scene(cfg, sigma_table=s_raw, coarse_sigma=s_raw, att_logit=logit)
+    orc = O.oracle_for_scene(sc)
+    dt = 1.0 / 64.0
+    opts = S.default_options(cfg, step_base=dt, max_samples=1000, t_term=0.0)
+    o = np.array([[-3.0, 0.1, 0.2]], np.float32)
+    d = np.array([[1.0, 0.0, 0.0]], np.float32)
+    r = orc.render(opts, rays_o=o, rays_d=d)
+    sigma = math.exp(s_raw * (1 + L * om))
+    A = 1 - math.exp(-2 * sigma)
+    assert r["stats"][0, 1] == 128
+    assert abs(r["opacity"][0] - A) < 1e-12
+    q = math.exp(-sigma * dt)
+    n = 128
+    series = q * (1 - n * q ** (n - 1) + (n - 1) * q ** n) / (1 - q) ** 2
+    depth = (1 - q) * (2.0 * (1 - q ** n) / (1 - q) + dt * series)
+    assert abs(r["depth"][0] - depth) < 1e-10
+
+
+def test_slab_colour_with_zero_mlp():
+    """With MLP_psi = 0, Eq. 5 and the colour sigmoid give A * sigmoid(A c) + (1 - A) bg
+    for a constant fused colour feature c."""
+    cfg = S.small_config()
+    L = cfg.L
+    logit = float(np.float32(-0.4))
+    be = 1 / (1 + math.exp(-logit))
+    col = float(np.float32(0.3))
+    sc = _full_scene(cfg, sigma_table=0.1, coarse_sigma=0.1, att_logit=logit, color=col)
+    orc = O.oracle_for_scene(sc)
+    opts = S.default_options(cfg, step_base=1.0 / 64.0, max_samples=1000, t_term=0.0, bg=(0.2, 0.4, 0.6))
+    r = orc.render(opts, rays_o=np.array([[-3.0, 0.1, 0.2]], np.float32),
+                   rays_d=np.array([[1.0, 0.0, 0.0]], np.float32))
+    A = r["opacity"][0]
+    c = col * (1 + L * be)
+    want = A / (1 + np.exp(-A * c)) + (1 - A) * np.array([0.2, 0.4, 0.6])
+    np.testing.assert_allclose(r["rgb"][0], want, atol=1e-12)
+
+
+def test_sum_attention_is_the_limit_of_saturated_gates():
+    """Eq. 8 with omega = beta = 1 is the plain sum of levels (MERF's SUM)."""
+    cfg = S.small_config()
+    sc = S.make_scene(cfg)
+    sc.coarse[:, 8:] = 60.0  # sigmoid(60) = 1 - 9e-27
+    orc = O.oracle_for_scene(sc)
+    cams = S.orbit_cameras(cfg, 1)
+    a = orc.render(S.default_options(cfg), cams=cams)
+    b = orc.render(S.default_options(cfg, attn_mode=1), cams=cams)
+    np.testing.assert_allclose(a["rgb"], b["rgb"], atol=1e-13)
+    assert np.array_equal(a["stats"], b["stats"])
+
+
+def test_weights_nonnegative_and_opacity_at_most_one():
+    cfg = S.small_config()
+    sc = S.make_scene(cfg)
+    orc = O.oracle_for_scene(sc)
+    o, d = S.random_rays(64, 4, True)
+    opts = S.default_options(cfg)
+    for i in range(64):
+        smp = orc.ray_samples(opts, o[i], d[i])
+        assert np.all(smp[:, 6] >= 0)
+        assert smp[:, 6].sum() <= 1 + 1e-12
+    r = orc.render(opts, rays_o=o, rays_d=d)
+    assert np.all(r["opacity"] <= 1) and np.all(r["opacity"] >= 0)
+
+
+def test_early_termination_after_an_opaque_sample():
+    cfg = S.small_config()
+    sc = _full_scene(cfg, sigma_table=0.0, coarse_sigma=9.0)
+    orc = O.oracle_for_scene(sc)
+    r = orc.render(S.default_options(cfg), rays_o=np.array([[-3.0, 0.1, 0.2]], np.float32),
+                   rays_d=np.array([[1.0, 0.0, 0.0]], np.float32))
+    assert r["stats"][0, 1] == 1
+    assert r["opacity"][0] > 1 - 2e-3
+
+
+def test_lattice_snap_makes_distance_grid_invisible():
+    """With samples snapped to the uniform lattice, skipping with G changes only the
+    marching points, never the sample set: renders are identical (the exact form of
+    Table 4's unchanged '# Occupied')."""
+    cfg = S.small_config(blob_std=(0.05, 0.12))
+    sc = S.make_scene(cfg)
+    orc = O.oracle_for_scene(sc)
+    cams = S.orbit_cameras(cfg, 1)
+    a = orc.render(S.default_options(cfg, lattice_snap=True, use_dist=True), cams=cams)
+    b = orc.render(S.default_options(cfg, lattice_snap=True, use_dist=False), cams=cams)
+    assert np.array_equal(a["rgb"], b["rgb"])
+    assert np.array_equal(a["stats"][:, 1], b["stats"][:, 1])
+    assert a["stats"][:, 0].sum() < b["stats"][:, 0].sum()
+
+
+def test_distance_grid_cuts_marching_points_not_samples():
+    """Table 4's trend without snapping: with the distance step taken as the larger of
+    v G and s_O, fewer marching points and about the same number of samples."""
+    cfg = S.small_config(blob_std=(0.04, 0.1))
+    sc = S.make_scene(cfg)
+    orc = O.oracle_for_scene(sc)
+    cams = S.orbit_cameras(cfg, 1)
+    a = orc.render(S.default_options(cfg, use_dist=True, dist_rule=1), cams=cams)
+    b = orc.render(S.default_options(cfg, use_dist=False), cams=cams)
+    assert a["stats"][:, 0].mean() < 0.95 * b["stats"][:, 0].mean()
+    assert abs(a["stats"][:, 1].mean() - b["stats"][:, 1].mean()) < 0.05 * b["stats"][:, 1].mean() + 0.5
+
+
+# ------------------------------------------------------ paper-printed values
+
+def test_table_s4_attention_scales_the_corner_weight():
+    """Table S4: the influence of a sample on a hash entry is xi (its trilinear corner
+    weight) before attention and xi * omega (density) / xi * beta (colour) after.
+    The oracle's gradient into one entry, divided by the gradient into the fused
+    feature (read off the coarse grid, whose corner weights sum to 1), must give the
+    printed products."""
+    g = json.load(open(os.path.join(GOLDEN, "table_s4.json")))
+    for row in g["rows"]:
+        cfg = S.small_config(L=1, N=[16], T_log2=12)
+        sc = _full_scene(cfg, sigma_table=0.0, coarse_sigma=-2.0, color=0.1)
+        sc.coarse[:, 8] = math.log(row["omega"] / (1 - row["omega"]))
+        sc.coarse[:, 9] = math.log(row["beta"] / (1 - row["beta"]))
+        orc = O.oracle_for_scene(sc)
+        # a single sample at a point whose fine-cell corner (0,0,0) has weight xi:
+        # per-axis low-side weight xi^(1/3) inside cell 7 of the 16-vertex grid
+        a = row["xi"] ** (1.0 / 3.0)
+        x = 2 * ((7 + (1 - a)) / 15.0) - 1
+        start = np.array([[x, x, x]], np.float32)  # inside the box: first sample at t = 0
+        d = np.array([[0.0, 0.0, 1.0]], np.float32)
+        opts = S.default_options(cfg, max_samples=1, t_term=0.0)
+        idx, w = O.grid_indices(cfg.N, cfg.T_log2, (start + np.float32(1)) * np.float32(0.5))
+        e0 = int(idx[0, 0, 0])
+        # density: L = A; entry gradient over fused-density gradient = xi * omega
+        r = orc.render_backward(opts, d_rgb=np.zeros((1, 3)), d_opacity=np.ones(1),
+                                rays_o=start, rays_d=d)
+        xi_om = r["tables"][e0, 0] / r["coarse"][:, 0].sum()
+        assert round(xi_om, 3) == pytest.approx(row["xi_omega"], abs=1e-9)
+        # colour: L = red channel through the zero MLP; ratio = xi * beta
+        r2 = orc.render_backward(opts, d_rgb=np.array([[1.0, 0.0, 0.0]]), rays_o=start, rays_d=d)
+        xi_be = r2["tables"][e0, 1] / r2["coarse"][:, 1].sum()
+        assert round(xi_be, 3) == pytest.approx(row["xi_beta"], abs=1e-9)
+
+
+def test_parameter_count_formula_eq_s1():
+    """Eq. S1: 12 x 0.02 x L_C^3 + 8 x L x 2^22 = 99.32M for L = 2, L_C = 512, with the
+    coarse channel count 8 + 2L and the 8-channel entry of this layout."""
+    g = json.load(open(os.path.join(GOLDEN, "paper_constants.json")))["param_count"]
+    cfg = S.small_config(L=g["L"], N=[16, 32])
+    sc = S.make_scene(cfg)
+    ch = sc.coarse.shape[1]
+    assert ch == O.coarse_channels(g["L"]) == 12
+    n = ch * g["sparsity"] * g["L_C"] ** 3 + sc.tables.shape[1] * g["L"] * g["T"]
+    assert round(n / 1e6, 2) == g["ours_M"]
+    merf = 8 * (0.02 * 512 ** 3 + 3 * 2048 ** 2)
+    assert round(merf / 1e6, 1) == g["merf_M"]
