@@ -1,0 +1,317 @@
+"""Benchmark of the NGP-RT render path on GB300: 1080p frames/s and Grays/s.
+
+``python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]``
+
+One step = one 1920x1080 frame of the hd workload (unbounded 360-style scene, L=16
+levels 16..4096, T=2^19, 128^3 occupancy + distance grid, MLP 23->64->64->3), plain
+FP32 tables and MLP: the march kernel (occupancy-distance marching, coarse fetch,
+16-level gathers, attention, compositing) then the deferred-MLP kernel.  Inputs are
+resident in HBM; L2 is flushed (a 256 MiB write) between timed frames, outside the
+timed events.  Under torchrun every rank renders its own view (weak scaling,
+replicas: no data-path collective); rank 0 prints one JSON line.
+
+``--impl reference`` times the CPU oracle (the only other program of the same
+computation) on a bounded pixel sample of the same frame, on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2407_10482_gb300 import scenes as S  # noqa: E402
+
+METRIC = "1080p frames/s & Grays/s, plain FP32 vs FP16+proposal at ≤0.1 dB PSNR loss"
+WORKLOAD = "hd 1920x1080 unbounded-360 synthetic scene, L=16 (16..4096), T=2^19, 128^3 occupancy+G, MLP 23-64-64-3"
+
+
+def _peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return dict(hbm_gbs=d.get("hbm_gbs"), bf16_tflops=d.get("bf16_tflops"), source="measured")
+    return dict(hbm_gbs=6800.0, bf16_tflops=1900.0, source="fallback")
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_baseline(cfg, scene, cams, opts, sample_stride: int = 16) -> dict:
+    """The oracle on a stratified pixel sample (every sample_stride-th pixel) of the
+    frame, on all host cores; rays/s scaled to frames/s of the full frame."""
+    from oracle import oracle as O
+    orc = O.oracle_for_scene(scene)
+    n = cfg.W * cfg.H
+    pix = np.arange(0, n, sample_stride, dtype=np.int32)
+    t0 = time.perf_counter()
+    orc.render(opts, cams=cams, pix=pix)
+    dt = time.perf_counter() - t0
+    rays_s = len(pix) / dt
+    return {"value": rays_s / n, "unit": "frames/s", "rays_per_s": rays_s, "cores": O.max_threads(),
+            "kind": "oracle", "seconds": dt,
+            "sample": f"{len(pix)} pixels (every {sample_stride}th pixel of the 1920x1080 frame), FP64 oracle, OpenMP"}
+
+
+def run_reference(args):
+    world, rank, _ = _dist_setup()
+    if rank != 0:
+        return
+    cfg = S.hd_config()
+    scene = S.make_scene(cfg)
+    cams = S.orbit_cameras(cfg, 1)
+    opts = S.default_options(cfg)
+    from oracle import oracle as O
+    orc = O.oracle_for_scene(scene)
+    stride = args.ref_stride
+    n = cfg.W * cfg.H
+    steps = []
+    for k in range(args.warmup + args.steps):
+        pix = np.arange(k % stride, n, stride, dtype=np.int32)
+        t0 = time.perf_counter()
+        orc.render(opts, cams=cams, pix=pix)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            steps.append(dt * stride)  # seconds per full frame
+    ms = 1000.0 * statistics.mean(steps)
+    value = 1000.0 / ms
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": f"1/{stride} of the pixels per step, extrapolated"},
+            "cpu_baseline": {"value": value, "unit": "frames/s", "cores": O.max_threads(), "kind": "oracle",
+                             "sample": f"every {stride}th pixel of the frame per step (offset by step)"},
+            "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--ref-stride", type=int, default=64)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--table-dtype", type=int, default=0, help="0 F32, 1 F16, 2 BF16 (plain form: 0)")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_2407_10482_gb300 import ngprt as ng
+
+    world, rank, local = _dist_setup()
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ng.lib()
+
+    cfg = S.hd_config()
+    scene = S.make_scene(cfg)
+    cams = S.orbit_cameras(cfg, 1, azimuth0=45.0 * rank)
+    opts = S.default_options(cfg)
+    ds = ng.DeviceScene(cfg, scene.tables, scene.coarse, scene.mlp_w, table_dtype=args.table_dtype, device=dev)
+    docc = ng.DeviceOcc(scene.occ, cfg.R_O, cfg.n_occ_levels, device=dev)
+    rend = ng.Renderer(ds, docc, device=dev)
+    n = cfg.W * cfg.H
+    cam_arr, n_cams = ng.cameras_struct(cams, cfg.W, cfg.H)
+    ro = ng.render_opts(opts)
+    state = torch.empty(n, ng.STATE_FLOATS, device=dev)
+    rgb = torch.empty(n, 3, device=dev)
+    depth = torch.empty(n, device=dev)
+    opac = torch.empty(n, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def march():
+        ng.ngprt_render(ds.struct, docc.struct, cam_arr, n_cams, None, None, None, n, None, ro, None,
+                        ray_state=state, stream=stream)
+
+    def shade():
+        ng.ngprt_shade(ds.struct, state, n, opts.bg, rgb, depth, opac, stream=stream)
+
+    # unit counts (samples, marching points) of this frame, with and without G
+    st = rend.render(opts, cams=cams, W=cfg.W, H=cfg.H, stats=True)["stats"].float()
+    samples = float(st[:, 1].sum())
+    marching = float(st[:, 0].sum())
+    st_nog = rend.render(opts, cams=cams, W=cfg.W, H=cfg.H, stats=True, use_dist=False)["stats"].float()
+    optsmax = S.default_options(cfg, dist_rule=1)
+    st_max = rend.render(optsmax, cams=cams, W=cfg.W, H=cfg.H, stats=True)["stats"].float()
+    march_stats = {
+        "marching_per_ray": marching / n, "samples_per_ray": samples / n,
+        "without_G": {"marching_per_ray": float(st_nog[:, 0].sum()) / n,
+                      "samples_per_ray": float(st_nog[:, 1].sum()) / n},
+        "G_max_rule": {"marching_per_ray": float(st_max[:, 0].sum()) / n,
+                       "samples_per_ray": float(st_max[:, 1].sum()) / n}}
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        march()
+        shade()
+    torch.cuda.synchronize(dev)
+
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        march()
+        ev[k][1].record(stream)
+        shade()
+        ev[k][2].record(stream)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    t_march = [ev[k][0].elapsed_time(ev[k][1]) for k in range(args.steps)]
+    t_shade = [ev[k][1].elapsed_time(ev[k][2]) for k in range(args.steps)]
+    ms = statistics.mean(a + b for a, b in zip(t_march, t_shade))
+    ms_t = torch.tensor([ms], device=dev)
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    fps = world * 1000.0 / ms_max
+
+    # end to end through the public call with host buffers: camera in, image out
+    host = {"rgb": torch.empty(n, 3, pin_memory=True), "depth": torch.empty(n, pin_memory=True),
+            "opacity": torch.empty(n, pin_memory=True)}
+    d2h = n * 5 * 4
+    h2d = 72 * n_cams
+    e2e_ms = []
+    for k in range(args.warmup + args.steps):
+        flush.fill_(float(k))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        cam_arr_k, _ = ng.cameras_struct(cams, cfg.W, cfg.H)
+        ng.ngprt_render(ds.struct, docc.struct, cam_arr_k, n_cams, None, None, None, n, None, ro, rgb, depth, opac,
+                        None, state, stream=stream)
+        host["rgb"].copy_(rgb, non_blocking=True)
+        host["depth"].copy_(depth, non_blocking=True)
+        host["opacity"].copy_(opac, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        if k >= args.warmup:
+            e2e_ms.append(e0.elapsed_time(e1))
+    e2e_t = torch.tensor([statistics.mean(e2e_ms)], device=dev)
+    if world > 1:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_fps = world * 1000.0 / float(e2e_t.item())
+
+    peaks = _peaks()
+    L = cfg.L
+    entry_b = 32 if args.table_dtype == 0 else 16
+    ch_b = 4 if args.table_dtype == 0 else 2
+    bytes_per_sample = L * 8 * entry_b + 8 * (8 + 2 * L) * ch_b
+    alg_bytes = samples * bytes_per_sample + marching * 2 + n * ng.STATE_FLOATS * 4
+    t_march_avg = statistics.mean(t_march)
+    achieved = alg_bytes / (t_march_avg * 1e-3) / 1e9
+
+    line = {
+        "metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {0: "f32", 1: "f16", 2: "bf16"}[args.table_dtype], "data": "synthetic",
+        "config": {"workload": WORKLOAD, "views_per_step": 1, "rays_per_step": n, "l2_flush": True,
+                   "parallelism": f"replicas x{world}", "table_dtype": args.table_dtype},
+        "grays_per_s": fps * n / 1e9,
+        "kernels_ms": {"march": t_march_avg, "shade_mlp": statistics.mean(t_shade)},
+        "march_stats": march_stats,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": "march_kernel<16,F32>",
+                     "peak_source": peaks["source"],
+                     "bytes_per_sample": bytes_per_sample,
+                     "note": "algorithmic gather bytes (L*8 entries + 8 coarse vertices per sample, 2 B per "
+                             "marching point, 48 B state per ray) over the march kernel's event time"},
+        "e2e": {"value": e2e_fps, "unit": "frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clk,
+        "wall_s": wall,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(cfg, scene, cams, opts)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,276 @@
+/*
+ * ngprt.h -- C ABI of the GB300 (sm_103a) NGP-RT render path, arXiv 2407.10482.
+ *
+ * Conventions shared by every entry point:
+ *   - Every array argument is caller-owned DEVICE memory (CUDA global memory of the
+ *     current device) unless its comment says "host".  The library keeps no pointer
+ *     after a call returns and allocates no device memory: scratch comes from the
+ *     caller's `workspace` (size from the matching *_workspace_bytes query, 256-byte
+ *     aligned).
+ *   - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy default
+ *     stream).  Outputs are valid once the stream reaches the call.
+ *   - The return value is an ngprt_status.  Argument errors are reported before
+ *     anything is launched and leave every output untouched; NGPRT_ERR_CUDA reports
+ *     a launch failure.  ngprt_last_error() returns a message for the calling host
+ *     thread's last failure.
+ *   - Layouts are row-major with the last index fastest.  Grids are x fastest:
+ *     vertex/voxel (x, y, z) of an R-per-axis grid is element x + R*(y + R*z).
+ */
+#ifndef NGPRT_H
+#define NGPRT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    NGPRT_OK = 0,
+    NGPRT_ERR_INVALID_ARG = -1, /* bad size, null pointer, misaligned pointer, bad enum */
+    NGPRT_ERR_UNSUPPORTED = -2, /* valid request this build does not implement (e.g. an L without a kernel) */
+    NGPRT_ERR_CUDA = -3,        /* a CUDA launch or query failed */
+    NGPRT_ERR_WORKSPACE = -4    /* workspace missing or smaller than the query asked for */
+} ngprt_status;
+
+typedef enum { NGPRT_F32 = 0, NGPRT_F16 = 1, NGPRT_BF16 = 2 } ngprt_dtype;
+
+#define NGPRT_MAX_LEVELS 32
+#define NGPRT_MAX_CAMERAS 64
+#define NGPRT_STATE_FLOATS 12 /* per-ray state: C_d(3), F(4), A, depth, d(3) */
+
+/*
+ * Render-time scene (Sec. 3.1, Eq. 6): L fine levels of explicit deferred features
+ * and a coarse grid holding the coarse feature and the attention logits.
+ *   tables : [n_entries][8] of table_dtype; entry = [sigma^, c_d^(3), v_s^(4)].
+ *            Level l owns min(N[l]^3, 2^T_log2) consecutive rows, levels in order.
+ *            A level with N^3 <= 2^T_log2 is dense (row x + N*y + N^2*z); the others
+ *            use the spatial hash (x*1 ^ y*2654435761 ^ z*805459861) mod 2^T_log2.
+ *            32-byte aligned (F32) or 16-byte aligned (F16/BF16).
+ *   coarse : [R_C^3][8 + 2L] of table_dtype, channels [sigma~, c_d~(3), v_s~(4),
+ *            omega^1, beta^1, ..., omega^L, beta^L] (attention logits, Eq. 7).
+ *   mlp_w  : deferred MLP_psi (Eq. 5) of mlp_layers dense layers without bias:
+ *            layer k is a [out_k][in_k] matrix, in_0 = 32 (C_d, F, SH16(d), zero
+ *            padding), out_k = mlp_width for hidden layers (ReLU), 3 for the last.
+ *            mlp_dtype F32 (float) or F16 (__half).
+ *   bounded: 1 = scene in the box [-1,1]^3; 0 = unbounded scene under the
+ *            mip-NeRF-360 contraction into [-2,2]^3.
+ * Vertex grids of N per axis cover the unit cube coordinate u in [0,1]^3 with
+ * p = u (N - 1) (trilinear interpolation, Eq. 6).
+ */
+typedef struct {
+    int32_t L;
+    int32_t T_log2;
+    int32_t N[NGPRT_MAX_LEVELS];
+    int32_t table_dtype;
+    int32_t R_C;
+    int32_t mlp_layers;
+    int32_t mlp_width;
+    int32_t mlp_dtype;
+    int32_t bounded;
+    const void* tables;
+    const void* coarse;
+    const void* mlp_w;
+} ngprt_scene;
+
+/*
+ * Occupancy (Sec. 3.3; Sec. S2.5).  bits: n_levels bit-packed grids, finest
+ * (R_O^3 bits) first, each next level halving the resolution, each level padded
+ * to whole 32-bit words (bit i of a level is word i/32, bit i%32).  dist: the
+ * R_O^3 uint8 occupancy distance grid G, or NULL to march without it.
+ */
+typedef struct {
+    int32_t R_O;
+    int32_t n_levels;
+    const uint32_t* bits;
+    const uint8_t* dist;
+} ngprt_occ;
+
+/* Pinhole camera, OpenCV axes (x right, y down, z forward).  c2w: 3x4 row-major
+ * camera-to-world.  Pixel (col, row) looks through (col + 0.5, row + 0.5). */
+typedef struct {
+    float c2w[12];
+    float fx, fy, cx, cy;
+    int32_t W, H;
+} ngprt_camera;
+
+/* Per-call knobs.  step_base = s_0 and step_gamma = gamma of the step s = gamma s_0
+ * (Sec. S2.3); t_min = near distance; r_far = world radius of the unbounded domain;
+ * t_term = transmittance threshold (2e-3 in Sec. S2.5); bg = background colour;
+ * max_march / max_samples = caps on marching points / samples per ray;
+ * use_dist = read G (Eq. 9); lattice_snap = (bounded only) keep samples on the
+ * uniform lattice; attn_mode 0 = separate attention (Eq. 8), 1 = SUM, 2 = one gate
+ * per level; dist_rule 0 = Eq. 9 as printed, 1 = max(v G, s_O). */
+typedef struct {
+    float step_base;
+    float step_gamma;
+    float t_min;
+    float r_far;
+    float t_term;
+    float bg[3];
+    int32_t max_march;
+    int32_t max_samples;
+    int32_t use_dist;
+    int32_t lattice_snap;
+    int32_t attn_mode;
+    int32_t dist_rule;
+} ngprt_render_opts;
+
+/* Number of uint32 words of an occupancy pyramid (see ngprt_occ). */
+size_t ngprt_occ_bits_words(int32_t R, int32_t n_levels);
+
+/* Workspace bytes ngprt_build_occ_dist needs for an R^3 grid. */
+size_t ngprt_build_occ_dist_workspace_bytes(int32_t R);
+
+/*
+ * Occupancy pyramid and occupancy distance grid G (Sec. 3.3: per voxel, the
+ * distance to the nearest occupied voxel, rounded down, in voxel units, uint8;
+ * Sec. S2.5: the grid down-sampled to coarser levels).
+ *   occ          : [R^3] uint8, nonzero = occupied.  R a power of two, 2..1024.
+ *   n_levels     : pyramid levels, 1 <= n_levels and R >> (n_levels-1) >= 1.
+ *   occ_bits_out : [ngprt_occ_bits_words(R, n_levels)] uint32, written in full.
+ *   dist_out     : [R^3] uint8 G, or NULL to skip it.  G = min(255, floor(D)), D the
+ *                  Euclidean distance between the voxel boxes in voxels; 0 on and next
+ *                  to occupied voxels; 255 everywhere if nothing is occupied.
+ *   workspace    : >= ngprt_build_occ_dist_workspace_bytes(R) bytes.
+ */
+int32_t ngprt_build_occ_dist(const uint8_t* occ, int32_t R, int32_t n_levels, uint32_t* occ_bits_out,
+                             uint8_t* dist_out, void* workspace, size_t ws_bytes, void* stream);
+
+/* Rows of the concatenated fine tables (sum over levels of min(N^3, 2^T_log2)). */
+int64_t ngprt_table_entries(const ngprt_scene* scene);
+
+/* Workspace bytes of ngprt_render / ngprt_render_backward for n_rays rays. */
+size_t ngprt_render_workspace_bytes(const ngprt_scene* scene, int64_t n_rays);
+
+/*
+ * Render rays (Eq. 2, 5, 6, 8, 9): occupancy-distance marching, per-sample coarse
+ * fetch + per-level gathers + lightweight attention, alpha compositing, one
+ * deferred MLP per ray, colour over the background.
+ * Rays: with cams != NULL (host array of n_cams <= 64 cameras sharing W, H) ray i
+ * is pixel pixel_ids[i] (or i if pixel_ids == NULL) of the multi-view image,
+ * id = view*W*H + row*W + col; else ray i is (rays_o[i], rays_d[i]) (float [n][3],
+ * d need not be unit: it is normalised).  n_rays >= 0 (0 launches nothing).
+ *   t_interval : NULL or float [n][2] (t_near, t_far): march only inside it.
+ *   rgb [n][3], depth [n], opacity [n] : float outputs (NULL allowed for depth/opacity).
+ *                If rgb is NULL only the march kernel runs: ray_state is then required
+ *                and ngprt_shade turns it into colours.
+ *   ray_stats  : NULL or int32 [n][2] = (marching points, samples).
+ *   ray_state  : NULL or float [n][NGPRT_STATE_FLOATS], the per-ray composite state
+ *                ngprt_render_backward consumes.
+ */
+int32_t ngprt_render(const ngprt_scene* scene, const ngprt_occ* occ, const ngprt_camera* cams, int32_t n_cams,
+                     const int32_t* pixel_ids, const float* rays_o, const float* rays_d, int64_t n_rays,
+                     const float* t_interval, const ngprt_render_opts* opts, float* rgb, float* depth,
+                     float* opacity, int32_t* ray_stats, float* ray_state, void* workspace, size_t ws_bytes,
+                     void* stream);
+
+/*
+ * Deferred shading of marched rays (Eq. 5 and the colour sigmoid of Sec. S2.1):
+ * rgb = A sigmoid(C_d + MLP_psi(C_d, F, SH16(d))) + (1 - A) bg from ray_state
+ * ([n][NGPRT_STATE_FLOATS], written by ngprt_render); depth and opacity (NULL
+ * allowed) are copied out of the state.  Only scene->mlp_* fields are read.
+ */
+int32_t ngprt_shade(const ngprt_scene* scene, const float* ray_state, int64_t n_rays, const float bg[3],
+                    float* rgb, float* depth, float* opacity, void* stream);
+
+/*
+ * Reverse pass of ngprt_render (F32 tables and F32 MLP): given dL/d rgb, depth,
+ * opacity of the same rays (same cams/pixel_ids or rays, same opts, and the
+ * ray_state a forward call wrote), ACCUMULATE (+=) dL/d tables into g_tables
+ * ([n_entries][8] float), dL/d coarse into g_coarse ([R_C^3][8+2L] float) and
+ * dL/d mlp_w into g_mlp (float, mlp_w's layout).  Each ray is marched again; the
+ * sample set is the forward's.  Table and grid gradients are atomic adds, so their
+ * float summation order varies from run to run.
+ *   d_rgb [n][3]; d_depth, d_opacity [n] or NULL (zero).
+ */
+int32_t ngprt_render_backward(const ngprt_scene* scene, const ngprt_occ* occ, const ngprt_camera* cams,
+                              int32_t n_cams, const int32_t* pixel_ids, const float* rays_o,
+                              const float* rays_d, int64_t n_rays, const ngprt_render_opts* opts,
+                              const float* ray_state, const float* d_rgb, const float* d_depth,
+                              const float* d_opacity, float* g_tables, float* g_coarse, float* g_mlp,
+                              void* workspace, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------------
+ * Learned proposal (not in the paper, which leaves adaptive sampling aside in
+ * Sec. 2): a 6 -> 32 -> 32 -> 3 MLP on (o / in_scale, d / |d|) predicting the interval
+ * [t_near, t_far] that holds a ray's significant weights and its opacity A^:
+ *   h1 = relu(W0 e + b0), h2 = relu(W1 h1 + b1), z = W2 h2 + b2,
+ *   t_near = t_scale sigmoid(z0), t_far = t_scale sigmoid(z1), A^ = sigmoid(z2).
+ * prop_w: float [ngprt_proposal_param_count()] = W0 [32][6], b0 [32], W1 [32][32],
+ * b1 [32], W2 [3][32], b2 [3].  Rays are given as for ngprt_render.
+ * ------------------------------------------------------------------------------ */
+int32_t ngprt_proposal_param_count(void);
+
+/* Interval per ray, t_interval_out [n][2] = (t_near - margin, t_far + margin); a ray
+ * with A^ < a_min gets an empty interval (+inf, -inf) (nothing is marched), a ray with
+ * t_far <= t_near gets (-inf, +inf) (the whole ray).  a_hat_out [n] (NULL allowed). */
+int32_t ngprt_propose(const float* prop_w, const ngprt_camera* cams, int32_t n_cams, const int32_t* pixel_ids,
+                      const float* rays_o, const float* rays_d, int64_t n_rays, float in_scale, float t_scale,
+                      float margin, float a_min, float* t_interval_out, float* a_hat_out, void* stream);
+
+/* Training loss of the proposal against targets [n][3] = (t_near*, t_far*, A*):
+ * mean over rays of A* (sl1(dt_near / t_scale) + sl1(dt_far / t_scale)) + (A^ - A*)^2,
+ * sl1 = smooth L1 with beta 0.01.  ACCUMULATES the gradient into g_prop_w and the loss
+ * into *loss (one device float, NULL to skip). */
+int32_t ngprt_propose_backward(const float* prop_w, const ngprt_camera* cams, int32_t n_cams,
+                               const int32_t* pixel_ids, const float* rays_o, const float* rays_d, int64_t n_rays,
+                               float in_scale, float t_scale, const float* targets, float* g_prop_w, float* loss,
+                               void* stream);
+
+/* Proposal targets from a plain render of the same rays (ray_state from ngprt_render
+ * without t_interval): targets [n][3] = t of the first sample whose cumulative weight
+ * exceeds 0.005 A, t + delta of the first sample whose cumulative weight reaches
+ * 0.995 A, and A (0, 0, 0 for rays without samples). */
+int32_t ngprt_proposal_targets(const ngprt_scene* scene, const ngprt_occ* occ, const ngprt_camera* cams,
+                               int32_t n_cams, const int32_t* pixel_ids, const float* rays_o, const float* rays_d,
+                               int64_t n_rays, const ngprt_render_opts* opts, const float* ray_state, float* targets,
+                               void* stream);
+
+/* Fallback pass after a render with t_interval: every ray whose interval was not the
+ * whole ray and whose composited opacity A (ray_state) fell short of the prediction,
+ * a_hat - A > threshold, is marched again over its whole domain and its ray_state
+ * overwritten; ray_stats (NULL allowed) then adds the second march's counts.  Then
+ * ngprt_shade gives the colours. */
+int32_t ngprt_render_fallback(const ngprt_scene* scene, const ngprt_occ* occ, const ngprt_camera* cams,
+                              int32_t n_cams, const int32_t* pixel_ids, const float* rays_o, const float* rays_d,
+                              int64_t n_rays, const float* t_interval, const float* a_hat, float threshold,
+                              const ngprt_render_opts* opts, float* ray_state, int32_t* ray_stats, void* stream);
+
+/*
+ * Photometric L2 loss of a training step: *loss += scale * sum_i (rgb_i - target_i)^2
+ * (loss: one device float, NULL to skip) and d_rgb = 2 scale (rgb - target) (NULL to
+ * skip), over n floats.
+ */
+int32_t ngprt_l2_loss(const float* rgb, const float* target, int64_t n, float scale, float* loss, float* d_rgb,
+                      void* stream);
+
+/*
+ * One Adam step over n floats (the optimiser of Sec. S2.4): m = b1 m + (1-b1) g,
+ * v = b2 v + (1-b2) g^2, param -= lr (m/(1-b1^step)) / (sqrt(v/(1-b2^step)) + eps);
+ * step >= 1 counts from 1; zero_grad != 0 also clears grad.  All four arrays 16-byte
+ * aligned.
+ */
+int32_t ngprt_adam_step(float* param, float* grad, float* m, float* v, int64_t n, float lr, float beta1, float beta2,
+                        float eps, int32_t step, int32_t zero_grad, void* stream);
+
+/*
+ * Test hook for the per-level indexing (Eq. 3, Eq. 6): for n positions u (float
+ * [n][3] in the unit cube) write the absolute table row of each of the 8 corners
+ * of each fine level, uint32 [n][L][8], corner c = +x if bit0, +y if bit1, +z if bit2.
+ */
+int32_t ngprt_grid_indices(const ngprt_scene* scene, const float* u, int64_t n, uint32_t* idx_out,
+                           void* stream);
+
+/* Message of the calling thread's last failed call ("" if none). */
+const char* ngprt_last_error(void);
+
+/* ABI version of this header (major*100 + minor). */
+int32_t ngprt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NGPRT_H */

@@ -866,3 +866,181 @@ int or_max_threads(void) { return omp_get_max_threads(); }
 void or_set_threads(int n) { (void)n; }
 int or_max_threads(void) { return 1; }
 #endif
+
+/* ------------------------------------------------------------ training step */
+
+/* Photometric L2 loss L = scale * sum (rgb - target)^2 and its gradient
+ * d_rgb = 2 scale (rgb - target) (the configs' training objective). */
+double or_l2_loss(const double* rgb, const double* target, int64_t n, double scale, double* d_rgb) {
+    double L = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double e = rgb[i] - target[i];
+        L += scale * e * e;
+        if (d_rgb) d_rgb[i] = 2.0 * scale * e;
+    }
+    return L;
+}
+
+/* One Adam step (Kingma and Ba; the optimiser of Sec. S2.4): m = b1 m + (1-b1) g,
+ * v = b2 v + (1-b2) g^2, p -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps). */
+void or_adam_step(double* p, const double* g, double* m, double* v, int64_t n, double lr, double b1, double b2,
+                  double eps, int step) {
+    double c1 = 1.0 - pow(b1, step), c2 = 1.0 - pow(b2, step);
+    for (int64_t i = 0; i < n; ++i) {
+        m[i] = b1 * m[i] + (1.0 - b1) * g[i];
+        v[i] = b2 * v[i] + (1.0 - b2) * g[i] * g[i];
+        p[i] -= lr * (m[i] / c1) / (sqrt(v[i] / c2) + eps);
+    }
+}
+
+/* ------------------------------------------------------- learned proposal */
+/* Not in the paper (it calls adaptive sampling orthogonal, Sec. 2).  A small MLP
+ * maps a ray (o / in_scale, d) to [t_near, t_far] and the expected opacity A^:
+ *   h1 = relu(W0 e + b0), h2 = relu(W1 h1 + b1), z = W2 h2 + b2,
+ *   t_near = t_scale sigmoid(z0), t_far = t_scale sigmoid(z1), A^ = sigmoid(z2).
+ * Parameters, flat: W0 [W][6], b0 [W], W1 [W][W], b1 [W], W2 [3][W], b2 [3].
+ * Loss per ray: A* (sl1((t_near - t_near*)/t_scale) + sl1((t_far - t_far*)/t_scale))
+ * + (A^ - A*)^2, sl1 = smooth L1 with beta = 0.01. */
+
+#define OR_PROP_IN 6
+
+static void or_prop_input(const float o[3], const float d[3], double in_scale, double e[OR_PROP_IN]) {
+    double n = sqrt((double)d[0] * d[0] + (double)d[1] * d[1] + (double)d[2] * d[2]);
+    for (int a = 0; a < 3; ++a) {
+        e[a] = (double)o[a] / in_scale;
+        e[3 + a] = (double)d[a] / n;
+    }
+}
+
+static double or_sl1(double x, double beta) {
+    double ax = fabs(x);
+    return ax < beta ? 0.5 * x * x / beta : ax - 0.5 * beta;
+}
+
+static double or_sl1_grad(double x, double beta) {
+    double ax = fabs(x);
+    return ax < beta ? x / beta : (x > 0 ? 1.0 : -1.0);
+}
+
+/* Forward for n rays: out [n][3] = t_near, t_far, A^. */
+void or_prop_forward(const double* w, int W, const float* rays_o, const float* rays_d, int n, double in_scale,
+                     double t_scale, double* out) {
+    const double *W0 = w, *b0 = W0 + W * OR_PROP_IN, *W1 = b0 + W, *b1 = W1 + W * W, *W2 = b1 + W, *b2 = W2 + 3 * W;
+    for (int i = 0; i < n; ++i) {
+        double e[OR_PROP_IN], h1[256], h2[256], z[3];
+        or_prop_input(rays_o + 3 * i, rays_d + 3 * i, in_scale, e);
+        for (int o = 0; o < W; ++o) {
+            double a = b0[o];
+            for (int k = 0; k < OR_PROP_IN; ++k) a += W0[o * OR_PROP_IN + k] * e[k];
+            h1[o] = a > 0 ? a : 0;
+        }
+        for (int o = 0; o < W; ++o) {
+            double a = b1[o];
+            for (int k = 0; k < W; ++k) a += W1[o * W + k] * h1[k];
+            h2[o] = a > 0 ? a : 0;
+        }
+        for (int o = 0; o < 3; ++o) {
+            double a = b2[o];
+            for (int k = 0; k < W; ++k) a += W2[o * W + k] * h2[k];
+            z[o] = a;
+        }
+        out[3 * i + 0] = t_scale * or_sigmoid(z[0]);
+        out[3 * i + 1] = t_scale * or_sigmoid(z[1]);
+        out[3 * i + 2] = or_sigmoid(z[2]);
+    }
+}
+
+/* Mean loss over n rays against targets [n][3] = t_near*, t_far*, A*, and its
+ * gradient (accumulated into g, same layout as w). */
+double or_prop_loss_grad(const double* w, int W, const float* rays_o, const float* rays_d, int n, double in_scale,
+                         double t_scale, const double* targets, double* g) {
+    const double *W0 = w, *b0 = W0 + W * OR_PROP_IN, *W1 = b0 + W, *b1 = W1 + W * W, *W2 = b1 + W, *b2 = W2 + 3 * W;
+    double *gW0 = g, *gb0 = gW0 + W * OR_PROP_IN, *gW1 = gb0 + W, *gb1 = gW1 + W * W, *gW2 = gb1 + W, *gb2 = gW2 + 3 * W;
+    double total = 0.0;
+    const double beta = 0.01, inv_n = 1.0 / (double)n;
+    for (int i = 0; i < n; ++i) {
+        double e[OR_PROP_IN], a1[256], h1[256], a2[256], h2[256], z[3];
+        or_prop_input(rays_o + 3 * i, rays_d + 3 * i, in_scale, e);
+        for (int o = 0; o < W; ++o) {
+            double a = b0[o];
+            for (int k = 0; k < OR_PROP_IN; ++k) a += W0[o * OR_PROP_IN + k] * e[k];
+            a1[o] = a;
+            h1[o] = a > 0 ? a : 0;
+        }
+        for (int o = 0; o < W; ++o) {
+            double a = b1[o];
+            for (int k = 0; k < W; ++k) a += W1[o * W + k] * h1[k];
+            a2[o] = a;
+            h2[o] = a > 0 ? a : 0;
+        }
+        for (int o = 0; o < 3; ++o) {
+            double a = b2[o];
+            for (int k = 0; k < W; ++k) a += W2[o * W + k] * h2[k];
+            z[o] = a;
+        }
+        const double *tg = targets + 3 * i;
+        double s0 = or_sigmoid(z[0]), s1 = or_sigmoid(z[1]), s2 = or_sigmoid(z[2]);
+        double x0 = (t_scale * s0 - tg[0]) / t_scale, x1 = (t_scale * s1 - tg[1]) / t_scale;
+        double L = tg[2] * (or_sl1(x0, beta) + or_sl1(x1, beta)) + (s2 - tg[2]) * (s2 - tg[2]);
+        total += L * inv_n;
+        double gz[3];
+        gz[0] = inv_n * tg[2] * or_sl1_grad(x0, beta) * s0 * (1 - s0);
+        gz[1] = inv_n * tg[2] * or_sl1_grad(x1, beta) * s1 * (1 - s1);
+        gz[2] = inv_n * 2.0 * (s2 - tg[2]) * s2 * (1 - s2);
+        double gh2[256], ga2[256], gh1[256], ga1[256];
+        for (int k = 0; k < W; ++k) gh2[k] = 0.0;
+        for (int o = 0; o < 3; ++o) {
+            gb2[o] += gz[o];
+            for (int k = 0; k < W; ++k) {
+                gW2[o * W + k] += gz[o] * h2[k];
+                gh2[k] += W2[o * W + k] * gz[o];
+            }
+        }
+        for (int k = 0; k < W; ++k) { ga2[k] = a2[k] > 0 ? gh2[k] : 0.0; gh1[k] = 0.0; }
+        for (int o = 0; o < W; ++o) {
+            gb1[o] += ga2[o];
+            for (int k = 0; k < W; ++k) {
+                gW1[o * W + k] += ga2[o] * h1[k];
+                gh1[k] += W1[o * W + k] * ga2[o];
+            }
+        }
+        for (int k = 0; k < W; ++k) ga1[k] = a1[k] > 0 ? gh1[k] : 0.0;
+        for (int o = 0; o < W; ++o) {
+            gb0[o] += ga1[o];
+            for (int k = 0; k < OR_PROP_IN; ++k) gW0[o * OR_PROP_IN + k] += ga1[o] * e[k];
+        }
+    }
+    return total;
+}
+
+/* Training targets from the plain render (per ray): with the final opacity A,
+ * t_near* = t_i of the first sample whose cumulative weight exceeds 0.005 A, and
+ * t_far* = t_i + delta_i of the first sample whose cumulative weight reaches
+ * 0.995 A; A* = A.  Rays without samples get (0, 0, 0). */
+void or_prop_targets(const or_scene* s, const or_occ* oc, const or_opts* op, const float* cams, int n_cams, int W,
+                     int H, const int32_t* pix, const float* rays_o, const float* rays_d, int n, double* targets) {
+    int cap = op->max_samples > 0 ? op->max_samples : 1;
+    #pragma omp parallel
+    {
+        or_sample* sm = (or_sample*)malloc(sizeof(or_sample) * (size_t)cap);
+        #pragma omp for schedule(dynamic, 16)
+        for (int i = 0; i < n; ++i) {
+            float o[3], dv[3];
+            or_ray_input(cams, n_cams, W, H, pix, rays_o, rays_d, i, o, dv);
+            or_ray_out rr;
+            or_march(s, oc, op, o, dv, -INFINITY, INFINITY, &rr, sm, NULL);
+            double tn = 0.0, tf = 0.0, cum = 0.0;
+            int got_near = 0, got_far = 0;
+            for (int k = 0; k < rr.n_samples; ++k) {
+                cum += sm[k].T_before * sm[k].alpha;
+                if (!got_near && cum > 0.005 * rr.A) { tn = sm[k].t; got_near = 1; }
+                if (!got_far && cum >= 0.995 * rr.A) { tf = (double)sm[k].t + (double)sm[k].delta; got_far = 1; }
+            }
+            if (rr.n_samples > 0 && !got_far) tf = (double)sm[rr.n_samples - 1].t + (double)sm[rr.n_samples - 1].delta;
+            targets[3 * i + 0] = tn;
+            targets[3 * i + 1] = tf;
+            targets[3 * i + 2] = rr.A;
+        }
+        free(sm);
+    }
+}

@@ -304,3 +304,64 @@ def contract(x: np.ndarray, bounded: bool = False):
 def coarse_channels(L: int) -> int:
     """Channels per coarse-grid vertex: deferred feature (8) plus omega, beta per level."""
     return 8 + 2 * L
+
+
+def l2_loss(rgb, target, scale=1.0):
+    rgb = _c(rgb, np.float64).reshape(-1)
+    target = _c(target, np.float64).reshape(-1)
+    d = np.empty_like(rgb)
+    f = lib().or_l2_loss
+    f.restype = C.c_double
+    L = f(_p(rgb), _p(target), C.c_int64(len(rgb)), C.c_double(scale), _p(d))
+    return float(L), d
+
+
+def adam_step(p, g, m, v, lr, b1, b2, eps, step):
+    """In-place FP64 Adam step on numpy arrays p, m, v with gradient g."""
+    for a in (p, m, v):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    g = _c(g, np.float64)
+    lib().or_adam_step(_p(p), _p(g), _p(m), _p(v), C.c_int64(p.size), C.c_double(lr), C.c_double(b1),
+                       C.c_double(b2), C.c_double(eps), C.c_int(step))
+
+
+def prop_param_count(W: int = 32) -> int:
+    """Flat proposal-MLP parameters: W0 [W][6], b0 [W], W1 [W][W], b1 [W], W2 [3][W], b2 [3]."""
+    return W * 6 + W + W * W + W + 3 * W + 3
+
+
+def prop_forward(w, rays_o, rays_d, in_scale, t_scale, W=32):
+    w = _c(w, np.float64)
+    o = _c(rays_o, np.float32).reshape(-1, 3)
+    d = _c(rays_d, np.float32).reshape(-1, 3)
+    out = np.empty((len(o), 3), np.float64)
+    lib().or_prop_forward(_p(w), C.c_int(W), _p(o), _p(d), C.c_int(len(o)), C.c_double(in_scale),
+                          C.c_double(t_scale), _p(out))
+    return out
+
+
+def prop_loss_grad(w, rays_o, rays_d, targets, in_scale, t_scale, W=32):
+    w = _c(w, np.float64)
+    o = _c(rays_o, np.float32).reshape(-1, 3)
+    d = _c(rays_d, np.float32).reshape(-1, 3)
+    tg = _c(targets, np.float64).reshape(-1, 3)
+    g = np.zeros_like(w)
+    f = lib().or_prop_loss_grad
+    f.restype = C.c_double
+    L = f(_p(w), C.c_int(W), _p(o), _p(d), C.c_int(len(o)), C.c_double(in_scale), C.c_double(t_scale), _p(tg), _p(g))
+    return float(L), g
+
+
+def _prop_targets(self, opts, cams=None, pix=None, rays_o=None, rays_d=None, W=None, H=None):
+    W = W or self.cfg.W
+    H = H or self.cfg.H
+    cams, pix, ro, rd, n = self._rays(cams, pix, rays_o, rays_d)
+    out = np.empty((n, 3), np.float64)
+    op = self._opts(opts)
+    lib().or_prop_targets(C.byref(self._s), C.byref(self._o), C.byref(op), _p(cams),
+                          C.c_int(0 if cams is None else len(cams)), C.c_int(W), C.c_int(H), _p(pix), _p(ro), _p(rd),
+                          C.c_int(n), _p(out))
+    return out
+
+
+Oracle.prop_targets = _prop_targets

@@ -1,0 +1,468 @@
+// backward.cu -- reverse pass of the render (Eq. 2, 5, 8; Sec. S2.1 activations).
+//
+// Kernel 1 (shade_backward_kernel): per ray, the deferred MLP_psi and colour
+// sigmoid again from the stored composite state, then their reverse pass: the
+// cotangents of C_d, F, A and depth go to a per-ray record, and the MLP weight
+// gradients are summed over the warp's rays with shuffles, over the block in shared
+// memory, and added to g_mlp once per block.
+// Kernel 2 (march_backward_kernel): per ray, the same march as the forward (same
+// decisions: march_loop), and at each sample i the derivative of the composite
+// sums Q = sum_j w_j q_j:
+//     dQ/dq_i = w_i,   dQ/dsigma_i = delta_i (T_{i+1} q_i - sum_{j>i} w_j q_j),
+// where the suffix sum is the stored total minus the running prefix.  The density
+// activation exp has the truncated derivative exp(min(sigma_raw, 15)).  Through
+// the attention (Eq. 8) and the trilinear weights the gradient reaches 8 entries
+// of each fine level and 8 coarse vertices; it is added with 16-byte vector atomics.
+#include "march.cuh"
+
+namespace ngprt {
+namespace {
+
+constexpr int kCotFloats = 12;  // g_Cd(3), g_F(4), g_A, g_depth, S_total, pad(2)
+
+struct ShadeBwdParams {
+    const float* state;
+    const float* w;
+    const float* d_rgb;
+    const float* d_depth;
+    const float* d_opacity;
+    float bg[3];
+    int64_t n;
+    float* cot;
+    float* g_mlp;
+};
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int WIDTH, int LAYERS>
+__global__ void __launch_bounds__(128) shade_backward_kernel(const __grid_constant__ ShadeBwdParams p) {
+    constexpr int n_w0 = WIDTH * kMlpIn;
+    constexpr int n_mid = (LAYERS - 2) * WIDTH * WIDTH;
+    constexpr int n_last = 3 * WIDTH;
+    constexpr int n_all = n_w0 + n_mid + n_last;
+    __shared__ __align__(16) float ws[n_all];
+    __shared__ float gw[n_all];
+    for (int i = threadIdx.x; i < n_all; i += blockDim.x) {
+        ws[i] = p.w[i];
+        gw[i] = 0.0f;
+    }
+    __syncthreads();
+    const int64_t ray = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = ray < p.n;
+    // ---- forward again (inactive lanes carry zeros so that warp sums stay valid)
+    float x[24];
+    float A = 0.0f;
+    float Cd[3] = {0, 0, 0}, F[4] = {0, 0, 0, 0}, depth = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 24; ++i) x[i] = 0.0f;
+    if (active) {
+        const float4* s4 = reinterpret_cast<const float4*>(p.state + ray * NGPRT_STATE_FLOATS);
+        const float4 q0 = s4[0], q1 = s4[1], q2 = s4[2];
+        Cd[0] = q0.x; Cd[1] = q0.y; Cd[2] = q0.z;
+        F[0] = q0.w; F[1] = q1.x; F[2] = q1.y; F[3] = q1.z;
+        A = q1.w;
+        depth = q2.x;
+        x[0] = Cd[0]; x[1] = Cd[1]; x[2] = Cd[2];
+        x[3] = F[0]; x[4] = F[1]; x[5] = F[2]; x[6] = F[3];
+        sh16(q2.y, q2.z, q2.w, x + 7);
+    }
+    float a1[WIDTH];  // pre-activation of hidden layer 1
+#pragma unroll
+    for (int o = 0; o < WIDTH; ++o) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 23; ++i) acc = fmaf(ws[o * kMlpIn + i], x[i], acc);
+        a1[o] = acc;
+    }
+    const float* wl = ws + n_w0 + n_mid;
+    float a2[LAYERS == 3 ? WIDTH : 1];
+    float out[3] = {0.0f, 0.0f, 0.0f};
+    if constexpr (LAYERS == 3) {
+        const float* wm = ws + n_w0;
+#pragma unroll 4
+        for (int o = 0; o < WIDTH; ++o) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int i = 0; i < WIDTH; ++i) acc = fmaf(wm[o * WIDTH + i], fmaxf(a1[i], 0.0f), acc);
+            a2[o] = acc;
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int i = 0; i < WIDTH; ++i) acc = fmaf(wl[k * WIDTH + i], fmaxf(a2[i], 0.0f), acc);
+            out[k] = acc;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int i = 0; i < WIDTH; ++i) acc = fmaf(wl[k * WIDTH + i], fmaxf(a1[i], 0.0f), acc);
+            out[k] = acc;
+        }
+    }
+    // ---- colour: rgb = A sigmoid(z) + (1 - A) bg, z = C_d + out
+    float gz[3], gA = 0.0f;
+    if (active) {
+        gA = p.d_opacity ? p.d_opacity[ray] : 0.0f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float sg = sigmoidf_(Cd[k] + out[k]);
+            const float gr = p.d_rgb[3 * ray + k];
+            gz[k] = gr * A * sg * (1.0f - sg);
+            gA += gr * (sg - p.bg[k]);
+        }
+    } else {
+        gz[0] = gz[1] = gz[2] = 0.0f;
+    }
+    // ---- last layer: dW_last[k][i] = gz[k] h_last[i]; g_h = W_last^T gz
+    float* gwl = gw + n_w0 + n_mid;
+    const int lane = threadIdx.x & 31;
+    float gh[WIDTH];
+#pragma unroll
+    for (int i = 0; i < WIDTH; ++i) {
+        float pre;
+        if constexpr (LAYERS == 3) pre = a2[i];
+        else pre = a1[i];
+        const float hi = fmaxf(pre, 0.0f);
+        float g = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float s = warp_sum(gz[k] * hi);
+            if (lane == 0) atomicAdd(&gwl[k * WIDTH + i], s);
+            g = fmaf(wl[k * WIDTH + i], gz[k], g);
+        }
+        gh[i] = pre > 0.0f ? g : 0.0f;  // gradient of the pre-activation
+    }
+    if constexpr (LAYERS == 3) {
+        // middle layer: dW1[o][i] = gh[o] relu(a1[i]); g_a1 = (W1^T gh) * [a1 > 0]
+        const float* wm = ws + n_w0;
+        float* gwm = gw + n_w0;
+#pragma unroll 2
+        for (int o = 0; o < WIDTH; ++o) {
+#pragma unroll
+            for (int i = 0; i < WIDTH; ++i) {
+                const float s = warp_sum(gh[o] * fmaxf(a1[i], 0.0f));
+                if (lane == 0) atomicAdd(&gwm[o * WIDTH + i], s);
+            }
+        }
+        float g1[WIDTH];
+#pragma unroll
+        for (int i = 0; i < WIDTH; ++i) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int o = 0; o < WIDTH; ++o) acc = fmaf(wm[o * WIDTH + i], gh[o], acc);
+            g1[i] = a1[i] > 0.0f ? acc : 0.0f;
+        }
+#pragma unroll
+        for (int i = 0; i < WIDTH; ++i) gh[i] = g1[i];
+    }
+    // first layer: dW0[o][i] = gh[o] x[i] (i < 23; padding columns get zero); g_x = W0^T gh
+#pragma unroll 2
+    for (int o = 0; o < WIDTH; ++o) {
+#pragma unroll
+        for (int i = 0; i < 23; ++i) {
+            const float s = warp_sum(gh[o] * x[i]);
+            if (lane == 0) atomicAdd(&gw[o * kMlpIn + i], s);
+        }
+    }
+    if (active) {
+        float gx[7];
+#pragma unroll
+        for (int i = 0; i < 7; ++i) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int o = 0; o < WIDTH; ++o) acc = fmaf(ws[o * kMlpIn + i], gh[o], acc);
+            gx[i] = acc;
+        }
+        const float gCd[3] = {gz[0] + gx[0], gz[1] + gx[1], gz[2] + gx[2]};
+        const float gD = p.d_depth ? p.d_depth[ray] : 0.0f;
+        const float S = gCd[0] * Cd[0] + gCd[1] * Cd[1] + gCd[2] * Cd[2] + gx[3] * F[0] + gx[4] * F[1] +
+                        gx[5] * F[2] + gx[6] * F[3] + gA * A + gD * depth;
+        float4* c4 = reinterpret_cast<float4*>(p.cot + ray * kCotFloats);
+        c4[0] = make_float4(gCd[0], gCd[1], gCd[2], gx[3]);
+        c4[1] = make_float4(gx[4], gx[5], gx[6], gA);
+        c4[2] = make_float4(gD, S, 0.0f, 0.0f);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n_all; i += blockDim.x) {
+        const float v = gw[i];
+        if (v != 0.0f) atomicAdd(&p.g_mlp[i], v);
+    }
+}
+
+struct MarchBwdParams {
+    MarchParams m;
+    const float* state;
+    const float* cot;
+    float* g_tables;
+    float* g_coarse;
+};
+
+__device__ __forceinline__ void atomic_add4(float* p, float a, float b, float c, float d) {
+#ifdef NGPRT_SCALAR_ATOMICS
+    atomicAdd(p, a);
+    atomicAdd(p + 1, b);
+    atomicAdd(p + 2, c);
+    atomicAdd(p + 3, d);
+#else
+    atomicAdd(reinterpret_cast<float4*>(p), make_float4(a, b, c, d));
+#endif
+}
+
+// Reverse of sample_features at u for the feature cotangent gf[8]: attention
+// logits, coarse vertices and fine entries.
+template <int L>
+__device__ __forceinline__ void scatter_features(const Grid& g, const float u[3], int attn_mode, const float gf[8],
+                                                 float* g_tables, float* g_coarse) {
+    constexpr int NC = kNFeat + 2 * L;
+    int b[3];
+    float w[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) grid_cell(u[a], g.R_C, b[a], w[a]);
+    const uint32_t R = (uint32_t)g.R_C;
+    uint32_t cv[8];
+    float logit[2 * L];
+#pragma unroll
+    for (int k = 0; k < 2 * L; ++k) logit[k] = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        cv[c] = (uint32_t)(b[0] + (c & 1)) + R * ((uint32_t)(b[1] + ((c >> 1) & 1)) + R * (uint32_t)(b[2] + ((c >> 2) & 1)));
+        float val[NC];
+        load_channels<NGPRT_F32, NC>(g.coarse, cv[c], val);
+        const float cw = corner_w(w, c);
+#pragma unroll
+        for (int k = 0; k < 2 * L; ++k) logit[k] = fmaf(cw, val[kNFeat + k], logit[k]);
+    }
+    float glog[2 * L];
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+        float om, be;
+        if (attn_mode == 1) {
+            om = 1.0f;
+            be = 1.0f;
+        } else if (attn_mode == 2) {
+            om = sigmoidf_(logit[2 * l]);
+            be = om;
+        } else {
+            om = sigmoidf_(logit[2 * l]);
+            be = sigmoidf_(logit[2 * l + 1]);
+        }
+        int bl[3];
+        float wl[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) grid_cell(u[a], g.N[l], bl[a], wl[a]);
+        uint32_t rows[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+            rows[c] = level_row(g, l, (uint32_t)(bl[0] + (c & 1)), (uint32_t)(bl[1] + ((c >> 1) & 1)),
+                                (uint32_t)(bl[2] + ((c >> 2) & 1)));
+        float fl[8];
+#pragma unroll
+        for (int ch = 0; ch < 8; ++ch) fl[ch] = 0.0f;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            float e[8];
+            load_entry<NGPRT_F32>(g.tables, rows[c], e);
+            const float cw = corner_w(wl, c);
+#pragma unroll
+            for (int ch = 0; ch < 8; ++ch) fl[ch] = fmaf(cw, e[ch], fl[ch]);
+        }
+        const float g_om = fl[0] * gf[0];
+        float g_be = 0.0f;
+#pragma unroll
+        for (int ch = 1; ch < 8; ++ch) g_be = fmaf(fl[ch], gf[ch], g_be);
+        if (attn_mode == 0) {
+            glog[2 * l] = g_om * om * (1.0f - om);
+            glog[2 * l + 1] = g_be * be * (1.0f - be);
+        } else if (attn_mode == 2) {
+            glog[2 * l] = (g_om + g_be) * om * (1.0f - om);
+            glog[2 * l + 1] = 0.0f;
+        } else {
+            glog[2 * l] = 0.0f;
+            glog[2 * l + 1] = 0.0f;
+        }
+        const float s0 = om * gf[0];
+        float sc[7];
+#pragma unroll
+        for (int ch = 0; ch < 7; ++ch) sc[ch] = be * gf[1 + ch];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const float cw = corner_w(wl, c);
+            float* gp = g_tables + (size_t)rows[c] * 8;
+            atomic_add4(gp, cw * s0, cw * sc[0], cw * sc[1], cw * sc[2]);
+            atomic_add4(gp + 4, cw * sc[3], cw * sc[4], cw * sc[5], cw * sc[6]);
+        }
+    }
+    // coarse vertices: [gf(8), logit grads(2L)] times the corner weight
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const float cw = corner_w(w, c);
+        float* gp = g_coarse + (size_t)cv[c] * NC;
+        if constexpr (NC % 4 == 0) {
+            atomic_add4(gp, cw * gf[0], cw * gf[1], cw * gf[2], cw * gf[3]);
+            atomic_add4(gp + 4, cw * gf[4], cw * gf[5], cw * gf[6], cw * gf[7]);
+#pragma unroll
+            for (int k = 0; k < 2 * L; k += 4)
+                atomic_add4(gp + 8 + k, cw * glog[k], cw * glog[k + 1], cw * glog[k + 2], cw * glog[k + 3]);
+        } else {
+#pragma unroll
+            for (int ch = 0; ch < 8; ++ch) atomicAdd(gp + ch, cw * gf[ch]);
+#pragma unroll
+            for (int k = 0; k < 2 * L; ++k) atomicAdd(gp + 8 + k, cw * glog[k]);
+        }
+    }
+}
+
+template <int L>
+struct BackwardSampler {
+    const Grid& g;
+    int attn_mode;
+    float t_term;
+    float T, S_le, S_tot;
+    float gCd[3], gF[4], gA, gD;
+    float* g_tables;
+    float* g_coarse;
+    float* gates;
+    __device__ __forceinline__ bool sample(const float u[3], float t, float delta) {
+        float f[8];
+        sample_features<L, NGPRT_F32>(g, u, attn_mode, f, gates, blockDim.x);
+        const float sigma = expf(f[0]);
+        const float trans = expf(-sigma * delta);
+        const float w = T * (1.0f - trans);
+        const float T_next = T * trans;
+        float qg = fmaf(gD, t, gA);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) qg = fmaf(gCd[k], f[1 + k], qg);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) qg = fmaf(gF[k], f[4 + k], qg);
+        S_le = fmaf(w, qg, S_le);
+        const float g_sigma = delta * (T_next * qg - (S_tot - S_le));
+        float gf[8];
+        gf[0] = g_sigma * expf(fminf(f[0], 15.0f));
+#pragma unroll
+        for (int k = 0; k < 3; ++k) gf[1 + k] = w * gCd[k];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) gf[4 + k] = w * gF[k];
+        scatter_features<L>(g, u, attn_mode, gf, g_tables, g_coarse);
+        T = T_next;
+        return T < t_term;
+    }
+};
+
+template <int L>
+__global__ void __launch_bounds__(128) march_backward_kernel(const __grid_constant__ MarchBwdParams p) {
+    extern __shared__ float gate_smem[];
+    int64_t ray;
+    float o[3], d[3], t, t_out;
+    bool hit;
+    if (!ray_setup(p.m, ray, o, d, t, t_out, hit)) return;
+    if (!hit) return;
+    const float4* c4 = reinterpret_cast<const float4*>(p.cot + ray * kCotFloats);
+    const float4 q0 = c4[0], q1 = c4[1], q2 = c4[2];
+    BackwardSampler<L> smp{p.m.g, p.m.opts.attn_mode, p.m.opts.t_term, 1.0f, 0.0f, q2.y,
+                           {q0.x, q0.y, q0.z}, {q0.w, q1.x, q1.y, q1.z}, q1.w, q2.x, p.g_tables, p.g_coarse,
+                           gate_smem + threadIdx.x};
+    int n_march = 0, n_samp = 0;
+    march_loop(p.m, o, d, t, t_out, smp, n_march, n_samp);
+}
+
+template <int L>
+void launch_bwd(const MarchBwdParams& p, dim3 grid, cudaStream_t st) {
+    march_backward_kernel<L><<<grid, 128, (size_t)2 * L * 128 * sizeof(float), st>>>(p);
+}
+
+}  // namespace
+
+int32_t make_grid(const ngprt_scene* s, Grid& g, const char* fn);
+int32_t make_occ(const ngprt_occ* o, OccView& v, const char* fn);
+int32_t check_opts(const ngprt_render_opts* o, const char* fn);
+int32_t setup_rays(MarchParams& p, const ngprt_camera* cams, int32_t n_cams, const int32_t* pixel_ids,
+                   const float* rays_o, const float* rays_d, int64_t n_rays, dim3& grid, const char* fn);
+bool march_supports(int L);
+bool mlp_supports(int width, int layers);
+
+}  // namespace ngprt
+
+using namespace ngprt;
+
+extern "C" int32_t ngprt_render_backward(const ngprt_scene* scene, const ngprt_occ* occ, const ngprt_camera* cams,
+                                         int32_t n_cams, const int32_t* pixel_ids, const float* rays_o,
+                                         const float* rays_d, int64_t n_rays, const ngprt_render_opts* opts,
+                                         const float* ray_state, const float* d_rgb, const float* d_depth,
+                                         const float* d_opacity, float* g_tables, float* g_coarse, float* g_mlp,
+                                         void* workspace, size_t ws_bytes, void* stream) {
+    const char* fn = "ngprt_render_backward";
+    MarchBwdParams p;
+    memset(&p, 0, sizeof p);
+    int32_t rc;
+    if ((rc = make_grid(scene, p.m.g, fn)) != NGPRT_OK) return rc;
+    if ((rc = make_occ(occ, p.m.occ, fn)) != NGPRT_OK) return rc;
+    if ((rc = check_opts(opts, fn)) != NGPRT_OK) return rc;
+    NGPRT_REQUIRE(n_rays >= 0, "%s: n_rays=%lld", fn, (long long)n_rays);
+    NGPRT_REQUIRE(scene->table_dtype == NGPRT_F32 && scene->mlp_dtype == NGPRT_F32,
+                  "%s: gradients need F32 tables and F32 MLP weights", fn);
+    if (!march_supports(scene->L) || !(scene->L == 1 || scene->L == 2 || scene->L == 4 || scene->L == 16)) {
+        set_error("%s: no backward kernel for L=%d (built: 1, 2, 4, 16)", fn, scene->L);
+        return NGPRT_ERR_UNSUPPORTED;
+    }
+    if (!mlp_supports(scene->mlp_width, scene->mlp_layers)) {
+        set_error("%s: MLP %d layers x %d not built", fn, scene->mlp_layers, scene->mlp_width);
+        return NGPRT_ERR_UNSUPPORTED;
+    }
+    dim3 grid;
+    if ((rc = setup_rays(p.m, cams, n_cams, pixel_ids, rays_o, rays_d, n_rays, grid, fn)) != NGPRT_OK) return rc;
+    if (n_rays == 0) return NGPRT_OK;
+    NGPRT_REQUIRE(ray_state && d_rgb && g_tables && g_coarse && g_mlp, "%s: NULL buffer", fn);
+    NGPRT_REQUIRE(((uintptr_t)g_tables & 15) == 0 && ((uintptr_t)g_coarse & 15) == 0 && ((uintptr_t)ray_state & 15) == 0,
+                  "%s: g_tables, g_coarse, ray_state must be 16-byte aligned", fn);
+    const size_t need = ngprt_render_workspace_bytes(scene, n_rays);
+    if (!workspace || ws_bytes < need) {
+        set_error("%s: workspace %zu bytes < %zu needed", fn, ws_bytes, need);
+        return NGPRT_ERR_WORKSPACE;
+    }
+    NGPRT_REQUIRE(((uintptr_t)workspace & 15) == 0, "%s: workspace must be 16-byte aligned", fn);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    float* cot = static_cast<float*>(workspace);
+    ShadeBwdParams s;
+    s.state = ray_state;
+    s.w = static_cast<const float*>(scene->mlp_w);
+    s.d_rgb = d_rgb;
+    s.d_depth = d_depth;
+    s.d_opacity = d_opacity;
+    s.bg[0] = opts->bg[0];
+    s.bg[1] = opts->bg[1];
+    s.bg[2] = opts->bg[2];
+    s.n = n_rays;
+    s.cot = cot;
+    s.g_mlp = g_mlp;
+    const unsigned sb = (unsigned)((n_rays + 127) / 128);
+    const int W = scene->mlp_width, Ly = scene->mlp_layers;
+    if (Ly == 2) {
+        if (W == 16) shade_backward_kernel<16, 2><<<sb, 128, 0, st>>>(s);
+        else if (W == 32) shade_backward_kernel<32, 2><<<sb, 128, 0, st>>>(s);
+        else shade_backward_kernel<64, 2><<<sb, 128, 0, st>>>(s);
+    } else {
+        if (W == 16) shade_backward_kernel<16, 3><<<sb, 128, 0, st>>>(s);
+        else if (W == 32) shade_backward_kernel<32, 3><<<sb, 128, 0, st>>>(s);
+        else shade_backward_kernel<64, 3><<<sb, 128, 0, st>>>(s);
+    }
+    p.m.opts = *opts;
+    p.m.t_interval = nullptr;
+    p.state = ray_state;
+    p.cot = cot;
+    p.g_tables = g_tables;
+    p.g_coarse = g_coarse;
+    switch (scene->L) {
+        case 1: launch_bwd<1>(p, grid, st); break;
+        case 2: launch_bwd<2>(p, grid, st); break;
+        case 4: launch_bwd<4>(p, grid, st); break;
+        default: launch_bwd<16>(p, grid, st); break;
+    }
+    return cuda_status(fn);
+}

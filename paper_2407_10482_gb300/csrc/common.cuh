@@ -1,0 +1,266 @@
+// common.cuh -- device helpers shared by the NGP-RT kernels (sm_103a).
+//
+// The march is an FP32 recurrence whose results are integers (which voxel is
+// tested, which point is sampled).  Every operation of it goes through the
+// explicitly rounded intrinsics below, so that no multiply-add is fused and each
+// result is the IEEE round-to-nearest value: the decisions are then a fixed
+// function of the inputs.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ngprt.h"
+
+namespace ngprt {
+
+constexpr int kMaxL = NGPRT_MAX_LEVELS;
+constexpr int kMaxOccLevels = 16;
+constexpr int kMlpIn = 32;
+constexpr int kNFeat = 8;
+
+// ------------------------------------------------------------ host-side errors
+void set_error(const char* fmt, ...);
+int32_t cuda_status(const char* what);   // NGPRT_OK or NGPRT_ERR_CUDA with message
+
+#define NGPRT_REQUIRE(cond, ...)                    \
+    do {                                            \
+        if (!(cond)) {                              \
+            ::ngprt::set_error(__VA_ARGS__);        \
+            return NGPRT_ERR_INVALID_ARG;           \
+        }                                           \
+    } while (0)
+
+// ------------------------------------------------------- kernel-side scene view
+struct Grid {
+    const void* tables;
+    const void* coarse;
+    uint32_t level_off[kMaxL];   // first row of each level
+    int32_t N[kMaxL];
+    uint32_t dense_mask;         // bit l: level l is dense
+    uint32_t T_mask;             // 2^T_log2 - 1
+    int32_t L;
+    int32_t R_C;
+    int32_t bounded;
+};
+
+struct OccView {
+    const uint32_t* bits;
+    const uint8_t* dist;
+    uint32_t word_off[kMaxOccLevels];  // first word of each pyramid level
+    int32_t R_O;
+    int32_t n_levels;
+};
+
+// ------------------------------------------------- exactly rounded FP32 helpers
+__device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ float fsqrt(float a) { return __fsqrt_rn(a); }
+
+// Pinhole ray through the centre of pixel (col, row); OpenCV axes.
+__device__ __forceinline__ void camera_ray(const ngprt_camera& c, int col, int row, float o[3], float d[3]) {
+    float px = fdiv(fsub(fadd((float)col, 0.5f), c.cx), c.fx);
+    float py = fdiv(fsub(fadd((float)row, 0.5f), c.cy), c.fy);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        d[r] = fadd(fadd(fmul(c.c2w[4 * r + 0], px), fmul(c.c2w[4 * r + 1], py)), c.c2w[4 * r + 2]);
+        o[r] = c.c2w[4 * r + 3];
+    }
+}
+
+__device__ __forceinline__ float dot3(const float a[3], const float b[3]) {
+    return fadd(fadd(fmul(a[0], b[0]), fmul(a[1], b[1])), fmul(a[2], b[2]));
+}
+
+// Normalise d and find the parametric interval [t, t_out) inside the domain
+// (bounded: the box [-1,1]^3; unbounded: the world ball of radius r_far), then
+// clip it to [t_min, inf) and to the optional interval [t_lo, t_hi].
+__device__ __forceinline__ bool ray_interval(int bounded, const float o[3], float d[3], float t_min, float r_far,
+                                             float t_lo, float t_hi, float& t, float& t_out) {
+    float nn = fsqrt(dot3(d, d));
+    d[0] = fdiv(d[0], nn);
+    d[1] = fdiv(d[1], nn);
+    d[2] = fdiv(d[2], nn);
+    float t_in;
+    if (bounded) {
+        float lo[3], hi[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            float ia = fdiv(1.0f, d[a]);
+            float t0 = fmul(fsub(-1.0f, o[a]), ia), t1 = fmul(fsub(1.0f, o[a]), ia);
+            lo[a] = fminf(t0, t1);
+            hi[a] = fmaxf(t0, t1);
+        }
+        t_in = fmaxf(fmaxf(lo[0], lo[1]), lo[2]);
+        t_out = fminf(fminf(hi[0], hi[1]), hi[2]);
+    } else {
+        float b = dot3(o, d);
+        float c = fsub(dot3(o, o), fmul(r_far, r_far));
+        float disc = fsub(fmul(b, b), c);
+        if (!(disc >= 0.0f)) return false;
+        float sq = fsqrt(disc);
+        t_in = fsub(-b, sq);
+        t_out = fadd(-b, sq);
+    }
+    t = fmaxf(t_in, t_min);
+    t = fmaxf(t, t_lo);
+    t_out = fminf(t_out, t_hi);
+    return t < t_out;
+}
+
+// Position at t: world x, contracted y (mip-NeRF 360 when unbounded), unit-cube u.
+__device__ __forceinline__ void march_point(int bounded, const float o[3], const float d[3], float t, float x[3],
+                                            float y[3], float u[3], float& r) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) x[a] = fadd(o[a], fmul(t, d[a]));
+    r = fsqrt(dot3(x, x));
+    if (!bounded && r > 1.0f) {
+        float k = fdiv(fsub(2.0f, fdiv(1.0f, r)), r);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) y[a] = fmul(x[a], k);
+    } else {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) y[a] = x[a];
+    }
+    const float B = bounded ? 1.0f : 2.0f, hB = bounded ? 0.5f : 0.25f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) u[a] = fmul(fadd(y[a], B), hB);
+}
+
+__device__ __forceinline__ int occ_vox(float u, int Rk) {
+    float c = floorf(fmul(u, (float)Rk));
+    c = fminf(fmaxf(c, 0.0f), (float)(Rk - 1));
+    return (int)c;
+}
+
+// Grid cell of a vertex grid of N per axis: base chosen in FP32, clamped to
+// [0, N-2]; the weight w = u (N-1) - base carries the product's rounding error
+// back in (an exact FMA residual) so it is accurate to ~1 ulp of w.
+__device__ __forceinline__ void grid_cell(float u, int N, int& base, float& w) {
+    const float nm1 = (float)(N - 1);
+    float pf = fmul(u, nm1);
+    float bf = floorf(pf);
+    bf = fminf(fmaxf(bf, 0.0f), (float)(N - 2));
+    base = (int)bf;
+    w = fadd(fsub(pf, bf), __fmaf_rn(u, nm1, -pf));
+}
+
+// Absolute table row of vertex (x, y, z) of level l: dense row-major or the
+// Instant-NGP spatial hash.
+__device__ __forceinline__ uint32_t level_row(const Grid& g, int l, uint32_t x, uint32_t y, uint32_t z) {
+    uint32_t idx;
+    if ((g.dense_mask >> l) & 1u) {
+        const uint32_t n = (uint32_t)g.N[l];
+        idx = x + n * (y + n * z);
+    } else {
+        idx = (x ^ (y * 2654435761u) ^ (z * 805459861u)) & g.T_mask;
+    }
+    return g.level_off[l] + idx;
+}
+
+// ------------------------------------------------------------ vector loads
+// One 8-channel table entry, read-only path.  F32: a single 256-bit load (entries
+// are 32-byte aligned); F16/BF16: a single 128-bit load.
+template <int DT>
+__device__ __forceinline__ void load_entry(const void* base, uint32_t row, float v[8]);
+
+template <>
+__device__ __forceinline__ void load_entry<NGPRT_F32>(const void* base, uint32_t row, float v[8]) {
+    const float* p = static_cast<const float*>(base) + (size_t)row * 8;
+    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+                 : "l"(p));
+}
+
+template <>
+__device__ __forceinline__ void load_entry<NGPRT_F16>(const void* base, uint32_t row, float v[8]) {
+    const uint4 q = __ldg(static_cast<const uint4*>(base) + row);
+    const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        __half2 h = *reinterpret_cast<const __half2*>(&w[k]);
+        float2 f = __half22float2(h);
+        v[2 * k] = f.x;
+        v[2 * k + 1] = f.y;
+    }
+}
+
+template <>
+__device__ __forceinline__ void load_entry<NGPRT_BF16>(const void* base, uint32_t row, float v[8]) {
+    const uint4 q = __ldg(static_cast<const uint4*>(base) + row);
+    const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162*>(&w[k]);
+        float2 f = __bfloat1622float2(h);
+        v[2 * k] = f.x;
+        v[2 * k + 1] = f.y;
+    }
+}
+
+// Read NC consecutive channels (NC even) of one coarse-grid vertex.
+template <int DT, int NC>
+__device__ __forceinline__ void load_channels(const void* base, uint32_t vertex, float v[NC]) {
+    if constexpr (DT == NGPRT_F32) {
+        const float* p = static_cast<const float*>(base) + (size_t)vertex * NC;
+        if constexpr (NC % 4 == 0) {
+#pragma unroll
+            for (int k = 0; k < NC / 4; ++k) {
+                float4 q = __ldg(reinterpret_cast<const float4*>(p) + k);
+                v[4 * k] = q.x; v[4 * k + 1] = q.y; v[4 * k + 2] = q.z; v[4 * k + 3] = q.w;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < NC / 2; ++k) {
+                float2 q = __ldg(reinterpret_cast<const float2*>(p) + k);
+                v[2 * k] = q.x; v[2 * k + 1] = q.y;
+            }
+        }
+    } else {
+        const uint16_t* p = static_cast<const uint16_t*>(base) + (size_t)vertex * NC;
+        const uint32_t* p32 = reinterpret_cast<const uint32_t*>(p);  // NC even: 4-byte aligned
+#pragma unroll
+        for (int k = 0; k < NC / 2; ++k) {
+            uint32_t w = __ldg(p32 + k);
+            float2 f;
+            if constexpr (DT == NGPRT_F16) f = __half22float2(*reinterpret_cast<const __half2*>(&w));
+            else f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w));
+            v[2 * k] = f.x;
+            v[2 * k + 1] = f.y;
+        }
+    }
+}
+
+__device__ __forceinline__ float sigmoidf_(float x) { return 1.0f / (1.0f + expf(-x)); }
+
+// Attention gate sigma(x) = 1 / (1 + e^-x) with the hardware exponential and
+// reciprocal (relative error ~1e-6; the gates only scale feature values).
+__device__ __forceinline__ float gate_sigmoid(float x) { return __frcp_rn(1.0f + __expf(-x)); }
+
+// Real spherical harmonics, bands 0..3, order l^2 + l + m, no Condon-Shortley
+// phase, orthonormal on the sphere (Cartesian polynomial form).
+__device__ __forceinline__ void sh16(float x, float y, float z, float out[16]) {
+    const float xx = x * x, yy = y * y, zz = z * z;
+    out[0] = 0.28209479177387814f;
+    out[1] = 0.48860251190291992f * y;
+    out[2] = 0.48860251190291992f * z;
+    out[3] = 0.48860251190291992f * x;
+    out[4] = 1.09254843059207907f * x * y;
+    out[5] = 1.09254843059207907f * y * z;
+    out[6] = 0.31539156525252001f * (3.0f * zz - 1.0f);
+    out[7] = 1.09254843059207907f * x * z;
+    out[8] = 0.54627421529603953f * (xx - yy);
+    out[9] = 0.59004358992664352f * y * (3.0f * xx - yy);
+    out[10] = 2.89061144264055406f * x * y * z;
+    out[11] = 0.45704579946446573f * y * (5.0f * zz - 1.0f);
+    out[12] = 0.37317633259011540f * z * (5.0f * zz - 3.0f);
+    out[13] = 0.45704579946446573f * x * (5.0f * zz - 1.0f);
+    out[14] = 1.44530572132027735f * z * (xx - yy);
+    out[15] = 0.59004358992664352f * x * (xx - 3.0f * yy);
+}
+
+}  // namespace ngprt

@@ -1,0 +1,307 @@
+// march.cuh -- the ray march shared by the forward render and its reverse pass.
+//
+// march_loop() walks one ray: coarse-to-fine occupancy test at each marching point,
+// the empty-space step s_O or the distance step v*G (Eq. 9; Sec. 3.3), and at each
+// occupied point a call to the sampler, which composites (forward) or scatters
+// gradients (backward) and reports early termination (Sec. S2.5).  Both passes run
+// this one function, so they visit the same samples.
+#pragma once
+
+#include <math.h>
+
+#include "common.cuh"
+
+// Occupancy hint for the march kernel (blocks of 128 threads per SM the register
+// allocation must allow) and the warp's pixel tile (TILE_W x 32/TILE_W).
+#ifndef NGPRT_MARCH_MIN_BLOCKS
+#define NGPRT_MARCH_MIN_BLOCKS 4
+#endif
+#ifndef NGPRT_TILE_W
+#define NGPRT_TILE_W 4
+#endif
+
+namespace ngprt {
+
+constexpr int kTileW = NGPRT_TILE_W;
+constexpr int kTileH = 32 / NGPRT_TILE_W;
+
+struct Cams {
+    ngprt_camera c[NGPRT_MAX_CAMERAS];
+};
+
+struct MarchParams {
+    Grid g;
+    OccView occ;
+    ngprt_render_opts opts;
+    Cams cams;
+    int32_t mode;  // 0: camera pixels in warp tiles, 1: camera pixel ids, 2: explicit rays
+    int32_t n_cams, W, H, tiles_x, tiles_per_view;
+    const int32_t* pixel_ids;
+    const float* rays_o;
+    const float* rays_d;
+    const float* t_interval;
+    int64_t n_rays;
+    float* state;
+    int32_t* stats;
+    const float* fb_a_hat;  // fallback pass: predicted opacity per ray (NULL otherwise)
+    float fb_thr;           // re-march a ray when a_hat - A(interval) > fb_thr
+};
+
+// Ray of this thread (false if the lane has none).
+__device__ __forceinline__ bool thread_ray(const MarchParams& p, int64_t& ray, float o[3], float d[3]) {
+    if (p.mode == 0) {
+        const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+        const int lane = threadIdx.x & 31;
+        const int64_t view = warp / p.tiles_per_view;
+        if (view >= p.n_cams) return false;
+        const int tile = (int)(warp - view * p.tiles_per_view);
+        const int col = (tile % p.tiles_x) * kTileW + (lane % kTileW);
+        const int row = (tile / p.tiles_x) * kTileH + (lane / kTileW);
+        if (col >= p.W || row >= p.H) return false;
+        ray = view * (int64_t)p.W * p.H + (int64_t)row * p.W + col;
+        camera_ray(p.cams.c[view], col, row, o, d);
+        return true;
+    }
+    ray = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (ray >= p.n_rays) return false;
+    if (p.mode == 1) {
+        int64_t id = p.pixel_ids[ray];
+        if (id < 0) id = 0;
+        const int64_t wh = (int64_t)p.W * p.H;
+        int64_t view = id / wh;
+        if (view >= p.n_cams) view = p.n_cams - 1;
+        const int64_t rem = id - (id / wh) * wh;
+        camera_ray(p.cams.c[view], (int)(rem % p.W), (int)(rem / p.W), o, d);
+    } else {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            o[a] = p.rays_o[3 * ray + a];
+            d[a] = p.rays_d[3 * ray + a];
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ float corner_w(const float w[3], int c) {
+    const float wx = (c & 1) ? w[0] : 1.0f - w[0];
+    const float wy = (c & 2) ? w[1] : 1.0f - w[1];
+    const float wz = (c & 4) ? w[2] : 1.0f - w[2];
+    return wx * wy * wz;
+}
+
+// Packed FP32 multiply-add on a pair of lanes (Blackwell fma.rn.f32x2): each
+// half is exactly fmaf(a, b, c), so the result equals the scalar form bit for bit.
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+    unsigned long long A, Bv, Cv, D;
+    A = *reinterpret_cast<unsigned long long*>(&a);
+    Bv = *reinterpret_cast<unsigned long long*>(&b);
+    Cv = *reinterpret_cast<unsigned long long*>(&c);
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(D) : "l"(A), "l"(Bv), "l"(Cv));
+    return *reinterpret_cast<float2*>(&D);
+}
+
+#ifndef NGPRT_LEVEL_UNROLL
+#define NGPRT_LEVEL_UNROLL 2
+#endif
+constexpr int kLevelUnroll = NGPRT_LEVEL_UNROLL;
+
+// Eq. 6-8 at unit-cube position u: f = f~ + Att(f^1..f^L; a).  The coarse fetch
+// interpolates the 8 + 2L channels of the coarse grid; the 2L attention gates
+// (sigmoid of the interpolated logits) are parked in shared memory, gates[k*stride],
+// so that the level loop need not be unrolled.
+template <int L, int DT>
+__device__ __forceinline__ void sample_features(const Grid& g, const float u[3], int attn_mode, float f[8],
+                                                float* gates, int stride) {
+    constexpr int NC = kNFeat + 2 * L;
+    int b[3];
+    float w[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) grid_cell(u[a], g.R_C, b[a], w[a]);
+    float2 acc[NC / 2];
+#pragma unroll
+    for (int ch = 0; ch < NC / 2; ++ch) acc[ch] = make_float2(0.0f, 0.0f);
+    const uint32_t R = (uint32_t)g.R_C;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const uint32_t v = (uint32_t)(b[0] + (c & 1)) + R * ((uint32_t)(b[1] + ((c >> 1) & 1)) + R * (uint32_t)(b[2] + ((c >> 2) & 1)));
+        float val[NC];
+        load_channels<DT, NC>(g.coarse, v, val);
+        const float cw = corner_w(w, c);
+        const float2 cw2 = make_float2(cw, cw);
+#pragma unroll
+        for (int ch = 0; ch < NC / 2; ++ch) acc[ch] = ffma2(cw2, make_float2(val[2 * ch], val[2 * ch + 1]), acc[ch]);
+    }
+#pragma unroll
+    for (int ch = 0; ch < kNFeat / 2; ++ch) {
+        f[2 * ch] = acc[ch].x;
+        f[2 * ch + 1] = acc[ch].y;
+    }
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+        float om, be;
+        const float2 lg = acc[kNFeat / 2 + l];
+        if (attn_mode == 1) {
+            om = 1.0f;
+            be = 1.0f;
+        } else if (attn_mode == 2) {
+            om = gate_sigmoid(lg.x);
+            be = om;
+        } else {
+            om = gate_sigmoid(lg.x);
+            be = gate_sigmoid(lg.y);
+        }
+        gates[(2 * l) * stride] = om;
+        gates[(2 * l + 1) * stride] = be;
+    }
+#pragma unroll kLevelUnroll
+    for (int l = 0; l < L; ++l) {
+        int bl[3];
+        float wl[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) grid_cell(u[a], g.N[l], bl[a], wl[a]);
+        uint32_t rows[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+            rows[c] = level_row(g, l, (uint32_t)(bl[0] + (c & 1)), (uint32_t)(bl[1] + ((c >> 1) & 1)),
+                                (uint32_t)(bl[2] + ((c >> 2) & 1)));
+        float e[8][8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) load_entry<DT>(g.tables, rows[c], e[c]);
+        float2 fl[4];
+#pragma unroll
+        for (int ch = 0; ch < 4; ++ch) fl[ch] = make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const float cw = corner_w(wl, c);
+            const float2 cw2 = make_float2(cw, cw);
+#pragma unroll
+            for (int ch = 0; ch < 4; ++ch) fl[ch] = ffma2(cw2, make_float2(e[c][2 * ch], e[c][2 * ch + 1]), fl[ch]);
+        }
+        const float om = gates[(2 * l) * stride], be = gates[(2 * l + 1) * stride];
+        f[0] = fmaf(om, fl[0].x, f[0]);
+        f[1] = fmaf(be, fl[0].y, f[1]);
+#pragma unroll
+        for (int ch = 1; ch < 4; ++ch) {
+            f[2 * ch] = fmaf(be, fl[ch].x, f[2 * ch]);
+            f[2 * ch + 1] = fmaf(be, fl[ch].y, f[2 * ch + 1]);
+        }
+    }
+}
+
+// Walk one ray from t to t_out; smp.sample(u, t, delta) is called at every
+// occupied marching point and returns true when the ray terminates.
+template <class Sampler>
+__device__ __forceinline__ void march_loop(const MarchParams& p, const float o[3], const float d[3], float t,
+                                           float t_out, Sampler& smp, int& n_march, int& n_samp) {
+    const ngprt_render_opts& op = p.opts;
+    const int bounded = p.g.bounded;
+    const float B = bounded ? 1.0f : 2.0f;
+    const float dt0 = fmul(op.step_base, op.step_gamma);
+    const int R_O = p.occ.R_O;
+    const float vG = fdiv(2.0f * B, (float)R_O);
+    const float t_start = t;
+    int lat_k = 0;
+    const bool snap = op.lattice_snap && bounded;
+    while (true) {
+        // phase 1: advance through empty space to the next occupied marching point
+        bool found = false;
+        float u[3], delta = 0.0f, dt = 0.0f;
+        while (t < t_out && n_march < op.max_march && n_samp < op.max_samples) {
+            ++n_march;
+            float x[3], y[3], r;
+            march_point(bounded, o, d, t, x, y, u, r);
+            int empty_level = -1, ev[3] = {0, 0, 0};
+            for (int k = p.occ.n_levels - 1; k >= 0; --k) {
+                const int Rk = R_O >> k;
+                const int c0 = occ_vox(u[0], Rk), c1 = occ_vox(u[1], Rk), c2 = occ_vox(u[2], Rk);
+                const uint32_t bi = (uint32_t)c0 + (uint32_t)Rk * ((uint32_t)c1 + (uint32_t)Rk * (uint32_t)c2);
+                const uint32_t word = __ldg(p.occ.bits + p.occ.word_off[k] + (bi >> 5));
+                if (!((word >> (bi & 31)) & 1u)) {
+                    empty_level = k;
+                    ev[0] = c0; ev[1] = c1; ev[2] = c2;
+                    break;
+                }
+            }
+            if (empty_level < 0) {
+                dt = bounded ? dt0 : fmul(dt0, fmaxf(1.0f, r));
+                delta = fminf(dt, fsub(t_out, t));
+                found = true;
+                break;
+            }
+            // s_O: leave the empty voxel along the ray's direction in grid space
+            const int Rk = R_O >> empty_level;
+            const float vk = fdiv(2.0f * B, (float)Rk);
+            float v[3];
+            if (bounded || !(r > 1.0f)) {
+                v[0] = d[0]; v[1] = d[1]; v[2] = d[2];
+            } else {
+                const float kk = fdiv(fsub(2.0f, fdiv(1.0f, r)), r);
+                const float px = dot3(x, d);
+                const float r2 = fmul(r, r);
+                const float m = fdiv(fmul(px, fmul(2.0f, fsub(1.0f, r))), fmul(r2, r2));
+#pragma unroll
+                for (int a = 0; a < 3; ++a) v[a] = fadd(fmul(kk, d[a]), fmul(m, x[a]));
+            }
+            float se = INFINITY;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const float lo = fsub(fmul((float)ev[a], vk), B);
+                const float hi = fadd(lo, vk);
+                float ta = INFINITY;
+                if (v[a] > 0.0f) ta = fdiv(fsub(hi, y[a]), v[a]);
+                else if (v[a] < 0.0f) ta = fdiv(fsub(lo, y[a]), v[a]);
+                se = fminf(se, ta);
+            }
+            const float s_O = fadd(fmaxf(se, 0.0f), fmul(1e-5f, fmaxf(1.0f, t)));
+            float step = s_O;
+            if (op.use_dist && p.occ.dist && empty_level >= 1) {
+                const int g0 = occ_vox(u[0], R_O), g1 = occ_vox(u[1], R_O), g2 = occ_vox(u[2], R_O);
+                const int gv = __ldg(p.occ.dist + ((size_t)g0 + (size_t)R_O * ((size_t)g1 + (size_t)R_O * g2)));
+                if (gv > 0) {
+                    const float rho = fmul((float)gv, vG);
+                    float sg = rho;
+                    if (!bounded && r > 1.0f) {
+                        const float r1 = fadd(r, 1.0f);
+                        const float a = fdiv(fmul(fmul(r1, r1), rho), fmul(4.0f, r));
+                        const float cap = fmul(fsub(r, 1.0f), 0.5f);
+                        sg = fmaxf(rho, fminf(a, cap));
+                    }
+                    step = op.dist_rule == 1 ? fmaxf(sg, s_O) : sg;
+                }
+            }
+            if (snap) {
+                const int kk = (int)floorf(fdiv(fsub(fadd(t, step), t_start), dt0));
+                lat_k = kk > lat_k + 1 ? kk : lat_k + 1;
+                t = fadd(t_start, fmul((float)lat_k, dt0));
+            } else {
+                t = fadd(t, step);
+            }
+        }
+        if (!found) break;
+        // phase 2: the lanes holding a sample gather and composite it together
+        const bool stop = smp.sample(u, t, delta);
+        ++n_samp;
+        if (stop) break;
+        if (snap) {
+            lat_k += 1;
+            t = fadd(t_start, fmul((float)lat_k, dt0));
+        } else {
+            t = fadd(t, dt);
+        }
+    }
+}
+
+// Ray set-up shared by both passes: this thread's ray, its domain interval.
+__device__ __forceinline__ bool ray_setup(const MarchParams& p, int64_t& ray, float o[3], float d[3], float& t,
+                                          float& t_out, bool& hit) {
+    if (!thread_ray(p, ray, o, d)) return false;
+    float t_lo = -INFINITY, t_hi = INFINITY;
+    if (p.t_interval && !p.fb_a_hat) {
+        t_lo = p.t_interval[2 * ray];
+        t_hi = p.t_interval[2 * ray + 1];
+    }
+    hit = ray_interval(p.g.bounded, o, d, p.opts.t_min, p.opts.r_far, t_lo, t_hi, t, t_out);
+    return true;
+}
+
+}  // namespace ngprt

@@ -1,0 +1,91 @@
+"""GPU reverse pass against the oracle's reverse pass (itself pinned by central
+finite differences), through the C ABI and through torch.autograd.
+
+FP32 atomics against FP64: per tensor, |g_gpu - g_oracle| <= 1e-3 |g_oracle| +
+3e-5 max|g_oracle|.  Termination is kept away from the threshold (t_term = 0) so
+that both sides sum the same samples."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as O
+from paper_2407_10482_gb300 import scenes as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ng():
+    from paper_2407_10482_gb300 import ngprt
+    ngprt.lib()
+    return ngprt
+
+
+def _close(name, g, ref):
+    g = np.asarray(g, np.float64).reshape(-1)
+    ref = np.asarray(ref, np.float64).reshape(-1)
+    scale = np.abs(ref).max()
+    assert scale > 0, name
+    bad = np.abs(g - ref) > 1e-3 * np.abs(ref) + 3e-5 * scale
+    assert not bad.any(), f"{name}: {bad.sum()} of {bad.size} differ, worst {np.abs(g - ref).max():.3g} / {scale:.3g}"
+
+
+def _run(ng, cfg, opts, n_rays=2000, seed=3, sc=None):
+    sc = sc or S.make_scene(cfg)
+    sc.coarse[:, 8:] *= 10.0
+    ds = ng.DeviceScene(cfg, sc.tables, sc.coarse, sc.mlp_w)
+    docc = ng.DeviceOcc(sc.occ, cfg.R_O, cfg.n_occ_levels)
+    rend = ng.Renderer(ds, docc)
+    o, d = S.random_rays(n_rays, seed, cfg.bounded)
+    rng = np.random.default_rng(seed + 1)
+    d_rgb = rng.normal(size=(n_rays, 3)).astype(np.float32)
+    d_dep = (0.3 * rng.normal(size=n_rays)).astype(np.float32)
+    d_op = rng.normal(size=n_rays).astype(np.float32)
+    rays = dict(rays_o=torch.as_tensor(o).cuda(), rays_d=torch.as_tensor(d).cuda())
+    out = rend.render(opts, state=True, **rays)
+    g_t = torch.zeros_like(ds.tables)
+    g_c = torch.zeros_like(ds.coarse)
+    g_m = torch.zeros_like(ds.mlp_w)
+    rend.backward(opts, out["state"], torch.as_tensor(d_rgb).cuda(), torch.as_tensor(d_dep).cuda(),
+                  torch.as_tensor(d_op).cuda(), g_t, g_c, g_m, **rays)
+    torch.cuda.synchronize()
+    orc = O.oracle_for_scene(sc)
+    ref = orc.render_backward(opts, d_rgb=d_rgb, d_depth=d_dep, d_opacity=d_op, rays_o=o, rays_d=d)
+    _close("tables", g_t.cpu().numpy(), ref["tables"])
+    _close("coarse", g_c.cpu().numpy(), ref["coarse"])
+    _close("mlp_w", g_m.cpu().numpy(), ref["mlp_w"])
+    return ds, rend, rays, (d_rgb, d_dep, d_op), (g_t, g_c, g_m)
+
+
+@pytest.mark.parametrize("attn_mode", [0, 1, 2])
+def test_backward_small_bounded(ng, attn_mode):
+    cfg = S.small_config(blob_std=(0.05, 0.15))
+    _run(ng, cfg, S.default_options(cfg, t_term=0.0, attn_mode=attn_mode))
+
+
+def test_backward_unbounded_wide_mlp(ng):
+    cfg = S.small_config(bounded=False, R_O=32, n_occ_levels=4, t_min=0.05, r_far=16.0, shell=True, mlp_layers=3,
+                         mlp_width=64, step_base=2 * 3 ** 0.5 / 256, blob_std=(0.05, 0.15))
+    _run(ng, cfg, S.default_options(cfg, t_term=0.0), n_rays=1500)
+
+
+def test_backward_hd_levels(ng):
+    """The hd workload's 16 levels (5 dense, 11 hashed, T = 2^19), 3-layer MLP."""
+    cfg = S.hd_config(density_bias=0.5)
+    _run(ng, cfg, S.default_options(cfg, t_term=0.0, max_samples=64), n_rays=512)
+
+
+def test_autograd_function_matches_direct_call(ng):
+    cfg = S.small_config(blob_std=(0.05, 0.15))
+    opts = S.default_options(cfg, t_term=0.0)
+    ds, rend, rays, cot, grads = _run(ng, cfg, opts)
+    t = ds.tables.requires_grad_(True)
+    c = ds.coarse.requires_grad_(True)
+    m = ds.mlp_w.requires_grad_(True)
+    rgb, dep, opa = ng.RenderFunction.apply(t, c, m, rend, opts, rays)
+    loss = (rgb * torch.as_tensor(cot[0]).cuda()).sum() + (dep * torch.as_tensor(cot[1]).cuda()).sum() + \
+        (opa * torch.as_tensor(cot[2]).cuda()).sum()
+    loss.backward()
+    for a, b in zip((t.grad, c.grad, m.grad), grads):
+        np.testing.assert_allclose(a.cpu().numpy(), b.cpu().numpy(), rtol=1e-4, atol=1e-6)
