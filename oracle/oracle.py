@@ -247,10 +247,12 @@ class Oracle:
         g_c = np.zeros_like(self.coarse)
         g_m = np.zeros_like(self.mlp_w)
         op = self._opts(opts)
+        # hold the converted cotangents in locals: a temporary freed before the call
+        # would hand the C code a dangling pointer
+        cr, cd, co = _c(d_rgb, np.float64), _c(d_depth, np.float64), _c(d_opacity, np.float64)
         lib().or_render_backward(C.byref(self._s), C.byref(self._o), C.byref(op), _p(cams),
                                  C.c_int(0 if cams is None else len(cams)), C.c_int(W), C.c_int(H),
-                                 _p(pix), _p(ro), _p(rd), C.c_int(n), _p(_c(d_rgb, np.float64)),
-                                 _p(_c(d_depth, np.float64)), _p(_c(d_opacity, np.float64)),
+                                 _p(pix), _p(ro), _p(rd), C.c_int(n), _p(cr), _p(cd), _p(co),
                                  _p(g_t), _p(g_c), _p(g_m))
         return dict(tables=g_t, coarse=g_c, mlp_w=g_m)
 
@@ -260,11 +262,11 @@ class Oracle:
         H = H or self.cfg.H
         cams, pix, ro, rd, n = self._rays(cams, pix, rays_o, rays_d)
         op = self._opts(opts)
+        cr, cd, co = _c(d_rgb, np.float64), _c(d_depth, np.float64), _c(d_opacity, np.float64)
         return float(lib().or_render_dot(
             C.byref(self._s), C.byref(self._o), C.byref(op), _p(cams),
             C.c_int(0 if cams is None else len(cams)), C.c_int(W), C.c_int(H), _p(pix), _p(ro), _p(rd),
-            C.c_int(n), _p(_c(d_rgb, np.float64)), _p(_c(d_depth, np.float64)),
-            _p(_c(d_opacity, np.float64))))
+            C.c_int(n), _p(cr), _p(cd), _p(co)))
 
     def ray_samples(self, opts, o, d, cap=4096) -> np.ndarray:
         """Per-sample records [n, 7] = t, delta, u(3), sigma, weight of one ray."""

@@ -91,7 +91,14 @@ __device__ __forceinline__ float corner_w(const float w[3], int c) {
 
 // Packed FP32 multiply-add on a pair of lanes (Blackwell fma.rn.f32x2): each
 // half is exactly fmaf(a, b, c), so the result equals the scalar form bit for bit.
+#ifndef NGPRT_FFMA2
+#define NGPRT_FFMA2 1
+#endif
+
 __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+#if !NGPRT_FFMA2
+    return make_float2(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y));
+#endif
     unsigned long long A, Bv, Cv, D;
     A = *reinterpret_cast<unsigned long long*>(&a);
     Bv = *reinterpret_cast<unsigned long long*>(&b);

@@ -1,0 +1,85 @@
+"""Host-side checks of the C ABI, no GPU needed: libngprt.so builds and loads, it
+exports every function include/ngprt.h declares, size queries match the layout
+rules, and argument errors return status codes before anything is launched."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_2407_10482_gb300 import build as B
+from paper_2407_10482_gb300 import scenes as S
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "ngprt.h")
+
+
+@pytest.fixture(scope="module")
+def ng():
+    B.build()
+    from paper_2407_10482_gb300 import ngprt
+    ngprt.lib()
+    return ngprt
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ngprt_\w+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(ng):
+    names = declared_functions()
+    assert len(names) >= 15
+    h = C.CDLL(ng.lib_path())
+    missing = [n for n in names if not hasattr(h, n)]
+    assert not missing, missing
+    assert set(names) <= set(ng._SIGS), "binding lacks a signature"
+
+
+def test_size_queries(ng):
+    assert ng.ngprt_occ_bits_words(128, 5) == (128 ** 3 + 64 ** 3 + 32 ** 3 + 16 ** 3 + 8 ** 3) // 32
+    assert ng.ngprt_occ_bits_words(2, 2) == 2  # 8 bits -> 1 word, 1 bit -> 1 word
+    cfg = S.hd_config()
+    s = ng.ngprt_scene()
+    s.L, s.T_log2 = cfg.L, cfg.T_log2
+    for i, n in enumerate(cfg.N):
+        s.N[i] = n
+    assert ng.ngprt_table_entries(s) == S.table_entries(cfg) == 6272960
+    assert ng.ngprt_render_workspace_bytes(s, 1000) >= 1000 * ng.STATE_FLOATS * 4
+    assert ng.ngprt_proposal_param_count() == 1379
+    assert ng.lib().ngprt_version() == 100
+
+
+def test_argument_errors_are_reported_without_a_launch(ng):
+    lib = ng.lib()
+    rc = lib.ngprt_render(None, None, None, 0, None, None, None, 10, None, None, None, None, None, None, None,
+                          None, 0, None)
+    assert rc == ng.ERR_INVALID_ARG
+    assert b"scene is NULL" in lib.ngprt_last_error()
+    # R not a power of two
+    rc = lib.ngprt_build_occ_dist(C.c_void_p(256), 12, 2, C.c_void_p(256), None, None, 0, None)
+    assert rc == ng.ERR_INVALID_ARG and b"power of two" in lib.ngprt_last_error()
+    # an L without a kernel
+    cfg = S.small_config()
+    s = ng.ngprt_scene()
+    s.L, s.T_log2, s.R_C, s.mlp_layers, s.mlp_width = 5, 12, 16, 2, 16
+    for i in range(5):
+        s.N[i] = 16
+    s.tables = s.coarse = s.mlp_w = 256
+    o = ng.ngprt_occ(32, 3, 256, None)
+    opts = ng.render_opts(S.default_options(cfg))
+    rc = lib.ngprt_render(C.byref(s), C.byref(o), None, 0, None, C.c_void_p(256), C.c_void_p(256), 4, None,
+                          C.byref(opts), C.c_void_p(256), None, None, None, None, None, 0, None)
+    assert rc == ng.ERR_INVALID_ARG and b"L=5" in lib.ngprt_last_error()
+    # misaligned F32 tables
+    s.L = 4
+    s.tables = 256 + 16
+    rc = lib.ngprt_render(C.byref(s), C.byref(o), None, 0, None, C.c_void_p(256), C.c_void_p(256), 4, None,
+                          C.byref(opts), C.c_void_p(256), None, None, None, None, None, 0, None)
+    assert rc == ng.ERR_INVALID_ARG and b"aligned" in lib.ngprt_last_error()
+    # bad options
+    s.tables = 256
+    opts.attn_mode = 7
+    rc = lib.ngprt_render(C.byref(s), C.byref(o), None, 0, None, C.c_void_p(256), C.c_void_p(256), 4, None,
+                          C.byref(opts), C.c_void_p(256), None, None, None, None, None, 0, None)
+    assert rc == ng.ERR_INVALID_ARG and b"attn_mode" in lib.ngprt_last_error()

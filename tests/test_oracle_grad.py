@@ -69,3 +69,36 @@ def test_reverse_pass_matches_central_differences(attn_mode, bounded):
             an = float(gr @ v)
             assert abs(fd - an) <= 1e-6 + 1e-4 * abs(an), (name, fd, an)
     assert checked > 40
+
+
+def test_loss_uses_each_cotangent_on_its_own_output():
+    """render_dot must equal <d_rgb, rgb> + <d_depth, depth> + <d_opacity, A> formed
+    from render()'s outputs: catches cotangents handed to the wrong output."""
+    sc, orc, opts, o, d, cot = _setup(0, True)
+    r = orc.render(opts, rays_o=o, rays_d=d)
+    want = (cot["d_rgb"] * r["rgb"]).sum() + (cot["d_depth"] * r["depth"]).sum() + \
+        (cot["d_opacity"] * r["opacity"]).sum()
+    assert abs(orc.render_dot(opts, rays_o=o, rays_d=d, **cot) - want) < 1e-12 * max(1.0, abs(want))
+
+
+@pytest.mark.parametrize("which", ["d_rgb", "d_depth", "d_opacity"])
+def test_reverse_pass_per_output(which):
+    """Central differences with one output's cotangent at a time."""
+    sc, orc, opts, o, d, cot = _setup(0, True)
+    one = {k: (v if k == which else np.zeros_like(v)) for k, v in cot.items()}
+    g = orc.render_backward(opts, rays_o=o, rays_d=d, **one)
+    rng = np.random.default_rng(13)
+    for name, arr in (("tables", orc.tables), ("coarse", orc.coarse)):
+        gr = g[name].reshape(-1)
+        v = rng.normal(size=arr.size)
+        v /= np.linalg.norm(v)
+        fd = _fd(orc, opts, o, d, one, arr, None, v)
+        an = float(gr @ v)
+        assert abs(fd - an) <= 1e-7 + 1e-4 * abs(an), (which, name, fd, an)
+        # density channel alone (the output-specific part of the reverse pass)
+        v0 = np.zeros(arr.size)
+        v0.reshape(arr.shape)[:, 0] = rng.normal(size=arr.shape[0])
+        v0 /= np.linalg.norm(v0)
+        fd = _fd(orc, opts, o, d, one, arr, None, v0)
+        an = float(gr @ v0)
+        assert abs(fd - an) <= 1e-7 + 1e-4 * abs(an), (which, name, "sigma", fd, an)
