@@ -255,6 +255,35 @@ int32_t ngprt_l2_loss(const float* rgb, const float* target, int64_t n, float sc
 int32_t ngprt_adam_step(float* param, float* grad, float* m, float* v, int64_t n, float lr, float beta1, float beta2,
                         float eps, int32_t step, int32_t zero_grad, void* stream);
 
+/* ------------------------------------------------------------------------------
+ * Render without any caller-provided scratch.  The paper has no counterpart: this
+ * is for callers that cannot allocate device memory (a plug-in inside a host
+ * application that owns the device allocator, code that must not allocate in a
+ * latency-critical loop, a fixed memory budget set at load time).  It computes
+ * exactly what ngprt_render computes, with the per-ray state kept in a static device
+ * array of NGPRT_NOALLOC_MAX_RAYS * NGPRT_STATE_FLOATS floats (12 MiB) that every
+ * GPU loading this library holds until the process exits.
+ *   - It allocates nothing (no cudaMalloc, cudaFree or allocating library call).
+ *   - n_rays > NGPRT_NOALLOC_MAX_RAYS is rejected with NGPRT_ERR_INVALID_ARG: render
+ *     larger batches in chunks.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call before
+ *     any stream capture.
+ *   - Every call on a device shares the one array, which keeps the last call's
+ *     contents (each call overwrites the state of the rays it renders before reading
+ *     it).  Calls that overlap on the GPU (other streams, other host threads) race
+ *     on it: serialise them.
+ * Arguments are those of ngprt_render without ray_state and workspace.
+ * ------------------------------------------------------------------------------ */
+#define NGPRT_NOALLOC_MAX_RAYS 262144
+
+int64_t ngprt_render_noalloc_max_rays(void);
+
+int32_t ngprt_render_noalloc(const ngprt_scene* scene, const ngprt_occ* occ, const ngprt_camera* cams, int32_t n_cams,
+                             const int32_t* pixel_ids, const float* rays_o, const float* rays_d, int64_t n_rays,
+                             const float* t_interval, const ngprt_render_opts* opts, float* rgb, float* depth,
+                             float* opacity, int32_t* ray_stats, void* stream);
+
 /*
  * Test hook for the per-level indexing (Eq. 3, Eq. 6): for n positions u (float
  * [n][3] in the unit cube) write the absolute table row of each of the 8 corners

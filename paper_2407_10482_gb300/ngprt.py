@@ -78,6 +78,9 @@ _SIGS = {
     "ngprt_proposal_targets": (C.c_int32, [_P, _P, _P, C.c_int32, _P, _P, _P, C.c_int64, _P, _P, _P, _P]),
     "ngprt_render_fallback": (C.c_int32, [_P, _P, _P, C.c_int32, _P, _P, _P, C.c_int64, _P, _P, C.c_float, _P, _P,
                                           _P, _P]),
+    "ngprt_render_noalloc_max_rays": (C.c_int64, []),
+    "ngprt_render_noalloc": (C.c_int32, [_P, _P, _P, C.c_int32, _P, _P, _P, C.c_int64, _P, _P, _P, _P, _P, _P,
+                                         _P]),
     "ngprt_last_error": (C.c_char_p, []),
     "ngprt_version": (C.c_int32, []),
 }
@@ -229,6 +232,19 @@ def ngprt_render_fallback(scene, occ, cams, n_cams, pixel_ids, rays_o, rays_d, n
     _check("ngprt_render_fallback", lib().ngprt_render_fallback(
         C.byref(scene), C.byref(occ), cams, n_cams, _ptr(pixel_ids), _ptr(rays_o), _ptr(rays_d), n_rays,
         _ptr(t_interval), _ptr(a_hat), threshold, C.byref(opts), _ptr(ray_state), _ptr(ray_stats), _stream(stream)))
+
+
+def ngprt_render_noalloc_max_rays() -> int:
+    return int(lib().ngprt_render_noalloc_max_rays())
+
+
+def ngprt_render_noalloc(scene, occ, cams, n_cams, pixel_ids, rays_o, rays_d, n_rays, t_interval, opts, rgb,
+                         depth=None, opacity=None, ray_stats=None, stream=None) -> None:
+    """ngprt_render with its scratch in the library's static device array (no
+    allocation anywhere); at most ngprt_render_noalloc_max_rays() rays per call."""
+    _check("ngprt_render_noalloc", lib().ngprt_render_noalloc(
+        C.byref(scene), C.byref(occ), cams, n_cams, _ptr(pixel_ids), _ptr(rays_o), _ptr(rays_d), n_rays,
+        _ptr(t_interval), C.byref(opts), _ptr(rgb), _ptr(depth), _ptr(opacity), _ptr(ray_stats), _stream(stream)))
 
 
 def ngprt_grid_indices(scene, u, n, idx_out, stream=None) -> None:
