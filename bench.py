@@ -194,9 +194,12 @@ def main():
     opac = torch.empty(n, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    def march():
+    ws = torch.empty(ng.ngprt_render_workspace_bytes(ds.struct, n), dtype=torch.uint8, device=dev)
+
+    def march(workspace=ws):
+        # wavefront engine (advance / gather rounds) when given the workspace
         ng.ngprt_render(ds.struct, docc.struct, cam_arr, n_cams, None, None, None, n, None, ro, None,
-                        ray_state=state, stream=stream)
+                        ray_state=state, workspace=workspace, stream=stream)
 
     def shade():
         ng.ngprt_shade(ds.struct, state, n, opts.bg, rgb, depth, opac, stream=stream)
@@ -250,6 +253,19 @@ def main():
     ms_max = float(ms_t.item())
     fps = world * 1000.0 / ms_max
 
+    # the single fused march kernel on the same frame, for comparison
+    fused = []
+    for k in range(args.warmup + 5):
+        flush.fill_(float(k))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        march(None)
+        e1.record(stream)
+        e1.synchronize()
+        if k >= args.warmup:
+            fused.append(e0.elapsed_time(e1))
+
     # end to end through the public call with host buffers: camera in, image out
     host = {"rgb": torch.empty(n, 3, pin_memory=True), "depth": torch.empty(n, pin_memory=True),
             "opacity": torch.empty(n, pin_memory=True)}
@@ -263,7 +279,7 @@ def main():
         e0.record(stream)
         cam_arr_k, _ = ng.cameras_struct(cams, cfg.W, cfg.H)
         ng.ngprt_render(ds.struct, docc.struct, cam_arr_k, n_cams, None, None, None, n, None, ro, rgb, depth, opac,
-                        None, state, stream=stream)
+                        None, state, ws, stream=stream)
         host["rgb"].copy_(rgb, non_blocking=True)
         host["depth"].copy_(depth, non_blocking=True)
         host["opacity"].copy_(opac, non_blocking=True)
@@ -292,16 +308,17 @@ def main():
         "config": {"workload": WORKLOAD, "views_per_step": 1, "rays_per_step": n, "l2_flush": True,
                    "parallelism": f"replicas x{world}", "table_dtype": args.table_dtype},
         "grays_per_s": fps * n / 1e9,
-        "kernels_ms": {"march": t_march_avg, "shade_mlp": statistics.mean(t_shade)},
+        "kernels_ms": {"march": t_march_avg, "shade_mlp": statistics.mean(t_shade),
+                       "march_fused_engine": statistics.mean(fused)},
         "march_stats": march_stats,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                     "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": "march_kernel<16,F32>",
+                     "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": "march phase (wavefront rounds: advance + gather kernels)",
                      "peak_source": peaks["source"],
                      "bytes_per_sample": bytes_per_sample,
                      "note": "algorithmic gather bytes (L*8 entries + 8 coarse vertices per sample, 2 B per "
                              "marching point, 48 B state per ray) over the march kernel's event time"},
         "e2e": {"value": e2e_fps, "unit": "frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": (2 * 8 + 3) * args.steps,
         "clocks": clk,
         "wall_s": wall,
     }

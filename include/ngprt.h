@@ -159,6 +159,10 @@ size_t ngprt_render_workspace_bytes(const ngprt_scene* scene, int64_t n_rays);
  *   ray_stats  : NULL or int32 [n][2] = (marching points, samples).
  *   ray_state  : NULL or float [n][NGPRT_STATE_FLOATS], the per-ray composite state
  *                ngprt_render_backward consumes.
+ *   workspace  : with ngprt_render_workspace_bytes(n) bytes (256-byte aligned) the march
+ *                runs as rounds over the unfinished rays (advance / gather kernels);
+ *                without it (workspace NULL, ray_state given) one fused march kernel
+ *                runs.  Both give identical results.
  */
 int32_t ngprt_render(const ngprt_scene* scene, const ngprt_occ* occ, const ngprt_camera* cams, int32_t n_cams,
                      const int32_t* pixel_ids, const float* rays_o, const float* rays_d, int64_t n_rays,

@@ -79,12 +79,16 @@ __device__ __forceinline__ float dot3(const float a[3], const float b[3]) {
 // Normalise d and find the parametric interval [t, t_out) inside the domain
 // (bounded: the box [-1,1]^3; unbounded: the world ball of radius r_far), then
 // clip it to [t_min, inf) and to the optional interval [t_lo, t_hi].
-__device__ __forceinline__ bool ray_interval(int bounded, const float o[3], float d[3], float t_min, float r_far,
-                                             float t_lo, float t_hi, float& t, float& t_out) {
+__device__ __forceinline__ void normalize_dir(float d[3]) {
     float nn = fsqrt(dot3(d, d));
     d[0] = fdiv(d[0], nn);
     d[1] = fdiv(d[1], nn);
     d[2] = fdiv(d[2], nn);
+}
+
+__device__ __forceinline__ bool ray_interval(int bounded, const float o[3], float d[3], float t_min, float r_far,
+                                             float t_lo, float t_hi, float& t, float& t_out) {
+    normalize_dir(d);
     float t_in;
     if (bounded) {
         float lo[3], hi[3];

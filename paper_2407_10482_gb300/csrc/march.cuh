@@ -82,6 +82,25 @@ __device__ __forceinline__ bool thread_ray(const MarchParams& p, int64_t& ray, f
     return true;
 }
 
+// Origin and (unnormalised) direction of ray `ray` of the batch, by its index.
+__device__ __forceinline__ void ray_of(const MarchParams& p, int64_t ray, float o[3], float d[3]) {
+    if (p.mode == 2) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            o[a] = p.rays_o[3 * ray + a];
+            d[a] = p.rays_d[3 * ray + a];
+        }
+        return;
+    }
+    int64_t id = p.mode == 1 ? (int64_t)p.pixel_ids[ray] : ray;
+    if (id < 0) id = 0;
+    const int64_t wh = (int64_t)p.W * p.H;
+    int64_t view = id / wh;
+    const int64_t rem = id - view * wh;
+    if (view >= p.n_cams) view = p.n_cams - 1;
+    camera_ray(p.cams.c[view], (int)(rem % p.W), (int)(rem / p.W), o, d);
+}
+
 __device__ __forceinline__ float corner_w(const float w[3], int c) {
     const float wx = (c & 1) ? w[0] : 1.0f - w[0];
     const float wy = (c & 2) ? w[1] : 1.0f - w[1];
@@ -195,108 +214,193 @@ __device__ __forceinline__ void sample_features(const Grid& g, const float u[3],
     }
 }
 
-// Walk one ray from t to t_out; smp.sample(u, t, delta) is called at every
-// occupied marching point and returns true when the ray terminates.
-template <class Sampler>
-__device__ __forceinline__ void march_loop(const MarchParams& p, const float o[3], const float d[3], float t,
-                                           float t_out, Sampler& smp, int& n_march, int& n_samp) {
+// Position of a ray's march between calls: the current point t, the domain end,
+// the lattice origin and index (lattice_snap), and the counters.
+struct MarchState {
+    float t, t_out, t_start;
+    int lat_k, n_march, n_samp;
+};
+
+__device__ __forceinline__ MarchState march_state(float t, float t_out) {
+    MarchState st;
+    st.t = t;
+    st.t_out = t_out;
+    st.t_start = t;
+    st.lat_k = 0;
+    st.n_march = 0;
+    st.n_samp = 0;
+    return st;
+}
+
+// Advance from st.t through empty space to the next occupied marching point.
+// Returns true with u (unit-cube position), delta (clipped sample step) and dt (the
+// sample step) of the point at st.t, or false when the ray is exhausted (t_out or a
+// cap reached).
+__device__ __forceinline__ bool march_advance(const MarchParams& p, const float o[3], const float d[3],
+                                              MarchState& st, float u[3], float& delta, float& dt) {
     const ngprt_render_opts& op = p.opts;
     const int bounded = p.g.bounded;
     const float B = bounded ? 1.0f : 2.0f;
     const float dt0 = fmul(op.step_base, op.step_gamma);
     const int R_O = p.occ.R_O;
     const float vG = fdiv(2.0f * B, (float)R_O);
-    const float t_start = t;
-    int lat_k = 0;
     const bool snap = op.lattice_snap && bounded;
-    while (true) {
-        // phase 1: advance through empty space to the next occupied marching point
-        bool found = false;
-        float u[3], delta = 0.0f, dt = 0.0f;
-        while (t < t_out && n_march < op.max_march && n_samp < op.max_samples) {
-            ++n_march;
-            float x[3], y[3], r;
-            march_point(bounded, o, d, t, x, y, u, r);
-            int empty_level = -1, ev[3] = {0, 0, 0};
-            for (int k = p.occ.n_levels - 1; k >= 0; --k) {
-                const int Rk = R_O >> k;
-                const int c0 = occ_vox(u[0], Rk), c1 = occ_vox(u[1], Rk), c2 = occ_vox(u[2], Rk);
-                const uint32_t bi = (uint32_t)c0 + (uint32_t)Rk * ((uint32_t)c1 + (uint32_t)Rk * (uint32_t)c2);
-                const uint32_t word = __ldg(p.occ.bits + p.occ.word_off[k] + (bi >> 5));
-                if (!((word >> (bi & 31)) & 1u)) {
-                    empty_level = k;
-                    ev[0] = c0; ev[1] = c1; ev[2] = c2;
-                    break;
-                }
-            }
-            if (empty_level < 0) {
-                dt = bounded ? dt0 : fmul(dt0, fmaxf(1.0f, r));
-                delta = fminf(dt, fsub(t_out, t));
-                found = true;
+    float t = st.t;
+    while (t < st.t_out && st.n_march < op.max_march && st.n_samp < op.max_samples) {
+        ++st.n_march;
+        float x[3], y[3], r;
+        march_point(bounded, o, d, t, x, y, u, r);
+        int empty_level = -1, ev[3] = {0, 0, 0};
+        for (int k = p.occ.n_levels - 1; k >= 0; --k) {
+            const int Rk = R_O >> k;
+            const int c0 = occ_vox(u[0], Rk), c1 = occ_vox(u[1], Rk), c2 = occ_vox(u[2], Rk);
+            const uint32_t bi = (uint32_t)c0 + (uint32_t)Rk * ((uint32_t)c1 + (uint32_t)Rk * (uint32_t)c2);
+            const uint32_t word = __ldg(p.occ.bits + p.occ.word_off[k] + (bi >> 5));
+            if (!((word >> (bi & 31)) & 1u)) {
+                empty_level = k;
+                ev[0] = c0; ev[1] = c1; ev[2] = c2;
                 break;
             }
-            // s_O: leave the empty voxel along the ray's direction in grid space
-            const int Rk = R_O >> empty_level;
-            const float vk = fdiv(2.0f * B, (float)Rk);
-            float v[3];
-            if (bounded || !(r > 1.0f)) {
-                v[0] = d[0]; v[1] = d[1]; v[2] = d[2];
-            } else {
-                const float kk = fdiv(fsub(2.0f, fdiv(1.0f, r)), r);
-                const float px = dot3(x, d);
-                const float r2 = fmul(r, r);
-                const float m = fdiv(fmul(px, fmul(2.0f, fsub(1.0f, r))), fmul(r2, r2));
+        }
+        if (empty_level < 0) {
+            dt = bounded ? dt0 : fmul(dt0, fmaxf(1.0f, r));
+            delta = fminf(dt, fsub(st.t_out, t));
+            st.t = t;
+            return true;
+        }
+        // s_O: leave the empty voxel along the ray's direction in grid space
+        const int Rk = R_O >> empty_level;
+        const float vk = fdiv(2.0f * B, (float)Rk);
+        float v[3];
+        if (bounded || !(r > 1.0f)) {
+            v[0] = d[0]; v[1] = d[1]; v[2] = d[2];
+        } else {
+            const float kk = fdiv(fsub(2.0f, fdiv(1.0f, r)), r);
+            const float px = dot3(x, d);
+            const float r2 = fmul(r, r);
+            const float m = fdiv(fmul(px, fmul(2.0f, fsub(1.0f, r))), fmul(r2, r2));
 #pragma unroll
-                for (int a = 0; a < 3; ++a) v[a] = fadd(fmul(kk, d[a]), fmul(m, x[a]));
-            }
-            float se = INFINITY;
+            for (int a = 0; a < 3; ++a) v[a] = fadd(fmul(kk, d[a]), fmul(m, x[a]));
+        }
+        float se = INFINITY;
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const float lo = fsub(fmul((float)ev[a], vk), B);
-                const float hi = fadd(lo, vk);
-                float ta = INFINITY;
-                if (v[a] > 0.0f) ta = fdiv(fsub(hi, y[a]), v[a]);
-                else if (v[a] < 0.0f) ta = fdiv(fsub(lo, y[a]), v[a]);
-                se = fminf(se, ta);
-            }
-            const float s_O = fadd(fmaxf(se, 0.0f), fmul(1e-5f, fmaxf(1.0f, t)));
-            float step = s_O;
-            if (op.use_dist && p.occ.dist && empty_level >= 1) {
-                const int g0 = occ_vox(u[0], R_O), g1 = occ_vox(u[1], R_O), g2 = occ_vox(u[2], R_O);
-                const int gv = __ldg(p.occ.dist + ((size_t)g0 + (size_t)R_O * ((size_t)g1 + (size_t)R_O * g2)));
-                if (gv > 0) {
-                    const float rho = fmul((float)gv, vG);
-                    float sg = rho;
-                    if (!bounded && r > 1.0f) {
-                        const float r1 = fadd(r, 1.0f);
-                        const float a = fdiv(fmul(fmul(r1, r1), rho), fmul(4.0f, r));
-                        const float cap = fmul(fsub(r, 1.0f), 0.5f);
-                        sg = fmaxf(rho, fminf(a, cap));
-                    }
-                    step = op.dist_rule == 1 ? fmaxf(sg, s_O) : sg;
+        for (int a = 0; a < 3; ++a) {
+            const float lo = fsub(fmul((float)ev[a], vk), B);
+            const float hi = fadd(lo, vk);
+            float ta = INFINITY;
+            if (v[a] > 0.0f) ta = fdiv(fsub(hi, y[a]), v[a]);
+            else if (v[a] < 0.0f) ta = fdiv(fsub(lo, y[a]), v[a]);
+            se = fminf(se, ta);
+        }
+        const float s_O = fadd(fmaxf(se, 0.0f), fmul(1e-5f, fmaxf(1.0f, t)));
+        float step = s_O;
+        if (op.use_dist && p.occ.dist && empty_level >= 1) {
+            const int g0 = occ_vox(u[0], R_O), g1 = occ_vox(u[1], R_O), g2 = occ_vox(u[2], R_O);
+            const int gv = __ldg(p.occ.dist + ((size_t)g0 + (size_t)R_O * ((size_t)g1 + (size_t)R_O * g2)));
+            if (gv > 0) {
+                const float rho = fmul((float)gv, vG);
+                float sg = rho;
+                if (!bounded && r > 1.0f) {
+                    const float r1 = fadd(r, 1.0f);
+                    const float a = fdiv(fmul(fmul(r1, r1), rho), fmul(4.0f, r));
+                    const float cap = fmul(fsub(r, 1.0f), 0.5f);
+                    sg = fmaxf(rho, fminf(a, cap));
                 }
-            }
-            if (snap) {
-                const int kk = (int)floorf(fdiv(fsub(fadd(t, step), t_start), dt0));
-                lat_k = kk > lat_k + 1 ? kk : lat_k + 1;
-                t = fadd(t_start, fmul((float)lat_k, dt0));
-            } else {
-                t = fadd(t, step);
+                step = op.dist_rule == 1 ? fmaxf(sg, s_O) : sg;
             }
         }
-        if (!found) break;
-        // phase 2: the lanes holding a sample gather and composite it together
-        const bool stop = smp.sample(u, t, delta);
-        ++n_samp;
-        if (stop) break;
         if (snap) {
-            lat_k += 1;
-            t = fadd(t_start, fmul((float)lat_k, dt0));
+            const int kk = (int)floorf(fdiv(fsub(fadd(t, step), st.t_start), dt0));
+            st.lat_k = kk > st.lat_k + 1 ? kk : st.lat_k + 1;
+            t = fadd(st.t_start, fmul((float)st.lat_k, dt0));
         } else {
-            t = fadd(t, dt);
+            t = fadd(t, step);
         }
     }
+    st.t = t;
+    return false;
 }
+
+// Move past the sample just taken at st.t (sample step dt, or the next lattice point).
+__device__ __forceinline__ void march_after_sample(const MarchParams& p, MarchState& st, float dt) {
+    ++st.n_samp;
+    if (p.opts.lattice_snap && p.g.bounded) {
+        st.lat_k += 1;
+        st.t = fadd(st.t_start, fmul((float)st.lat_k, fmul(p.opts.step_base, p.opts.step_gamma)));
+    } else {
+        st.t = fadd(st.t, dt);
+    }
+}
+
+// Walk one ray from its state; smp.sample(u, t, delta) is called at every occupied
+// marching point and returns true when the ray terminates.  The lanes of a warp
+// first advance through empty space each to its own next sample, then sample
+// together.
+template <class Sampler>
+__device__ __forceinline__ void march_loop_from(const MarchParams& p, const float o[3], const float d[3],
+                                                MarchState& st, Sampler& smp) {
+    float u[3], delta, dt;
+    while (march_advance(p, o, d, st, u, delta, dt)) {
+        const bool stop = smp.sample(u, st.t, delta);
+        if (stop) {
+            ++st.n_samp;
+            break;
+        }
+        march_after_sample(p, st, dt);
+    }
+}
+
+template <class Sampler>
+__device__ __forceinline__ void march_loop(const MarchParams& p, const float o[3], const float d[3], float t,
+                                           float t_out, Sampler& smp, int& n_march, int& n_samp) {
+    MarchState st = march_state(t, t_out);
+    march_loop_from(p, o, d, st, smp);
+    n_march = st.n_march;
+    n_samp = st.n_samp;
+}
+
+// Forward sampler: features (Eq. 6-8), alpha compositing (Eq. 2, Eq. 5).
+template <int L, int DT>
+struct ForwardSampler {
+    const Grid& g;
+    int attn_mode;
+    float t_term;
+    float* gates;
+    float T, A, depth;
+    float Cd[3], F[4];
+    __device__ __forceinline__ ForwardSampler(const Grid& g_, int mode, float term, float* gate_buf)
+        : g(g_), attn_mode(mode), t_term(term), gates(gate_buf), T(1.0f), A(0.0f), depth(0.0f) {
+        Cd[0] = Cd[1] = Cd[2] = 0.0f;
+        F[0] = F[1] = F[2] = F[3] = 0.0f;
+    }
+    // Resume from a stored state [C_d(3), F(4), A, depth, ...] and transmittance.
+    __device__ __forceinline__ void resume(const float* s, float T_) {
+        Cd[0] = s[0]; Cd[1] = s[1]; Cd[2] = s[2];
+        F[0] = s[3]; F[1] = s[4]; F[2] = s[5]; F[3] = s[6];
+        A = s[7];
+        depth = s[8];
+        T = T_;
+    }
+    // One composited sample from its features (the arithmetic of sample()).
+    __device__ __forceinline__ bool composite(const float f[8], float t, float delta) {
+        const float sigma = expf(f[0]);
+        const float trans = expf(-sigma * delta);
+        const float w = T * (1.0f - trans);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) Cd[k] = fmaf(w, f[1 + k], Cd[k]);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) F[k] = fmaf(w, f[4 + k], F[k]);
+        A += w;
+        depth = fmaf(w, t, depth);
+        T *= trans;
+        return T < t_term;
+    }
+    __device__ __forceinline__ bool sample(const float u[3], float t, float delta) {
+        float f[8];
+        sample_features<L, DT>(g, u, attn_mode, f, gates, blockDim.x);
+        return composite(f, t, delta);
+    }
+};
 
 // Ray set-up shared by both passes: this thread's ray, its domain interval.
 __device__ __forceinline__ bool ray_setup(const MarchParams& p, int64_t& ray, float o[3], float d[3], float& t,

@@ -13,37 +13,6 @@
 
 namespace ngprt {
 
-// Forward sampler: features (Eq. 6-8), alpha compositing (Eq. 2, Eq. 5).
-template <int L, int DT>
-struct ForwardSampler {
-    const Grid& g;
-    int attn_mode;
-    float t_term;
-    float* gates;
-    float T, A, depth;
-    float Cd[3], F[4];
-    __device__ __forceinline__ ForwardSampler(const Grid& g_, int mode, float term, float* gate_buf)
-        : g(g_), attn_mode(mode), t_term(term), gates(gate_buf), T(1.0f), A(0.0f), depth(0.0f) {
-        Cd[0] = Cd[1] = Cd[2] = 0.0f;
-        F[0] = F[1] = F[2] = F[3] = 0.0f;
-    }
-    __device__ __forceinline__ bool sample(const float u[3], float t, float delta) {
-        float f[8];
-        sample_features<L, DT>(g, u, attn_mode, f, gates, blockDim.x);
-        const float sigma = expf(f[0]);
-        const float trans = expf(-sigma * delta);
-        const float w = T * (1.0f - trans);
-#pragma unroll
-        for (int k = 0; k < 3; ++k) Cd[k] = fmaf(w, f[1 + k], Cd[k]);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) F[k] = fmaf(w, f[4 + k], F[k]);
-        A += w;
-        depth = fmaf(w, t, depth);
-        T *= trans;
-        return T < t_term;
-    }
-};
-
 template <int L, int DT>
 __global__ void __launch_bounds__(128, NGPRT_MARCH_MIN_BLOCKS) march_kernel(const __grid_constant__ MarchParams p) {
     int64_t ray;
@@ -339,10 +308,16 @@ int32_t check_opts(const ngprt_render_opts* o, const char* fn) {
 
 using namespace ngprt;
 
+namespace ngprt {
+size_t wavefront_bytes(int64_t n);
+int32_t run_wavefront(int L, int dt, const MarchParams& m, dim3 grid, void* ws, cudaStream_t st);
+static size_t state_bytes(int64_t n) { return ((size_t)n * NGPRT_STATE_FLOATS * sizeof(float) + 255) / 256 * 256; }
+}  // namespace ngprt
+
 extern "C" size_t ngprt_render_workspace_bytes(const ngprt_scene* scene, int64_t n_rays) {
     (void)scene;
     if (n_rays < 0) return 0;
-    return ((size_t)n_rays * NGPRT_STATE_FLOATS * sizeof(float) + 255) / 256 * 256 + 256;
+    return state_bytes(n_rays) + wavefront_bytes(n_rays) + 256;
 }
 
 extern "C" int32_t ngprt_render(const ngprt_scene* scene, const ngprt_occ* occ, const ngprt_camera* cams,
@@ -370,22 +345,31 @@ extern "C" int32_t ngprt_render(const ngprt_scene* scene, const ngprt_occ* occ, 
     dim3 grid;
     if ((rc = setup_rays(p, cams, n_cams, pixel_ids, rays_o, rays_d, n_rays, grid, fn)) != NGPRT_OK) return rc;
     if (n_rays == 0) return NGPRT_OK;
+    // Engine: the wavefront rounds when the workspace holds their scratch, else the
+    // fused march kernel (same results); the state goes to ray_state or the workspace.
     float* state = ray_state;
+    char* ws = static_cast<char*>(workspace);
+    const size_t need_state = ray_state ? 0 : state_bytes(n_rays);
+    const bool wavefront = ws && ws_bytes >= need_state + wavefront_bytes(n_rays);
     if (!state) {
-        const size_t need = ngprt_render_workspace_bytes(scene, n_rays);
-        if (!workspace || ws_bytes < need) {
-            set_error("%s: workspace %zu bytes < %zu needed", fn, ws_bytes, need);
+        if (!ws || ws_bytes < need_state) {
+            set_error("%s: workspace %zu bytes < %zu needed", fn, ws_bytes, ngprt_render_workspace_bytes(scene, n_rays));
             return NGPRT_ERR_WORKSPACE;
         }
-        state = static_cast<float*>(workspace);
+        state = reinterpret_cast<float*>(ws);
     }
     NGPRT_REQUIRE(((uintptr_t)state & 15) == 0, "%s: ray_state/workspace must be 16-byte aligned", fn);
+    NGPRT_REQUIRE(!ws || ((uintptr_t)ws & 255) == 0, "%s: workspace must be 256-byte aligned", fn);
     p.opts = *opts;
     p.t_interval = t_interval;
     p.state = state;
     p.stats = ray_stats;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if ((rc = launch_march_any(scene->L, scene->table_dtype, p, grid, st)) != NGPRT_OK) return rc;
+    if (wavefront) {
+        if ((rc = run_wavefront(scene->L, scene->table_dtype, p, grid, ws + need_state, st)) != NGPRT_OK) return rc;
+    } else {
+        if ((rc = launch_march_any(scene->L, scene->table_dtype, p, grid, st)) != NGPRT_OK) return rc;
+    }
     if (!rgb) return cuda_status(fn);
     MlpParams m;
     m.state = state;

@@ -234,3 +234,29 @@ def test_hd_frame_sampled_parity(ng):
     _compare(sub, orc.render(opts, cams=cams, pix=pix))
     st = r["stats"].cpu().numpy()
     assert 5 < st[:, 1].mean() < 60
+
+
+@pytest.mark.parametrize("cfg_name", ["small", "hd"])
+def test_wavefront_equals_fused_bit_for_bit(ng, cfg_name):
+    """The round-based engine (with a workspace) and the single fused march kernel
+    (ray_state only) must give identical values and counts."""
+    cfg = S.small_config(blob_std=(0.05, 0.15), W=97, H=61) if cfg_name == "small" else S.hd_config(W=480, H=270)
+    sc = S.make_scene(cfg)
+    ds = ng.DeviceScene(cfg, sc.tables, sc.coarse, sc.mlp_w)
+    docc = ng.DeviceOcc(sc.occ, cfg.R_O, cfg.n_occ_levels)
+    n = cfg.W * cfg.H
+    cams, nc = ng.cameras_struct(S.orbit_cameras(cfg, 1, azimuth0=33.0), cfg.W, cfg.H)
+    for kw in (dict(), dict(lattice_snap=True), dict(max_samples=7), dict(t_term=0.0)):
+        opts = ng.render_opts(S.default_options(cfg, **kw))
+        outs = []
+        for wavefront in (True, False):
+            st = torch.empty(n, ng.STATE_FLOATS, device="cuda")
+            stats = torch.empty(n, 2, dtype=torch.int32, device="cuda")
+            ws = torch.empty(ng.ngprt_render_workspace_bytes(ds.struct, n), dtype=torch.uint8, device="cuda") \
+                if wavefront else None
+            ng.ngprt_render(ds.struct, docc.struct, cams, nc, None, None, None, n, None, opts, None, ray_stats=stats,
+                            ray_state=st, workspace=ws)
+            outs.append((st[:, :9].clone(), stats.clone()))
+        torch.cuda.synchronize()
+        assert torch.equal(outs[0][1], outs[1][1]), kw
+        assert torch.equal(outs[0][0], outs[1][0]), kw
