@@ -104,6 +104,24 @@ def _dist_setup():
     return world, rank, local
 
 
+def rank_views(rank: int, views_per_rank: int = 1, step_deg: float = 45.0) -> list:
+    """Azimuths (degrees) of the views rank `rank` renders: ranks are independent
+    replicas, each with its own views of the orbit, so there is no data-path
+    collective; the whole-job rate is the views of all ranks over the slowest rank."""
+    return [step_deg * (rank * views_per_rank + k) for k in range(views_per_rank)]
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """Largest value over the ranks (the timing of the slowest rank)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def cpu_baseline(cfg, scene, cams, opts, sample_stride: int = 16) -> dict:
     """The oracle on a stratified pixel sample (every sample_stride-th pixel) of the
     frame, on all host cores; rays/s scaled to frames/s of the full frame."""
@@ -152,6 +170,137 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _timed(fn, stream, flush, reps, warmup):
+    """Mean CUDA-event time (ms) of fn() on `stream`, L2 flushed before each call."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    out = []
+    for k in range(reps):
+        flush.fill_(float(k))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        out.append(e0.elapsed_time(e1))
+    return statistics.mean(out)
+
+
+def other_forms(args, cfg, scene, ds, docc, cams, opts, dev, stream, flush, plain_rgb):
+    """The FP16 + proposal form, 8-view batches, the training step and the gather
+    ceiling, on the same GPU (reported beside the plain FP32 frame)."""
+    import torch
+    from paper_2407_10482_gb300 import ngprt as ng
+    from paper_2407_10482_gb300 import proposal as P
+    n = cfg.W * cfg.H
+    res = {}
+    reps, warm = max(3, args.steps // 2), args.warmup
+    rend32 = ng.Renderer(ds, docc, device=dev)
+    plain = rend32.render(opts, cams=cams, W=cfg.W, H=cfg.H, stats=True)
+    plain_rgb = plain["rgb"].clone()
+    plain_st = plain["stats"].float().mean(0)
+    # learned proposal: trained on the plain renderer's weights over 64 orbit views
+    # that differ from the test views, every step in the library's kernels
+    t0 = time.perf_counter()
+    train_cams = S.orbit_cameras(cfg, 64, azimuth0=2.8125, step_deg=5.625)
+    pix = torch.as_tensor(S.random_pixels(1 << 20, 64, cfg.W, cfg.H, 4)).to(dev)
+    targets = P.make_targets(rend32, opts, train_cams, cfg.W, cfg.H, pix)
+    pc = P.ProposalConfig()
+    w, hist = P.train(train_cams, cfg.W, cfg.H, pix, targets, pc, log_every=500)
+    torch.cuda.synchronize(dev)
+    train_s = time.perf_counter() - t0
+    # FP16 tables, FP16 tensor-core MLP, proposal + fallback
+    ds16 = ng.DeviceScene(cfg, scene.tables, scene.coarse, scene.mlp_w, table_dtype=1, mlp_dtype=1, device=dev)
+    fr = P.FastRenderer(ds16, docc, w, pc, device=dev)
+    rgb = torch.empty(n, 3, device=dev)
+    fr.render(opts, cams, cfg.W, cfg.H, rgb, stats=True)
+    torch.cuda.synchronize(dev)
+    fast_st = fr.stats.float().mean(0)
+    fast_psnr = P.psnr(rgb, plain_rgb)
+    ms_fast = _timed(lambda: fr.render(opts, cams, cfg.W, cfg.H, rgb, stream=stream), stream, flush, reps, warm)
+    # a 4x finer-step render of the same model approximates its continuous volume
+    # rendering: the PSNR loss of the fast form is measured against it as well
+    opts_fine = S.default_options(cfg, step_gamma=0.25, max_march=4096, max_samples=4096)
+    ref = rend32.render(opts_fine, cams=cams, W=cfg.W, H=cfg.H)["rgb"].clone()
+    psnr_plain_ref = P.psnr(plain_rgb, ref)
+    psnr_fast_ref = P.psnr(rgb, ref)
+    # FP16 tables + tensor-core MLP without the proposal (precision form alone)
+    r16 = ng.Renderer(ds16, docc, device=dev)
+    o16 = r16.render(opts, cams=cams, W=cfg.W, H=cfg.H)
+    p16 = P.psnr(o16["rgb"], plain_rgb)
+    ms_16 = _timed(lambda: r16.render(opts, cams=cams, W=cfg.W, H=cfg.H, out=o16), stream, flush, reps, warm)
+    res["forms"] = {
+        "fp16_tables_tc_mlp": {"ms_per_frame": ms_16, "frames_per_s": 1000.0 / ms_16, "psnr_vs_plain_db": p16},
+        "fp16_tc_mlp_proposal": {
+            "ms_per_frame": ms_fast, "frames_per_s": 1000.0 / ms_fast, "grays_per_s": n / ms_fast / 1e6,
+            "psnr_vs_plain_db": fast_psnr, "loss_0p1dB_threshold_db": 41.9,
+            "psnr_vs_fine_ref_db": psnr_fast_ref, "plain_psnr_vs_fine_ref_db": psnr_plain_ref,
+            "psnr_loss_vs_fine_ref_db": psnr_plain_ref - psnr_fast_ref,
+            "marching_per_ray": float(fast_st[0]), "samples_per_ray": float(fast_st[1]),
+            "plain_marching_per_ray": float(plain_st[0]), "plain_samples_per_ray": float(plain_st[1]),
+            "fallback_rays": float(((fr.a_hat - fr.state[:, 7]) > pc.fallback).float().mean()),
+            "proposal_train_s": train_s, "proposal_loss": hist,
+            "training": "2^20 rays of 64 orbit views (azimuth 2.8125 + 5.625 k deg), 2000 Adam steps of 2^15"}}
+    # batches of 8 views (azimuth 45 k deg): plain FP32 and the fast form
+    cams8 = S.orbit_cameras(cfg, 8)
+    n8 = 8 * n
+    out8 = {"rgb": torch.empty(n8, 3, device=dev), "depth": torch.empty(n8, device=dev),
+            "opacity": torch.empty(n8, device=dev)}
+    ms8 = _timed(lambda: rend32.render(opts, cams=cams8, W=cfg.W, H=cfg.H, out=out8), stream, flush, 3, 2)
+    rgb8 = torch.empty(n8, 3, device=dev)
+    fr8 = P.FastRenderer(ds16, docc, w, pc, device=dev)
+    ms8f = _timed(lambda: fr8.render(opts, cams8, cfg.W, cfg.H, rgb8, stream=stream), stream, flush, 3, 2)
+    psnr8 = [P.psnr(rgb8[k * n:(k + 1) * n], out8["rgb"][k * n:(k + 1) * n]) for k in range(8)]
+    res["batch8"] = {"plain_fp32_frames_per_s": 8000.0 / ms8, "fast_frames_per_s": 8000.0 / ms8f,
+                     "fast_psnr_vs_plain_db_per_view": psnr8}
+    del out8, rgb8, fr8
+    # one training step: 2^18 random rays of 8 views, L2 loss against the plain
+    # render of a perturbed scene, reverse pass, Adam over all parameters
+    tgt = rend32.render(opts, cams=cams8, W=cfg.W, H=cfg.H)["rgb"]
+    student_t = ds.tables + 0.02 * torch.randn_like(ds.tables)
+    dss = ng.DeviceScene(cfg, student_t.cpu().numpy(), scene.coarse, scene.mlp_w, device=dev)
+    rs = ng.Renderer(dss, docc, device=dev)
+    pix8 = torch.as_tensor(S.random_pixels(1 << 18, 8, cfg.W, cfg.H, 3)).to(dev)
+    tg = tgt[pix8.long()].contiguous()
+    params = [dss.tables, dss.coarse, dss.mlp_w]
+    grads = [torch.zeros_like(t) for t in params]
+    moms = [(torch.zeros_like(t), torch.zeros_like(t)) for t in params]
+    loss = torch.zeros(1, device=dev)
+    d_rgb = torch.empty(1 << 18, 3, device=dev)
+    step_no = [0]
+
+    def train_step():
+        o = rs.render(opts, cams=cams8, W=cfg.W, H=cfg.H, pixel_ids=pix8, state=True)
+        ng.ngprt_l2_loss(o["rgb"], tg, 3 * (1 << 18), 1.0 / (3 * (1 << 18)), loss, d_rgb, stream=stream)
+        rs.backward(opts, o["state"], d_rgb, None, None, grads[0], grads[1], grads[2], cams=cams8, W=cfg.W,
+                    H=cfg.H, pixel_ids=pix8)
+        step_no[0] += 1
+        for t, g, (m, v) in zip(params, grads, moms):
+            ng.ngprt_adam_step(t, g, m, v, 1e-3, 0.9, 0.99, 1e-8, step_no[0], True, stream=stream)
+    ms_train = _timed(train_step, stream, flush, 5, 3)
+    res["train_step"] = {"rays": 1 << 18, "ms": ms_train, "rays_per_s": (1 << 18) / ms_train * 1e3,
+                         "parts": "render (with state) + L2 loss + reverse pass + Adam on 50.5M table, grid and MLP "
+                                  "parameters"}
+    del dss, rs, params, grads, moms
+    # gather ceiling: random whole-entry gathers at three footprints
+    sink = torch.zeros(1, device=dev)
+    gcl = {}
+    for name, dt, rows in (("l1_resident_f32", 0, 1 << 11), ("l1_resident_f16", 1, 1 << 12),
+                           ("l2_resident_f32", 0, 1 << 20), ("hd_footprint_f32", 0, 1 << 23)):
+        tab = torch.rand(rows, 8, device=dev, dtype=torch.float32 if dt == 0 else torch.float16)
+        nthr, per = 152 * 2048, 256
+
+        def g():
+            ng.ngprt_gather_bench(tab, dt, rows, nthr, per, 7, sink, stream=stream)
+        ms_g = _timed(g, stream, flush, 5, 2)
+        gcl[name + "_GBps"] = nthr * per * (32 if dt == 0 else 16) / (ms_g * 1e-3) / 1e9
+        del tab
+    res["gather_ceiling"] = gcl
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -161,6 +310,9 @@ def main():
     ap.add_argument("--ref-stride", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--table-dtype", type=int, default=0, help="0 F32, 1 F16, 2 BF16 (plain form: 0)")
+    ap.add_argument("--mlp-dtype", type=int, default=0, help="0 F32 (CUDA cores), 1 F16 (tensor cores)")
+    ap.add_argument("--engine", default="fused", choices=["wavefront", "fused"])
+    ap.add_argument("--plain-only", action="store_true", help="time only the plain FP32 frame")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -180,9 +332,10 @@ def main():
 
     cfg = S.hd_config()
     scene = S.make_scene(cfg)
-    cams = S.orbit_cameras(cfg, 1, azimuth0=45.0 * rank)
+    cams = S.orbit_cameras(cfg, 1, azimuth0=rank_views(rank)[0])
     opts = S.default_options(cfg)
-    ds = ng.DeviceScene(cfg, scene.tables, scene.coarse, scene.mlp_w, table_dtype=args.table_dtype, device=dev)
+    ds = ng.DeviceScene(cfg, scene.tables, scene.coarse, scene.mlp_w, table_dtype=args.table_dtype, device=dev,
+                        mlp_dtype=args.mlp_dtype)
     docc = ng.DeviceOcc(scene.occ, cfg.R_O, cfg.n_occ_levels, device=dev)
     rend = ng.Renderer(ds, docc, device=dev)
     n = cfg.W * cfg.H
@@ -194,9 +347,11 @@ def main():
     opac = torch.empty(n, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    ws = torch.empty(ng.ngprt_render_workspace_bytes(ds.struct, n), dtype=torch.uint8, device=dev)
+    ws = torch.empty(ng.ngprt_wavefront_workspace_bytes(ds.struct, n), dtype=torch.uint8, device=dev)
 
-    def march(workspace=ws):
+    main_ws = ws if args.engine == "wavefront" else None
+
+    def march(workspace=main_ws):
         # wavefront engine (advance / gather rounds) when given the workspace
         ng.ngprt_render(ds.struct, docc.struct, cam_arr, n_cams, None, None, None, n, None, ro, None,
                         ray_state=state, workspace=workspace, stream=stream)
@@ -247,10 +402,7 @@ def main():
     t_march = [ev[k][0].elapsed_time(ev[k][1]) for k in range(args.steps)]
     t_shade = [ev[k][1].elapsed_time(ev[k][2]) for k in range(args.steps)]
     ms = statistics.mean(a + b for a, b in zip(t_march, t_shade))
-    ms_t = torch.tensor([ms], device=dev)
-    if world > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
+    ms_max = max_over_ranks(ms, world, dev)
     fps = world * 1000.0 / ms_max
 
     # the single fused march kernel on the same frame, for comparison
@@ -279,7 +431,7 @@ def main():
         e0.record(stream)
         cam_arr_k, _ = ng.cameras_struct(cams, cfg.W, cfg.H)
         ng.ngprt_render(ds.struct, docc.struct, cam_arr_k, n_cams, None, None, None, n, None, ro, rgb, depth, opac,
-                        None, state, ws, stream=stream)
+                        None, state, main_ws, stream=stream)
         host["rgb"].copy_(rgb, non_blocking=True)
         host["depth"].copy_(depth, non_blocking=True)
         host["opacity"].copy_(opac, non_blocking=True)
@@ -287,10 +439,12 @@ def main():
         e1.synchronize()
         if k >= args.warmup:
             e2e_ms.append(e0.elapsed_time(e1))
-    e2e_t = torch.tensor([statistics.mean(e2e_ms)], device=dev)
-    if world > 1:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_fps = world * 1000.0 / float(e2e_t.item())
+    e2e_fps = world * 1000.0 / max_over_ranks(statistics.mean(e2e_ms), world, dev)
+
+    # ---------------------------------------------------------------- other forms
+    extra = {}
+    if not args.plain_only:
+        extra = other_forms(args, cfg, scene, ds, docc, cams, opts, dev, stream, flush, rgb)
 
     peaks = _peaks()
     L = cfg.L
@@ -309,19 +463,25 @@ def main():
                    "parallelism": f"replicas x{world}", "table_dtype": args.table_dtype},
         "grays_per_s": fps * n / 1e9,
         "kernels_ms": {"march": t_march_avg, "shade_mlp": statistics.mean(t_shade),
-                       "march_fused_engine": statistics.mean(fused)},
+                       "march_fused_engine": statistics.mean(fused), "engine": args.engine},
         "march_stats": march_stats,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                     "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": "march phase (wavefront rounds: advance + gather kernels)",
+                     "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": "march_kernel<16,F32> (fused march: occupancy, coarse fetch, 16-level gathers, attention, compositing)",
                      "peak_source": peaks["source"],
                      "bytes_per_sample": bytes_per_sample,
                      "note": "algorithmic gather bytes (L*8 entries + 8 coarse vertices per sample, 2 B per "
                              "marching point, 48 B state per ray) over the march kernel's event time"},
         "e2e": {"value": e2e_fps, "unit": "frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": (2 * 8 + 3) * args.steps,
+        "gpu_launches": (2 if args.engine == "fused" else 2 * 8 + 3) * args.steps,
         "clocks": clk,
         "wall_s": wall,
     }
+    line.update(extra)
+    if "gather_ceiling" in extra:
+        gc = extra["gather_ceiling"]
+        ceil = gc["l1_resident_f32_GBps"] if args.table_dtype == 0 else gc["l1_resident_f16_GBps"]
+        line["roofline"]["gather_ceiling_GBps"] = ceil
+        line["roofline"]["gather_frac"] = achieved / ceil
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg, scene, cams, opts)
     if rank == 0:

@@ -53,7 +53,8 @@ typedef enum { NGPRT_F32 = 0, NGPRT_F16 = 1, NGPRT_BF16 = 2 } ngprt_dtype;
  *   mlp_w  : deferred MLP_psi (Eq. 5) of mlp_layers dense layers without bias:
  *            layer k is a [out_k][in_k] matrix, in_0 = 32 (C_d, F, SH16(d), zero
  *            padding), out_k = mlp_width for hidden layers (ReLU), 3 for the last.
- *            mlp_dtype F32 (float) or F16 (__half).
+ *            mlp_dtype F32 (float; CUDA-core FMA) or F16 (__half; tcgen05 tensor-core
+ *            MMA with FP32 accumulation, activations rounded to FP16 between layers).
  *   bounded: 1 = scene in the box [-1,1]^3; 0 = unbounded scene under the
  *            mip-NeRF-360 contraction into [-2,2]^3.
  * Vertex grids of N per axis cover the unit cube coordinate u in [0,1]^3 with
@@ -144,6 +145,11 @@ int64_t ngprt_table_entries(const ngprt_scene* scene);
 /* Workspace bytes of ngprt_render / ngprt_render_backward for n_rays rays. */
 size_t ngprt_render_workspace_bytes(const ngprt_scene* scene, int64_t n_rays);
 
+/* Workspace bytes with which ngprt_render runs its march as rounds over the
+ * unfinished rays (advance / gather kernels) instead of one fused kernel; the
+ * results are identical, the speed differs with the scene. */
+size_t ngprt_wavefront_workspace_bytes(const ngprt_scene* scene, int64_t n_rays);
+
 /*
  * Render rays (Eq. 2, 5, 6, 8, 9): occupancy-distance marching, per-sample coarse
  * fetch + per-level gathers + lightweight attention, alpha compositing, one
@@ -159,10 +165,9 @@ size_t ngprt_render_workspace_bytes(const ngprt_scene* scene, int64_t n_rays);
  *   ray_stats  : NULL or int32 [n][2] = (marching points, samples).
  *   ray_state  : NULL or float [n][NGPRT_STATE_FLOATS], the per-ray composite state
  *                ngprt_render_backward consumes.
- *   workspace  : with ngprt_render_workspace_bytes(n) bytes (256-byte aligned) the march
- *                runs as rounds over the unfinished rays (advance / gather kernels);
- *                without it (workspace NULL, ray_state given) one fused march kernel
- *                runs.  Both give identical results.
+ *   workspace  : 256-byte aligned; ngprt_render_workspace_bytes(n) bytes run one fused
+ *                march kernel, ngprt_wavefront_workspace_bytes(n) bytes run the march
+ *                as rounds (advance / gather kernels).  Identical results.
  */
 int32_t ngprt_render(const ngprt_scene* scene, const ngprt_occ* occ, const ngprt_camera* cams, int32_t n_cams,
                      const int32_t* pixel_ids, const float* rays_o, const float* rays_d, int64_t n_rays,
@@ -215,8 +220,9 @@ int32_t ngprt_propose(const float* prop_w, const ngprt_camera* cams, int32_t n_c
                       float margin, float a_min, float* t_interval_out, float* a_hat_out, void* stream);
 
 /* Training loss of the proposal against targets [n][3] = (t_near*, t_far*, A*):
- * mean over rays of A* (sl1(dt_near / t_scale) + sl1(dt_far / t_scale)) + (A^ - A*)^2,
- * sl1 = smooth L1 with beta 0.01.  ACCUMULATES the gradient into g_prop_w and the loss
+ * mean over rays of A* (a_n sl1(dt_near / t_scale) + a_f sl1(dt_far / t_scale)) +
+ * (A^ - A*)^2, sl1 = smooth L1 with beta 0.01, a_n = 4 if t_near is later than its
+ * target else 1, a_f = 4 if t_far is earlier than its target else 1.  ACCUMULATES the gradient into g_prop_w and the loss
  * into *loss (one device float, NULL to skip). */
 int32_t ngprt_propose_backward(const float* prop_w, const ngprt_camera* cams, int32_t n_cams,
                                const int32_t* pixel_ids, const float* rays_o, const float* rays_d, int64_t n_rays,
@@ -295,6 +301,20 @@ int32_t ngprt_render_noalloc(const ngprt_scene* scene, const ngprt_occ* occ, con
  */
 int32_t ngprt_grid_indices(const ngprt_scene* scene, const float* u, int64_t n, uint32_t* idx_out,
                            void* stream);
+
+/* Measured ceiling of the render's gathers: n_threads threads each load per_thread
+ * random whole entries (rows drawn by a counter-based hash of seed, thread and step)
+ * of an [n_rows][8] table of dtype F32 (one 32-byte load each) or F16 (16 bytes).
+ * Bytes moved = n_threads * per_thread * entry size; time it on `stream`.
+ * n_rows a power of two, n_threads a multiple of 256, per_thread of 8; sink: one
+ * device float (written only in a case that cannot occur with finite tables). */
+int32_t ngprt_gather_bench(const void* table, int32_t dtype, int64_t n_rows, int64_t n_threads, int32_t per_thread,
+                           uint32_t seed, float* sink, void* stream);
+
+/* 1 if a tensor-core MLP kernel (mlp_dtype F16) ever gave up waiting for its MMAs
+ * (it then frees its tensor memory and leaves its rays unwritten), 0 if not, -1 if
+ * the flag cannot be read.  Synchronises with the device. */
+int32_t ngprt_tensor_core_error(void);
 
 /* Message of the calling thread's last failed call ("" if none). */
 const char* ngprt_last_error(void);

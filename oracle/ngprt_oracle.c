@@ -397,7 +397,8 @@ static void or_point(const or_scene* s, const float o[3], const float d[3], floa
     *r_out = r;
     float B = s->bounded ? 1.0f : 2.0f, hB = s->bounded ? 0.5f : 0.25f;
     if (!s->bounded && r > 1.0f) {
-        float k = (2.0f - 1.0f / r) / r;
+        float ir = 1.0f / r;
+        float k = (2.0f - ir) * ir;  /* (2 - 1/r) / r */
         for (int a = 0; a < 3; ++a) y[a] = x[a] * k;
     } else {
         for (int a = 0; a < 3; ++a) y[a] = x[a];
@@ -414,6 +415,36 @@ void or_contract_batch(int bounded, const float* x, int n, float* y_out, float* 
     for (int i = 0; i < n; ++i) {
         float xx[3], r;
         or_point(&s, o, x + 3 * i, 1.0f, xx, y_out + 3 * i, u_out + 3 * i, &r);
+    }
+}
+
+/* World length of a step whose contracted image stays within distance rho of its
+ * start, so that a step of rho = v G cannot enter an occupied voxel (Eq. 9 in the
+ * unbounded scene).  The box and the unit ball map by the identity and the
+ * contraction is 1-Lipschitz, so rho itself is always safe.  Beyond the unit ball
+ * the image of the segment [x, x + s d] moves at speed |J d| with
+ * |J d|^2 <= 1/r^4 + (2r - 1)^2 b^2 / r^6, b = |x x d| the ray's distance from the
+ * origin (constant along it) and r the radius on the segment; that bound falls
+ * with r, and with s <= (r - 1)/2 the segment stays at radius >= max((r+1)/2, b).
+ * FP32, one rounding per operation. */
+static float or_dist_step(int bounded, const float x[3], const float d[3], float r, float rho) {
+    if (bounded || !(r > 1.0f)) return rho;
+    float cx = x[1] * d[2] - x[2] * d[1];
+    float cy = x[2] * d[0] - x[0] * d[2];
+    float cz = x[0] * d[1] - x[1] * d[0];
+    float b2 = (cx * cx + cy * cy) + cz * cz;
+    float rl = fmaxf((r + 1.0f) * 0.5f, sqrtf(b2));
+    float q = (2.0f * rl - 1.0f) / rl;
+    float s_dir = (rho * (rl * rl)) / sqrtf(1.0f + (q * q) * b2);
+    float cap = (r - 1.0f) * 0.5f;
+    return fmaxf(rho, fminf(s_dir, cap));
+}
+
+void or_dist_step_batch(int bounded, const float* x, const float* d, const float* rho, int n, float* out) {
+    for (int i = 0; i < n; ++i) {
+        const float* xi = x + 3 * i;
+        float r = sqrtf((xi[0] * xi[0] + xi[1] * xi[1]) + xi[2] * xi[2]);
+        out[i] = or_dist_step(bounded, xi, d + 3 * i, r, rho[i]);
     }
 }
 
@@ -536,10 +567,12 @@ static void or_march(const or_scene* s, const or_occ* oc, const or_opts* op,
             if (s->bounded || !(r > 1.0f)) {
                 v[0] = d[0]; v[1] = d[1]; v[2] = d[2];
             } else {
-                float k = (2.0f - 1.0f / r) / r;
+                /* J(x) d = k d + m x, k = (2 - 1/r)/r, m = (x.d) 2 (1 - r) / r^4 */
+                float ir = 1.0f / r;
+                float k = (2.0f - ir) * ir;
                 float px = (x[0] * d[0] + x[1] * d[1]) + x[2] * d[2];
-                float r2 = r * r;
-                float m = (px * (2.0f * (1.0f - r))) / (r2 * r2);
+                float ir2 = ir * ir;
+                float m = (px * (2.0f * (1.0f - r))) * (ir2 * ir2);
                 for (int a = 0; a < 3; ++a) v[a] = k * d[a] + m * x[a];
             }
             float se = INFINITY;
@@ -558,13 +591,7 @@ static void or_march(const or_scene* s, const or_occ* oc, const or_opts* op,
                 int c0[3] = {or_vox(u[0], R_O), or_vox(u[1], R_O), or_vox(u[2], R_O)};
                 int g = oc->dist[(size_t)c0[0] + (size_t)R_O * ((size_t)c0[1] + (size_t)R_O * c0[2])];
                 if (g > 0) {
-                    float rho = (float)g * vG;
-                    float sg = rho;
-                    if (!s->bounded && r > 1.0f) {
-                        float a = ((r + 1.0f) * (r + 1.0f) * rho) / (4.0f * r);
-                        float cap = (r - 1.0f) * 0.5f;
-                        sg = fmaxf(rho, fminf(a, cap));
-                    }
+                    float sg = or_dist_step(s->bounded, x, d, r, (float)g * vG);
                     step = op->dist_rule == 1 ? fmaxf(sg, s_O) : sg;
                 }
             }
@@ -899,8 +926,10 @@ void or_adam_step(double* p, const double* g, double* m, double* v, int64_t n, d
  *   h1 = relu(W0 e + b0), h2 = relu(W1 h1 + b1), z = W2 h2 + b2,
  *   t_near = t_scale sigmoid(z0), t_far = t_scale sigmoid(z1), A^ = sigmoid(z2).
  * Parameters, flat: W0 [W][6], b0 [W], W1 [W][W], b1 [W], W2 [3][W], b2 [3].
- * Loss per ray: A* (sl1((t_near - t_near*)/t_scale) + sl1((t_far - t_far*)/t_scale))
- * + (A^ - A*)^2, sl1 = smooth L1 with beta = 0.01. */
+ * Loss per ray: A* (a_n sl1((t_near - t_near*)/t_scale) + a_f sl1((t_far - t_far*)/t_scale))
+ * + (A^ - A*)^2, sl1 = smooth L1 with beta = 0.01, a_n = 4 when t_near is late
+ * (> target) else 1, a_f = 4 when t_far is early (< target) else 1: intervals err
+ * on the wide side, where a miss costs marching points instead of opacity. */
 
 #define OR_PROP_IN 6
 
@@ -981,11 +1010,13 @@ double or_prop_loss_grad(const double* w, int W, const float* rays_o, const floa
         const double *tg = targets + 3 * i;
         double s0 = or_sigmoid(z[0]), s1 = or_sigmoid(z[1]), s2 = or_sigmoid(z[2]);
         double x0 = (t_scale * s0 - tg[0]) / t_scale, x1 = (t_scale * s1 - tg[1]) / t_scale;
-        double L = tg[2] * (or_sl1(x0, beta) + or_sl1(x1, beta)) + (s2 - tg[2]) * (s2 - tg[2]);
+        /* conservative intervals: a late t_near or an early t_far costs 4x */
+        double an = x0 > 0 ? 4.0 : 1.0, af = x1 < 0 ? 4.0 : 1.0;
+        double L = tg[2] * (an * or_sl1(x0, beta) + af * or_sl1(x1, beta)) + (s2 - tg[2]) * (s2 - tg[2]);
         total += L * inv_n;
         double gz[3];
-        gz[0] = inv_n * tg[2] * or_sl1_grad(x0, beta) * s0 * (1 - s0);
-        gz[1] = inv_n * tg[2] * or_sl1_grad(x1, beta) * s1 * (1 - s1);
+        gz[0] = inv_n * tg[2] * an * or_sl1_grad(x0, beta) * s0 * (1 - s0);
+        gz[1] = inv_n * tg[2] * af * or_sl1_grad(x1, beta) * s1 * (1 - s1);
         gz[2] = inv_n * 2.0 * (s2 - tg[2]) * s2 * (1 - s2);
         double gh2[256], ga2[256], gh1[256], ga1[256];
         for (int k = 0; k < W; ++k) gh2[k] = 0.0;

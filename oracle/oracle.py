@@ -367,3 +367,14 @@ def _prop_targets(self, opts, cams=None, pix=None, rays_o=None, rays_d=None, W=N
 
 
 Oracle.prop_targets = _prop_targets
+
+
+def dist_step(x, d, rho, bounded=False):
+    """World length of the distance step (Eq. 9) from points x along unit d for
+    contracted radii rho (FP32, as the march takes it)."""
+    x = _c(x, np.float32).reshape(-1, 3)
+    d = _c(d, np.float32).reshape(-1, 3)
+    rho = _c(rho, np.float32).reshape(-1)
+    out = np.empty(len(x), np.float32)
+    lib().or_dist_step_batch(C.c_int(1 if bounded else 0), _p(x), _p(d), _p(rho), C.c_int(len(x)), _p(out))
+    return out

@@ -123,7 +123,8 @@ __device__ __forceinline__ void march_point(int bounded, const float o[3], const
     for (int a = 0; a < 3; ++a) x[a] = fadd(o[a], fmul(t, d[a]));
     r = fsqrt(dot3(x, x));
     if (!bounded && r > 1.0f) {
-        float k = fdiv(fsub(2.0f, fdiv(1.0f, r)), r);
+        const float ir = fdiv(1.0f, r);
+        const float k = fmul(fsub(2.0f, ir), ir);  // (2 - 1/r) / r
 #pragma unroll
         for (int a = 0; a < 3; ++a) y[a] = fmul(x[a], k);
     } else {
@@ -243,7 +244,7 @@ __device__ __forceinline__ float sigmoidf_(float x) { return 1.0f / (1.0f + expf
 
 // Attention gate sigma(x) = 1 / (1 + e^-x) with the hardware exponential and
 // reciprocal (relative error ~1e-6; the gates only scale feature values).
-__device__ __forceinline__ float gate_sigmoid(float x) { return __frcp_rn(1.0f + __expf(-x)); }
+__device__ __forceinline__ float gate_sigmoid(float x) { return __fdividef(1.0f, 1.0f + __expf(-x)); }
 
 // Real spherical harmonics, bands 0..3, order l^2 + l + m, no Condon-Shortley
 // phase, orthonormal on the sphere (Cartesian polynomial form).

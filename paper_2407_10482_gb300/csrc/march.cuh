@@ -14,7 +14,7 @@
 // Occupancy hint for the march kernel (blocks of 128 threads per SM the register
 // allocation must allow) and the warp's pixel tile (TILE_W x 32/TILE_W).
 #ifndef NGPRT_MARCH_MIN_BLOCKS
-#define NGPRT_MARCH_MIN_BLOCKS 4
+#define NGPRT_MARCH_MIN_BLOCKS 8
 #endif
 #ifndef NGPRT_TILE_W
 #define NGPRT_TILE_W 4
@@ -214,6 +214,25 @@ __device__ __forceinline__ void sample_features(const Grid& g, const float u[3],
     }
 }
 
+// World length of a step whose contracted image stays within rho of its start (so
+// a step of rho = v G cannot enter an occupied voxel, Eq. 9).  Within the box or
+// the unit ball, and as a floor, rho itself (the contraction is 1-Lipschitz).
+// Beyond the unit ball the image moves at |J d| <= sqrt(1/r^4 + (2r-1)^2 b^2 / r^6)
+// with b = |x x d| (the ray's distance from the origin); that bound falls with r,
+// and a step of at most (r-1)/2 keeps the radius >= max((r+1)/2, b).
+__device__ __forceinline__ float dist_step(int bounded, const float x[3], const float d[3], float r, float rho) {
+    if (bounded || !(r > 1.0f)) return rho;
+    const float cx = fsub(fmul(x[1], d[2]), fmul(x[2], d[1]));
+    const float cy = fsub(fmul(x[2], d[0]), fmul(x[0], d[2]));
+    const float cz = fsub(fmul(x[0], d[1]), fmul(x[1], d[0]));
+    const float b2 = fadd(fadd(fmul(cx, cx), fmul(cy, cy)), fmul(cz, cz));
+    const float rl = fmaxf(fmul(fadd(r, 1.0f), 0.5f), fsqrt(b2));
+    const float q = fdiv(fsub(fmul(2.0f, rl), 1.0f), rl);
+    const float s_dir = fdiv(fmul(rho, fmul(rl, rl)), fsqrt(fadd(1.0f, fmul(fmul(q, q), b2))));
+    const float cap = fmul(fsub(r, 1.0f), 0.5f);
+    return fmaxf(rho, fminf(s_dir, cap));
+}
+
 // Position of a ray's march between calls: the current point t, the domain end,
 // the lattice origin and index (lattice_snap), and the counters.
 struct MarchState {
@@ -275,10 +294,12 @@ __device__ __forceinline__ bool march_advance(const MarchParams& p, const float 
         if (bounded || !(r > 1.0f)) {
             v[0] = d[0]; v[1] = d[1]; v[2] = d[2];
         } else {
-            const float kk = fdiv(fsub(2.0f, fdiv(1.0f, r)), r);
+            // J(x) d = k d + m x, k = (2 - 1/r)/r, m = (x.d) 2 (1 - r) / r^4
+            const float ir = fdiv(1.0f, r);
+            const float kk = fmul(fsub(2.0f, ir), ir);
             const float px = dot3(x, d);
-            const float r2 = fmul(r, r);
-            const float m = fdiv(fmul(px, fmul(2.0f, fsub(1.0f, r))), fmul(r2, r2));
+            const float ir2 = fmul(ir, ir);
+            const float m = fmul(fmul(px, fmul(2.0f, fsub(1.0f, r))), fmul(ir2, ir2));
 #pragma unroll
             for (int a = 0; a < 3; ++a) v[a] = fadd(fmul(kk, d[a]), fmul(m, x[a]));
         }
@@ -298,14 +319,7 @@ __device__ __forceinline__ bool march_advance(const MarchParams& p, const float 
             const int g0 = occ_vox(u[0], R_O), g1 = occ_vox(u[1], R_O), g2 = occ_vox(u[2], R_O);
             const int gv = __ldg(p.occ.dist + ((size_t)g0 + (size_t)R_O * ((size_t)g1 + (size_t)R_O * g2)));
             if (gv > 0) {
-                const float rho = fmul((float)gv, vG);
-                float sg = rho;
-                if (!bounded && r > 1.0f) {
-                    const float r1 = fadd(r, 1.0f);
-                    const float a = fdiv(fmul(fmul(r1, r1), rho), fmul(4.0f, r));
-                    const float cap = fmul(fsub(r, 1.0f), 0.5f);
-                    sg = fmaxf(rho, fminf(a, cap));
-                }
+                const float sg = dist_step(bounded, x, d, r, fmul((float)gv, vG));
                 step = op.dist_rule == 1 ? fmaxf(sg, s_O) : sg;
             }
         }
@@ -370,6 +384,13 @@ struct ForwardSampler {
     float Cd[3], F[4];
     __device__ __forceinline__ ForwardSampler(const Grid& g_, int mode, float term, float* gate_buf)
         : g(g_), attn_mode(mode), t_term(term), gates(gate_buf), T(1.0f), A(0.0f), depth(0.0f) {
+        Cd[0] = Cd[1] = Cd[2] = 0.0f;
+        F[0] = F[1] = F[2] = F[3] = 0.0f;
+    }
+    __device__ __forceinline__ void reset() {
+        T = 1.0f;
+        A = 0.0f;
+        depth = 0.0f;
         Cd[0] = Cd[1] = Cd[2] = 0.0f;
         F[0] = F[1] = F[2] = F[3] = 0.0f;
     }

@@ -133,9 +133,11 @@ __global__ void __launch_bounds__(128) propose_backward_kernel(const __grid_cons
         const float t0 = p.targets[3 * ray], t1 = p.targets[3 * ray + 1], A = p.targets[3 * ray + 2];
         const float s0 = psig(z[0]), s1 = psig(z[1]), s2 = psig(z[2]);
         const float x0 = (p.t_scale * s0 - t0) / p.t_scale, x1 = (p.t_scale * s1 - t1) / p.t_scale;
-        L = inv_n * (A * (sl1(x0, beta) + sl1(x1, beta)) + (s2 - A) * (s2 - A));
-        gz[0] = inv_n * A * sl1_grad(x0, beta) * s0 * (1.0f - s0);
-        gz[1] = inv_n * A * sl1_grad(x1, beta) * s1 * (1.0f - s1);
+        // conservative intervals: a late t_near or an early t_far costs 4x
+        const float a0 = x0 > 0.0f ? 4.0f : 1.0f, a1 = x1 < 0.0f ? 4.0f : 1.0f;
+        L = inv_n * (A * (a0 * sl1(x0, beta) + a1 * sl1(x1, beta)) + (s2 - A) * (s2 - A));
+        gz[0] = inv_n * A * a0 * sl1_grad(x0, beta) * s0 * (1.0f - s0);
+        gz[1] = inv_n * A * a1 * sl1_grad(x1, beta) * s1 * (1.0f - s1);
         gz[2] = inv_n * 2.0f * (s2 - A) * s2 * (1.0f - s2);
     }
     const int lane = threadIdx.x & 31;

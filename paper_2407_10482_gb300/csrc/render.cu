@@ -251,6 +251,45 @@ void launch_mlp(int width, int layers, const MlpParams& p, cudaStream_t st) {
     }
 }
 
+bool mlp_tc_supports(int width, int layers);
+void launch_mlp_tc(int width, int layers, const float* state, const void* w, const float bg[3], int64_t n, float* rgb,
+                   float* depth, float* opacity, cudaStream_t st);
+
+// Deferred MLP stage: FP32 weights on the CUDA cores, FP16 weights on the tensor cores.
+int32_t launch_shade(const ngprt_scene* scene, const float* state, int64_t n, const float bg[3], float* rgb,
+                     float* depth, float* opacity, cudaStream_t st, const char* fn) {
+    if (scene->mlp_dtype == NGPRT_F16) {
+        if (!mlp_tc_supports(scene->mlp_width, scene->mlp_layers)) {
+            set_error("%s: FP16 MLP %d layers x %d not built (2 or 3 layers, width 16/32/64)", fn, scene->mlp_layers,
+                      scene->mlp_width);
+            return NGPRT_ERR_UNSUPPORTED;
+        }
+        launch_mlp_tc(scene->mlp_width, scene->mlp_layers, state, scene->mlp_w, bg, n, rgb, depth, opacity, st);
+        return NGPRT_OK;
+    }
+    if (scene->mlp_dtype != NGPRT_F32) {
+        set_error("%s: mlp_dtype=%d (F32 or F16)", fn, scene->mlp_dtype);
+        return NGPRT_ERR_INVALID_ARG;
+    }
+    if (!mlp_supports(scene->mlp_width, scene->mlp_layers)) {
+        set_error("%s: MLP %d layers x %d not built (2 or 3 layers, width 16/32/64)", fn, scene->mlp_layers,
+                  scene->mlp_width);
+        return NGPRT_ERR_UNSUPPORTED;
+    }
+    MlpParams m;
+    m.state = state;
+    m.w = static_cast<const float*>(scene->mlp_w);
+    m.bg[0] = bg[0];
+    m.bg[1] = bg[1];
+    m.bg[2] = bg[2];
+    m.n = n;
+    m.rgb = rgb;
+    m.depth = depth;
+    m.opacity = opacity;
+    launch_mlp(scene->mlp_width, scene->mlp_layers, m, st);
+    return NGPRT_OK;
+}
+
 // Shared by the forward and backward entry points: validates the ray source and
 // fills the ray part of MarchParams; returns the launch grid.
 int32_t setup_rays(MarchParams& p, const ngprt_camera* cams, int32_t n_cams, const int32_t* pixel_ids,
@@ -317,6 +356,12 @@ static size_t state_bytes(int64_t n) { return ((size_t)n * NGPRT_STATE_FLOATS * 
 extern "C" size_t ngprt_render_workspace_bytes(const ngprt_scene* scene, int64_t n_rays) {
     (void)scene;
     if (n_rays < 0) return 0;
+    return state_bytes(n_rays) + 256;
+}
+
+extern "C" size_t ngprt_wavefront_workspace_bytes(const ngprt_scene* scene, int64_t n_rays) {
+    (void)scene;
+    if (n_rays < 0) return 0;
     return state_bytes(n_rays) + wavefront_bytes(n_rays) + 256;
 }
 
@@ -336,12 +381,8 @@ extern "C" int32_t ngprt_render(const ngprt_scene* scene, const ngprt_occ* occ, 
     NGPRT_REQUIRE(n_rays == 0 || rgb != nullptr || ray_state != nullptr, "%s: rgb and ray_state both NULL", fn);
     NGPRT_REQUIRE(march_supports(scene->L), "%s: no kernel for L=%d (built: 1, 2, 3, 4, 8, 16)", fn, scene->L);
     if (!march_supports(scene->L)) return NGPRT_ERR_UNSUPPORTED;
-    NGPRT_REQUIRE(scene->mlp_dtype == NGPRT_F32, "%s: mlp_dtype must be F32", fn);
-    if (!mlp_supports(scene->mlp_width, scene->mlp_layers)) {
-        set_error("%s: MLP %d layers x %d not built (2 or 3 layers, width 16/32/64)", fn, scene->mlp_layers,
-                  scene->mlp_width);
-        return NGPRT_ERR_UNSUPPORTED;
-    }
+    NGPRT_REQUIRE(scene->mlp_dtype == NGPRT_F32 || scene->mlp_dtype == NGPRT_F16, "%s: mlp_dtype=%d", fn,
+                  scene->mlp_dtype);
     dim3 grid;
     if ((rc = setup_rays(p, cams, n_cams, pixel_ids, rays_o, rays_d, n_rays, grid, fn)) != NGPRT_OK) return rc;
     if (n_rays == 0) return NGPRT_OK;
@@ -371,17 +412,7 @@ extern "C" int32_t ngprt_render(const ngprt_scene* scene, const ngprt_occ* occ, 
         if ((rc = launch_march_any(scene->L, scene->table_dtype, p, grid, st)) != NGPRT_OK) return rc;
     }
     if (!rgb) return cuda_status(fn);
-    MlpParams m;
-    m.state = state;
-    m.w = static_cast<const float*>(scene->mlp_w);
-    m.bg[0] = opts->bg[0];
-    m.bg[1] = opts->bg[1];
-    m.bg[2] = opts->bg[2];
-    m.n = n_rays;
-    m.rgb = rgb;
-    m.depth = depth;
-    m.opacity = opacity;
-    launch_mlp(scene->mlp_width, scene->mlp_layers, m, st);
+    if ((rc = launch_shade(scene, state, n_rays, opts->bg, rgb, depth, opacity, st, fn)) != NGPRT_OK) return rc;
     return cuda_status(fn);
 }
 
@@ -408,26 +439,11 @@ extern "C" int32_t ngprt_shade(const ngprt_scene* scene, const float* ray_state,
     NGPRT_REQUIRE(n_rays >= 0, "%s: n_rays=%lld", fn, (long long)n_rays);
     NGPRT_REQUIRE(n_rays == 0 || (ray_state && rgb), "%s: ray_state and rgb required", fn);
     NGPRT_REQUIRE(bg != nullptr, "%s: bg is NULL", fn);
-    NGPRT_REQUIRE(scene->mlp_dtype == NGPRT_F32, "%s: mlp_dtype must be F32", fn);
     NGPRT_REQUIRE(((uintptr_t)scene->mlp_w & 15) == 0 && ((uintptr_t)ray_state & 15) == 0,
                   "%s: mlp_w and ray_state must be 16-byte aligned", fn);
-    if (!mlp_supports(scene->mlp_width, scene->mlp_layers)) {
-        set_error("%s: MLP %d layers x %d not built (2 or 3 layers, width 16/32/64)", fn, scene->mlp_layers,
-                  scene->mlp_width);
-        return NGPRT_ERR_UNSUPPORTED;
-    }
     if (n_rays == 0) return NGPRT_OK;
-    MlpParams m;
-    m.state = ray_state;
-    m.w = static_cast<const float*>(scene->mlp_w);
-    m.bg[0] = bg[0];
-    m.bg[1] = bg[1];
-    m.bg[2] = bg[2];
-    m.n = n_rays;
-    m.rgb = rgb;
-    m.depth = depth;
-    m.opacity = opacity;
-    launch_mlp(scene->mlp_width, scene->mlp_layers, m, static_cast<cudaStream_t>(stream));
+    int32_t rc = launch_shade(scene, ray_state, n_rays, bg, rgb, depth, opacity, static_cast<cudaStream_t>(stream), fn);
+    if (rc != NGPRT_OK) return rc;
     return cuda_status(fn);
 }
 

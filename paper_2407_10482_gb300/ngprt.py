@@ -61,6 +61,7 @@ _SIGS = {
     "ngprt_build_occ_dist": (C.c_int32, [_P, C.c_int32, C.c_int32, _P, _P, _P, C.c_size_t, _P]),
     "ngprt_table_entries": (C.c_int64, [_P]),
     "ngprt_render_workspace_bytes": (C.c_size_t, [_P, C.c_int64]),
+    "ngprt_wavefront_workspace_bytes": (C.c_size_t, [_P, C.c_int64]),
     "ngprt_render": (C.c_int32, [_P, _P, _P, C.c_int32, _P, _P, _P, C.c_int64, _P, _P, _P, _P, _P, _P, _P,
                                  _P, C.c_size_t, _P]),
     "ngprt_render_backward": (C.c_int32, [_P, _P, _P, C.c_int32, _P, _P, _P, C.c_int64, _P, _P, _P, _P, _P,
@@ -81,6 +82,8 @@ _SIGS = {
     "ngprt_render_noalloc_max_rays": (C.c_int64, []),
     "ngprt_render_noalloc": (C.c_int32, [_P, _P, _P, C.c_int32, _P, _P, _P, C.c_int64, _P, _P, _P, _P, _P, _P,
                                          _P]),
+    "ngprt_tensor_core_error": (C.c_int32, []),
+    "ngprt_gather_bench": (C.c_int32, [_P, C.c_int32, C.c_int64, C.c_int64, C.c_int32, C.c_uint32, _P, _P]),
     "ngprt_last_error": (C.c_char_p, []),
     "ngprt_version": (C.c_int32, []),
 }
@@ -153,6 +156,10 @@ def ngprt_table_entries(scene: ngprt_scene) -> int:
 
 def ngprt_render_workspace_bytes(scene: ngprt_scene, n_rays: int) -> int:
     return int(lib().ngprt_render_workspace_bytes(C.byref(scene), n_rays))
+
+
+def ngprt_wavefront_workspace_bytes(scene: ngprt_scene, n_rays: int) -> int:
+    return int(lib().ngprt_wavefront_workspace_bytes(C.byref(scene), n_rays))
 
 
 def cameras_struct(cams: np.ndarray, W: int, H: int):
@@ -247,6 +254,11 @@ def ngprt_render_noalloc(scene, occ, cams, n_cams, pixel_ids, rays_o, rays_d, n_
         _ptr(t_interval), C.byref(opts), _ptr(rgb), _ptr(depth), _ptr(opacity), _ptr(ray_stats), _stream(stream)))
 
 
+def ngprt_gather_bench(table, dtype, n_rows, n_threads, per_thread, seed, sink, stream=None) -> None:
+    _check("ngprt_gather_bench", lib().ngprt_gather_bench(_ptr(table), dtype, n_rows, n_threads, per_thread, seed,
+                                                          _ptr(sink), _stream(stream)))
+
+
 def ngprt_grid_indices(scene, u, n, idx_out, stream=None) -> None:
     _check("ngprt_grid_indices", lib().ngprt_grid_indices(C.byref(scene), _ptr(u), n, _ptr(idx_out),
                                                            _stream(stream)))
@@ -273,13 +285,15 @@ class DeviceScene:
     ``tables``/``coarse`` are uploaded in ``table_dtype`` (F32, F16 or BF16; the
     16-bit forms round to nearest even from the FP32 master)."""
 
-    def __init__(self, cfg, tables, coarse, mlp_w, table_dtype: int = F32, device="cuda"):
+    def __init__(self, cfg, tables, coarse, mlp_w, table_dtype: int = F32, device="cuda", mlp_dtype: int = F32):
         dt = _TORCH_DT[table_dtype]
         self.cfg = cfg
         self.table_dtype = table_dtype
+        self.mlp_dtype = mlp_dtype
         self.tables = torch.as_tensor(np.asarray(tables, np.float32)).to(device=device, dtype=dt).contiguous()
         self.coarse = torch.as_tensor(np.asarray(coarse, np.float32)).to(device=device, dtype=dt).contiguous()
-        self.mlp_w = torch.as_tensor(np.asarray(mlp_w, np.float32)).to(device).contiguous()
+        self.mlp_w = torch.as_tensor(np.asarray(mlp_w, np.float32)).to(device=device,
+                                                                        dtype=_TORCH_DT[mlp_dtype]).contiguous()
         self.refresh()
 
     def refresh(self) -> None:
@@ -289,7 +303,7 @@ class DeviceScene:
         for i, n in enumerate(c.N):
             s.N[i] = int(n)
         s.table_dtype, s.R_C = self.table_dtype, c.R_C
-        s.mlp_layers, s.mlp_width, s.mlp_dtype = c.mlp_layers, c.mlp_width, F32
+        s.mlp_layers, s.mlp_width, s.mlp_dtype = c.mlp_layers, c.mlp_width, self.mlp_dtype
         s.bounded = 1 if c.bounded else 0
         s.tables, s.coarse, s.mlp_w = _ptr(self.tables), _ptr(self.coarse), _ptr(self.mlp_w)
         self.struct = s

@@ -252,7 +252,7 @@ def test_wavefront_equals_fused_bit_for_bit(ng, cfg_name):
         for wavefront in (True, False):
             st = torch.empty(n, ng.STATE_FLOATS, device="cuda")
             stats = torch.empty(n, 2, dtype=torch.int32, device="cuda")
-            ws = torch.empty(ng.ngprt_render_workspace_bytes(ds.struct, n), dtype=torch.uint8, device="cuda") \
+            ws = torch.empty(ng.ngprt_wavefront_workspace_bytes(ds.struct, n), dtype=torch.uint8, device="cuda") \
                 if wavefront else None
             ng.ngprt_render(ds.struct, docc.struct, cams, nc, None, None, None, n, None, opts, None, ray_stats=stats,
                             ray_state=st, workspace=ws)

@@ -416,3 +416,34 @@ def test_parameter_count_formula_eq_s1():
     assert round(n / 1e6, 2) == g["ours_M"]
     merf = 8 * (0.02 * 512 ** 3 + 3 * 2048 ** 2)
     assert round(merf / 1e6, 1) == g["merf_M"]
+
+
+def test_contracted_distance_step_stays_within_rho():
+    """Safety of the unbounded distance step: along the whole world segment the
+    mip-NeRF-360 image moves less than rho from its start (dense sampling, FP64),
+    and the step is never shorter than rho."""
+    rng = np.random.default_rng(21)
+    n = 3000
+    r = rng.uniform(1.0, 14.0, n)
+    dirx = rng.normal(size=(n, 3))
+    dirx /= np.linalg.norm(dirx, axis=1, keepdims=True)
+    x = (dirx * r[:, None]).astype(np.float32)
+    d = rng.normal(size=(n, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    d = d.astype(np.float32)
+    rho = rng.uniform(0.005, 0.5, n).astype(np.float32)
+    s = O.dist_step(x, d, rho).astype(np.float64)
+    assert np.all(s >= rho * (1 - 1e-6))
+
+    def contract(p):
+        rr = np.linalg.norm(p, axis=-1, keepdims=True)
+        return np.where(rr <= 1, p, (2 - 1 / np.maximum(rr, 1e-12)) * p / np.maximum(rr, 1e-12))
+
+    tau = np.linspace(0, 1, 801)
+    pts = x[:, None, :].astype(np.float64) + (s[:, None] * tau[None, :])[..., None] * d[:, None, :]
+    y = contract(pts)
+    disp = np.linalg.norm(y - y[:, :1, :], axis=-1).max(1)
+    assert np.all(disp <= rho * (1 + 1e-4) + 1e-7)
+    # the bound pays off for rays aimed near the centre: much longer than rho
+    central = np.abs(np.sum(dirx * d, 1)) > 0.99
+    assert np.median(s[central] / rho[central]) > 2.0
