@@ -32,6 +32,9 @@ sys.path.insert(0, ROOT)
 from paper_2407_10482_gb300 import scenes as S  # noqa: E402
 
 METRIC = "1080p frames/s & Grays/s, plain FP32 vs FP16+proposal at ≤0.1 dB PSNR loss"
+# DRAM bytes (read + write) of one march_kernel<16,F32> launch on this frame, from the
+# ncu capture summarised in profiles/march_kernel_hd_1080p_fp32.md (3.581 GB + 0.920 GB)
+MARCH_DRAM_BYTES = 4.500846e9
 WORKLOAD = "hd 1920x1080 unbounded-360 synthetic scene, L=16 (16..4096), T=2^19, 128^3 occupancy+G, MLP 23-64-64-3"
 
 
@@ -298,7 +301,44 @@ def other_forms(args, cfg, scene, ds, docc, cams, opts, dev, stream, flush, plai
         gcl[name + "_GBps"] = nthr * per * (32 if dt == 0 else 16) / (ms_g * 1e-3) / 1e9
         del tab
     res["gather_ceiling"] = gcl
+    if not args.no_paper_shape:
+        res["paper_shape"] = paper_shape(args, dev, stream, flush)
     return res
+
+
+def paper_shape(args, dev, stream, flush):
+    """The paper's render-time shape (L = 2, 3, 4 fine levels at 1024 * 2^l, T = 2^22,
+    512^3 coarse grid, 512^3 occupancy with 5 levels; Tables 2 and 4) on the hd scene:
+    1080p frames/s in FP32 and FP16, and marching / occupied points per ray with and
+    without G.  The paper's numbers (RTX 3090, Mip-NeRF 360): 108 / 79.7 / 61.8 fps."""
+    import torch
+    from paper_2407_10482_gb300 import ngprt as ng
+    out = {}
+    for L in (2, 3, 4):
+        cfg = S.paper_config(L)
+        sc = S.make_scene_torch(cfg, device=dev)
+        docc = ng.DeviceOcc(sc.occ, cfg.R_O, cfg.n_occ_levels, device=dev)
+        opts = S.default_options(cfg)
+        cams = S.orbit_cameras(cfg, 1)
+        n = cfg.W * cfg.H
+        row = {}
+        for dt in (0, 1):
+            ds = ng.DeviceScene(cfg, sc.tables, sc.coarse, sc.mlp_w, table_dtype=dt, mlp_dtype=dt, device=dev)
+            rend = ng.Renderer(ds, docc, device=dev)
+            o = rend.render(opts, cams=cams, W=cfg.W, H=cfg.H, stats=True)
+            ms = _timed(lambda: rend.render(opts, cams=cams, W=cfg.W, H=cfg.H, out=o), stream, flush, 5, 3)
+            row["fp32" if dt == 0 else "fp16_tc"] = {"ms_per_frame": ms, "frames_per_s": 1000.0 / ms}
+            if dt == 0:
+                st = o["stats"].float().mean(0)
+                st0 = rend.render(opts, cams=cams, W=cfg.W, H=cfg.H, stats=True, use_dist=False)["stats"].float().mean(0)
+                row["marching_per_ray"] = {"with_G": float(st[0]), "without_G": float(st0[0])}
+                row["occupied_per_ray"] = {"with_G": float(st[1]), "without_G": float(st0[1])}
+            del ds, rend, o
+        out[f"L{L}"] = row
+        del sc, docc
+        torch.cuda.empty_cache()
+    out["config"] = "N_l = 1024 * 2^l, T = 2^22, R_C = 512 dense (8 + 2L channels), R_O = 512 (5 levels), G at 512^3"
+    return out
 
 
 def main():
@@ -313,6 +353,7 @@ def main():
     ap.add_argument("--mlp-dtype", type=int, default=0, help="0 F32 (CUDA cores), 1 F16 (tensor cores)")
     ap.add_argument("--engine", default="fused", choices=["wavefront", "fused"])
     ap.add_argument("--plain-only", action="store_true", help="time only the plain FP32 frame")
+    ap.add_argument("--no-paper-shape", action="store_true", help="skip the paper-shaped L = 2, 3, 4 frames")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -466,7 +507,9 @@ def main():
                        "march_fused_engine": statistics.mean(fused), "engine": args.engine},
         "march_stats": march_stats,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                     "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": "march_kernel<16,F32> (fused march: occupancy, coarse fetch, 16-level gathers, attention, compositing)",
+                     "frac": achieved / peaks["hbm_gbs"],
+                     "traffic": MARCH_DRAM_BYTES if (args.table_dtype == 0 and args.engine == "fused") else None,
+                     "traffic_unit": "bytes per launch (ncu dram__bytes_read + write)", "kernel": "march_kernel<16,F32> (fused march: occupancy, coarse fetch, 16-level gathers, attention, compositing)",
                      "peak_source": peaks["source"],
                      "bytes_per_sample": bytes_per_sample,
                      "note": "algorithmic gather bytes (L*8 entries + 8 coarse vertices per sample, 2 B per "

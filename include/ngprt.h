@@ -212,12 +212,14 @@ int32_t ngprt_render_backward(const ngprt_scene* scene, const ngprt_occ* occ, co
  * ------------------------------------------------------------------------------ */
 int32_t ngprt_proposal_param_count(void);
 
-/* Interval per ray, t_interval_out [n][2] = (t_near - margin, t_far + margin); a ray
- * with A^ < a_min gets an empty interval (+inf, -inf) (nothing is marched), a ray with
+/* Interval per ray, t_interval_out [n][2] = (t_near - margin_near, t_far + margin_far)
+ * (margin_far = +inf: no far clip, early termination ends the ray); a ray with
+ * A^ < a_min gets an empty interval (+inf, -inf) (nothing is marched), a ray with
  * t_far <= t_near gets (-inf, +inf) (the whole ray).  a_hat_out [n] (NULL allowed). */
 int32_t ngprt_propose(const float* prop_w, const ngprt_camera* cams, int32_t n_cams, const int32_t* pixel_ids,
                       const float* rays_o, const float* rays_d, int64_t n_rays, float in_scale, float t_scale,
-                      float margin, float a_min, float* t_interval_out, float* a_hat_out, void* stream);
+                      float margin_near, float margin_far, float a_min, float* t_interval_out, float* a_hat_out,
+                      void* stream);
 
 /* Training loss of the proposal against targets [n][3] = (t_near*, t_far*, A*):
  * mean over rays of A* (a_n sl1(dt_near / t_scale) + a_f sl1(dt_far / t_scale)) +

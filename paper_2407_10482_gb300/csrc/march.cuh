@@ -134,7 +134,9 @@ constexpr int kLevelUnroll = NGPRT_LEVEL_UNROLL;
 // Eq. 6-8 at unit-cube position u: f = f~ + Att(f^1..f^L; a).  The coarse fetch
 // interpolates the 8 + 2L channels of the coarse grid; the 2L attention gates
 // (sigmoid of the interpolated logits) are parked in shared memory, gates[k*stride],
-// so that the level loop need not be unrolled.
+// so that the level loop need not be unrolled.  FP32 and BF16 tables interpolate
+// in FP32; FP16 tables interpolate in packed half2 FMAs (FP16 products and sums,
+// one conversion per channel), the rest of the sample in FP32.
 template <int L, int DT>
 __device__ __forceinline__ void sample_features(const Grid& g, const float u[3], int attn_mode, float f[8],
                                                 float* gates, int stride) {
@@ -144,18 +146,38 @@ __device__ __forceinline__ void sample_features(const Grid& g, const float u[3],
 #pragma unroll
     for (int a = 0; a < 3; ++a) grid_cell(u[a], g.R_C, b[a], w[a]);
     float2 acc[NC / 2];
-#pragma unroll
-    for (int ch = 0; ch < NC / 2; ++ch) acc[ch] = make_float2(0.0f, 0.0f);
     const uint32_t R = (uint32_t)g.R_C;
+    if constexpr (DT == NGPRT_F16) {
+        // FP16 tables: trilinear sums in packed half2 FMAs, converted once
+        __half2 hacc[NC / 2];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        const uint32_t v = (uint32_t)(b[0] + (c & 1)) + R * ((uint32_t)(b[1] + ((c >> 1) & 1)) + R * (uint32_t)(b[2] + ((c >> 2) & 1)));
-        float val[NC];
-        load_channels<DT, NC>(g.coarse, v, val);
-        const float cw = corner_w(w, c);
-        const float2 cw2 = make_float2(cw, cw);
+        for (int ch = 0; ch < NC / 2; ++ch) hacc[ch] = __float2half2_rn(0.0f);
 #pragma unroll
-        for (int ch = 0; ch < NC / 2; ++ch) acc[ch] = ffma2(cw2, make_float2(val[2 * ch], val[2 * ch + 1]), acc[ch]);
+        for (int c = 0; c < 8; ++c) {
+            const uint32_t v = (uint32_t)(b[0] + (c & 1)) + R * ((uint32_t)(b[1] + ((c >> 1) & 1)) + R * (uint32_t)(b[2] + ((c >> 2) & 1)));
+            const uint32_t* p32 = static_cast<const uint32_t*>(g.coarse) + (size_t)v * (NC / 2);
+            const __half2 cw2 = __float2half2_rn(corner_w(w, c));
+#pragma unroll
+            for (int ch = 0; ch < NC / 2; ++ch) {
+                const uint32_t q = __ldg(p32 + ch);
+                hacc[ch] = __hfma2(cw2, *reinterpret_cast<const __half2*>(&q), hacc[ch]);
+            }
+        }
+#pragma unroll
+        for (int ch = 0; ch < NC / 2; ++ch) acc[ch] = __half22float2(hacc[ch]);
+    } else {
+#pragma unroll
+        for (int ch = 0; ch < NC / 2; ++ch) acc[ch] = make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const uint32_t v = (uint32_t)(b[0] + (c & 1)) + R * ((uint32_t)(b[1] + ((c >> 1) & 1)) + R * (uint32_t)(b[2] + ((c >> 2) & 1)));
+            float val[NC];
+            load_channels<DT, NC>(g.coarse, v, val);
+            const float cw = corner_w(w, c);
+            const float2 cw2 = make_float2(cw, cw);
+#pragma unroll
+            for (int ch = 0; ch < NC / 2; ++ch) acc[ch] = ffma2(cw2, make_float2(val[2 * ch], val[2 * ch + 1]), acc[ch]);
+        }
     }
 #pragma unroll
     for (int ch = 0; ch < kNFeat / 2; ++ch) {
@@ -190,18 +212,36 @@ __device__ __forceinline__ void sample_features(const Grid& g, const float u[3],
         for (int c = 0; c < 8; ++c)
             rows[c] = level_row(g, l, (uint32_t)(bl[0] + (c & 1)), (uint32_t)(bl[1] + ((c >> 1) & 1)),
                                 (uint32_t)(bl[2] + ((c >> 2) & 1)));
-        float e[8][8];
-#pragma unroll
-        for (int c = 0; c < 8; ++c) load_entry<DT>(g.tables, rows[c], e[c]);
         float2 fl[4];
+        if constexpr (DT == NGPRT_F16) {
+            uint4 q[8];
 #pragma unroll
-        for (int ch = 0; ch < 4; ++ch) fl[ch] = make_float2(0.0f, 0.0f);
+            for (int c = 0; c < 8; ++c) q[c] = __ldg(static_cast<const uint4*>(g.tables) + rows[c]);
+            __half2 h[4];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const float cw = corner_w(wl, c);
-            const float2 cw2 = make_float2(cw, cw);
+            for (int ch = 0; ch < 4; ++ch) h[ch] = __float2half2_rn(0.0f);
 #pragma unroll
-            for (int ch = 0; ch < 4; ++ch) fl[ch] = ffma2(cw2, make_float2(e[c][2 * ch], e[c][2 * ch + 1]), fl[ch]);
+            for (int c = 0; c < 8; ++c) {
+                const __half2 cw2 = __float2half2_rn(corner_w(wl, c));
+                const __half2* e2 = reinterpret_cast<const __half2*>(&q[c]);
+#pragma unroll
+                for (int ch = 0; ch < 4; ++ch) h[ch] = __hfma2(cw2, e2[ch], h[ch]);
+            }
+#pragma unroll
+            for (int ch = 0; ch < 4; ++ch) fl[ch] = __half22float2(h[ch]);
+        } else {
+            float e[8][8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) load_entry<DT>(g.tables, rows[c], e[c]);
+#pragma unroll
+            for (int ch = 0; ch < 4; ++ch) fl[ch] = make_float2(0.0f, 0.0f);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const float cw = corner_w(wl, c);
+                const float2 cw2 = make_float2(cw, cw);
+#pragma unroll
+                for (int ch = 0; ch < 4; ++ch) fl[ch] = ffma2(cw2, make_float2(e[c][2 * ch], e[c][2 * ch + 1]), fl[ch]);
+            }
         }
         const float om = gates[(2 * l) * stride], be = gates[(2 * l + 1) * stride];
         f[0] = fmaf(om, fl[0].x, f[0]);

@@ -18,7 +18,7 @@ constexpr int kPParams = kPW * kPIn + kPW + kPW * kPW + kPW + 3 * kPW + 3;
 struct PropParams {
     MarchParams m;  // ray source only
     const float* w;
-    float in_scale, t_scale, margin, a_min;
+    float in_scale, t_scale, margin_near, margin_far, a_min;
     float* interval;
     float* a_hat;
     const float* targets;
@@ -91,8 +91,8 @@ __global__ void __launch_bounds__(128) propose_kernel(const __grid_constant__ Pr
         lo = -INFINITY;  // no usable interval: march the whole ray
         hi = INFINITY;
     } else {
-        lo = tn - p.margin;
-        hi = tf + p.margin;
+        lo = tn - p.margin_near;
+        hi = tf + p.margin_far;  // +inf: no far clip (termination ends the ray)
     }
     p.interval[2 * ray] = lo;
     p.interval[2 * ray + 1] = hi;
@@ -209,13 +209,14 @@ extern "C" int32_t ngprt_proposal_param_count(void) { return kPParams; }
 
 extern "C" int32_t ngprt_propose(const float* prop_w, const ngprt_camera* cams, int32_t n_cams,
                                  const int32_t* pixel_ids, const float* rays_o, const float* rays_d, int64_t n_rays,
-                                 float in_scale, float t_scale, float margin, float a_min, float* t_interval_out,
-                                 float* a_hat_out, void* stream) {
+                                 float in_scale, float t_scale, float margin_near, float margin_far, float a_min,
+                                 float* t_interval_out, float* a_hat_out, void* stream) {
     const char* fn = "ngprt_propose";
     PropParams p;
     memset(&p, 0, sizeof p);
     NGPRT_REQUIRE(prop_w != nullptr, "%s: prop_w is NULL", fn);
-    NGPRT_REQUIRE(n_rays >= 0 && in_scale > 0.0f && t_scale > 0.0f && margin >= 0.0f, "%s: bad scalar argument", fn);
+    NGPRT_REQUIRE(n_rays >= 0 && in_scale > 0.0f && t_scale > 0.0f && margin_near >= 0.0f && margin_far >= 0.0f,
+                  "%s: bad scalar argument", fn);
     dim3 grid;
     int32_t rc;
     if ((rc = setup_rays(p.m, cams, n_cams, pixel_ids, rays_o, rays_d, n_rays, grid, fn)) != NGPRT_OK) return rc;
@@ -224,7 +225,8 @@ extern "C" int32_t ngprt_propose(const float* prop_w, const ngprt_camera* cams, 
     p.w = prop_w;
     p.in_scale = in_scale;
     p.t_scale = t_scale;
-    p.margin = margin;
+    p.margin_near = margin_near;
+    p.margin_far = margin_far;
     p.a_min = a_min;
     p.interval = t_interval_out;
     p.a_hat = a_hat_out;

@@ -73,7 +73,7 @@ _SIGS = {
                                     C.c_int32, C.c_int32, _P]),
     "ngprt_proposal_param_count": (C.c_int32, []),
     "ngprt_propose": (C.c_int32, [_P, _P, C.c_int32, _P, _P, _P, C.c_int64, C.c_float, C.c_float, C.c_float,
-                                  C.c_float, _P, _P, _P]),
+                                  C.c_float, C.c_float, _P, _P, _P]),
     "ngprt_propose_backward": (C.c_int32, [_P, _P, C.c_int32, _P, _P, _P, C.c_int64, C.c_float, C.c_float, _P, _P,
                                            _P, _P]),
     "ngprt_proposal_targets": (C.c_int32, [_P, _P, _P, C.c_int32, _P, _P, _P, C.c_int64, _P, _P, _P, _P]),
@@ -213,11 +213,11 @@ def ngprt_proposal_param_count() -> int:
     return int(lib().ngprt_proposal_param_count())
 
 
-def ngprt_propose(prop_w, cams, n_cams, pixel_ids, rays_o, rays_d, n_rays, in_scale, t_scale, margin, a_min,
-                  t_interval_out, a_hat_out=None, stream=None) -> None:
+def ngprt_propose(prop_w, cams, n_cams, pixel_ids, rays_o, rays_d, n_rays, in_scale, t_scale, margin_near,
+                  margin_far, a_min, t_interval_out, a_hat_out=None, stream=None) -> None:
     _check("ngprt_propose", lib().ngprt_propose(
-        _ptr(prop_w), cams, n_cams, _ptr(pixel_ids), _ptr(rays_o), _ptr(rays_d), n_rays, in_scale, t_scale, margin,
-        a_min, _ptr(t_interval_out), _ptr(a_hat_out), _stream(stream)))
+        _ptr(prop_w), cams, n_cams, _ptr(pixel_ids), _ptr(rays_o), _ptr(rays_d), n_rays, in_scale, t_scale,
+        margin_near, margin_far, a_min, _ptr(t_interval_out), _ptr(a_hat_out), _stream(stream)))
 
 
 def ngprt_propose_backward(prop_w, cams, n_cams, pixel_ids, rays_o, rays_d, n_rays, in_scale, t_scale, targets,
@@ -279,6 +279,13 @@ def render_opts(o) -> ngprt_render_opts:
     return p
 
 
+def _device_array(a, dtype, device):
+    """A contiguous device tensor of `dtype` from a numpy array or a tensor."""
+    if isinstance(a, torch.Tensor):
+        return a.to(device=device, dtype=dtype).contiguous()
+    return torch.as_tensor(np.asarray(a, np.float32)).to(device=device, dtype=dtype).contiguous()
+
+
 class DeviceScene:
     """Scene arrays resident on the GPU plus the ngprt_scene struct pointing at them.
 
@@ -290,10 +297,9 @@ class DeviceScene:
         self.cfg = cfg
         self.table_dtype = table_dtype
         self.mlp_dtype = mlp_dtype
-        self.tables = torch.as_tensor(np.asarray(tables, np.float32)).to(device=device, dtype=dt).contiguous()
-        self.coarse = torch.as_tensor(np.asarray(coarse, np.float32)).to(device=device, dtype=dt).contiguous()
-        self.mlp_w = torch.as_tensor(np.asarray(mlp_w, np.float32)).to(device=device,
-                                                                        dtype=_TORCH_DT[mlp_dtype]).contiguous()
+        self.tables = _device_array(tables, dt, device)
+        self.coarse = _device_array(coarse, dt, device)
+        self.mlp_w = _device_array(mlp_w, _TORCH_DT[mlp_dtype], device)
         self.refresh()
 
     def refresh(self) -> None:
@@ -314,7 +320,8 @@ class DeviceOcc:
 
     def __init__(self, occ: np.ndarray, R: int, n_levels: int, with_dist: bool = True, device="cuda"):
         self.R, self.n_levels = R, n_levels
-        self.occ = torch.as_tensor(np.asarray(occ, np.uint8)).to(device).contiguous()
+        self.occ = (occ.to(device=device, dtype=torch.uint8) if isinstance(occ, torch.Tensor)
+                    else torch.as_tensor(np.asarray(occ, np.uint8)).to(device)).contiguous()
         self.bits = torch.empty(ngprt_occ_bits_words(R, n_levels), dtype=torch.int32, device=device)
         self.dist = torch.empty(R ** 3, dtype=torch.uint8, device=device) if with_dist else None
         ws = torch.empty(ngprt_build_occ_dist_workspace_bytes(R), dtype=torch.uint8, device=device)

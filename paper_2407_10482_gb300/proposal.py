@@ -25,7 +25,8 @@ from . import ngprt as ng
 class ProposalConfig:
     in_scale: float = 3.0      # origins are divided by this (the orbit radius)
     t_scale: float = 16.0      # t_near, t_far = t_scale * sigmoid(.)
-    margin: float = 0.05       # world units added on both sides of the interval
+    margin_near: float = 0.5   # world units the march starts before t_near
+    margin_far: float = float("inf")  # after t_far (inf: no far clip, termination ends the ray)
     a_min: float = 0.01        # predicted opacity below which nothing is marched
     fallback: float = 0.01     # re-march when a_hat - A(interval) exceeds this
     steps: int = 2000
@@ -118,8 +119,8 @@ class FastRenderer:
         ro = ng.render_opts(opts)
         c = self.cfg
         st = self.stats if stats else None
-        ng.ngprt_propose(self.w, cam_arr, n_cams, None, None, None, n, c.in_scale, c.t_scale, c.margin, c.a_min,
-                         self.interval, self.a_hat, stream=stream)
+        ng.ngprt_propose(self.w, cam_arr, n_cams, None, None, None, n, c.in_scale, c.t_scale, c.margin_near,
+                         c.margin_far, c.a_min, self.interval, self.a_hat, stream=stream)
         ng.ngprt_render(self.scene.struct, self.occ.struct, cam_arr, n_cams, None, None, None, n, self.interval, ro,
                         None, ray_stats=st, ray_state=self.state, workspace=self.ws if wavefront else None,
                         stream=stream)

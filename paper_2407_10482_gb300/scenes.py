@@ -288,3 +288,63 @@ def default_options(cfg: SceneConfig, **kw) -> RenderOptions:
     o = RenderOptions(step_base=cfg.step_base, t_min=cfg.t_min, r_far=cfg.r_far,
                       max_march=cfg.max_march, max_samples=cfg.max_samples)
     return replace(o, **kw)
+
+
+# ------------------------------------------------------------- paper-shaped scenes
+
+def paper_config(L: int = 2, **kw) -> SceneConfig:
+    """The paper's render-time shape (Sec. S2.1, S2.5; Tables 2 and 4): L fine levels
+    at 1024 * 2^l with T = 2^22, a 512^3 coarse grid (8 + 2L channels; the paper's is
+    sparse, this one dense), a 512^3 occupancy grid with 5 levels down to 32^3 and the
+    distance grid at the occupancy resolution; hd's unbounded blob scene and orbit."""
+    c = hd_config(name=f"paper_L{L}", L=L, N=[1024 * 2 ** l for l in range(L)], T_log2=22, R_C=512, R_O=512,
+                  n_occ_levels=5, seed=7)
+    return replace(c, **kw)
+
+
+def make_scene_torch(cfg: SceneConfig, device="cuda", occ_chunk: int = 1 << 22) -> Scene:
+    """make_scene for grids too large for numpy: the same recipe drawn with a seeded
+    torch generator on `device` (tables and coarse grid ~N(0, init_std), density
+    offset on the coarse density channel, blob occupancy evaluated in chunks of voxel
+    centres).  Arrays stay on the device (torch tensors); the MLP is drawn as in
+    make_scene."""
+    import torch
+    rng = np.random.default_rng(cfg.seed)
+    blobs = _blobs(cfg, rng)
+    ws = []
+    for k, (o, i) in enumerate(mlp_shapes(cfg)):
+        real_in = 23 if k == 0 else i
+        w = rng.normal(0.0, 1.0 / math.sqrt(real_in), (o, i)).astype(np.float32)
+        if k == 0:
+            w[:, 23:] = 0.0
+        ws.append(w.reshape(-1))
+    mlp_w = np.concatenate(ws).astype(np.float32)
+    g = torch.Generator(device=device)
+    g.manual_seed(cfg.seed)
+    tables = torch.randn(table_entries(cfg), N_FEAT, generator=g, device=device) * cfg.init_std
+    coarse = torch.randn(cfg.R_C ** 3, N_FEAT + 2 * cfg.L, generator=g, device=device) * cfg.init_std
+    coarse[:, 0] += cfg.density_bias
+    # occupancy: blob density at voxel centres of the contracted cube (world points by
+    # the inverse radial map), plus every voxel whose box meets the shell
+    R = cfg.R_O
+    mu = torch.as_tensor(blobs["mu"], device=device, dtype=torch.float64)
+    std = torch.as_tensor(blobs["std"], device=device, dtype=torch.float64)
+    peak = torch.as_tensor(blobs["peak"], device=device, dtype=torch.float64)
+    occ = torch.empty(R ** 3, dtype=torch.uint8, device=device)
+    for s0 in range(0, R ** 3, occ_chunk):
+        idx = torch.arange(s0, min(s0 + occ_chunk, R ** 3), device=device, dtype=torch.int64)
+        vx, vy, vz = idx % R, (idx // R) % R, idx // (R * R)
+        y = (torch.stack([vx, vy, vz], 1).double() + 0.5) / R * 4.0 - 2.0
+        ry = torch.linalg.norm(y, dim=1)
+        rx = torch.where(ry <= 1.0, ry, 1.0 / torch.clamp(2.0 - ry, min=1e-9))
+        pts = y * (rx / torch.clamp(ry, min=1e-30)).unsqueeze(1)
+        d2 = ((pts.unsqueeze(1) - mu.unsqueeze(0)) ** 2).sum(-1)
+        sig = (peak * torch.exp(-d2 / (2.0 * std ** 2))).sum(1)
+        o = (sig > cfg.occ_threshold) & (ry < 2.0 - 1e-9)
+        if cfg.shell:
+            h = 2.0 / R
+            rmin = torch.linalg.norm(torch.clamp(y.abs() - h, min=0.0), dim=1)
+            rmax = torch.linalg.norm(y.abs() + h, dim=1)
+            o |= (rmin <= 1.9) & (rmax >= 1.875)
+        occ[s0:s0 + len(idx)] = o.to(torch.uint8)
+    return Scene(cfg=cfg, tables=tables, coarse=coarse, mlp_w=mlp_w, occ=occ, blobs=blobs)

@@ -29,7 +29,7 @@ def test_propose_forward(ng):
     iv = torch.empty(5000, 2, device="cuda")
     ah = torch.empty(5000, device="cuda")
     ng.ngprt_propose(torch.as_tensor(w).cuda(), None, 0, None, torch.as_tensor(o).cuda(), torch.as_tensor(d).cuda(),
-                     5000, IN_SCALE, T_SCALE, 0.0, 0.0, iv, ah)
+                     5000, IN_SCALE, T_SCALE, 0.0, 0.0, 0.0, iv, ah)
     torch.cuda.synchronize()
     ref = O.prop_forward(w, o, d, IN_SCALE, T_SCALE)
     ivn = iv.cpu().numpy()

@@ -207,17 +207,45 @@ def test_unbounded_small_parity(ng):
         _compare(r, orc.render(opts, cams=cams))
 
 
-@pytest.mark.parametrize("table_dtype", [1, 2])
-def test_half_tables_against_oracle_on_rounded_values(ng, table_dtype):
-    """FP16/BF16 tables: the kernel reads 16-bit entries, the oracle gets the same
-    rounded values widened to FP64; compositing stays FP32 on the GPU."""
+def test_bf16_tables_against_oracle_on_rounded_values(ng):
+    """BF16 tables: the kernel reads 16-bit entries and interpolates in FP32; the
+    oracle gets the same rounded values widened to FP64: the FP32 bound holds."""
     cfg = S.small_config(blob_std=(0.05, 0.15))
-    sc, rend, orc = _pair(ng, cfg, table_dtype=table_dtype)
+    sc, rend, orc = _pair(ng, cfg, table_dtype=2)
     opts = S.default_options(cfg)
     cams = S.orbit_cameras(cfg, 1)
     r = rend.render(opts, cams=cams, W=cfg.W, H=cfg.H, stats=True)
     torch.cuda.synchronize()
     _compare(r, orc.render(opts, cams=cams))
+
+
+@pytest.mark.parametrize("cfg_name", ["small", "hd"])
+def test_fp16_tables_error_against_oracle(ng, cfg_name):
+    """FP16 tables interpolate in half2 arithmetic (FP16 products and sums over the 8
+    corners, one rounding each), the rest in FP32.  Against the FP64 oracle on the
+    same rounded table values the colour error stays below 5e-3 (8 FP16 roundings of
+    features |f| < 1 per level, scaled by the attention and the compositing), and
+    the image PSNR above 55 dB; a termination test moved by that error may change
+    a ray's sample count, so counts are not compared."""
+    if cfg_name == "small":
+        cfg = S.small_config(blob_std=(0.05, 0.15))
+        pix = None
+    else:
+        cfg = S.hd_config()
+        pix = np.random.default_rng(5).choice(cfg.W * cfg.H, 3000, replace=False).astype(np.int32)
+    sc, rend, orc = _pair(ng, cfg, table_dtype=1)
+    opts = S.default_options(cfg)
+    cams = S.orbit_cameras(cfg, 1)
+    kw = dict(pixel_ids=torch.as_tensor(pix).cuda()) if pix is not None else {}
+    r = rend.render(opts, cams=cams, W=cfg.W, H=cfg.H, **kw)
+    torch.cuda.synchronize()
+    ro = orc.render(opts, cams=cams, pix=pix)
+    rgb = r["rgb"].cpu().numpy().astype(np.float64)
+    err = np.abs(rgb - ro["rgb"])
+    mse = float((err ** 2).mean())
+    psnr = 10 * np.log10(1.0 / max(mse, 1e-30))
+    assert np.quantile(err.max(1), 0.999) <= 5e-3, err.max()
+    assert psnr > 55.0, psnr
 
 
 def test_hd_frame_sampled_parity(ng):
@@ -260,3 +288,26 @@ def test_wavefront_equals_fused_bit_for_bit(ng, cfg_name):
         torch.cuda.synchronize()
         assert torch.equal(outs[0][1], outs[1][1]), kw
         assert torch.equal(outs[0][0], outs[1][0]), kw
+
+
+@pytest.mark.parametrize("L", [2, 4])
+def test_paper_shape_sampled_parity(ng, L):
+    """The paper's render-time shape (hashed fine levels at 1024 * 2^l, a large dense
+    coarse grid of 8 + 2L channels, a 5-level pyramid), reduced to a 128^3 coarse
+    grid, 128^3 occupancy and T = 2^20 so that the oracle holds it; inputs drawn on the
+    GPU by the torch generator and copied to the host; 2000 sampled 1080p pixels."""
+    cfg = S.paper_config(L, R_C=128, R_O=128, T_log2=20)
+    sc = S.make_scene_torch(cfg, device="cuda")
+    ds = ng.DeviceScene(cfg, sc.tables, sc.coarse, sc.mlp_w)
+    docc = ng.DeviceOcc(sc.occ, cfg.R_O, cfg.n_occ_levels)
+    rend = ng.Renderer(ds, docc)
+    opts = S.default_options(cfg)
+    cams = S.orbit_cameras(cfg, 1, azimuth0=60.0)
+    pix = np.random.default_rng(L).choice(cfg.W * cfg.H, 2000, replace=False).astype(np.int32)
+    r = rend.render(opts, cams=cams, W=cfg.W, H=cfg.H, pixel_ids=torch.as_tensor(pix).cuda(), stats=True)
+    torch.cuda.synchronize()
+    occ = sc.occ.cpu().numpy()
+    orc = O.Oracle(cfg, sc.tables.cpu().numpy(), sc.coarse.cpu().numpy(), sc.mlp_w,
+                   O.build_pyramid(occ, cfg.R_O, cfg.n_occ_levels), O.occ_dist(occ, cfg.R_O))
+    _compare(r, orc.render(opts, cams=cams, pix=pix))
+    assert r["stats"][:, 1].float().mean() > 3
