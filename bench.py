@@ -245,7 +245,7 @@ def other_forms(args, cfg, scene, ds, docc, cams, opts, dev, stream, flush, plai
             "plain_marching_per_ray": float(plain_st[0]), "plain_samples_per_ray": float(plain_st[1]),
             "fallback_rays": float(((fr.a_hat - fr.state[:, 7]) > pc.fallback).float().mean()),
             "proposal_train_s": train_s, "proposal_loss": hist,
-            "training": "2^20 rays of 64 orbit views (azimuth 2.8125 + 5.625 k deg), 2000 Adam steps of 2^15"}}
+            "training": "2^20 rays of 64 orbit views (azimuth 2.8125 + 5.625 k deg), 6000 Adam steps of 2^15"}}
     # batches of 8 views (azimuth 45 k deg): plain FP32 and the fast form
     cams8 = S.orbit_cameras(cfg, 8)
     n8 = 8 * n
@@ -303,7 +303,45 @@ def other_forms(args, cfg, scene, ds, docc, cams, opts, dev, stream, flush, plai
     res["gather_ceiling"] = gcl
     if not args.no_paper_shape:
         res["paper_shape"] = paper_shape(args, dev, stream, flush)
+        res["aggregation_ablation"] = aggregation_ablation(args, dev, stream, flush)
     return res
+
+
+AGG_NAMES = {0: "Separate-Att (V)", 1: "Shared-Att (V)", 2: "Separate-Att (Inv)", 3: "Shared-Att (Inv)", 4: "SUM",
+             5: "MLP"}
+
+
+def aggregation_ablation(args, dev, stream, flush):
+    """Table 3's aggregation methods on the paper-shaped L = 4 scene (T = 2^22, 512^3
+    coarse grid in each method's own layout), 1080p FP32 frames; per method the frame
+    time, samples per ray and the multiply-adds that fuse the levels per sample.  The
+    paper's times (RTX 3090, L = 4): MLP 68.02, SUM 14.94, Shared-Att (Inv) 15.18,
+    Separate-Att (Inv) 15.13, Shared-Att (V) 16.04, Separate-Att (V) 16.17 ms."""
+    import torch
+    from paper_2407_10482_gb300 import ngprt as ng
+    out = {}
+    L = 4
+    occ = None
+    for agg in (0, 1, 2, 3, 4, 5):
+        cfg = S.paper_config(L, aggregation=agg)
+        sc = S.make_scene_torch(cfg, device=dev)
+        if occ is None:
+            occ = ng.DeviceOcc(sc.occ, cfg.R_O, cfg.n_occ_levels, device=dev)
+        ds = ng.DeviceScene(cfg, sc.tables, sc.coarse, sc.mlp_w, device=dev, attn_inv=sc.attn_inv, agg_mlp=sc.agg_mlp)
+        rend = ng.Renderer(ds, occ, device=dev)
+        opts = S.default_options(cfg)
+        cams = S.orbit_cameras(cfg, 1)
+        o = rend.render(opts, cams=cams, W=cfg.W, H=cfg.H, stats=True)
+        st = o["stats"].float().mean(0)
+        ms = _timed(lambda: rend.render(opts, cams=cams, W=cfg.W, H=cfg.H, out=o), stream, flush, 5, 3)
+        macs = {5: S.AGG_HIDDEN * 8 * L + 8 * S.AGG_HIDDEN, 4: 0}.get(agg, 8 * L)
+        out[AGG_NAMES[agg]] = {"ms_per_frame": ms, "frames_per_s": 1000.0 / ms, "samples_per_ray": float(st[1]),
+                               "marching_per_ray": float(st[0]), "fusion_macs_per_sample": macs,
+                               "coarse_channels": S.coarse_channels(cfg)}
+        del sc, ds, rend, o
+        torch.cuda.empty_cache()
+    out["config"] = "paper shape L = 4 (N_l = 1024 * 2^l, T = 2^22, R_C = 512, R_O = 512), FP32, 1080p, hd scene"
+    return out
 
 
 def paper_shape(args, dev, stream, flush):

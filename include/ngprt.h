@@ -41,6 +41,32 @@ typedef enum { NGPRT_F32 = 0, NGPRT_F16 = 1, NGPRT_BF16 = 2 } ngprt_dtype;
 #define NGPRT_STATE_FLOATS 12 /* per-ray state: C_d(3), F(4), A, depth, d(3) */
 
 /*
+ * How the L fine levels fuse into f^ (Eq. 7-8 and the variants of Table 3).  The
+ * coarse grid holds f~ (8 channels) and, for the spatially variant forms, the
+ * attention logits; the spatially invariant forms take one logit per level (and
+ * modality) from attn_inv; gates are sigmoid(logit) in every attention form.
+ *   SEPARATE_V  : Eq. 8 as printed: omega^l on sigma^l, beta^l on (c_d^l, v_s^l),
+ *                 logits interpolated from the coarse grid (8 + 2L channels)
+ *   SHARED_V    : one gate per level on all 8 channels, from the coarse grid (8 + L)
+ *   SEPARATE_INV: omega^l, beta^l constant over space (coarse grid 8 channels)
+ *   SHARED_INV  : one constant gate per level (coarse grid 8 channels)
+ *   SUM         : f^ = sum of the levels (coarse grid 8 channels)
+ *   MLP         : f^ = W2 relu(W1 [f^1, ..., f^L]), the tiny-MLP aggregation of
+ *                 Instant-NGP (one hidden layer of NGPRT_AGG_MLP_HIDDEN, no biases;
+ *                 coarse grid 8 channels)
+ */
+typedef enum {
+    NGPRT_AGG_SEPARATE_V = 0,
+    NGPRT_AGG_SHARED_V = 1,
+    NGPRT_AGG_SEPARATE_INV = 2,
+    NGPRT_AGG_SHARED_INV = 3,
+    NGPRT_AGG_SUM = 4,
+    NGPRT_AGG_MLP = 5
+} ngprt_aggregation;
+
+#define NGPRT_AGG_MLP_HIDDEN 64
+
+/*
  * Render-time scene (Sec. 3.1, Eq. 6): L fine levels of explicit deferred features
  * and a coarse grid holding the coarse feature and the attention logits.
  *   tables : [n_entries][8] of table_dtype; entry = [sigma^, c_d^(3), v_s^(4)].
@@ -48,8 +74,10 @@ typedef enum { NGPRT_F32 = 0, NGPRT_F16 = 1, NGPRT_BF16 = 2 } ngprt_dtype;
  *            A level with N^3 <= 2^T_log2 is dense (row x + N*y + N^2*z); the others
  *            use the spatial hash (x*1 ^ y*2654435761 ^ z*805459861) mod 2^T_log2.
  *            32-byte aligned (F32) or 16-byte aligned (F16/BF16).
- *   coarse : [R_C^3][8 + 2L] of table_dtype, channels [sigma~, c_d~(3), v_s~(4),
- *            omega^1, beta^1, ..., omega^L, beta^L] (attention logits, Eq. 7).
+ *   coarse : [R_C^3][ngprt_coarse_channels(L, aggregation)] of table_dtype,
+ *            channels [sigma~, c_d~(3), v_s~(4)] then, for SEPARATE_V, the logits
+ *            omega^1, beta^1, ..., omega^L, beta^L (Eq. 7), for SHARED_V one logit
+ *            per level a^1, ..., a^L.
  *   mlp_w  : deferred MLP_psi (Eq. 5) of mlp_layers dense layers without bias:
  *            layer k is a [out_k][in_k] matrix, in_0 = 32 (C_d, F, SH16(d), zero
  *            padding), out_k = mlp_width for hidden layers (ReLU), 3 for the last.
@@ -57,6 +85,12 @@ typedef enum { NGPRT_F32 = 0, NGPRT_F16 = 1, NGPRT_BF16 = 2 } ngprt_dtype;
  *            MMA with FP32 accumulation, activations rounded to FP16 between layers).
  *   bounded: 1 = scene in the box [-1,1]^3; 0 = unbounded scene under the
  *            mip-NeRF-360 contraction into [-2,2]^3.
+ *   aggregation: ngprt_aggregation (0 = Eq. 8).
+ *   attn_inv: device FP32 logits of the invariant forms: SEPARATE_INV [L][2]
+ *            (omega^l, beta^l), SHARED_INV [L]; NULL otherwise.
+ *   agg_mlp: device FP32 weights of the MLP form, W1 [64][8L] then W2 [8][64]
+ *            ([out][in] row-major; input = level 1's 8 channels, then level 2's, ...),
+ *            16-byte aligned; NULL otherwise.
  * Vertex grids of N per axis cover the unit cube coordinate u in [0,1]^3 with
  * p = u (N - 1) (trilinear interpolation, Eq. 6).
  */
@@ -73,7 +107,13 @@ typedef struct {
     const void* tables;
     const void* coarse;
     const void* mlp_w;
+    int32_t aggregation;
+    const float* attn_inv;
+    const float* agg_mlp;
 } ngprt_scene;
+
+/* Channels per coarse-grid vertex for L levels under `aggregation` (0 if invalid). */
+int32_t ngprt_coarse_channels(int32_t L, int32_t aggregation);
 
 /*
  * Occupancy (Sec. 3.3; Sec. S2.5).  bits: n_levels bit-packed grids, finest
@@ -101,8 +141,10 @@ typedef struct {
  * t_term = transmittance threshold (2e-3 in Sec. S2.5); bg = background colour;
  * max_march / max_samples = caps on marching points / samples per ray;
  * use_dist = read G (Eq. 9); lattice_snap = (bounded only) keep samples on the
- * uniform lattice; attn_mode 0 = separate attention (Eq. 8), 1 = SUM, 2 = one gate
- * per level; dist_rule 0 = Eq. 9 as printed, 1 = max(v G, s_O). */
+ * uniform lattice; attn_mode (SEPARATE_V scenes only; 0 for every other
+ * aggregation) 0 = separate attention (Eq. 8), 1 = gates fixed at 1 (SUM over the
+ * same grid), 2 = omega^l for both modalities; dist_rule 0 = Eq. 9 as printed,
+ * 1 = max(v G, s_O). */
 typedef struct {
     float step_base;
     float step_gamma;

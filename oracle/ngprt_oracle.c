@@ -50,7 +50,13 @@ typedef struct {
     int mlp_width;
     const double* mlp_w;   /* layer k: [out_k][in_k] row-major, concatenated */
     int bounded;
+    int aggregation;       /* 0 Eq. 8; 1 one gate per level from the grid; 2, 3 the same
+                              two with constant gates; 4 plain sum; 5 tiny MLP (Table 3) */
+    const double* attn_inv;/* constant logits: [L][2] (aggregation 2) or [L] (3) */
+    const double* agg_mlp; /* aggregation 5: W1 [64][8L] then W2 [8][64] */
 } or_scene;
+
+#define OR_AGG_HIDDEN 64
 
 typedef struct {
     int R_O;
@@ -348,14 +354,29 @@ static double or_corner_weight(const double w[3], int c) {
     return wx * wy * wz;
 }
 
+/* Channels per coarse-grid vertex: f~ (8), then the attention logits of the
+ * spatially variant forms (omega, beta per level for Eq. 8; one per level for the
+ * shared form); the other forms keep f~ alone. */
+int or_coarse_channels(int L, int aggregation) {
+    if (aggregation == 0) return OR_NFEAT + 2 * L;
+    if (aggregation == 1) return OR_NFEAT + L;
+    return OR_NFEAT;
+}
+
 /* Eq. 6-8: f = f~ + Att(f^1..f^L; a), f~ and a trilinear in the coarse grid, a
- * squashed by a sigmoid after interpolation (Sec. S2.1), f^l trilinear in level l. */
+ * squashed by a sigmoid after interpolation (Sec. S2.1), f^l trilinear in level l.
+ * The aggregation variants of Table 3 replace Att: one gate per level for all
+ * channels (shared), gates constant over space (invariant: sigmoid of a logit per
+ * level), the plain sum, or Instant-NGP's tiny MLP on the concatenated levels,
+ * f^ = W2 relu(W1 [f^1, ..., f^L]). */
 static void or_features(const or_scene* s, const or_opts* op, const float u[3], double f[OR_NFEAT]) {
-    int nch = OR_NFEAT + 2 * s->L;
+    int nch = or_coarse_channels(s->L, s->aggregation);
     double coarse[OR_NFEAT + 2 * OR_MAXL];
+    double hid[OR_AGG_HIDDEN];
     int base[3];
     double w[3];
     memset(coarse, 0, sizeof coarse);
+    memset(hid, 0, sizeof hid);
     or_cell(u, s->R_C, base, w);
     for (int c = 0; c < 8; ++c) {
         int x = base[0] + (c & 1), y = base[1] + ((c >> 1) & 1), z = base[2] + ((c >> 2) & 1);
@@ -366,10 +387,18 @@ static void or_features(const or_scene* s, const or_opts* op, const float u[3], 
     for (int ch = 0; ch < OR_NFEAT; ++ch) f[ch] = coarse[ch];
     uint32_t T = 1u << s->T_log2;
     for (int l = 0; l < s->L; ++l) {
-        double om, be;
-        if (op->attn_mode == 1) { om = 1.0; be = 1.0; }
-        else if (op->attn_mode == 2) { om = or_sigmoid(coarse[OR_NFEAT + 2 * l]); be = om; }
-        else { om = or_sigmoid(coarse[OR_NFEAT + 2 * l]); be = or_sigmoid(coarse[OR_NFEAT + 2 * l + 1]); }
+        double om = 1.0, be = 1.0;
+        switch (s->aggregation) {
+            case 0:
+                if (op->attn_mode == 1) { om = 1.0; be = 1.0; }
+                else if (op->attn_mode == 2) { om = or_sigmoid(coarse[OR_NFEAT + 2 * l]); be = om; }
+                else { om = or_sigmoid(coarse[OR_NFEAT + 2 * l]); be = or_sigmoid(coarse[OR_NFEAT + 2 * l + 1]); }
+                break;
+            case 1: om = or_sigmoid(coarse[OR_NFEAT + l]); be = om; break;
+            case 2: om = or_sigmoid(s->attn_inv[2 * l]); be = or_sigmoid(s->attn_inv[2 * l + 1]); break;
+            case 3: om = or_sigmoid(s->attn_inv[l]); be = om; break;
+            default: break; /* 4: sum; 5: MLP below */
+        }
         double fl[OR_NFEAT];
         memset(fl, 0, sizeof fl);
         or_cell(u, s->N[l], base, w);
@@ -380,8 +409,22 @@ static void or_features(const or_scene* s, const or_opts* op, const float u[3], 
             double cw = or_corner_weight(w, c);
             for (int ch = 0; ch < OR_NFEAT; ++ch) fl[ch] += cw * s->tables[e * OR_NFEAT + ch];
         }
-        f[0] += om * fl[0];
-        for (int ch = 1; ch < OR_NFEAT; ++ch) f[ch] += be * fl[ch];
+        if (s->aggregation == 5) {
+            for (int j = 0; j < OR_AGG_HIDDEN; ++j)
+                for (int ch = 0; ch < OR_NFEAT; ++ch)
+                    hid[j] += s->agg_mlp[(size_t)j * OR_NFEAT * s->L + OR_NFEAT * l + ch] * fl[ch];
+        } else {
+            f[0] += om * fl[0];
+            for (int ch = 1; ch < OR_NFEAT; ++ch) f[ch] += be * fl[ch];
+        }
+    }
+    if (s->aggregation == 5) {
+        const double* w2 = s->agg_mlp + (size_t)OR_AGG_HIDDEN * OR_NFEAT * s->L;
+        for (int k = 0; k < OR_NFEAT; ++k) {
+            double o = 0.0;
+            for (int j = 0; j < OR_AGG_HIDDEN; ++j) o += w2[k * OR_AGG_HIDDEN + j] * fmax(hid[j], 0.0);
+            f[k] += o;
+        }
     }
 }
 
@@ -739,6 +782,7 @@ void or_render_backward(const or_scene* s, const or_occ* oc, const or_opts* op,
                         const float* rays_o, const float* rays_d, int n,
                         const double* d_rgb, const double* d_depth, const double* d_opacity,
                         double* g_tables, double* g_coarse, double* g_mlp) {
+    if (s->aggregation != 0) return; /* the reverse pass covers Eq. 8 only (oracle.py refuses the rest) */
     int cap = op->max_samples > 0 ? op->max_samples : 1;
     or_sample* sm = (or_sample*)malloc(sizeof(or_sample) * (size_t)cap);
     double* qg = (double*)malloc(sizeof(double) * (size_t)cap);

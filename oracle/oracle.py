@@ -38,7 +38,8 @@ class OrScene(C.Structure):
     _fields_ = [("L", C.c_int), ("T_log2", C.c_int), ("N", C.c_int * MAXL),
                 ("tables", C.c_void_p), ("R_C", C.c_int), ("coarse", C.c_void_p),
                 ("mlp_layers", C.c_int), ("mlp_width", C.c_int), ("mlp_w", C.c_void_p),
-                ("bounded", C.c_int)]
+                ("bounded", C.c_int), ("aggregation", C.c_int), ("attn_inv", C.c_void_p),
+                ("agg_mlp", C.c_void_p)]
 
 
 class OrOcc(C.Structure):
@@ -161,11 +162,19 @@ class Oracle:
     """FP64 renderer over one scene.  ``tables``/``coarse``/``mlp_w`` may be FP32 or
     FP16/BF16-rounded copies (pass them as float arrays); they are widened to FP64."""
 
-    def __init__(self, cfg, tables, coarse, mlp_w, occ_bits, dist=None):
+    def __init__(self, cfg, tables, coarse, mlp_w, occ_bits, dist=None, attn_inv=None, agg_mlp=None):
         self.cfg = cfg
         self.tables = _c(np.asarray(tables, np.float64), np.float64)
         self.coarse = _c(np.asarray(coarse, np.float64), np.float64)
         self.mlp_w = _c(np.asarray(mlp_w, np.float64), np.float64)
+        agg = int(getattr(cfg, "aggregation", 0))
+        assert self.coarse.size == (cfg.R_C ** 3) * coarse_channels(cfg.L, agg), "coarse grid layout"
+        self.attn_inv = None if attn_inv is None else _c(np.asarray(attn_inv, np.float64), np.float64)
+        self.agg_mlp = None if agg_mlp is None else _c(np.asarray(agg_mlp, np.float64), np.float64)
+        if agg in (2, 3):
+            assert self.attn_inv is not None and self.attn_inv.size == (2 if agg == 2 else 1) * cfg.L
+        if agg == 5:
+            assert self.agg_mlp is not None and self.agg_mlp.size == AGG_HIDDEN * 8 * cfg.L + 8 * AGG_HIDDEN
         self.bits = _c(occ_bits, np.uint32)
         self.dist = _c(dist, np.uint8)
         s = OrScene()
@@ -180,6 +189,9 @@ class Oracle:
         s.mlp_width = cfg.mlp_width
         s.mlp_w = self.mlp_w.ctypes.data
         s.bounded = 1 if cfg.bounded else 0
+        s.aggregation = agg
+        s.attn_inv = self.attn_inv.ctypes.data if self.attn_inv is not None else None
+        s.agg_mlp = self.agg_mlp.ctypes.data if self.agg_mlp is not None else None
         self._s = s
         o = OrOcc()
         o.R_O = cfg.R_O
@@ -240,6 +252,8 @@ class Oracle:
 
     def render_backward(self, opts, d_rgb=None, d_depth=None, d_opacity=None, cams=None, pix=None,
                         rays_o=None, rays_d=None, W=None, H=None):
+        if int(getattr(self.cfg, "aggregation", 0)) != 0:
+            raise NotImplementedError("the reverse pass follows Eq. 8 (aggregation 0) only")
         W = W or self.cfg.W
         H = H or self.cfg.H
         cams, pix, ro, rd, n = self._rays(cams, pix, rays_o, rays_d)
@@ -291,7 +305,8 @@ def oracle_for_scene(scene, tables=None, coarse=None, use_dist=True) -> Oracle:
     bits = build_pyramid(scene.occ, cfg.R_O, cfg.n_occ_levels)
     dist = occ_dist(scene.occ, cfg.R_O) if use_dist else None
     return Oracle(cfg, scene.tables if tables is None else tables,
-                  scene.coarse if coarse is None else coarse, scene.mlp_w, bits, dist)
+                  scene.coarse if coarse is None else coarse, scene.mlp_w, bits, dist,
+                  attn_inv=getattr(scene, "attn_inv", None), agg_mlp=getattr(scene, "agg_mlp", None))
 
 
 def contract(x: np.ndarray, bounded: bool = False):
@@ -303,9 +318,13 @@ def contract(x: np.ndarray, bounded: bool = False):
     return y, u
 
 
-def coarse_channels(L: int) -> int:
-    """Channels per coarse-grid vertex: deferred feature (8) plus omega, beta per level."""
-    return 8 + 2 * L
+AGG_HIDDEN = 64  # hidden units of the tiny-MLP aggregation
+
+
+def coarse_channels(L: int, aggregation: int = 0) -> int:
+    """Channels per coarse-grid vertex: deferred feature (8) plus omega, beta per level
+    (Eq. 8), one logit per level (shared gates), or nothing (the other aggregations)."""
+    return {0: 8 + 2 * L, 1: 8 + L}.get(int(aggregation), 8)
 
 
 def l2_loss(rgb, target, scale=1.0):

@@ -385,6 +385,7 @@ int32_t check_opts(const ngprt_render_opts* o, const char* fn);
 int32_t setup_rays(MarchParams& p, const ngprt_camera* cams, int32_t n_cams, const int32_t* pixel_ids,
                    const float* rays_o, const float* rays_d, int64_t n_rays, dim3& grid, const char* fn);
 bool march_supports(int L);
+int32_t check_agg(const ngprt_scene* s, const ngprt_render_opts* o, bool forward_only_ok, const char* fn);
 bool mlp_supports(int width, int layers);
 
 }  // namespace ngprt
@@ -404,6 +405,7 @@ extern "C" int32_t ngprt_render_backward(const ngprt_scene* scene, const ngprt_o
     if ((rc = make_grid(scene, p.m.g, fn)) != NGPRT_OK) return rc;
     if ((rc = make_occ(occ, p.m.occ, fn)) != NGPRT_OK) return rc;
     if ((rc = check_opts(opts, fn)) != NGPRT_OK) return rc;
+    if ((rc = check_agg(scene, opts, false, fn)) != NGPRT_OK) return rc;
     NGPRT_REQUIRE(n_rays >= 0, "%s: n_rays=%lld", fn, (long long)n_rays);
     NGPRT_REQUIRE(scene->table_dtype == NGPRT_F32 && scene->mlp_dtype == NGPRT_F32,
                   "%s: gradients need F32 tables and F32 MLP weights", fn);

@@ -54,7 +54,16 @@ int32_t make_grid(const ngprt_scene* s, Grid& g, const char* fn) {
         NGPRT_REQUIRE(s->N[l] >= 2 && s->N[l] <= (1 << 20), "%s: N[%d]=%d not in [2, 2^20]", fn, l, s->N[l]);
     NGPRT_REQUIRE(entries_of(s) < (int64_t)1 << 31, "%s: more than 2^31 table rows", fn);
     NGPRT_REQUIRE(s->mlp_layers >= 2 && s->mlp_width >= 1, "%s: MLP %d layers x %d", fn, s->mlp_layers, s->mlp_width);
+    NGPRT_REQUIRE(s->aggregation >= NGPRT_AGG_SEPARATE_V && s->aggregation <= NGPRT_AGG_MLP, "%s: aggregation=%d", fn,
+                  s->aggregation);
+    const bool inv = s->aggregation == NGPRT_AGG_SEPARATE_INV || s->aggregation == NGPRT_AGG_SHARED_INV;
+    NGPRT_REQUIRE(!inv || s->attn_inv != nullptr, "%s: the invariant aggregations need attn_inv", fn);
+    NGPRT_REQUIRE(s->aggregation != NGPRT_AGG_MLP || (s->agg_mlp != nullptr && ((uintptr_t)s->agg_mlp % 16) == 0),
+                  "%s: the MLP aggregation needs 16-byte aligned agg_mlp", fn);
     memset(&g, 0, sizeof g);
+    g.agg = s->aggregation;
+    g.attn_inv = s->attn_inv;
+    g.agg_mlp = s->agg_mlp;
     g.tables = s->tables;
     g.coarse = s->coarse;
     g.L = s->L;
@@ -99,6 +108,19 @@ int32_t make_occ(const ngprt_occ* o, OccView& v, const char* fn) {
 extern "C" const char* ngprt_last_error(void) { return ngprt::g_err; }
 
 extern "C" int32_t ngprt_version(void) { return 100; }
+
+extern "C" int32_t ngprt_coarse_channels(int32_t L, int32_t aggregation) {
+    if (L < 1 || L > ngprt::kMaxL) return 0;
+    switch (aggregation) {
+        case NGPRT_AGG_SEPARATE_V: return ngprt::kNFeat + 2 * L;
+        case NGPRT_AGG_SHARED_V: return ngprt::kNFeat + L;
+        case NGPRT_AGG_SEPARATE_INV:
+        case NGPRT_AGG_SHARED_INV:
+        case NGPRT_AGG_SUM:
+        case NGPRT_AGG_MLP: return ngprt::kNFeat;
+        default: return 0;
+    }
+}
 
 extern "C" int64_t ngprt_table_entries(const ngprt_scene* scene) {
     if (!scene || scene->L < 1 || scene->L > ngprt::kMaxL || scene->T_log2 < 1 || scene->T_log2 > 30) return -1;

@@ -44,7 +44,15 @@ struct Grid {
     int32_t L;
     int32_t R_C;
     int32_t bounded;
+    int32_t agg;                 // ngprt_aggregation
+    const float* attn_inv;       // invariant attention logits
+    const float* agg_mlp;        // MLP aggregation weights
 };
+
+// Coarse-grid channels per vertex under an aggregation (f~ plus the variant's logits).
+__host__ __device__ constexpr int coarse_channels(int L, int agg) {
+    return agg == NGPRT_AGG_SEPARATE_V ? kNFeat + 2 * L : agg == NGPRT_AGG_SHARED_V ? kNFeat + L : kNFeat;
+}
 
 struct OccView {
     const uint32_t* bits;

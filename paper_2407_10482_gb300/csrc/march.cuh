@@ -131,16 +131,21 @@ __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
 #endif
 constexpr int kLevelUnroll = NGPRT_LEVEL_UNROLL;
 
-// Eq. 6-8 at unit-cube position u: f = f~ + Att(f^1..f^L; a).  The coarse fetch
-// interpolates the 8 + 2L channels of the coarse grid; the 2L attention gates
-// (sigmoid of the interpolated logits) are parked in shared memory, gates[k*stride],
-// so that the level loop need not be unrolled.  FP32 and BF16 tables interpolate
-// in FP32; FP16 tables interpolate in packed half2 FMAs (FP16 products and sums,
-// one conversion per channel), the rest of the sample in FP32.
-template <int L, int DT>
+// Eq. 6-8 at unit-cube position u: f = f~ + Att(f^1..f^L; a), or one of the
+// aggregations of Table 3 (AGG, an ngprt_aggregation).  The coarse fetch
+// interpolates the coarse grid's channels (f~ and, for the spatially variant forms,
+// the attention logits); the 2L gates (sigmoid of the interpolated or constant
+// logits) are parked in shared memory, gates[k*stride], so that the level loop need
+// not be unrolled.  FP32 and BF16 tables interpolate in FP32; FP16 tables
+// interpolate in packed half2 FMAs (FP16 products and sums, one conversion per
+// channel), the rest of the sample in FP32.  The MLP form accumulates its 64 hidden
+// units level by level (W1 columns of level l against f^l), then applies W2.
+template <int L, int DT, int AGG = NGPRT_AGG_SEPARATE_V>
 __device__ __forceinline__ void sample_features(const Grid& g, const float u[3], int attn_mode, float f[8],
                                                 float* gates, int stride) {
-    constexpr int NC = kNFeat + 2 * L;
+    constexpr int NC = coarse_channels(L, AGG);
+    static_assert(NC % 2 == 0, "coarse channels are fetched in pairs");
+    constexpr bool kGated = AGG != NGPRT_AGG_SUM && AGG != NGPRT_AGG_MLP;
     int b[3];
     float w[3];
 #pragma unroll
@@ -184,22 +189,42 @@ __device__ __forceinline__ void sample_features(const Grid& g, const float u[3],
         f[2 * ch] = acc[ch].x;
         f[2 * ch + 1] = acc[ch].y;
     }
+    if constexpr (kGated) {
 #pragma unroll
-    for (int l = 0; l < L; ++l) {
-        float om, be;
-        const float2 lg = acc[kNFeat / 2 + l];
-        if (attn_mode == 1) {
-            om = 1.0f;
-            be = 1.0f;
-        } else if (attn_mode == 2) {
-            om = gate_sigmoid(lg.x);
-            be = om;
-        } else {
-            om = gate_sigmoid(lg.x);
-            be = gate_sigmoid(lg.y);
+        for (int l = 0; l < L; ++l) {
+            float om, be;
+            if constexpr (AGG == NGPRT_AGG_SEPARATE_V) {
+                const float2 lg = acc[kNFeat / 2 + l];
+                if (attn_mode == 1) {
+                    om = 1.0f;
+                    be = 1.0f;
+                } else if (attn_mode == 2) {
+                    om = gate_sigmoid(lg.x);
+                    be = om;
+                } else {
+                    om = gate_sigmoid(lg.x);
+                    be = gate_sigmoid(lg.y);
+                }
+            } else if constexpr (AGG == NGPRT_AGG_SHARED_V) {
+                const float2 lg = acc[(kNFeat + l) / 2];
+                om = gate_sigmoid((l & 1) ? lg.y : lg.x);
+                be = om;
+            } else if constexpr (AGG == NGPRT_AGG_SEPARATE_INV) {
+                om = gate_sigmoid(__ldg(g.attn_inv + 2 * l));
+                be = gate_sigmoid(__ldg(g.attn_inv + 2 * l + 1));
+            } else {
+                om = gate_sigmoid(__ldg(g.attn_inv + l));
+                be = om;
+            }
+            gates[(2 * l) * stride] = om;
+            gates[(2 * l + 1) * stride] = be;
         }
-        gates[(2 * l) * stride] = om;
-        gates[(2 * l + 1) * stride] = be;
+    }
+    constexpr int kHid = AGG == NGPRT_AGG_MLP ? NGPRT_AGG_MLP_HIDDEN : 1;
+    float hid[kHid];
+    if constexpr (AGG == NGPRT_AGG_MLP) {
+#pragma unroll
+        for (int j = 0; j < kHid; ++j) hid[j] = 0.0f;
     }
 #pragma unroll kLevelUnroll
     for (int l = 0; l < L; ++l) {
@@ -243,13 +268,54 @@ __device__ __forceinline__ void sample_features(const Grid& g, const float u[3],
                 for (int ch = 0; ch < 4; ++ch) fl[ch] = ffma2(cw2, make_float2(e[c][2 * ch], e[c][2 * ch + 1]), fl[ch]);
             }
         }
-        const float om = gates[(2 * l) * stride], be = gates[(2 * l + 1) * stride];
-        f[0] = fmaf(om, fl[0].x, f[0]);
-        f[1] = fmaf(be, fl[0].y, f[1]);
+        if constexpr (AGG == NGPRT_AGG_SUM) {
 #pragma unroll
-        for (int ch = 1; ch < 4; ++ch) {
-            f[2 * ch] = fmaf(be, fl[ch].x, f[2 * ch]);
-            f[2 * ch + 1] = fmaf(be, fl[ch].y, f[2 * ch + 1]);
+            for (int ch = 0; ch < 4; ++ch) {
+                f[2 * ch] += fl[ch].x;
+                f[2 * ch + 1] += fl[ch].y;
+            }
+        } else if constexpr (AGG == NGPRT_AGG_MLP) {
+            // W1 row j holds 8L inputs; level l's 8 columns are float4s 2(jL + l), +1
+            const float4* w1 = reinterpret_cast<const float4*>(g.agg_mlp) + 2 * l;
+#pragma unroll
+            for (int j = 0; j < kHid; ++j) {
+                const float4 a = __ldg(w1 + 2 * L * j), c = __ldg(w1 + 2 * L * j + 1);
+                float h = hid[j];
+                h = fmaf(a.x, fl[0].x, h);
+                h = fmaf(a.y, fl[0].y, h);
+                h = fmaf(a.z, fl[1].x, h);
+                h = fmaf(a.w, fl[1].y, h);
+                h = fmaf(c.x, fl[2].x, h);
+                h = fmaf(c.y, fl[2].y, h);
+                h = fmaf(c.z, fl[3].x, h);
+                h = fmaf(c.w, fl[3].y, h);
+                hid[j] = h;
+            }
+        } else {
+            const float om = gates[(2 * l) * stride], be = gates[(2 * l + 1) * stride];
+            f[0] = fmaf(om, fl[0].x, f[0]);
+            f[1] = fmaf(be, fl[0].y, f[1]);
+#pragma unroll
+            for (int ch = 1; ch < 4; ++ch) {
+                f[2 * ch] = fmaf(be, fl[ch].x, f[2 * ch]);
+                f[2 * ch + 1] = fmaf(be, fl[ch].y, f[2 * ch + 1]);
+            }
+        }
+    }
+    if constexpr (AGG == NGPRT_AGG_MLP) {
+        const float4* w2 = reinterpret_cast<const float4*>(g.agg_mlp + (size_t)kHid * kNFeat * L);
+#pragma unroll
+        for (int k = 0; k < kNFeat; ++k) {
+            float o = 0.0f;
+#pragma unroll
+            for (int j = 0; j < kHid / 4; ++j) {
+                const float4 a = __ldg(w2 + k * (kHid / 4) + j);
+                o = fmaf(a.x, fmaxf(hid[4 * j], 0.0f), o);
+                o = fmaf(a.y, fmaxf(hid[4 * j + 1], 0.0f), o);
+                o = fmaf(a.z, fmaxf(hid[4 * j + 2], 0.0f), o);
+                o = fmaf(a.w, fmaxf(hid[4 * j + 3], 0.0f), o);
+            }
+            f[k] += o;
         }
     }
 }
@@ -414,7 +480,7 @@ __device__ __forceinline__ void march_loop(const MarchParams& p, const float o[3
 }
 
 // Forward sampler: features (Eq. 6-8), alpha compositing (Eq. 2, Eq. 5).
-template <int L, int DT>
+template <int L, int DT, int AGG = NGPRT_AGG_SEPARATE_V>
 struct ForwardSampler {
     const Grid& g;
     int attn_mode;
@@ -458,7 +524,7 @@ struct ForwardSampler {
     }
     __device__ __forceinline__ bool sample(const float u[3], float t, float delta) {
         float f[8];
-        sample_features<L, DT>(g, u, attn_mode, f, gates, blockDim.x);
+        sample_features<L, DT, AGG>(g, u, attn_mode, f, gates, blockDim.x);
         return composite(f, t, delta);
     }
 };
@@ -474,6 +540,54 @@ __device__ __forceinline__ bool ray_setup(const MarchParams& p, int64_t& ray, fl
     }
     hit = ray_interval(p.g.bounded, o, d, p.opts.t_min, p.opts.r_far, t_lo, t_hi, t, t_out);
     return true;
+}
+
+// The fused forward kernel: one ray per thread over the warp's pixel tile (or one
+// ray id / explicit ray per thread), march + features + compositing, the per-ray
+// composite state written to `state`.  In the fallback pass it re-marches only the
+// rays whose interval result missed the predicted opacity.
+// Blocks per SM the register allocation must allow: the MLP aggregation keeps its
+// 64 hidden units in registers and runs with fewer resident blocks.
+template <int AGG>
+constexpr int march_min_blocks() { return AGG == NGPRT_AGG_MLP ? 3 : NGPRT_MARCH_MIN_BLOCKS; }
+
+template <int L, int DT, int AGG>
+__global__ void __launch_bounds__(128, march_min_blocks<AGG>()) march_kernel(const __grid_constant__ MarchParams p) {
+    int64_t ray;
+    float o[3], d[3], t, t_out;
+    bool hit;
+    extern __shared__ float gate_smem[];
+    if (!ray_setup(p, ray, o, d, t, t_out, hit)) return;
+    float* s = p.state + ray * NGPRT_STATE_FLOATS;
+    if (p.fb_a_hat) {
+        // fallback pass: keep the interval result unless it missed predicted opacity
+        const float lo = p.t_interval[2 * ray], hi = p.t_interval[2 * ray + 1];
+        const bool was_full = lo == -INFINITY && hi == INFINITY;
+        if (was_full || !(p.fb_a_hat[ray] - s[7] > p.fb_thr)) return;
+    }
+    ForwardSampler<L, DT, AGG> smp(p.g, p.opts.attn_mode, p.opts.t_term, gate_smem + threadIdx.x);
+    int n_march = 0, n_samp = 0;
+    if (hit) march_loop(p, o, d, t, t_out, smp, n_march, n_samp);
+    reinterpret_cast<float4*>(s)[0] = make_float4(smp.Cd[0], smp.Cd[1], smp.Cd[2], smp.F[0]);
+    reinterpret_cast<float4*>(s)[1] = make_float4(smp.F[1], smp.F[2], smp.F[3], smp.A);
+    reinterpret_cast<float4*>(s)[2] = make_float4(smp.depth, d[0], d[1], d[2]);
+    if (p.stats) {
+        int2* st = reinterpret_cast<int2*>(p.stats) + ray;
+        if (p.fb_a_hat) {
+            const int2 prev = *st;
+            *st = make_int2(prev.x + n_march, prev.y + n_samp);
+        } else {
+            *st = make_int2(n_march, n_samp);
+        }
+    }
+}
+
+template <int L, int AGG>
+void launch_march_kernel(int dt, const MarchParams& p, dim3 grid, cudaStream_t st) {
+    const size_t shm = (size_t)2 * L * 128 * sizeof(float);  // attention gates of the block's rays
+    if (dt == NGPRT_F32) march_kernel<L, NGPRT_F32, AGG><<<grid, 128, shm, st>>>(p);
+    else if (dt == NGPRT_F16) march_kernel<L, NGPRT_F16, AGG><<<grid, 128, shm, st>>>(p);
+    else march_kernel<L, NGPRT_BF16, AGG><<<grid, 128, shm, st>>>(p);
 }
 
 }  // namespace ngprt

@@ -13,37 +13,6 @@
 
 namespace ngprt {
 
-template <int L, int DT>
-__global__ void __launch_bounds__(128, NGPRT_MARCH_MIN_BLOCKS) march_kernel(const __grid_constant__ MarchParams p) {
-    int64_t ray;
-    float o[3], d[3], t, t_out;
-    bool hit;
-    extern __shared__ float gate_smem[];
-    if (!ray_setup(p, ray, o, d, t, t_out, hit)) return;
-    float* s = p.state + ray * NGPRT_STATE_FLOATS;
-    if (p.fb_a_hat) {
-        // fallback pass: keep the interval result unless it missed predicted opacity
-        const float lo = p.t_interval[2 * ray], hi = p.t_interval[2 * ray + 1];
-        const bool was_full = lo == -INFINITY && hi == INFINITY;
-        if (was_full || !(p.fb_a_hat[ray] - s[7] > p.fb_thr)) return;
-    }
-    ForwardSampler<L, DT> smp(p.g, p.opts.attn_mode, p.opts.t_term, gate_smem + threadIdx.x);
-    int n_march = 0, n_samp = 0;
-    if (hit) march_loop(p, o, d, t, t_out, smp, n_march, n_samp);
-    reinterpret_cast<float4*>(s)[0] = make_float4(smp.Cd[0], smp.Cd[1], smp.Cd[2], smp.F[0]);
-    reinterpret_cast<float4*>(s)[1] = make_float4(smp.F[1], smp.F[2], smp.F[3], smp.A);
-    reinterpret_cast<float4*>(s)[2] = make_float4(smp.depth, d[0], d[1], d[2]);
-    if (p.stats) {
-        int2* st = reinterpret_cast<int2*>(p.stats) + ray;
-        if (p.fb_a_hat) {
-            const int2 prev = *st;
-            *st = make_int2(prev.x + n_march, prev.y + n_samp);
-        } else {
-            *st = make_int2(n_march, n_samp);
-        }
-    }
-}
-
 // Proposal training targets (per ray): with the final opacity A of the plain
 // render, the position of the first sample whose cumulative weight exceeds
 // 0.005 A, the end (t + delta) of the first sample whose cumulative weight reaches
@@ -205,10 +174,7 @@ int32_t make_occ(const ngprt_occ* o, OccView& v, const char* fn);
 
 template <int L>
 void launch_march(int dt, const MarchParams& p, dim3 grid, cudaStream_t st) {
-    const size_t shm = (size_t)2 * L * 128 * sizeof(float);  // attention gates of the block's rays
-    if (dt == NGPRT_F32) march_kernel<L, NGPRT_F32><<<grid, 128, shm, st>>>(p);
-    else if (dt == NGPRT_F16) march_kernel<L, NGPRT_F16><<<grid, 128, shm, st>>>(p);
-    else march_kernel<L, NGPRT_BF16><<<grid, 128, shm, st>>>(p);
+    launch_march_kernel<L, NGPRT_AGG_SEPARATE_V>(dt, p, grid, st);
 }
 
 template <int L>
@@ -219,9 +185,17 @@ void launch_targets(int dt, const MarchParams& p, dim3 grid, cudaStream_t st, fl
     else targets_kernel<L, NGPRT_BF16><<<grid, 128, shm, st>>>(p, targets);
 }
 
-bool march_supports(int L) { return L == 1 || L == 2 || L == 3 || L == 4 || L == 8 || L == 16; }
+bool march_agg_supports(int L);
+int32_t launch_march_agg(int L, int dt, int agg, const MarchParams& p, dim3 grid, cudaStream_t st);
 
-int32_t launch_march_any(int L, int dt, const MarchParams& p, dim3 grid, cudaStream_t st) {
+bool march_supports(int L, int agg) {
+    if (agg != NGPRT_AGG_SEPARATE_V) return march_agg_supports(L);
+    return L == 1 || L == 2 || L == 3 || L == 4 || L == 8 || L == 16;
+}
+bool march_supports(int L) { return march_supports(L, NGPRT_AGG_SEPARATE_V); }
+
+int32_t launch_march_any(int L, int dt, int agg, const MarchParams& p, dim3 grid, cudaStream_t st) {
+    if (agg != NGPRT_AGG_SEPARATE_V) return launch_march_agg(L, dt, agg, p, grid, st);
     switch (L) {
         case 1: launch_march<1>(dt, p, grid, st); break;
         case 2: launch_march<2>(dt, p, grid, st); break;
@@ -334,6 +308,21 @@ int32_t setup_rays(MarchParams& p, const ngprt_camera* cams, int32_t n_cams, con
     return NGPRT_OK;
 }
 
+// The aggregation forms other than Eq. 8 are forward-only and take attn_mode 0.
+int32_t check_agg(const ngprt_scene* s, const ngprt_render_opts* o, bool forward_only_ok, const char* fn) {
+    if (s->aggregation == NGPRT_AGG_SEPARATE_V) return NGPRT_OK;
+    NGPRT_REQUIRE(o->attn_mode == 0, "%s: attn_mode=%d applies to the SEPARATE_V aggregation only", fn, o->attn_mode);
+    if (!forward_only_ok) {
+        set_error("%s: aggregation %d is built for the forward render only", fn, s->aggregation);
+        return NGPRT_ERR_UNSUPPORTED;
+    }
+    if (!march_supports(s->L, s->aggregation)) {
+        set_error("%s: aggregation %d not built for L=%d (built: 2, 4, 16)", fn, s->aggregation, s->L);
+        return NGPRT_ERR_UNSUPPORTED;
+    }
+    return NGPRT_OK;
+}
+
 int32_t check_opts(const ngprt_render_opts* o, const char* fn) {
     NGPRT_REQUIRE(o != nullptr, "%s: opts is NULL", fn);
     NGPRT_REQUIRE(o->step_base > 0.0f && o->step_gamma > 0.0f, "%s: step_base and step_gamma must be > 0", fn);
@@ -377,6 +366,7 @@ extern "C" int32_t ngprt_render(const ngprt_scene* scene, const ngprt_occ* occ, 
     if ((rc = make_grid(scene, p.g, fn)) != NGPRT_OK) return rc;
     if ((rc = make_occ(occ, p.occ, fn)) != NGPRT_OK) return rc;
     if ((rc = check_opts(opts, fn)) != NGPRT_OK) return rc;
+    if ((rc = check_agg(scene, opts, true, fn)) != NGPRT_OK) return rc;
     NGPRT_REQUIRE(n_rays >= 0, "%s: n_rays=%lld", fn, (long long)n_rays);
     NGPRT_REQUIRE(n_rays == 0 || rgb != nullptr || ray_state != nullptr, "%s: rgb and ray_state both NULL", fn);
     NGPRT_REQUIRE(march_supports(scene->L), "%s: no kernel for L=%d (built: 1, 2, 3, 4, 8, 16)", fn, scene->L);
@@ -391,7 +381,8 @@ extern "C" int32_t ngprt_render(const ngprt_scene* scene, const ngprt_occ* occ, 
     float* state = ray_state;
     char* ws = static_cast<char*>(workspace);
     const size_t need_state = ray_state ? 0 : state_bytes(n_rays);
-    const bool wavefront = ws && ws_bytes >= need_state + wavefront_bytes(n_rays);
+    const bool wavefront = ws && ws_bytes >= need_state + wavefront_bytes(n_rays) &&
+                           scene->aggregation == NGPRT_AGG_SEPARATE_V;
     if (!state) {
         if (!ws || ws_bytes < need_state) {
             set_error("%s: workspace %zu bytes < %zu needed", fn, ws_bytes, ngprt_render_workspace_bytes(scene, n_rays));
@@ -409,7 +400,8 @@ extern "C" int32_t ngprt_render(const ngprt_scene* scene, const ngprt_occ* occ, 
     if (wavefront) {
         if ((rc = run_wavefront(scene->L, scene->table_dtype, p, grid, ws + need_state, st)) != NGPRT_OK) return rc;
     } else {
-        if ((rc = launch_march_any(scene->L, scene->table_dtype, p, grid, st)) != NGPRT_OK) return rc;
+        if ((rc = launch_march_any(scene->L, scene->table_dtype, scene->aggregation, p, grid, st)) != NGPRT_OK)
+            return rc;
     }
     if (!rgb) return cuda_status(fn);
     if ((rc = launch_shade(scene, state, n_rays, opts->bg, rgb, depth, opacity, st, fn)) != NGPRT_OK) return rc;
@@ -459,8 +451,9 @@ extern "C" int32_t ngprt_render_fallback(const ngprt_scene* scene, const ngprt_o
     if ((rc = make_grid(scene, p.g, fn)) != NGPRT_OK) return rc;
     if ((rc = make_occ(occ, p.occ, fn)) != NGPRT_OK) return rc;
     if ((rc = check_opts(opts, fn)) != NGPRT_OK) return rc;
+    if ((rc = check_agg(scene, opts, true, fn)) != NGPRT_OK) return rc;
     NGPRT_REQUIRE(n_rays >= 0, "%s: n_rays=%lld", fn, (long long)n_rays);
-    if (!march_supports(scene->L)) {
+    if (!march_supports(scene->L, scene->aggregation)) {
         set_error("%s: no kernel for L=%d", fn, scene->L);
         return NGPRT_ERR_UNSUPPORTED;
     }
@@ -475,7 +468,8 @@ extern "C" int32_t ngprt_render_fallback(const ngprt_scene* scene, const ngprt_o
     p.stats = ray_stats;
     p.fb_a_hat = a_hat;
     p.fb_thr = threshold;
-    if ((rc = launch_march_any(scene->L, scene->table_dtype, p, grid, static_cast<cudaStream_t>(stream))) != NGPRT_OK)
+    if ((rc = launch_march_any(scene->L, scene->table_dtype, scene->aggregation, p, grid,
+                               static_cast<cudaStream_t>(stream))) != NGPRT_OK)
         return rc;
     return cuda_status(fn);
 }
@@ -491,6 +485,7 @@ extern "C" int32_t ngprt_proposal_targets(const ngprt_scene* scene, const ngprt_
     if ((rc = make_grid(scene, p.g, fn)) != NGPRT_OK) return rc;
     if ((rc = make_occ(occ, p.occ, fn)) != NGPRT_OK) return rc;
     if ((rc = check_opts(opts, fn)) != NGPRT_OK) return rc;
+    if ((rc = check_agg(scene, opts, false, fn)) != NGPRT_OK) return rc;
     NGPRT_REQUIRE(n_rays >= 0, "%s: n_rays=%lld", fn, (long long)n_rays);
     dim3 grid;
     if ((rc = setup_rays(p, cams, n_cams, pixel_ids, rays_o, rays_d, n_rays, grid, fn)) != NGPRT_OK) return rc;

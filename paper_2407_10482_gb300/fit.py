@@ -1,0 +1,108 @@
+"""Fitting an NGP-RT scene to images with the library's own kernels.
+
+A fitted model is what the render path is meant to draw: the PSNR loss of a faster
+form only means something against the images the model was fitted to (Sec. 4).
+``fit`` runs the training loop of Sec. S2.1 in its plainest form on the render path
+of this library: each step renders a random minibatch of pixels with
+``ngprt_render`` (keeping the per-ray state), takes the photometric L2 loss and its
+gradient with ``ngprt_l2_loss``, runs ``ngprt_render_backward`` into the table,
+coarse-grid and MLP gradients and applies ``ngprt_adam_step`` to each of them.
+torch only holds the buffers and draws the minibatch indices.
+"""
+from __future__ import annotations
+
+import math
+import time
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import ngprt as ng
+from . import scenes as S
+
+
+@dataclass
+class FitConfig:
+    steps: int = 1500
+    batch: int = 1 << 18
+    lr: float = 1e-2           # tables and coarse grid
+    lr_mlp: float = 3e-3
+    beta1: float = 0.9
+    beta2: float = 0.99
+    eps: float = 1e-15
+    warmup: int = 50           # linear learning-rate warm-up, steps
+    decay_from: float = 0.6    # cosine decay to lr / 10 over the last 40% of steps
+    table_std: float = 1e-4    # initial tables and coarse grid ~ N(0, table_std)
+    density_init: float = 0.0  # initial coarse density logit (sigma = exp(density_init))
+    seed: int = 3
+
+
+def initial_scene(cfg: S.SceneConfig, fc: FitConfig, device="cuda"):
+    """(tables, coarse, mlp_w) device tensors to start a fit from: small Gaussian
+    grids with the coarse density logit at ``density_init`` and an MLP ~ N(0, 1/fan_in)."""
+    g = torch.Generator(device=device)
+    g.manual_seed(fc.seed)
+    tables = torch.randn(S.table_entries(cfg), S.N_FEAT, generator=g, device=device) * fc.table_std
+    coarse = torch.randn(cfg.R_C ** 3, S.N_FEAT + 2 * cfg.L, generator=g, device=device) * fc.table_std
+    coarse[:, 0] += fc.density_init
+    rng = np.random.default_rng(fc.seed)
+    ws = []
+    for k, (o, i) in enumerate(S.mlp_shapes(cfg)):
+        real_in = 23 if k == 0 else i
+        w = rng.normal(0.0, 1.0 / math.sqrt(real_in), (o, i)).astype(np.float32)
+        if k == 0:
+            w[:, 23:] = 0.0
+        ws.append(w.reshape(-1))
+    mlp_w = torch.as_tensor(np.concatenate(ws)).to(device)
+    return tables, coarse, mlp_w
+
+
+def _lr_factor(step: int, fc: FitConfig) -> float:
+    f = min(1.0, step / max(1, fc.warmup))
+    s0 = fc.decay_from * fc.steps
+    if step > s0:
+        x = (step - s0) / max(1.0, fc.steps - s0)
+        f *= 0.1 + 0.45 * (1.0 + math.cos(math.pi * x))
+    return f
+
+
+def fit(scene: ng.DeviceScene, occ: ng.DeviceOcc, opts, cams: np.ndarray, W: int, H: int,
+        targets: torch.Tensor, fc: FitConfig = FitConfig(), log_every: int = 0, stream=None):
+    """Fit ``scene`` (FP32 tables, coarse grid and MLP, updated in place) to the images
+    ``targets`` [n_views * H * W, 3] of the cameras ``cams``.  Returns the loss history
+    [(step, loss)] and the wall time in seconds."""
+    dev = scene.tables.device
+    rend = ng.Renderer(scene, occ, device=dev)
+    params = [scene.tables, scene.coarse, scene.mlp_w]
+    lrs = [fc.lr, fc.lr, fc.lr_mlp]
+    grads = [torch.zeros_like(p) for p in params]
+    moms = [(torch.zeros_like(p), torch.zeros_like(p)) for p in params]
+    n_pix = len(cams) * W * H
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(fc.seed)
+    B = fc.batch
+    loss = torch.zeros(1, device=dev)
+    d_rgb = torch.empty(B, 3, device=dev)
+    out = dict(rgb=torch.empty(B, 3, device=dev), depth=torch.empty(B, device=dev),
+               opacity=torch.empty(B, device=dev), state=torch.empty(B, ng.STATE_FLOATS, device=dev))
+    hist = []
+    t0 = time.perf_counter()
+    for step in range(1, fc.steps + 1):
+        idx = torch.randint(0, n_pix, (B,), device=dev, generator=gen)
+        pix = idx.to(torch.int32)
+        tg = targets[idx].contiguous()
+        logging = bool(log_every) and (step % log_every == 0 or step == fc.steps)
+        if logging:
+            loss.zero_()
+        rend.render(opts, cams=cams, W=W, H=H, pixel_ids=pix, state=True, out=out)
+        ng.ngprt_l2_loss(out["rgb"], tg, 3 * B, 1.0 / (3 * B), loss if logging else None, d_rgb, stream=stream)
+        rend.backward(opts, out["state"], d_rgb, None, None, grads[0], grads[1], grads[2], cams=cams, W=W, H=H,
+                      pixel_ids=pix)
+        f = _lr_factor(step, fc)
+        for p, g, (m, v), lr in zip(params, grads, moms, lrs):
+            ng.ngprt_adam_step(p, g, m, v, lr * f, fc.beta1, fc.beta2, fc.eps, step, True, stream=stream)
+        if logging:
+            hist.append((step, float(loss.item())))
+    torch.cuda.synchronize(dev)
+    return hist, time.perf_counter() - t0

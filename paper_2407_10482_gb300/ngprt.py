@@ -35,7 +35,8 @@ class ngprt_scene(C.Structure):
     _fields_ = [("L", C.c_int32), ("T_log2", C.c_int32), ("N", C.c_int32 * MAX_LEVELS),
                 ("table_dtype", C.c_int32), ("R_C", C.c_int32), ("mlp_layers", C.c_int32),
                 ("mlp_width", C.c_int32), ("mlp_dtype", C.c_int32), ("bounded", C.c_int32),
-                ("tables", C.c_void_p), ("coarse", C.c_void_p), ("mlp_w", C.c_void_p)]
+                ("tables", C.c_void_p), ("coarse", C.c_void_p), ("mlp_w", C.c_void_p),
+                ("aggregation", C.c_int32), ("attn_inv", C.c_void_p), ("agg_mlp", C.c_void_p)]
 
 
 class ngprt_occ(C.Structure):
@@ -60,6 +61,7 @@ _SIGS = {
     "ngprt_build_occ_dist_workspace_bytes": (C.c_size_t, [C.c_int32]),
     "ngprt_build_occ_dist": (C.c_int32, [_P, C.c_int32, C.c_int32, _P, _P, _P, C.c_size_t, _P]),
     "ngprt_table_entries": (C.c_int64, [_P]),
+    "ngprt_coarse_channels": (C.c_int32, [C.c_int32, C.c_int32]),
     "ngprt_render_workspace_bytes": (C.c_size_t, [_P, C.c_int64]),
     "ngprt_wavefront_workspace_bytes": (C.c_size_t, [_P, C.c_int64]),
     "ngprt_render": (C.c_int32, [_P, _P, _P, C.c_int32, _P, _P, _P, C.c_int64, _P, _P, _P, _P, _P, _P, _P,
@@ -152,6 +154,10 @@ def ngprt_build_occ_dist(occ, R, n_levels, occ_bits_out, dist_out, workspace, st
 
 def ngprt_table_entries(scene: ngprt_scene) -> int:
     return int(lib().ngprt_table_entries(C.byref(scene)))
+
+
+def ngprt_coarse_channels(L: int, aggregation: int) -> int:
+    return int(lib().ngprt_coarse_channels(L, aggregation))
 
 
 def ngprt_render_workspace_bytes(scene: ngprt_scene, n_rays: int) -> int:
@@ -292,14 +298,18 @@ class DeviceScene:
     ``tables``/``coarse`` are uploaded in ``table_dtype`` (F32, F16 or BF16; the
     16-bit forms round to nearest even from the FP32 master)."""
 
-    def __init__(self, cfg, tables, coarse, mlp_w, table_dtype: int = F32, device="cuda", mlp_dtype: int = F32):
+    def __init__(self, cfg, tables, coarse, mlp_w, table_dtype: int = F32, device="cuda", mlp_dtype: int = F32,
+                 attn_inv=None, agg_mlp=None):
         dt = _TORCH_DT[table_dtype]
         self.cfg = cfg
         self.table_dtype = table_dtype
         self.mlp_dtype = mlp_dtype
+        self.aggregation = int(getattr(cfg, "aggregation", 0))
         self.tables = _device_array(tables, dt, device)
         self.coarse = _device_array(coarse, dt, device)
         self.mlp_w = _device_array(mlp_w, _TORCH_DT[mlp_dtype], device)
+        self.attn_inv = None if attn_inv is None else _device_array(attn_inv, torch.float32, device)
+        self.agg_mlp = None if agg_mlp is None else _device_array(agg_mlp, torch.float32, device)
         self.refresh()
 
     def refresh(self) -> None:
@@ -312,6 +322,8 @@ class DeviceScene:
         s.mlp_layers, s.mlp_width, s.mlp_dtype = c.mlp_layers, c.mlp_width, self.mlp_dtype
         s.bounded = 1 if c.bounded else 0
         s.tables, s.coarse, s.mlp_w = _ptr(self.tables), _ptr(self.coarse), _ptr(self.mlp_w)
+        s.aggregation = self.aggregation
+        s.attn_inv, s.agg_mlp = _ptr(self.attn_inv), _ptr(self.agg_mlp)
         self.struct = s
 
 

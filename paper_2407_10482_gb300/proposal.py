@@ -29,7 +29,7 @@ class ProposalConfig:
     margin_far: float = float("inf")  # after t_far (inf: no far clip, termination ends the ray)
     a_min: float = 0.01        # predicted opacity below which nothing is marched
     fallback: float = 0.01     # re-march when a_hat - A(interval) exceeds this
-    steps: int = 2000
+    steps: int = 6000
     batch: int = 1 << 15
     lr: float = 1e-2
     seed: int = 4

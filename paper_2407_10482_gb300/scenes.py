@@ -62,6 +62,7 @@ class SceneConfig:
     occ_threshold: float = 0.01
     blob_std: tuple = (0.08, 0.25)
     blob_peak: tuple = (5.0, 50.0)
+    aggregation: int = 0    # level fusion (Eq. 8 = 0; the Table 3 variants 1..5, see coarse_channels)
 
 
 def level_resolutions(n_min: int, n_max: int, L: int) -> list:
@@ -112,6 +113,33 @@ class Scene:
     mlp_w: np.ndarray         # float32 flat, layer matrices [out][in] concatenated
     occ: np.ndarray           # uint8 [R_O^3], x fastest
     blobs: dict = field(default_factory=dict)
+    attn_inv: np.ndarray = None  # float32 constant attention logits (aggregations 2, 3)
+    agg_mlp: np.ndarray = None   # float32 W1 [64][8L] then W2 [8][64] (aggregation 5)
+
+
+AGG_HIDDEN = 64  # hidden units of the tiny-MLP aggregation
+
+
+def coarse_channels(cfg: SceneConfig) -> int:
+    """Channels per coarse-grid vertex: the deferred feature (8), plus omega and beta per
+    level for Eq. 8 (aggregation 0) or one logit per level (1, shared gates); the
+    spatially invariant gates (2, 3), the plain sum (4) and the tiny MLP (5) keep 8."""
+    return {0: N_FEAT + 2 * cfg.L, 1: N_FEAT + cfg.L}.get(int(cfg.aggregation), N_FEAT)
+
+
+def _aggregation_params(cfg: SceneConfig, rng: np.random.Generator):
+    """(attn_inv, agg_mlp) of the aggregation variants, drawn after everything else so
+    that the Eq. 8 scenes do not change: invariant logits ~ N(0, init_std) (gates near
+    1/2, as the variant grids' logits), MLP weights ~ N(0, 1/fan_in)."""
+    agg = int(cfg.aggregation)
+    attn_inv = agg_mlp = None
+    if agg in (2, 3):
+        attn_inv = rng.normal(0.0, cfg.init_std, (2 if agg == 2 else 1) * cfg.L).astype(np.float32)
+    if agg == 5:
+        w1 = rng.normal(0.0, 1.0 / math.sqrt(N_FEAT * cfg.L), (AGG_HIDDEN, N_FEAT * cfg.L))
+        w2 = rng.normal(0.0, 1.0 / math.sqrt(AGG_HIDDEN), (N_FEAT, AGG_HIDDEN))
+        agg_mlp = np.concatenate([w1.reshape(-1), w2.reshape(-1)]).astype(np.float32)
+    return attn_inv, agg_mlp
 
 
 def mlp_shapes(cfg: SceneConfig) -> list:
@@ -201,7 +229,7 @@ def make_scene(cfg: SceneConfig) -> Scene:
     blobs = _blobs(cfg, rng)
     n_ent = table_entries(cfg)
     tables = rng.normal(0.0, cfg.init_std, (n_ent, N_FEAT)).astype(np.float32)
-    n_ch = N_FEAT + 2 * cfg.L
+    n_ch = coarse_channels(cfg)
     coarse = rng.normal(0.0, cfg.init_std, (cfg.R_C ** 3, n_ch)).astype(np.float32)
     coarse[:, 0] += np.float32(cfg.density_bias)
     ws = []
@@ -213,7 +241,9 @@ def make_scene(cfg: SceneConfig) -> Scene:
         ws.append(w.reshape(-1))
     mlp_w = np.concatenate(ws).astype(np.float32)
     occ = _occupancy(cfg, blobs)
-    return Scene(cfg=cfg, tables=tables, coarse=coarse, mlp_w=mlp_w, occ=occ, blobs=blobs)
+    attn_inv, agg_mlp = _aggregation_params(cfg, rng)
+    return Scene(cfg=cfg, tables=tables, coarse=coarse, mlp_w=mlp_w, occ=occ, blobs=blobs, attn_inv=attn_inv,
+                 agg_mlp=agg_mlp)
 
 
 # --------------------------------------------------------------------------- cameras
@@ -322,17 +352,28 @@ def make_scene_torch(cfg: SceneConfig, device="cuda", occ_chunk: int = 1 << 22) 
     g = torch.Generator(device=device)
     g.manual_seed(cfg.seed)
     tables = torch.randn(table_entries(cfg), N_FEAT, generator=g, device=device) * cfg.init_std
-    coarse = torch.randn(cfg.R_C ** 3, N_FEAT + 2 * cfg.L, generator=g, device=device) * cfg.init_std
+    coarse = torch.randn(cfg.R_C ** 3, coarse_channels(cfg), generator=g, device=device) * cfg.init_std
     coarse[:, 0] += cfg.density_bias
-    # occupancy: blob density at voxel centres of the contracted cube (world points by
-    # the inverse radial map), plus every voxel whose box meets the shell
+    occ = occupancy_torch(cfg, blobs, device, occ_chunk)
+    attn_inv, agg_mlp = _aggregation_params(cfg, rng)
+    return Scene(cfg=cfg, tables=tables, coarse=coarse, mlp_w=mlp_w, occ=occ, blobs=blobs, attn_inv=attn_inv,
+                 agg_mlp=agg_mlp)
+
+
+def occupancy_torch(cfg: SceneConfig, blobs: dict, device="cuda", chunk: int = 1 << 22):
+    """The unbounded scene's occupancy grid (as ``_occupancy``) evaluated with torch on
+    ``device`` in chunks of voxel centres: blob density above ``occ_threshold`` at
+    the voxel centre mapped back to world space, plus every voxel whose box meets the
+    shell.  uint8 [R_O^3], x fastest."""
+    import torch
+    assert not cfg.bounded
     R = cfg.R_O
     mu = torch.as_tensor(blobs["mu"], device=device, dtype=torch.float64)
     std = torch.as_tensor(blobs["std"], device=device, dtype=torch.float64)
     peak = torch.as_tensor(blobs["peak"], device=device, dtype=torch.float64)
     occ = torch.empty(R ** 3, dtype=torch.uint8, device=device)
-    for s0 in range(0, R ** 3, occ_chunk):
-        idx = torch.arange(s0, min(s0 + occ_chunk, R ** 3), device=device, dtype=torch.int64)
+    for s0 in range(0, R ** 3, chunk):
+        idx = torch.arange(s0, min(s0 + chunk, R ** 3), device=device, dtype=torch.int64)
         vx, vy, vz = idx % R, (idx // R) % R, idx // (R * R)
         y = (torch.stack([vx, vy, vz], 1).double() + 0.5) / R * 4.0 - 2.0
         ry = torch.linalg.norm(y, dim=1)
@@ -347,4 +388,4 @@ def make_scene_torch(cfg: SceneConfig, device="cuda", occ_chunk: int = 1 << 22) 
             rmax = torch.linalg.norm(y.abs() + h, dim=1)
             o |= (rmin <= 1.9) & (rmax >= 1.875)
         occ[s0:s0 + len(idx)] = o.to(torch.uint8)
-    return Scene(cfg=cfg, tables=tables, coarse=coarse, mlp_w=mlp_w, occ=occ, blobs=blobs)
+    return occ

@@ -83,3 +83,45 @@ def test_argument_errors_are_reported_without_a_launch(ng):
     rc = lib.ngprt_render(C.byref(s), C.byref(o), None, 0, None, C.c_void_p(256), C.c_void_p(256), 4, None,
                           C.byref(opts), C.c_void_p(256), None, None, None, None, None, 0, None)
     assert rc == ng.ERR_INVALID_ARG and b"attn_mode" in lib.ngprt_last_error()
+
+
+def test_aggregation_layouts_and_validation(ng):
+    """Coarse-grid channel counts of the Table 3 aggregations and the host-side checks
+    (no device work: every call below returns before any launch)."""
+    from oracle import oracle as O
+    lib = ng.lib()
+    for L in (2, 4, 16):
+        for agg in range(6):
+            n = ng.ngprt_coarse_channels(L, agg)
+            assert n == O.coarse_channels(L, agg) == S.coarse_channels(S.small_config(L=L, aggregation=agg))
+    assert ng.ngprt_coarse_channels(4, 6) == 0 and ng.ngprt_coarse_channels(0, 0) == 0
+    cfg = S.small_config()
+    s = ng.ngprt_scene()
+    s.L, s.T_log2, s.R_C, s.mlp_layers, s.mlp_width = 4, 12, 16, 2, 16
+    for i in range(4):
+        s.N[i] = 16 << i
+    s.tables = s.coarse = s.mlp_w = 256
+    o = ng.ngprt_occ(32, 3, 256, None)
+    opts = ng.render_opts(S.default_options(cfg))
+
+    def render():
+        return lib.ngprt_render(C.byref(s), C.byref(o), None, 0, None, C.c_void_p(256), C.c_void_p(256), 4, None,
+                                C.byref(opts), C.c_void_p(256), None, None, None, None, None, 0, None)
+    s.aggregation = 9
+    assert render() == ng.ERR_INVALID_ARG and b"aggregation" in lib.ngprt_last_error()
+    s.aggregation = 2                       # invariant gates without their logits
+    assert render() == ng.ERR_INVALID_ARG and b"attn_inv" in lib.ngprt_last_error()
+    s.aggregation = 5                       # MLP aggregation, misaligned weights
+    s.agg_mlp = 256 + 4
+    assert render() == ng.ERR_INVALID_ARG and b"agg_mlp" in lib.ngprt_last_error()
+    s.aggregation, s.agg_mlp = 4, None
+    opts.attn_mode = 1                      # attn_mode belongs to the Eq. 8 layout
+    assert render() == ng.ERR_INVALID_ARG and b"attn_mode" in lib.ngprt_last_error()
+    opts.attn_mode = 0
+    s.L = 3                                 # no variant kernel for L = 3
+    assert render() == ng.ERR_UNSUPPORTED and b"L=3" in lib.ngprt_last_error()
+    s.L = 4                                 # variants are forward-only
+    rc = lib.ngprt_render_backward(C.byref(s), C.byref(o), None, 0, None, C.c_void_p(256), C.c_void_p(256), 4,
+                                   C.byref(opts), C.c_void_p(256), C.c_void_p(256), None, None, C.c_void_p(256),
+                                   C.c_void_p(256), C.c_void_p(256), None, 0, None)
+    assert rc == ng.ERR_UNSUPPORTED and b"forward render only" in lib.ngprt_last_error()

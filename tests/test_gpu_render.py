@@ -89,7 +89,8 @@ def _compare(r_gpu, r_or, check_stats=True):
 
 def _pair(ng, cfg, table_dtype=0, sc=None):
     sc = sc or S.make_scene(cfg)
-    ds = ng.DeviceScene(cfg, sc.tables, sc.coarse, sc.mlp_w, table_dtype=table_dtype)
+    ds = ng.DeviceScene(cfg, sc.tables, sc.coarse, sc.mlp_w, table_dtype=table_dtype, attn_inv=sc.attn_inv,
+                        agg_mlp=sc.agg_mlp)
     docc = ng.DeviceOcc(sc.occ, cfg.R_O, cfg.n_occ_levels)
     rend = ng.Renderer(ds, docc)
     if table_dtype == 0:
@@ -98,7 +99,7 @@ def _pair(ng, cfg, table_dtype=0, sc=None):
         tq = ds.tables.float().cpu().numpy()
         cq = ds.coarse.float().cpu().numpy()
     orc = O.Oracle(cfg, tq, cq, sc.mlp_w, O.build_pyramid(sc.occ, cfg.R_O, cfg.n_occ_levels),
-                   O.occ_dist(sc.occ, cfg.R_O))
+                   O.occ_dist(sc.occ, cfg.R_O), attn_inv=sc.attn_inv, agg_mlp=sc.agg_mlp)
     return sc, rend, orc
 
 
@@ -311,3 +312,47 @@ def test_paper_shape_sampled_parity(ng, L):
                    O.build_pyramid(occ, cfg.R_O, cfg.n_occ_levels), O.occ_dist(occ, cfg.R_O))
     _compare(r, orc.render(opts, cams=cams, pix=pix))
     assert r["stats"][:, 1].float().mean() > 3
+
+
+@pytest.mark.parametrize("agg", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("L", [2, 4])
+def test_aggregation_variants_small(ng, agg, L):
+    """The Table 3 aggregations (shared / invariant gates, plain sum, tiny MLP) in
+    their own coarse-grid layouts, a full 64x64 view against the oracle."""
+    cfg = S.small_config(L=L, N=[16 * 2 ** l for l in range(L)], aggregation=agg)
+    sc, rend, orc = _pair(ng, cfg)
+    opts = S.default_options(cfg)
+    cams = S.orbit_cameras(cfg, 1, azimuth0=20.0)
+    r = rend.render(opts, cams=cams, W=cfg.W, H=cfg.H, stats=True)
+    torch.cuda.synchronize()
+    _compare(r, orc.render(opts, cams=cams))
+
+
+@pytest.mark.parametrize("agg,table_dtype", [(4, 0), (5, 0), (2, 1)])
+def test_aggregation_variants_hd_sampled(ng, agg, table_dtype):
+    """L = 16 variants (their own translation unit) on the hd frame, 1500 sampled
+    pixels; the FP16 case is compared with the oracle on the rounded tables."""
+    cfg = S.hd_config(aggregation=agg)
+    sc, rend, orc = _pair(ng, cfg, table_dtype=table_dtype)
+    opts = S.default_options(cfg)
+    cams = S.orbit_cameras(cfg, 1, azimuth0=10.0)
+    pix = np.random.default_rng(agg).choice(cfg.W * cfg.H, 1500, replace=False).astype(np.int32)
+    r = rend.render(opts, cams=cams, W=cfg.W, H=cfg.H, pixel_ids=torch.as_tensor(pix).cuda(), stats=True)
+    torch.cuda.synchronize()
+    ref = orc.render(opts, cams=cams, pix=pix)
+    if table_dtype == 0:
+        _compare(r, ref)
+    else:
+        # FP16 tables sum in half2 FMAs: values within the FP16 error, counts may
+        # differ where the rounding moves a termination
+        err = np.abs(r["rgb"].cpu().numpy() - ref["rgb"])
+        assert np.quantile(err, 0.999) < 5e-3
+
+
+def test_aggregation_variant_rejects_unbuilt_requests(ng):
+    cfg = S.small_config(L=3, N=[16, 32, 64], aggregation=4)
+    sc = S.make_scene(cfg)
+    ds = ng.DeviceScene(cfg, sc.tables, sc.coarse, sc.mlp_w)
+    docc = ng.DeviceOcc(sc.occ, cfg.R_O, cfg.n_occ_levels)
+    with pytest.raises(ng.NgprtError, match="not built for L=3"):
+        ng.Renderer(ds, docc).render(S.default_options(cfg), cams=S.orbit_cameras(cfg, 1), W=cfg.W, H=cfg.H)
