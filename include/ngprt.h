@@ -181,6 +181,43 @@ size_t ngprt_build_occ_dist_workspace_bytes(int32_t R);
 int32_t ngprt_build_occ_dist(const uint8_t* occ, int32_t R, int32_t n_levels, uint32_t* occ_bits_out,
                              uint8_t* dist_out, void* workspace, size_t ws_bytes, void* stream);
 
+/*
+ * Render-time occupancy pipeline (Sec. S2.5: occupancy from the trained model,
+ * visibility culling and dilation as in MERF, then the pyramid and G above).
+ * Grids are R^3 uint8 over the unit cube of the scene (x fastest), R a power of two
+ * in [2, 1024].  The three calls are asynchronous on `stream` and need the Eq. 8
+ * aggregation (SEPARATE_V).
+ *
+ * ngprt_occupancy_from_density: occ_out[v] = 1 when sigma = exp(sigma_raw) at the
+ *   centre u = (v + 1/2) / R of voxel v exceeds sigma_thr (features of Eq. 6-8 with
+ *   opts->attn_mode), else 0; sigma_out [R^3] (NULL allowed) receives sigma.
+ */
+int32_t ngprt_occupancy_from_density(const ngprt_scene* scene, const ngprt_render_opts* opts, int32_t R,
+                                     float sigma_thr, uint8_t* occ_out, float* sigma_out, void* stream);
+
+/*
+ * ngprt_occupancy_visibility: marches and composites the given rays as ngprt_render
+ *   does (occ, opts) and sets vis[v] = 1 for the voxel v (R^3 grid, voxel of the
+ *   unit-cube position) of every sample whose weight T_i alpha_i exceeds w_thr.
+ *   vis is only ever set: the caller clears it, and calls over several ray batches
+ *   accumulate.  Rays as for ngprt_render.
+ */
+int32_t ngprt_occupancy_visibility(const ngprt_scene* scene, const ngprt_occ* occ, const ngprt_camera* cams,
+                                   int32_t n_cams, const int32_t* pixel_ids, const float* rays_o,
+                                   const float* rays_d, int64_t n_rays, const ngprt_render_opts* opts, float w_thr,
+                                   int32_t R, uint8_t* vis, void* stream);
+
+/*
+ * ngprt_dilate: out[v] = max of occ over the voxels within `radius` of v along
+ *   every axis (a (2 radius + 1)^3 box clipped by the grid's faces), then 0 wherever
+ *   mask[v] == 0 (mask NULL: no mask; e.g. the density occupancy, so that the render
+ *   grid stays inside it).  R in [1, 1024], radius in [0, 64]; out distinct from occ
+ *   and mask; workspace >= ngprt_dilate_workspace_bytes(R).
+ */
+size_t ngprt_dilate_workspace_bytes(int32_t R);
+int32_t ngprt_dilate(const uint8_t* occ, int32_t R, int32_t radius, const uint8_t* mask, uint8_t* out,
+                     void* workspace, size_t ws_bytes, void* stream);
+
 /* Rows of the concatenated fine tables (sum over levels of min(N^3, 2^T_log2)). */
 int64_t ngprt_table_entries(const ngprt_scene* scene);
 

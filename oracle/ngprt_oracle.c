@@ -1119,3 +1119,70 @@ void or_prop_targets(const or_scene* s, const or_occ* oc, const or_opts* op, con
         free(sm);
     }
 }
+
+/* ------------------------------------------------------- occupancy pipeline */
+
+/* Occupancy from the model's own density (Sec. S2.5): voxel (i, j, k) of an R^3
+ * grid over the unit cube (x fastest) is occupied when sigma = exp(sigma_raw) at
+ * its centre u = ((i, j, k) + 1/2) / R exceeds sigma_thr.  sigma_out (NULL
+ * allowed) receives sigma per voxel. */
+void or_occupancy_density(const or_scene* s, const or_opts* op, int R, double sigma_thr, uint8_t* occ,
+                          double* sigma_out) {
+    long n = (long)R * R * R;
+    #pragma omp parallel for schedule(static)
+    for (long v = 0; v < n; ++v) {
+        int i = (int)(v % R), j = (int)((v / R) % R), k = (int)(v / ((long)R * R));
+        float u[3] = {((float)i + 0.5f) / (float)R, ((float)j + 0.5f) / (float)R, ((float)k + 0.5f) / (float)R};
+        double f[OR_NFEAT];
+        or_features(s, op, u, f);
+        double sg = exp(f[0]);
+        occ[v] = sg > sigma_thr ? 1 : 0;
+        if (sigma_out) sigma_out[v] = sg;
+    }
+}
+
+/* Visibility (Sec. S2.5, after MERF): every ray is marched and composited as in
+ * the render; each sample whose weight T_i alpha_i exceeds w_thr marks the voxel
+ * of its unit-cube position in an R^3 grid.  vis is only ever set (the caller
+ * clears it); wmax (NULL allowed, caller-initialised) receives the largest weight
+ * per voxel. */
+void or_occupancy_visibility(const or_scene* s, const or_occ* oc, const or_opts* op,
+                             const float* cams, int n_cams, int W, int H, const int32_t* pix,
+                             const float* rays_o, const float* rays_d, int n, int R, double w_thr,
+                             uint8_t* vis, double* wmax) {
+    or_sample* sm = (or_sample*)malloc(sizeof(or_sample) * (size_t)(op->max_samples > 0 ? op->max_samples : 1));
+    for (int i = 0; i < n; ++i) {
+        float o[3], dv[3];
+        or_ray_input(cams, n_cams, W, H, pix, rays_o, rays_d, i, o, dv);
+        or_ray_out rr;
+        or_march(s, oc, op, o, dv, -INFINITY, INFINITY, &rr, sm, NULL);
+        for (int a = 0; a < rr.n_samples; ++a) {
+            double w = sm[a].T_before * sm[a].alpha;
+            long v = (long)or_vox(sm[a].u[0], R) + (long)R * ((long)or_vox(sm[a].u[1], R) +
+                                                             (long)R * (long)or_vox(sm[a].u[2], R));
+            if (w > w_thr) vis[v] = 1;
+            if (wmax && w > wmax[v]) wmax[v] = w;
+        }
+    }
+    free(sm);
+}
+
+/* Dilation by a (2r+1)^3 box: out[v] = the largest occ over the voxels within r of
+ * v along every axis, the grid's faces clipping the box; with a mask, out[v] is
+ * cleared wherever mask[v] is 0. */
+void or_dilate(const uint8_t* occ, int R, int r, const uint8_t* mask, uint8_t* out) {
+    #pragma omp parallel for schedule(static)
+    for (long v = 0; v < (long)R * R * R; ++v) {
+        int i = (int)(v % R), j = (int)((v / R) % R), k = (int)(v / ((long)R * R));
+        uint8_t m = 0;
+        for (int dz = -r; dz <= r; ++dz)
+            for (int dy = -r; dy <= r; ++dy)
+                for (int dx = -r; dx <= r; ++dx) {
+                    int x = i + dx, y = j + dy, z = k + dz;
+                    if (x < 0 || y < 0 || z < 0 || x >= R || y >= R || z >= R) continue;
+                    uint8_t q = occ[(long)x + (long)R * ((long)y + (long)R * z)];
+                    if (q > m) m = q;
+                }
+        out[v] = (mask && !mask[v]) ? 0 : m;
+    }
+}

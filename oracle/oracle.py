@@ -123,6 +123,16 @@ def build_pyramid(occ: np.ndarray, R: int, n_levels: int) -> np.ndarray:
     return out
 
 
+def dilate(occ: np.ndarray, R: int, r: int, mask=None) -> np.ndarray:
+    """Box dilation of an R^3 uint8 grid by radius r (faces clip the box), cleared
+    where mask (optional) is 0."""
+    occ = _c(occ, np.uint8).reshape(-1)
+    mask = _c(mask, np.uint8)
+    out = np.empty(R ** 3, np.uint8)
+    lib().or_dilate(_p(occ), C.c_int(R), C.c_int(r), _p(mask), _p(out))
+    return out
+
+
 def occ_dist_brute(occ: np.ndarray, R: int) -> np.ndarray:
     occ = _c(occ, np.uint8).reshape(-1)
     out = np.empty(R ** 3, np.uint8)
@@ -249,6 +259,31 @@ class Oracle:
                         _p(amb), _p(state))
         return dict(rgb=rgb, depth=depth, opacity=opac, stats=stats, ambiguous=amb.astype(bool),
                     state=state)
+
+    def occupancy_density(self, opts, R: int, sigma_thr: float):
+        """Occupancy from the model's density at the centres of an R^3 grid (Sec. S2.5):
+        (uint8 occ [R^3], sigma [R^3])."""
+        occ = np.empty(R ** 3, np.uint8)
+        sig = np.empty(R ** 3, np.float64)
+        op = self._opts(opts)
+        lib().or_occupancy_density(C.byref(self._s), C.byref(op), C.c_int(R), C.c_double(sigma_thr), _p(occ),
+                                   _p(sig))
+        return occ, sig
+
+    def occupancy_visibility(self, opts, R: int, w_thr: float, cams=None, pix=None, rays_o=None, rays_d=None,
+                             W=None, H=None):
+        """Voxels of an R^3 grid holding a sample of weight > w_thr on the given rays:
+        (uint8 vis [R^3], largest weight per voxel [R^3])."""
+        W = W or self.cfg.W
+        H = H or self.cfg.H
+        cams, pix, ro, rd, n = self._rays(cams, pix, rays_o, rays_d)
+        vis = np.zeros(R ** 3, np.uint8)
+        wmax = np.zeros(R ** 3, np.float64)
+        op = self._opts(opts)
+        lib().or_occupancy_visibility(C.byref(self._s), C.byref(self._o), C.byref(op), _p(cams),
+                                      C.c_int(0 if cams is None else len(cams)), C.c_int(W), C.c_int(H), _p(pix),
+                                      _p(ro), _p(rd), C.c_int(n), C.c_int(R), C.c_double(w_thr), _p(vis), _p(wmax))
+        return vis, wmax
 
     def render_backward(self, opts, d_rgb=None, d_depth=None, d_opacity=None, cams=None, pix=None,
                         rays_o=None, rays_d=None, W=None, H=None):

@@ -487,9 +487,10 @@ struct ForwardSampler {
     float t_term;
     float* gates;
     float T, A, depth;
+    float w_last;  // weight of the last composited sample
     float Cd[3], F[4];
     __device__ __forceinline__ ForwardSampler(const Grid& g_, int mode, float term, float* gate_buf)
-        : g(g_), attn_mode(mode), t_term(term), gates(gate_buf), T(1.0f), A(0.0f), depth(0.0f) {
+        : g(g_), attn_mode(mode), t_term(term), gates(gate_buf), T(1.0f), A(0.0f), depth(0.0f), w_last(0.0f) {
         Cd[0] = Cd[1] = Cd[2] = 0.0f;
         F[0] = F[1] = F[2] = F[3] = 0.0f;
     }
@@ -513,6 +514,7 @@ struct ForwardSampler {
         const float sigma = expf(f[0]);
         const float trans = expf(-sigma * delta);
         const float w = T * (1.0f - trans);
+        w_last = w;
 #pragma unroll
         for (int k = 0; k < 3; ++k) Cd[k] = fmaf(w, f[1 + k], Cd[k]);
 #pragma unroll

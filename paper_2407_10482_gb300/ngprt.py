@@ -62,6 +62,11 @@ _SIGS = {
     "ngprt_build_occ_dist": (C.c_int32, [_P, C.c_int32, C.c_int32, _P, _P, _P, C.c_size_t, _P]),
     "ngprt_table_entries": (C.c_int64, [_P]),
     "ngprt_coarse_channels": (C.c_int32, [C.c_int32, C.c_int32]),
+    "ngprt_occupancy_from_density": (C.c_int32, [_P, _P, C.c_int32, C.c_float, _P, _P, _P]),
+    "ngprt_occupancy_visibility": (C.c_int32, [_P, _P, _P, C.c_int32, _P, _P, _P, C.c_int64, _P, C.c_float,
+                                               C.c_int32, _P, _P]),
+    "ngprt_dilate_workspace_bytes": (C.c_size_t, [C.c_int32]),
+    "ngprt_dilate": (C.c_int32, [_P, C.c_int32, C.c_int32, _P, _P, _P, C.c_size_t, _P]),
     "ngprt_render_workspace_bytes": (C.c_size_t, [_P, C.c_int64]),
     "ngprt_wavefront_workspace_bytes": (C.c_size_t, [_P, C.c_int64]),
     "ngprt_render": (C.c_int32, [_P, _P, _P, C.c_int32, _P, _P, _P, C.c_int64, _P, _P, _P, _P, _P, _P, _P,
@@ -158,6 +163,28 @@ def ngprt_table_entries(scene: ngprt_scene) -> int:
 
 def ngprt_coarse_channels(L: int, aggregation: int) -> int:
     return int(lib().ngprt_coarse_channels(L, aggregation))
+
+
+def ngprt_occupancy_from_density(scene, opts, R, sigma_thr, occ_out, sigma_out=None, stream=None) -> None:
+    _check("ngprt_occupancy_from_density", lib().ngprt_occupancy_from_density(
+        C.byref(scene), C.byref(opts), R, sigma_thr, _ptr(occ_out), _ptr(sigma_out), _stream(stream)))
+
+
+def ngprt_occupancy_visibility(scene, occ, cams, n_cams, pixel_ids, rays_o, rays_d, n_rays, opts, w_thr, R, vis,
+                               stream=None) -> None:
+    _check("ngprt_occupancy_visibility", lib().ngprt_occupancy_visibility(
+        C.byref(scene), C.byref(occ), cams, n_cams, _ptr(pixel_ids), _ptr(rays_o), _ptr(rays_d), n_rays,
+        C.byref(opts), w_thr, R, _ptr(vis), _stream(stream)))
+
+
+def ngprt_dilate_workspace_bytes(R: int) -> int:
+    return int(lib().ngprt_dilate_workspace_bytes(R))
+
+
+def ngprt_dilate(occ, R, radius, out, workspace, mask=None, stream=None) -> None:
+    ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    _check("ngprt_dilate", lib().ngprt_dilate(_ptr(occ), R, radius, _ptr(mask), _ptr(out), _ptr(workspace), ws_bytes,
+                                              _stream(stream)))
 
 
 def ngprt_render_workspace_bytes(scene: ngprt_scene, n_rays: int) -> int:
