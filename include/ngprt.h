@@ -338,6 +338,46 @@ int32_t ngprt_l2_loss(const float* rgb, const float* target, int64_t n, float sc
                       void* stream);
 
 /*
+ * Huber colour loss of the training objective (Sec. S2.4, L_color): per float
+ * h(e) = e^2 / 2 for |e| <= delta, else delta (|e| - delta / 2), e = rgb - target;
+ * *loss += scale * sum_i h(e_i) (NULL to skip) and d_rgb = scale * h'(e) (NULL to
+ * skip), h'(e) = e or delta sign(e).  delta > 0.
+ */
+int32_t ngprt_huber_loss(const float* rgb, const float* target, int64_t n, float delta, float scale, float* loss,
+                         float* d_rgb, void* stream);
+
+/*
+ * Distortion regulariser of the training objective (Eq. S2), per ray over the
+ * samples the render composites (same march, same weights):
+ *   L_dist = sum_{i,j} w_i w_j |m_i - m_j| + 1/3 sum_i w_i^2 delta_i,
+ * m_i = t_i + delta_i / 2.  ngprt_distortion_loss writes dist_state [n][4] =
+ * (L_dist, sum_i w_i, sum_i w_i m_i, 0) per ray (16-byte aligned) and adds
+ * scale * sum over rays of L_dist to *loss (NULL to skip).
+ * ngprt_distortion_backward ACCUMULATES scale * dL_dist/d(parameters) into g_tables
+ * and g_coarse (FP32, layouts of the scene) from that dist_state: the density path
+ * only (sigma~, the omega logits and the fine density channel).  Both need F32
+ * tables, the Eq. 8 aggregation and L in {1, 2, 4, 16}; rays as for ngprt_render.
+ */
+int32_t ngprt_distortion_loss(const ngprt_scene* scene, const ngprt_occ* occ, const ngprt_camera* cams,
+                              int32_t n_cams, const int32_t* pixel_ids, const float* rays_o, const float* rays_d,
+                              int64_t n_rays, const ngprt_render_opts* opts, float scale, float* dist_state,
+                              float* loss, void* stream);
+int32_t ngprt_distortion_backward(const ngprt_scene* scene, const ngprt_occ* occ, const ngprt_camera* cams,
+                                  int32_t n_cams, const int32_t* pixel_ids, const float* rays_o, const float* rays_d,
+                                  int64_t n_rays, const ngprt_render_opts* opts, const float* dist_state, float scale,
+                                  float* g_tables, float* g_coarse, void* stream);
+
+/*
+ * Step-size auto-tuning of training (Eq. S3).  ngprt_mean_samples writes to the
+ * device float *out the mean of the per-ray sample counts of ray_stats [n][2] (the
+ * second int of each pair).  ngprt_step_autotune (host, no device work) returns the
+ * next scaler gamma of the step s = gamma s_0: min(1, (1 + kappa) gamma) when
+ * n_mean >= n_min, else max(gamma_min, (1 - kappa) gamma).
+ */
+int32_t ngprt_mean_samples(const int32_t* ray_stats, int64_t n_rays, float* out, void* stream);
+float ngprt_step_autotune(float gamma, float n_mean, float n_min, float kappa, float gamma_min);
+
+/*
  * One Adam step over n floats (the optimiser of Sec. S2.4): m = b1 m + (1-b1) g,
  * v = b2 v + (1-b2) g^2, param -= lr (m/(1-b1^step)) / (sqrt(v/(1-b2^step)) + eps);
  * step >= 1 counts from 1; zero_grad != 0 also clears grad.  All four arrays 16-byte

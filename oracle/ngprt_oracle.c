@@ -1186,3 +1186,132 @@ void or_dilate(const uint8_t* occ, int R, int r, const uint8_t* mask, uint8_t* o
         out[v] = (mask && !mask[v]) ? 0 : m;
     }
 }
+
+/* ------------------------------------------------ training losses and controls */
+
+/* Huber colour loss (Sec. S2.4): sum of h(e) over n values, h(e) = e^2 / 2 when
+ * |e| <= delta, else delta (|e| - delta / 2); d[i] = h'(e_i) (NULL allowed). */
+double or_huber_loss(const double* rgb, const double* target, long n, double delta, double* d) {
+    double L = 0.0;
+    for (long i = 0; i < n; ++i) {
+        double e = rgb[i] - target[i];
+        if (fabs(e) <= delta) { L += 0.5 * e * e; if (d) d[i] = e; }
+        else { L += delta * (fabs(e) - 0.5 * delta); if (d) d[i] = e > 0 ? delta : -delta; }
+    }
+    return L;
+}
+
+/* Step-size auto-tuning (Eq. S3): the next gamma from the batch's mean samples. */
+double or_step_autotune(double gamma, double n_mean, double n_min, double kappa, double gamma_min) {
+    if (n_mean >= n_min) return fmin(1.0, (1.0 + kappa) * gamma);
+    return fmax(gamma_min, (1.0 - kappa) * gamma);
+}
+
+/* Distortion regulariser (Eq. S2) of each ray, by its definition: over the
+ * composited samples with weights w_i and intervals [t_i, t_i + delta_i],
+ * L = sum_{i,j} w_i w_j |m_i - m_j| + 1/3 sum_i w_i^2 delta_i, m_i the midpoints.
+ * out[n][4] = (L, sum w, sum w m, 0). */
+void or_distortion(const or_scene* s, const or_occ* oc, const or_opts* op,
+                   const float* cams, int n_cams, int W, int H, const int32_t* pix,
+                   const float* rays_o, const float* rays_d, int n, double* out) {
+    #pragma omp parallel
+    {
+        or_sample* sm = (or_sample*)malloc(sizeof(or_sample) * (size_t)(op->max_samples > 0 ? op->max_samples : 1));
+        #pragma omp for schedule(dynamic, 16)
+        for (int r = 0; r < n; ++r) {
+            float o[3], dv[3];
+            or_ray_input(cams, n_cams, W, H, pix, rays_o, rays_d, r, o, dv);
+            or_ray_out rr;
+            or_march(s, oc, op, o, dv, -INFINITY, INFINITY, &rr, sm, NULL);
+            double pair = 0.0, self = 0.0, Ws = 0.0, Ss = 0.0;
+            for (int i = 0; i < rr.n_samples; ++i) {
+                double wi = sm[i].T_before * sm[i].alpha, mi = (double)sm[i].t + 0.5 * (double)sm[i].delta;
+                for (int j = 0; j < rr.n_samples; ++j) {
+                    double wj = sm[j].T_before * sm[j].alpha, mj = (double)sm[j].t + 0.5 * (double)sm[j].delta;
+                    pair += wi * wj * fabs(mi - mj);
+                }
+                self += wi * wi * (double)sm[i].delta / 3.0;
+                Ws += wi;
+                Ss += wi * mi;
+            }
+            out[4 * r + 0] = pair + self;
+            out[4 * r + 1] = Ws;
+            out[4 * r + 2] = Ss;
+            out[4 * r + 3] = 0.0;
+        }
+        free(sm);
+    }
+}
+
+/* Reverse of or_distortion: g_tables / g_coarse += scale * dL/d(parameter) summed
+ * over rays.  g_j = dL/dw_j by differentiating the definition; w_j = T_j alpha_j
+ * gives dw_j/dsigma_i = delta_i T_{i+1} (j = i), -delta_i w_j (j > i), 0 (j < i);
+ * sigma = exp(sigma_raw) with the truncated derivative; then Eq. 6-8 backwards
+ * for the density channel only. */
+void or_distortion_backward(const or_scene* s, const or_occ* oc, const or_opts* op,
+                            const float* cams, int n_cams, int W, int H, const int32_t* pix,
+                            const float* rays_o, const float* rays_d, int n, double scale,
+                            double* g_tables, double* g_coarse) {
+    if (s->aggregation != 0) return; /* Eq. 8 only (oracle.py refuses the rest) */
+    or_sample* sm = (or_sample*)malloc(sizeof(or_sample) * (size_t)(op->max_samples > 0 ? op->max_samples : 1));
+    double* g = (double*)malloc(sizeof(double) * (size_t)(op->max_samples > 0 ? op->max_samples : 1));
+    int nch = OR_NFEAT + 2 * s->L;
+    uint32_t T = 1u << s->T_log2;
+    for (int r = 0; r < n; ++r) {
+        float o[3], dv[3];
+        or_ray_input(cams, n_cams, W, H, pix, rays_o, rays_d, r, o, dv);
+        or_ray_out rr;
+        or_march(s, oc, op, o, dv, -INFINITY, INFINITY, &rr, sm, NULL);
+        int ns = rr.n_samples;
+        for (int j = 0; j < ns; ++j) {
+            double mj = (double)sm[j].t + 0.5 * (double)sm[j].delta;
+            double acc = 0.0;
+            for (int k = 0; k < ns; ++k) {
+                double mk = (double)sm[k].t + 0.5 * (double)sm[k].delta;
+                acc += sm[k].T_before * sm[k].alpha * fabs(mj - mk);
+            }
+            double wj = sm[j].T_before * sm[j].alpha;
+            g[j] = 2.0 * acc + 2.0 / 3.0 * wj * (double)sm[j].delta;
+        }
+        for (int i = 0; i < ns; ++i) {
+            const or_sample* sp = sm + i;
+            double T_next = sp->T_before * (1.0 - sp->alpha);
+            double d_sigma = (double)sp->delta * T_next * g[i];
+            for (int j = i + 1; j < ns; ++j) d_sigma -= (double)sp->delta * sm[j].T_before * sm[j].alpha * g[j];
+            double gs = scale * d_sigma * exp(fmin(sp->sigma_raw, 15.0));
+            int base[3];
+            double wc[3];
+            or_cell(sp->u, s->R_C, base, wc);
+            size_t cv[8];
+            double cwt[8], logit_om[OR_MAXL];
+            for (int l = 0; l < s->L; ++l) logit_om[l] = 0.0;
+            for (int c = 0; c < 8; ++c) {
+                int xx = base[0] + (c & 1), yy = base[1] + ((c >> 1) & 1), zz = base[2] + ((c >> 2) & 1);
+                cv[c] = (size_t)xx + (size_t)s->R_C * ((size_t)yy + (size_t)s->R_C * zz);
+                cwt[c] = or_corner_weight(wc, c);
+                for (int l = 0; l < s->L; ++l) logit_om[l] += cwt[c] * s->coarse[cv[c] * nch + OR_NFEAT + 2 * l];
+            }
+            for (int c = 0; c < 8; ++c) g_coarse[cv[c] * nch] += cwt[c] * gs;
+            for (int l = 0; l < s->L; ++l) {
+                double om = op->attn_mode == 1 ? 1.0 : or_sigmoid(logit_om[l]);
+                int bl[3];
+                double wl[3];
+                or_cell(sp->u, s->N[l], bl, wl);
+                uint64_t off = or_level_offset(s->N, s->L, s->T_log2, l);
+                double sh = 0.0;
+                for (int c = 0; c < 8; ++c) {
+                    int xx = bl[0] + (c & 1), yy = bl[1] + ((c >> 1) & 1), zz = bl[2] + ((c >> 2) & 1);
+                    uint64_t e = off + or_level_entry(s->N[l], T, xx, yy, zz);
+                    double ew = or_corner_weight(wl, c);
+                    sh += ew * s->tables[e * OR_NFEAT];
+                    g_tables[e * OR_NFEAT] += ew * om * gs;
+                }
+                if (op->attn_mode != 1)
+                    for (int c = 0; c < 8; ++c)
+                        g_coarse[cv[c] * nch + OR_NFEAT + 2 * l] += cwt[c] * gs * sh * om * (1.0 - om);
+            }
+        }
+    }
+    free(g);
+    free(sm);
+}

@@ -285,6 +285,33 @@ class Oracle:
                                       _p(ro), _p(rd), C.c_int(n), C.c_int(R), C.c_double(w_thr), _p(vis), _p(wmax))
         return vis, wmax
 
+    def distortion(self, opts, cams=None, pix=None, rays_o=None, rays_d=None, W=None, H=None):
+        """Per-ray distortion regulariser (Eq. S2): [n][4] = (L_dist, sum w, sum w m, 0)."""
+        W = W or self.cfg.W
+        H = H or self.cfg.H
+        cams, pix, ro, rd, n = self._rays(cams, pix, rays_o, rays_d)
+        out = np.empty((n, 4), np.float64)
+        op = self._opts(opts)
+        lib().or_distortion(C.byref(self._s), C.byref(self._o), C.byref(op), _p(cams),
+                            C.c_int(0 if cams is None else len(cams)), C.c_int(W), C.c_int(H), _p(pix), _p(ro),
+                            _p(rd), C.c_int(n), _p(out))
+        return out
+
+    def distortion_backward(self, opts, scale=1.0, cams=None, pix=None, rays_o=None, rays_d=None, W=None, H=None):
+        """Gradients of scale * sum over rays of L_dist: (g_tables, g_coarse)."""
+        if int(getattr(self.cfg, "aggregation", 0)) != 0:
+            raise NotImplementedError("the reverse pass follows Eq. 8 (aggregation 0) only")
+        W = W or self.cfg.W
+        H = H or self.cfg.H
+        cams, pix, ro, rd, n = self._rays(cams, pix, rays_o, rays_d)
+        g_t = np.zeros_like(self.tables)
+        g_c = np.zeros_like(self.coarse)
+        op = self._opts(opts)
+        lib().or_distortion_backward(C.byref(self._s), C.byref(self._o), C.byref(op), _p(cams),
+                                     C.c_int(0 if cams is None else len(cams)), C.c_int(W), C.c_int(H), _p(pix),
+                                     _p(ro), _p(rd), C.c_int(n), C.c_double(scale), _p(g_t), _p(g_c))
+        return g_t, g_c
+
     def render_backward(self, opts, d_rgb=None, d_depth=None, d_opacity=None, cams=None, pix=None,
                         rays_o=None, rays_d=None, W=None, H=None):
         if int(getattr(self.cfg, "aggregation", 0)) != 0:
@@ -360,6 +387,25 @@ def coarse_channels(L: int, aggregation: int = 0) -> int:
     """Channels per coarse-grid vertex: deferred feature (8) plus omega, beta per level
     (Eq. 8), one logit per level (shared gates), or nothing (the other aggregations)."""
     return {0: 8 + 2 * L, 1: 8 + L}.get(int(aggregation), 8)
+
+
+def huber_loss(rgb, target, delta):
+    """Sum of the Huber loss h(rgb - target) and its derivative per value (Sec. S2.4)."""
+    rgb = _c(rgb, np.float64).reshape(-1)
+    target = _c(target, np.float64).reshape(-1)
+    d = np.empty_like(rgb)
+    f = lib().or_huber_loss
+    f.restype = C.c_double
+    L = f(_p(rgb), _p(target), C.c_long(len(rgb)), C.c_double(delta), _p(d))
+    return float(L), d
+
+
+def step_autotune(gamma, n_mean, n_min=3.0, kappa=1e-3, gamma_min=0.2217):
+    """Eq. S3: the next step scaler."""
+    f = lib().or_step_autotune
+    f.restype = C.c_double
+    return float(f(C.c_double(gamma), C.c_double(n_mean), C.c_double(n_min), C.c_double(kappa),
+                   C.c_double(gamma_min)))
 
 
 def l2_loss(rgb, target, scale=1.0):

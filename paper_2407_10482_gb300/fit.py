@@ -2,12 +2,15 @@
 
 A fitted model is what the render path is meant to draw: the PSNR loss of a faster
 form only means something against the images the model was fitted to (Sec. 4).
-``fit`` runs the training loop of Sec. S2.1 in its plainest form on the render path
-of this library: each step renders a random minibatch of pixels with
-``ngprt_render`` (keeping the per-ray state), takes the photometric L2 loss and its
-gradient with ``ngprt_l2_loss``, runs ``ngprt_render_backward`` into the table,
-coarse-grid and MLP gradients and applies ``ngprt_adam_step`` to each of them.
-torch only holds the buffers and draws the minibatch indices.
+``fit`` runs the training loop of Sec. S2.1 on the render path of this library:
+each step renders a random minibatch of pixels with ``ngprt_render`` (keeping the
+per-ray state), takes the colour loss and its gradient (L2, or the Huber loss of
+Sec. S2.4 with ``huber_delta`` > 0), runs ``ngprt_render_backward`` into the table,
+coarse-grid and MLP gradients, adds eta times the distortion regulariser of Eq. S2
+(``ngprt_distortion_loss`` / ``ngprt_distortion_backward``) when eta > 0, and applies
+``ngprt_adam_step`` to each parameter array.  With ``autotune`` the step scaler gamma
+follows Eq. S3 from the batch's mean sample count.  torch only holds the buffers
+and draws the minibatch indices.
 """
 from __future__ import annotations
 
@@ -35,6 +38,12 @@ class FitConfig:
     decay_from: float = 0.6    # cosine decay to lr / 10 over the last 40% of steps
     table_std: float = 1e-4    # initial tables and coarse grid ~ N(0, table_std)
     density_init: float = 0.0  # initial coarse density logit (sigma = exp(density_init))
+    huber_delta: float = 0.0   # > 0: Huber colour loss with this delta (Sec. S2.4); 0: L2
+    eta: float = 0.0           # weight of the distortion regulariser (Eq. S2; 0.01 in Sec. S2.4)
+    autotune: bool = False     # step scaler gamma by Eq. S3
+    n_min: float = 3.0
+    kappa: float = 1e-3
+    gamma_min: float = 0.2217
     seed: int = 3
 
 
@@ -71,7 +80,9 @@ def fit(scene: ng.DeviceScene, occ: ng.DeviceOcc, opts, cams: np.ndarray, W: int
         targets: torch.Tensor, fc: FitConfig = FitConfig(), log_every: int = 0, stream=None):
     """Fit ``scene`` (FP32 tables, coarse grid and MLP, updated in place) to the images
     ``targets`` [n_views * H * W, 3] of the cameras ``cams``.  Returns the loss history
-    [(step, loss)] and the wall time in seconds."""
+    [(step, loss)] and the wall time in seconds; with ``autotune`` the final gamma is
+    left in ``fit.last_gamma``."""
+    from dataclasses import replace
     dev = scene.tables.device
     rend = ng.Renderer(scene, occ, device=dev)
     params = [scene.tables, scene.coarse, scene.mlp_w]
@@ -86,6 +97,12 @@ def fit(scene: ng.DeviceScene, occ: ng.DeviceOcc, opts, cams: np.ndarray, W: int
     d_rgb = torch.empty(B, 3, device=dev)
     out = dict(rgb=torch.empty(B, 3, device=dev), depth=torch.empty(B, device=dev),
                opacity=torch.empty(B, device=dev), state=torch.empty(B, ng.STATE_FLOATS, device=dev))
+    if fc.autotune:
+        out["stats"] = torch.empty(B, 2, dtype=torch.int32, device=dev)
+        n_mean = torch.empty(1, device=dev)
+    dist_state = torch.empty(B, 4, device=dev) if fc.eta > 0 else None
+    cam_arr, n_cams = ng.cameras_struct(cams, W, H)
+    gamma = opts.step_gamma
     hist = []
     t0 = time.perf_counter()
     for step in range(1, fc.steps + 1):
@@ -95,14 +112,29 @@ def fit(scene: ng.DeviceScene, occ: ng.DeviceOcc, opts, cams: np.ndarray, W: int
         logging = bool(log_every) and (step % log_every == 0 or step == fc.steps)
         if logging:
             loss.zero_()
-        rend.render(opts, cams=cams, W=W, H=H, pixel_ids=pix, state=True, out=out)
-        ng.ngprt_l2_loss(out["rgb"], tg, 3 * B, 1.0 / (3 * B), loss if logging else None, d_rgb, stream=stream)
-        rend.backward(opts, out["state"], d_rgb, None, None, grads[0], grads[1], grads[2], cams=cams, W=W, H=H,
+        o_step = replace(opts, step_gamma=gamma) if fc.autotune else opts
+        rend.render(o_step, cams=cams, W=W, H=H, pixel_ids=pix, state=True, out=out)
+        if fc.huber_delta > 0:
+            ng.ngprt_huber_loss(out["rgb"], tg, 3 * B, fc.huber_delta, 1.0 / (3 * B), loss if logging else None,
+                                d_rgb, stream=stream)
+        else:
+            ng.ngprt_l2_loss(out["rgb"], tg, 3 * B, 1.0 / (3 * B), loss if logging else None, d_rgb, stream=stream)
+        rend.backward(o_step, out["state"], d_rgb, None, None, grads[0], grads[1], grads[2], cams=cams, W=W, H=H,
                       pixel_ids=pix)
+        if fc.eta > 0:
+            ro = ng.render_opts(o_step)
+            ng.ngprt_distortion_loss(scene.struct, occ.struct, cam_arr, n_cams, pix, None, None, B, ro, fc.eta / B,
+                                     dist_state, loss if logging else None, stream=stream)
+            ng.ngprt_distortion_backward(scene.struct, occ.struct, cam_arr, n_cams, pix, None, None, B, ro,
+                                         dist_state, fc.eta / B, grads[0], grads[1], stream=stream)
+        if fc.autotune:
+            ng.ngprt_mean_samples(out["stats"], B, n_mean, stream=stream)
+            gamma = ng.ngprt_step_autotune(gamma, float(n_mean.item()), fc.n_min, fc.kappa, fc.gamma_min)
         f = _lr_factor(step, fc)
         for p, g, (m, v), lr in zip(params, grads, moms, lrs):
             ng.ngprt_adam_step(p, g, m, v, lr * f, fc.beta1, fc.beta2, fc.eps, step, True, stream=stream)
         if logging:
             hist.append((step, float(loss.item())))
     torch.cuda.synchronize(dev)
+    fit.last_gamma = gamma
     return hist, time.perf_counter() - t0

@@ -65,6 +65,13 @@ _SIGS = {
     "ngprt_occupancy_from_density": (C.c_int32, [_P, _P, C.c_int32, C.c_float, _P, _P, _P]),
     "ngprt_occupancy_visibility": (C.c_int32, [_P, _P, _P, C.c_int32, _P, _P, _P, C.c_int64, _P, C.c_float,
                                                C.c_int32, _P, _P]),
+    "ngprt_huber_loss": (C.c_int32, [_P, _P, C.c_int64, C.c_float, C.c_float, _P, _P, _P]),
+    "ngprt_distortion_loss": (C.c_int32, [_P, _P, _P, C.c_int32, _P, _P, _P, C.c_int64, _P, C.c_float, _P, _P,
+                                          _P]),
+    "ngprt_distortion_backward": (C.c_int32, [_P, _P, _P, C.c_int32, _P, _P, _P, C.c_int64, _P, _P, C.c_float,
+                                              _P, _P, _P]),
+    "ngprt_mean_samples": (C.c_int32, [_P, C.c_int64, _P, _P]),
+    "ngprt_step_autotune": (C.c_float, [C.c_float, C.c_float, C.c_float, C.c_float, C.c_float]),
     "ngprt_dilate_workspace_bytes": (C.c_size_t, [C.c_int32]),
     "ngprt_dilate": (C.c_int32, [_P, C.c_int32, C.c_int32, _P, _P, _P, C.c_size_t, _P]),
     "ngprt_render_workspace_bytes": (C.c_size_t, [_P, C.c_int64]),
@@ -175,6 +182,33 @@ def ngprt_occupancy_visibility(scene, occ, cams, n_cams, pixel_ids, rays_o, rays
     _check("ngprt_occupancy_visibility", lib().ngprt_occupancy_visibility(
         C.byref(scene), C.byref(occ), cams, n_cams, _ptr(pixel_ids), _ptr(rays_o), _ptr(rays_d), n_rays,
         C.byref(opts), w_thr, R, _ptr(vis), _stream(stream)))
+
+
+def ngprt_huber_loss(rgb, target, n, delta, scale, loss=None, d_rgb=None, stream=None) -> None:
+    _check("ngprt_huber_loss", lib().ngprt_huber_loss(_ptr(rgb), _ptr(target), n, delta, scale, _ptr(loss),
+                                                      _ptr(d_rgb), _stream(stream)))
+
+
+def ngprt_distortion_loss(scene, occ, cams, n_cams, pixel_ids, rays_o, rays_d, n_rays, opts, scale, dist_state,
+                          loss=None, stream=None) -> None:
+    _check("ngprt_distortion_loss", lib().ngprt_distortion_loss(
+        C.byref(scene), C.byref(occ), cams, n_cams, _ptr(pixel_ids), _ptr(rays_o), _ptr(rays_d), n_rays,
+        C.byref(opts), scale, _ptr(dist_state), _ptr(loss), _stream(stream)))
+
+
+def ngprt_distortion_backward(scene, occ, cams, n_cams, pixel_ids, rays_o, rays_d, n_rays, opts, dist_state, scale,
+                              g_tables, g_coarse, stream=None) -> None:
+    _check("ngprt_distortion_backward", lib().ngprt_distortion_backward(
+        C.byref(scene), C.byref(occ), cams, n_cams, _ptr(pixel_ids), _ptr(rays_o), _ptr(rays_d), n_rays,
+        C.byref(opts), _ptr(dist_state), scale, _ptr(g_tables), _ptr(g_coarse), _stream(stream)))
+
+
+def ngprt_mean_samples(ray_stats, n_rays, out, stream=None) -> None:
+    _check("ngprt_mean_samples", lib().ngprt_mean_samples(_ptr(ray_stats), n_rays, _ptr(out), _stream(stream)))
+
+
+def ngprt_step_autotune(gamma, n_mean, n_min=3.0, kappa=1e-3, gamma_min=0.2217) -> float:
+    return float(lib().ngprt_step_autotune(gamma, n_mean, n_min, kappa, gamma_min))
 
 
 def ngprt_dilate_workspace_bytes(R: int) -> int:

@@ -5,6 +5,7 @@ import ctypes as C
 import os
 import re
 
+import numpy as np
 import pytest
 
 from paper_2407_10482_gb300 import build as B
@@ -125,3 +126,16 @@ def test_aggregation_layouts_and_validation(ng):
                                    C.byref(opts), C.c_void_p(256), C.c_void_p(256), None, None, C.c_void_p(256),
                                    C.c_void_p(256), C.c_void_p(256), None, 0, None)
     assert rc == ng.ERR_UNSUPPORTED and b"forward render only" in lib.ngprt_last_error()
+
+
+def test_step_autotune_matches_oracle(ng):
+    """Eq. S3's controller runs on the host: the library's FP32 result equals the
+    oracle's FP64 one rounded, on both branches and both clamps."""
+    from oracle import oracle as O
+    rng = np.random.default_rng(0)
+    for _ in range(200):
+        g = float(np.float32(rng.uniform(0.2, 1.0)))
+        n_mean = float(np.float32(rng.uniform(0.0, 6.0)))
+        want = O.step_autotune(g, n_mean, 3.0, 1e-3, float(np.float32(0.2217)))
+        got = ng.ngprt_step_autotune(g, n_mean, 3.0, 1e-3, 0.2217)
+        assert abs(got - want) <= 1e-6 * want

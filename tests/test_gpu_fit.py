@@ -44,3 +44,43 @@ def test_fit_small_scene(ng):
     assert hist[-1][1] < 0.2 * hist[0][1]
     assert after > before + 8.0 and after > 22.0
     assert after_h > before_h + 6.0
+
+
+def _mean_distortion(ng, ds, docc, opts, cams, cfg):
+    cam_arr, nc = ng.cameras_struct(cams, cfg.W, cfg.H)
+    n = nc * cfg.W * cfg.H
+    st = torch.empty(n, 4, device="cuda")
+    ng.ngprt_distortion_loss(ds.struct, docc.struct, cam_arr, nc, None, None, None, n, ng.render_opts(opts), 1.0, st)
+    torch.cuda.synchronize()
+    return float(st[:, 0].mean())
+
+
+def test_fit_with_huber_distortion_and_autotune(ng):
+    """The Sec. S2.4 objective (Huber colour loss + eta L_dist, Eq. S2) fitted with
+    the library's kernels: the regulariser at the paper's weight (eta = 0.01) lowers
+    the scene's distortion against the same fit without it and keeps the images; Eq. S3's controller shrinks gamma
+    geometrically while the batch stays under N_min samples per ray."""
+    cfg = S.small_config()
+    blobs = S._blobs(cfg, np.random.default_rng(cfg.seed))
+    occ = S._occupancy(cfg, blobs)
+    cams = S.orbit_cameras(cfg, 32, step_deg=360.0 / 32)
+    targets = GT.render_views(cfg, blobs, cams, device="cuda", n_steps=512)
+    docc = ng.DeviceOcc(occ, cfg.R_O, cfg.n_occ_levels)
+    opts = S.default_options(cfg)
+    res = {}
+    for eta in (0.0, 0.01):
+        fc = F.FitConfig(steps=400, batch=1 << 14, seed=5, huber_delta=0.1, eta=eta)
+        ds = ng.DeviceScene(cfg, *F.initial_scene(cfg, fc, "cuda"))
+        hist, _ = F.fit(ds, docc, opts, cams, cfg.W, cfg.H, targets, fc, log_every=100)
+        r = ng.Renderer(ds, docc)
+        res[eta] = (P.psnr(r.render(opts, cams=cams, W=cfg.W, H=cfg.H)["rgb"], targets),
+                    _mean_distortion(ng, ds, docc, opts, cams, cfg))
+        assert all(np.isfinite(l) for _, l in hist)
+    print("eta 0: %.2f dB, L_dist %.5f; eta 0.01: %.2f dB, L_dist %.5f" % (*res[0.0], *res[0.01]))
+    assert res[0.01][1] < 0.9 * res[0.0][1]
+    assert res[0.01][0] > 30.0 and res[0.0][0] > 30.0
+    # N_min above any batch mean: gamma shrinks by (1 - kappa) per step to its floor
+    fc = F.FitConfig(steps=300, batch=1 << 12, seed=5, autotune=True, n_min=1e9, kappa=1e-3, gamma_min=0.5)
+    ds = ng.DeviceScene(cfg, *F.initial_scene(cfg, fc, "cuda"))
+    F.fit(ds, docc, opts, cams, cfg.W, cfg.H, targets, fc)
+    assert abs(F.fit.last_gamma - max(0.5, 0.999 ** 300)) < 1e-4
