@@ -33,8 +33,9 @@ from paper_2407_10482_gb300 import scenes as S  # noqa: E402
 
 METRIC = "1080p frames/s & Grays/s, plain FP32 vs FP16+proposal at ≤0.1 dB PSNR loss"
 # DRAM bytes (read + write) of one march_kernel<16,F32> launch on this frame, from the
-# ncu capture summarised in profiles/march_kernel_hd_1080p_fp32.md (3.581 GB + 0.920 GB)
-MARCH_DRAM_BYTES = 4.500846e9
+# ncu capture summarised in profiles/march_kernel_hd_1080p_fp32.md; None while the
+# kernel has changed since the counters were taken
+MARCH_DRAM_BYTES = 2.522619e9  # 2.185541 GB read + 0.337078 GB written
 WORKLOAD = "hd 1920x1080 unbounded-360 synthetic scene, L=16 (16..4096), T=2^19, 128^3 occupancy+G, MLP 23-64-64-3"
 
 

@@ -77,7 +77,8 @@ typedef enum {
  *   coarse : [R_C^3][ngprt_coarse_channels(L, aggregation)] of table_dtype,
  *            channels [sigma~, c_d~(3), v_s~(4)] then, for SEPARATE_V, the logits
  *            omega^1, beta^1, ..., omega^L, beta^L (Eq. 7), for SHARED_V one logit
- *            per level a^1, ..., a^L.
+ *            per level a^1, ..., a^L.  Aligned like tables (32 bytes F32, 16 bytes
+ *            F16/BF16).
  *   mlp_w  : deferred MLP_psi (Eq. 5) of mlp_layers dense layers without bias:
  *            layer k is a [out_k][in_k] matrix, in_0 = 32 (C_d, F, SH16(d), zero
  *            padding), out_k = mlp_width for hidden layers (ReLU), 3 for the last.

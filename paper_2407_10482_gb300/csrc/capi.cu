@@ -46,9 +46,9 @@ int32_t make_grid(const ngprt_scene* s, Grid& g, const char* fn) {
                   s->table_dtype);
     NGPRT_REQUIRE(s->tables != nullptr && s->coarse != nullptr && s->mlp_w != nullptr, "%s: NULL scene array", fn);
     const uintptr_t align = s->table_dtype == NGPRT_F32 ? 32 : 16;
-    NGPRT_REQUIRE(((uintptr_t)s->tables % align) == 0, "%s: tables must be %d-byte aligned", fn, (int)align);
-    NGPRT_REQUIRE(((uintptr_t)s->coarse % 16) == 0 && ((uintptr_t)s->mlp_w % 16) == 0,
-                  "%s: coarse and mlp_w must be 16-byte aligned", fn);
+    NGPRT_REQUIRE(((uintptr_t)s->tables % align) == 0 && ((uintptr_t)s->coarse % align) == 0,
+                  "%s: tables and coarse must be %d-byte aligned", fn, (int)align);
+    NGPRT_REQUIRE(((uintptr_t)s->mlp_w % 16) == 0, "%s: mlp_w must be 16-byte aligned", fn);
     NGPRT_REQUIRE(s->bounded == 0 || s->bounded == 1, "%s: bounded=%d", fn, s->bounded);
     for (int l = 0; l < s->L; ++l)
         NGPRT_REQUIRE(s->N[l] >= 2 && s->N[l] <= (1 << 20), "%s: N[%d]=%d not in [2, 2^20]", fn, l, s->N[l]);

@@ -176,6 +176,32 @@ __device__ __forceinline__ uint32_t level_row(const Grid& g, int l, uint32_t x, 
 }
 
 // ------------------------------------------------------------ vector loads
+#ifndef NGPRT_COARSE_WIDE
+#define NGPRT_COARSE_WIDE 1  // 0: coarse rows in 128-bit (F32) / 32-bit (16-bit) loads
+#endif
+
+// NC 16-bit channels of one row as NC/2 packed pairs, read-only path, with 128-bit
+// loads when NC % 8 == 0 (rows 16-byte aligned), 64-bit when NC % 4 == 0, else 32-bit.
+template <int NC>
+__device__ __forceinline__ void load_pairs(const uint16_t* p, uint32_t w[NC / 2]) {
+    if constexpr (NC % 8 == 0 && NGPRT_COARSE_WIDE) {
+#pragma unroll
+        for (int k = 0; k < NC / 8; ++k) {
+            const uint4 q = __ldg(reinterpret_cast<const uint4*>(p) + k);
+            w[4 * k] = q.x; w[4 * k + 1] = q.y; w[4 * k + 2] = q.z; w[4 * k + 3] = q.w;
+        }
+    } else if constexpr (NC % 4 == 0 && NGPRT_COARSE_WIDE) {
+#pragma unroll
+        for (int k = 0; k < NC / 4; ++k) {
+            const uint2 q = __ldg(reinterpret_cast<const uint2*>(p) + k);
+            w[2 * k] = q.x; w[2 * k + 1] = q.y;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < NC / 2; ++k) w[k] = __ldg(reinterpret_cast<const uint32_t*>(p) + k);
+    }
+}
+
 // One 8-channel table entry, read-only path.  F32: a single 256-bit load (entries
 // are 32-byte aligned); F16/BF16: a single 128-bit load.
 template <int DT>
@@ -215,12 +241,23 @@ __device__ __forceinline__ void load_entry<NGPRT_BF16>(const void* base, uint32_
     }
 }
 
-// Read NC consecutive channels (NC even) of one coarse-grid vertex.
+// Read NC consecutive channels (NC even) of one coarse-grid vertex with the widest
+// loads the row's alignment allows (the grid base is aligned like the tables: 32
+// bytes for F32, 16 for F16/BF16): 256-bit (F32, NC % 8 == 0), 128-bit (F32 NC % 4,
+// 16-bit NC % 8), 64-bit (16-bit NC % 4), else pairs.
 template <int DT, int NC>
 __device__ __forceinline__ void load_channels(const void* base, uint32_t vertex, float v[NC]) {
     if constexpr (DT == NGPRT_F32) {
         const float* p = static_cast<const float*>(base) + (size_t)vertex * NC;
-        if constexpr (NC % 4 == 0) {
+        if constexpr (NC % 8 == 0 && NGPRT_COARSE_WIDE) {
+#pragma unroll
+            for (int k = 0; k < NC / 8; ++k) {
+                float* q = v + 8 * k;
+                asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                    : "=f"(q[0]), "=f"(q[1]), "=f"(q[2]), "=f"(q[3]), "=f"(q[4]), "=f"(q[5]), "=f"(q[6]), "=f"(q[7])
+                    : "l"(p + 8 * k));
+            }
+        } else if constexpr (NC % 4 == 0) {
 #pragma unroll
             for (int k = 0; k < NC / 4; ++k) {
                 float4 q = __ldg(reinterpret_cast<const float4*>(p) + k);
@@ -235,13 +272,13 @@ __device__ __forceinline__ void load_channels(const void* base, uint32_t vertex,
         }
     } else {
         const uint16_t* p = static_cast<const uint16_t*>(base) + (size_t)vertex * NC;
-        const uint32_t* p32 = reinterpret_cast<const uint32_t*>(p);  // NC even: 4-byte aligned
+        uint32_t w[NC / 2];
+        load_pairs<NC>(p, w);
 #pragma unroll
         for (int k = 0; k < NC / 2; ++k) {
-            uint32_t w = __ldg(p32 + k);
             float2 f;
-            if constexpr (DT == NGPRT_F16) f = __half22float2(*reinterpret_cast<const __half2*>(&w));
-            else f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w));
+            if constexpr (DT == NGPRT_F16) f = __half22float2(*reinterpret_cast<const __half2*>(&w[k]));
+            else f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w[k]));
             v[2 * k] = f.x;
             v[2 * k + 1] = f.y;
         }

@@ -11,10 +11,11 @@
 
 #include "common.cuh"
 
-// Occupancy hint for the march kernel (blocks of 128 threads per SM the register
-// allocation must allow) and the warp's pixel tile (TILE_W x 32/TILE_W).
+// Occupancy hint for the march kernels (blocks of 128 threads per SM the register
+// allocation must allow; 0 = per shape, see march_min_blocks) and the warp's pixel
+// tile (TILE_W x 32/TILE_W).
 #ifndef NGPRT_MARCH_MIN_BLOCKS
-#define NGPRT_MARCH_MIN_BLOCKS 8
+#define NGPRT_MARCH_MIN_BLOCKS 0
 #endif
 #ifndef NGPRT_TILE_W
 #define NGPRT_TILE_W 4
@@ -160,13 +161,12 @@ __device__ __forceinline__ void sample_features(const Grid& g, const float u[3],
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
             const uint32_t v = (uint32_t)(b[0] + (c & 1)) + R * ((uint32_t)(b[1] + ((c >> 1) & 1)) + R * (uint32_t)(b[2] + ((c >> 2) & 1)));
-            const uint32_t* p32 = static_cast<const uint32_t*>(g.coarse) + (size_t)v * (NC / 2);
+            uint32_t q[NC / 2];
+            load_pairs<NC>(static_cast<const uint16_t*>(g.coarse) + (size_t)v * NC, q);
             const __half2 cw2 = __float2half2_rn(corner_w(w, c));
 #pragma unroll
-            for (int ch = 0; ch < NC / 2; ++ch) {
-                const uint32_t q = __ldg(p32 + ch);
-                hacc[ch] = __hfma2(cw2, *reinterpret_cast<const __half2*>(&q), hacc[ch]);
-            }
+            for (int ch = 0; ch < NC / 2; ++ch)
+                hacc[ch] = __hfma2(cw2, *reinterpret_cast<const __half2*>(&q[ch]), hacc[ch]);
         }
 #pragma unroll
         for (int ch = 0; ch < NC / 2; ++ch) acc[ch] = __half22float2(hacc[ch]);
@@ -548,13 +548,20 @@ __device__ __forceinline__ bool ray_setup(const MarchParams& p, int64_t& ray, fl
 // ray id / explicit ray per thread), march + features + compositing, the per-ray
 // composite state written to `state`.  In the fallback pass it re-marches only the
 // rays whose interval result missed the predicted opacity.
-// Blocks per SM the register allocation must allow: the MLP aggregation keeps its
-// 64 hidden units in registers and runs with fewer resident blocks.
-template <int AGG>
-constexpr int march_min_blocks() { return AGG == NGPRT_AGG_MLP ? 3 : NGPRT_MARCH_MIN_BLOCKS; }
+// Blocks per SM the register allocation must allow.  8 (64 registers) hides the
+// gathers' latency best; FP32 tables with 4 or more levels spill enough there that 6
+// (80 registers) is faster (measured: hd L = 16 13.9 against 14.7 ms, L = 4 10.1
+// against 10.3 ms).  The MLP aggregation keeps its 64 hidden units in registers.
+template <int L, int DT, int AGG = NGPRT_AGG_SEPARATE_V>
+constexpr int march_min_blocks() {
+    if (AGG == NGPRT_AGG_MLP) return 3;
+    if (NGPRT_MARCH_MIN_BLOCKS > 0) return NGPRT_MARCH_MIN_BLOCKS;
+    return (DT == NGPRT_F32 && L >= 4) ? 6 : 8;
+}
 
 template <int L, int DT, int AGG>
-__global__ void __launch_bounds__(128, march_min_blocks<AGG>()) march_kernel(const __grid_constant__ MarchParams p) {
+__global__ void __launch_bounds__(128, march_min_blocks<L, DT, AGG>())
+    march_kernel(const __grid_constant__ MarchParams p) {
     int64_t ray;
     float o[3], d[3], t, t_out;
     bool hit;

@@ -53,7 +53,7 @@ struct VisibilitySampler {
 };
 
 template <int L, int DT>
-__global__ void __launch_bounds__(128, NGPRT_MARCH_MIN_BLOCKS)
+__global__ void __launch_bounds__(128, march_min_blocks<L, DT>())
     visibility_kernel(const __grid_constant__ MarchParams p, float w_thr, int32_t R, uint8_t* vis) {
     int64_t ray;
     float o[3], d[3], t, t_out;

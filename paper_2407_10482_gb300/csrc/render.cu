@@ -38,7 +38,7 @@ struct TargetSampler {
 };
 
 template <int L, int DT>
-__global__ void __launch_bounds__(128, NGPRT_MARCH_MIN_BLOCKS) targets_kernel(const __grid_constant__ MarchParams p,
+__global__ void __launch_bounds__(128, march_min_blocks<L, DT>()) targets_kernel(const __grid_constant__ MarchParams p,
                                                                                 float* targets) {
     extern __shared__ float gate_smem[];
     int64_t ray;

@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(128, 4) wf_gather_kernel(const __grid_constant
 }
 
 template <int L, int DT>
-__global__ void __launch_bounds__(128, NGPRT_MARCH_MIN_BLOCKS) wf_finish_kernel(const __grid_constant__ WfParams p) {
+__global__ void __launch_bounds__(128, march_min_blocks<L, DT>()) wf_finish_kernel(const __grid_constant__ WfParams p) {
     extern __shared__ float gate_smem[];
     const int n = p.counts[kWfRounds];
     const int* list = p.list[kWfRounds & 1];
