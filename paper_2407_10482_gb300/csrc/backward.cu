@@ -215,106 +215,80 @@ __device__ __forceinline__ void atomic_add4(float* p, float a, float b, float c,
 #endif
 }
 
-// Reverse of sample_features at u for the feature cotangent gf[8]: attention
-// logits, coarse vertices and fine entries.
+// Reverse of sample_features at u.  The sample's feature cotangent is
+// gf = [gs, w gq] (gs = dL/dsigma_raw, w the sample's weight, gq the ray's colour
+// cotangents); the forward half of the sampler left in the thread's slots the gates
+// omega^l, beta^l ([0, 2L)) and sigma^l, q^l = f^l[1..7] . gq ([2L, 4L)), so no
+// entry is read again: each level only recomputes its 8 corner rows and adds
+//     d entry = cw [omega^l gs, beta^l w gq],
+// and the logit gradients d omega-logit = sigma^l gs omega (1 - omega), d beta-logit =
+// w q^l beta (1 - beta) (both on omega for the shared mode) go to the slots [0, 2L)
+// and then, with gf, to the 8 coarse vertices.
 template <int L>
-__device__ __forceinline__ void scatter_features(const Grid& g, const float u[3], int attn_mode, const float gf[8],
-                                                 float* g_tables, float* g_coarse) {
+__device__ __forceinline__ void scatter_features(const Grid& g, const float u[3], int attn_mode, float gs, float w,
+                                                 const float gq[7], float* slots, int stride, float* g_tables,
+                                                 float* g_coarse) {
     constexpr int NC = kNFeat + 2 * L;
-    int b[3];
-    float w[3];
+    float gw[7];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) grid_cell(u[a], g.R_C, b[a], w[a]);
-    const uint32_t R = (uint32_t)g.R_C;
-    uint32_t cv[8];
-    float logit[2 * L];
-#pragma unroll
-    for (int k = 0; k < 2 * L; ++k) logit[k] = 0.0f;
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        cv[c] = (uint32_t)(b[0] + (c & 1)) + R * ((uint32_t)(b[1] + ((c >> 1) & 1)) + R * (uint32_t)(b[2] + ((c >> 2) & 1)));
-        float val[NC];
-        load_channels<NGPRT_F32, NC>(g.coarse, cv[c], val);
-        const float cw = corner_w(w, c);
-#pragma unroll
-        for (int k = 0; k < 2 * L; ++k) logit[k] = fmaf(cw, val[kNFeat + k], logit[k]);
-    }
-    float glog[2 * L];
-#pragma unroll
+    for (int k = 0; k < 7; ++k) gw[k] = w * gq[k];
+#pragma unroll kLevelUnroll
     for (int l = 0; l < L; ++l) {
-        float om, be;
-        if (attn_mode == 1) {
-            om = 1.0f;
-            be = 1.0f;
-        } else if (attn_mode == 2) {
-            om = sigmoidf_(logit[2 * l]);
-            be = om;
-        } else {
-            om = sigmoidf_(logit[2 * l]);
-            be = sigmoidf_(logit[2 * l + 1]);
-        }
+        const float om = slots[(2 * l) * stride], be = slots[(2 * l + 1) * stride];
+        const float sh = slots[(2 * L + 2 * l) * stride], q = slots[(2 * L + 2 * l + 1) * stride];
         int bl[3];
         float wl[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) grid_cell(u[a], g.N[l], bl[a], wl[a]);
-        uint32_t rows[8];
-#pragma unroll
-        for (int c = 0; c < 8; ++c)
-            rows[c] = level_row(g, l, (uint32_t)(bl[0] + (c & 1)), (uint32_t)(bl[1] + ((c >> 1) & 1)),
-                                (uint32_t)(bl[2] + ((c >> 2) & 1)));
-        float fl[8];
-#pragma unroll
-        for (int ch = 0; ch < 8; ++ch) fl[ch] = 0.0f;
+        const float s0 = om * gs;
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-            float e[8];
-            load_entry<NGPRT_F32>(g.tables, rows[c], e);
+            const uint32_t row = level_row(g, l, (uint32_t)(bl[0] + (c & 1)), (uint32_t)(bl[1] + ((c >> 1) & 1)),
+                                           (uint32_t)(bl[2] + ((c >> 2) & 1)));
             const float cw = corner_w(wl, c);
-#pragma unroll
-            for (int ch = 0; ch < 8; ++ch) fl[ch] = fmaf(cw, e[ch], fl[ch]);
+            const float cb = cw * be;
+            float* gp = g_tables + (size_t)row * 8;
+            atomic_add4(gp, cw * s0, cb * gw[0], cb * gw[1], cb * gw[2]);
+            atomic_add4(gp + 4, cb * gw[3], cb * gw[4], cb * gw[5], cb * gw[6]);
         }
-        const float g_om = fl[0] * gf[0];
-        float g_be = 0.0f;
-#pragma unroll
-        for (int ch = 1; ch < 8; ++ch) g_be = fmaf(fl[ch], gf[ch], g_be);
+        float go = 0.0f, gb = 0.0f;
         if (attn_mode == 0) {
-            glog[2 * l] = g_om * om * (1.0f - om);
-            glog[2 * l + 1] = g_be * be * (1.0f - be);
+            go = sh * gs * om * (1.0f - om);
+            gb = w * q * be * (1.0f - be);
         } else if (attn_mode == 2) {
-            glog[2 * l] = (g_om + g_be) * om * (1.0f - om);
-            glog[2 * l + 1] = 0.0f;
-        } else {
-            glog[2 * l] = 0.0f;
-            glog[2 * l + 1] = 0.0f;
+            go = (sh * gs + w * q) * om * (1.0f - om);
         }
-        const float s0 = om * gf[0];
-        float sc[7];
-#pragma unroll
-        for (int ch = 0; ch < 7; ++ch) sc[ch] = be * gf[1 + ch];
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const float cw = corner_w(wl, c);
-            float* gp = g_tables + (size_t)rows[c] * 8;
-            atomic_add4(gp, cw * s0, cw * sc[0], cw * sc[1], cw * sc[2]);
-            atomic_add4(gp + 4, cw * sc[3], cw * sc[4], cw * sc[5], cw * sc[6]);
-        }
+        slots[(2 * l) * stride] = go;
+        slots[(2 * l + 1) * stride] = gb;
     }
     // coarse vertices: [gf(8), logit grads(2L)] times the corner weight
+    int b[3];
+    float wc[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) grid_cell(u[a], g.R_C, b[a], wc[a]);
+    const uint32_t R = (uint32_t)g.R_C;
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
-        const float cw = corner_w(w, c);
-        float* gp = g_coarse + (size_t)cv[c] * NC;
+        const uint32_t cv = (uint32_t)(b[0] + (c & 1)) + R * ((uint32_t)(b[1] + ((c >> 1) & 1)) + R * (uint32_t)(b[2] + ((c >> 2) & 1)));
+        const float cw = corner_w(wc, c);
+        float* gp = g_coarse + (size_t)cv * NC;
         if constexpr (NC % 4 == 0) {
-            atomic_add4(gp, cw * gf[0], cw * gf[1], cw * gf[2], cw * gf[3]);
-            atomic_add4(gp + 4, cw * gf[4], cw * gf[5], cw * gf[6], cw * gf[7]);
-#pragma unroll
-            for (int k = 0; k < 2 * L; k += 4)
-                atomic_add4(gp + 8 + k, cw * glog[k], cw * glog[k + 1], cw * glog[k + 2], cw * glog[k + 3]);
+            atomic_add4(gp, cw * gs, cw * gw[0], cw * gw[1], cw * gw[2]);
+            atomic_add4(gp + 4, cw * gw[3], cw * gw[4], cw * gw[5], cw * gw[6]);
+            if (attn_mode != 1) {
+#pragma unroll 4
+                for (int k = 0; k < 2 * L; k += 4)
+                    atomic_add4(gp + 8 + k, cw * slots[k * stride], cw * slots[(k + 1) * stride],
+                                cw * slots[(k + 2) * stride], cw * slots[(k + 3) * stride]);
+            }
         } else {
+            atomicAdd(gp, cw * gs);
 #pragma unroll
-            for (int ch = 0; ch < 8; ++ch) atomicAdd(gp + ch, cw * gf[ch]);
+            for (int ch = 0; ch < 7; ++ch) atomicAdd(gp + 1 + ch, cw * gw[ch]);
+            if (attn_mode != 1) {
 #pragma unroll
-            for (int k = 0; k < 2 * L; ++k) atomicAdd(gp + 8 + k, cw * glog[k]);
+                for (int k = 0; k < 2 * L; ++k) atomicAdd(gp + 8 + k, cw * slots[k * stride]);
+            }
         }
     }
 }
@@ -331,7 +305,8 @@ struct BackwardSampler {
     float* gates;
     __device__ __forceinline__ bool sample(const float u[3], float t, float delta) {
         float f[8];
-        sample_features<L, NGPRT_F32>(g, u, attn_mode, f, gates, blockDim.x);
+        const float gq[7] = {gCd[0], gCd[1], gCd[2], gF[0], gF[1], gF[2], gF[3]};
+        sample_features<L, NGPRT_F32, NGPRT_AGG_SEPARATE_V, true>(g, u, attn_mode, f, gates, blockDim.x, gq);
         const float sigma = expf(f[0]);
         const float trans = expf(-sigma * delta);
         const float w = T * (1.0f - trans);
@@ -343,13 +318,8 @@ struct BackwardSampler {
         for (int k = 0; k < 4; ++k) qg = fmaf(gF[k], f[4 + k], qg);
         S_le = fmaf(w, qg, S_le);
         const float g_sigma = delta * (T_next * qg - (S_tot - S_le));
-        float gf[8];
-        gf[0] = g_sigma * expf(fminf(f[0], 15.0f));
-#pragma unroll
-        for (int k = 0; k < 3; ++k) gf[1 + k] = w * gCd[k];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) gf[4 + k] = w * gF[k];
-        scatter_features<L>(g, u, attn_mode, gf, g_tables, g_coarse);
+        const float gs = g_sigma * expf(fminf(f[0], 15.0f));
+        scatter_features<L>(g, u, attn_mode, gs, w, gq, gates, blockDim.x, g_tables, g_coarse);
         T = T_next;
         return T < t_term;
     }
@@ -374,7 +344,7 @@ __global__ void __launch_bounds__(128) march_backward_kernel(const __grid_consta
 
 template <int L>
 void launch_bwd(const MarchBwdParams& p, dim3 grid, cudaStream_t st) {
-    march_backward_kernel<L><<<grid, 128, (size_t)2 * L * 128 * sizeof(float), st>>>(p);
+    march_backward_kernel<L><<<grid, 128, (size_t)4 * L * 128 * sizeof(float), st>>>(p);
 }
 
 }  // namespace

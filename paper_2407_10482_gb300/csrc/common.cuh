@@ -40,6 +40,7 @@ struct Grid {
     uint32_t level_off[kMaxL];   // first row of each level
     int32_t N[kMaxL];
     uint32_t dense_mask;         // bit l: level l is dense
+    uint32_t na_mask;            // bit l: level l's FP32 entries are read without L1 allocation
     uint32_t T_mask;             // 2^T_log2 - 1
     int32_t L;
     int32_t R_C;
@@ -211,6 +212,15 @@ template <>
 __device__ __forceinline__ void load_entry<NGPRT_F32>(const void* base, uint32_t row, float v[8]) {
     const float* p = static_cast<const float*>(base) + (size_t)row * 8;
     asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+                 : "l"(p));
+}
+
+// The same 256-bit load without allocating in L1 (entries of hashed levels are
+// rarely reused; L1 is left to the coarse and dense levels).
+__device__ __forceinline__ void load_entry_f32_na(const void* base, uint32_t row, float v[8]) {
+    const float* p = static_cast<const float*>(base) + (size_t)row * 8;
+    asm("ld.global.nc.L1::no_allocate.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                  : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
                  : "l"(p));
 }

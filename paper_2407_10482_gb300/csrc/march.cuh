@@ -141,9 +141,12 @@ constexpr int kLevelUnroll = NGPRT_LEVEL_UNROLL;
 // interpolate in packed half2 FMAs (FP16 products and sums, one conversion per
 // channel), the rest of the sample in FP32.  The MLP form accumulates its 64 hidden
 // units level by level (W1 columns of level l against f^l), then applies W2.
-template <int L, int DT, int AGG = NGPRT_AGG_SEPARATE_V>
+// With kKeep (reverse pass), level l also leaves sigma^l and q^l = sum over the
+// colour channels of f^l times gq (the ray's colour cotangents) in the slots
+// gates[(2L + 2l) * stride] and gates[(2L + 2l + 1) * stride].
+template <int L, int DT, int AGG = NGPRT_AGG_SEPARATE_V, bool kKeep = false>
 __device__ __forceinline__ void sample_features(const Grid& g, const float u[3], int attn_mode, float f[8],
-                                                float* gates, int stride) {
+                                                float* gates, int stride, const float* gq = nullptr) {
     constexpr int NC = coarse_channels(L, AGG);
     static_assert(NC % 2 == 0, "coarse channels are fetched in pairs");
     constexpr bool kGated = AGG != NGPRT_AGG_SUM && AGG != NGPRT_AGG_MLP;
@@ -257,7 +260,14 @@ __device__ __forceinline__ void sample_features(const Grid& g, const float u[3],
         } else {
             float e[8][8];
 #pragma unroll
-            for (int c = 0; c < 8; ++c) load_entry<DT>(g.tables, rows[c], e[c]);
+            // FP32: large levels bypass L1 allocation (16-bit entries share sectors
+            // and gain from L1: they keep the default path)
+            const bool na = DT == NGPRT_F32 && ((g.na_mask >> l) & 1u);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                if (na) load_entry_f32_na(g.tables, rows[c], e[c]);
+                else load_entry<DT>(g.tables, rows[c], e[c]);
+            }
 #pragma unroll
             for (int ch = 0; ch < 4; ++ch) fl[ch] = make_float2(0.0f, 0.0f);
 #pragma unroll
@@ -267,6 +277,17 @@ __device__ __forceinline__ void sample_features(const Grid& g, const float u[3],
 #pragma unroll
                 for (int ch = 0; ch < 4; ++ch) fl[ch] = ffma2(cw2, make_float2(e[c][2 * ch], e[c][2 * ch + 1]), fl[ch]);
             }
+        }
+        if constexpr (kKeep) {
+            float q = fl[0].y * gq[0];
+            q = fmaf(fl[1].x, gq[1], q);
+            q = fmaf(fl[1].y, gq[2], q);
+            q = fmaf(fl[2].x, gq[3], q);
+            q = fmaf(fl[2].y, gq[4], q);
+            q = fmaf(fl[3].x, gq[5], q);
+            q = fmaf(fl[3].y, gq[6], q);
+            gates[(2 * L + 2 * l) * stride] = fl[0].x;
+            gates[(2 * L + 2 * l + 1) * stride] = q;
         }
         if constexpr (AGG == NGPRT_AGG_SUM) {
 #pragma unroll
