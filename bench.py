@@ -327,7 +327,7 @@ def aggregation_ablation(args, dev, stream, flush):
         cfg = S.paper_config(L, aggregation=agg)
         sc = S.make_scene_torch(cfg, device=dev)
         if occ is None:
-            occ = ng.DeviceOcc(sc.occ, cfg.R_O, cfg.n_occ_levels, device=dev)
+            occ = ng.DeviceOcc(sc.occ, cfg.R_O, cfg.n_occ_levels, device=dev, dist_level=cfg.dist_level)
         ds = ng.DeviceScene(cfg, sc.tables, sc.coarse, sc.mlp_w, device=dev, attn_inv=sc.attn_inv, agg_mlp=sc.agg_mlp)
         rend = ng.Renderer(ds, occ, device=dev)
         opts = S.default_options(cfg)
@@ -341,7 +341,7 @@ def aggregation_ablation(args, dev, stream, flush):
                                "coarse_channels": S.coarse_channels(cfg)}
         del sc, ds, rend, o
         torch.cuda.empty_cache()
-    out["config"] = "paper shape L = 4 (N_l = 1024 * 2^l, T = 2^22, R_C = 512, R_O = 512), FP32, 1080p, hd scene"
+    out["config"] = "paper shape L = 4 (N_l = 1024 * 2^l, T = 2^22, R_C = 512, R_O = 512, G at 256^3), FP32, 1080p, hd scene"
     return out
 
 
@@ -356,7 +356,7 @@ def paper_shape(args, dev, stream, flush):
     for L in (2, 3, 4):
         cfg = S.paper_config(L)
         sc = S.make_scene_torch(cfg, device=dev)
-        docc = ng.DeviceOcc(sc.occ, cfg.R_O, cfg.n_occ_levels, device=dev)
+        docc = ng.DeviceOcc(sc.occ, cfg.R_O, cfg.n_occ_levels, device=dev, dist_level=cfg.dist_level)
         opts = S.default_options(cfg)
         cams = S.orbit_cameras(cfg, 1)
         n = cfg.W * cfg.H
@@ -376,7 +376,7 @@ def paper_shape(args, dev, stream, flush):
         out[f"L{L}"] = row
         del sc, docc
         torch.cuda.empty_cache()
-    out["config"] = "N_l = 1024 * 2^l, T = 2^22, R_C = 512 dense (8 + 2L channels), R_O = 512 (5 levels), G at 512^3"
+    out["config"] = "N_l = 1024 * 2^l, T = 2^22, R_C = 512 dense (8 + 2L channels), R_O = 512 (5 levels), G at 256^3"
     return out
 
 

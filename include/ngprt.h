@@ -120,13 +120,17 @@ int32_t ngprt_coarse_channels(int32_t L, int32_t aggregation);
  * Occupancy (Sec. 3.3; Sec. S2.5).  bits: n_levels bit-packed grids, finest
  * (R_O^3 bits) first, each next level halving the resolution, each level padded
  * to whole 32-bit words (bit i of a level is word i/32, bit i%32).  dist: the
- * R_O^3 uint8 occupancy distance grid G, or NULL to march without it.
+ * R_G^3 uint8 occupancy distance grid G, or NULL to march without it; R_G is the
+ * resolution of one pyramid level, R_O >> k (0 means R_O; the paper's renders keep
+ * G at 256^3 beside a 512^3 finest level), and G is read at an empty point only
+ * when the empty level is coarser than R_G (Sec. 3.3).
  */
 typedef struct {
     int32_t R_O;
     int32_t n_levels;
     const uint32_t* bits;
     const uint8_t* dist;
+    int32_t R_G;
 } ngprt_occ;
 
 /* Pinhole camera, OpenCV axes (x right, y down, z forward).  c2w: 3x4 row-major
@@ -173,14 +177,18 @@ size_t ngprt_build_occ_dist_workspace_bytes(int32_t R);
  * Sec. S2.5: the grid down-sampled to coarser levels).
  *   occ          : [R^3] uint8, nonzero = occupied.  R a power of two, 2..1024.
  *   n_levels     : pyramid levels, 1 <= n_levels and R >> (n_levels-1) >= 1.
+ *   dist_level   : G is built on pyramid level dist_level (R_G = R >> dist_level,
+ *                  0 <= dist_level < n_levels): a voxel of that level is occupied when
+ *                  any of its finest voxels is.
  *   occ_bits_out : [ngprt_occ_bits_words(R, n_levels)] uint32, written in full.
- *   dist_out     : [R^3] uint8 G, or NULL to skip it.  G = min(255, floor(D)), D the
- *                  Euclidean distance between the voxel boxes in voxels; 0 on and next
- *                  to occupied voxels; 255 everywhere if nothing is occupied.
+ *   dist_out     : [R_G^3] uint8 G, or NULL to skip it.  G = min(255, floor(D)), D the
+ *                  Euclidean distance between the voxel boxes in voxels of R_G; 0 on and
+ *                  next to occupied voxels; 255 everywhere if nothing is occupied.
  *   workspace    : >= ngprt_build_occ_dist_workspace_bytes(R) bytes.
  */
-int32_t ngprt_build_occ_dist(const uint8_t* occ, int32_t R, int32_t n_levels, uint32_t* occ_bits_out,
-                             uint8_t* dist_out, void* workspace, size_t ws_bytes, void* stream);
+int32_t ngprt_build_occ_dist(const uint8_t* occ, int32_t R, int32_t n_levels, int32_t dist_level,
+                             uint32_t* occ_bits_out, uint8_t* dist_out, void* workspace, size_t ws_bytes,
+                             void* stream);
 
 /*
  * Render-time occupancy pipeline (Sec. S2.5: occupancy from the trained model,

@@ -62,7 +62,8 @@ typedef struct {
     int R_O;
     int n_levels;
     const uint32_t* bits;  /* pyramid, finest level first */
-    const uint8_t* dist;   /* R_O^3 occupancy distance grid, or NULL */
+    const uint8_t* dist;   /* R_G^3 occupancy distance grid, or NULL */
+    int R_G;               /* resolution of dist: R_O >> k for a pyramid level k (0: R_O) */
 } or_occ;
 
 typedef struct {
@@ -546,7 +547,10 @@ static void or_march(const or_scene* s, const or_occ* oc, const or_opts* op,
     const float t_start = t;
     int lat_k = 0;
     const int R_O = oc->R_O;
-    const float vG = (2.0f * B) / (float)R_O;
+    const int R_G = oc->R_G ? oc->R_G : oc->R_O;
+    int g_shift = 0;
+    while ((R_O >> g_shift) > R_G) ++g_shift;
+    const float vG = (2.0f * B) / (float)R_G;
     double T = 1.0;
     while (t < t_out && res->n_march < op->max_march && res->n_samples < op->max_samples) {
         res->n_march++;
@@ -630,9 +634,10 @@ static void or_march(const or_scene* s, const or_occ* oc, const or_opts* op,
             float s_O = fmaxf(se, 0.0f) + 1e-5f * fmaxf(1.0f, t);
             step = s_O;
             /* Eq. 9: read G only when the empty level is coarser than G's grid */
-            if (op->use_dist && oc->dist && empty_level >= 1) {
-                int c0[3] = {or_vox(u[0], R_O), or_vox(u[1], R_O), or_vox(u[2], R_O)};
-                int g = oc->dist[(size_t)c0[0] + (size_t)R_O * ((size_t)c0[1] + (size_t)R_O * c0[2])];
+            /* G is read when the empty level is coarser than G's own resolution */
+            if (op->use_dist && oc->dist && empty_level > g_shift) {
+                int c0[3] = {or_vox(u[0], R_G), or_vox(u[1], R_G), or_vox(u[2], R_G)};
+                int g = oc->dist[(size_t)c0[0] + (size_t)R_G * ((size_t)c0[1] + (size_t)R_G * c0[2])];
                 if (g > 0) {
                     float sg = or_dist_step(s->bounded, x, d, r, (float)g * vG);
                     step = op->dist_rule == 1 ? fmaxf(sg, s_O) : sg;

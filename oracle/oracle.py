@@ -43,7 +43,8 @@ class OrScene(C.Structure):
 
 
 class OrOcc(C.Structure):
-    _fields_ = [("R_O", C.c_int), ("n_levels", C.c_int), ("bits", C.c_void_p), ("dist", C.c_void_p)]
+    _fields_ = [("R_O", C.c_int), ("n_levels", C.c_int), ("bits", C.c_void_p), ("dist", C.c_void_p),
+                ("R_G", C.c_int)]
 
 
 class OrOpts(C.Structure):
@@ -172,7 +173,7 @@ class Oracle:
     """FP64 renderer over one scene.  ``tables``/``coarse``/``mlp_w`` may be FP32 or
     FP16/BF16-rounded copies (pass them as float arrays); they are widened to FP64."""
 
-    def __init__(self, cfg, tables, coarse, mlp_w, occ_bits, dist=None, attn_inv=None, agg_mlp=None):
+    def __init__(self, cfg, tables, coarse, mlp_w, occ_bits, dist=None, attn_inv=None, agg_mlp=None, R_G=0):
         self.cfg = cfg
         self.tables = _c(np.asarray(tables, np.float64), np.float64)
         self.coarse = _c(np.asarray(coarse, np.float64), np.float64)
@@ -208,6 +209,9 @@ class Oracle:
         o.n_levels = cfg.n_occ_levels
         o.bits = self.bits.ctypes.data
         o.dist = self.dist.ctypes.data if self.dist is not None else None
+        o.R_G = int(R_G)
+        if self.dist is not None:
+            assert self.dist.size == (R_G or cfg.R_O) ** 3, "distance grid size"
         self._o = o
 
     @staticmethod
@@ -361,14 +365,28 @@ class Oracle:
         return y
 
 
-def oracle_for_scene(scene, tables=None, coarse=None, use_dist=True) -> Oracle:
-    """Oracle over a generated scene: builds the pyramid and distance grid itself."""
+def downsample_occ(occ: np.ndarray, R: int, k: int) -> np.ndarray:
+    """Occupancy of pyramid level k as one byte per voxel: a voxel of R >> k is
+    occupied when any of its 2^k x 2^k x 2^k finest voxels is (x fastest)."""
+    g = np.asarray(occ, np.uint8).reshape(R, R, R)
+    if k == 0:
+        return np.ascontiguousarray(g.reshape(-1))
+    f = 1 << k
+    r = R >> k
+    return np.ascontiguousarray(g.reshape(r, f, r, f, r, f).max(axis=(1, 3, 5)).reshape(-1))
+
+
+def oracle_for_scene(scene, tables=None, coarse=None, use_dist=True, dist_level=0) -> Oracle:
+    """Oracle over a generated scene: builds the pyramid and distance grid itself (G
+    on pyramid level dist_level)."""
     cfg = scene.cfg
     bits = build_pyramid(scene.occ, cfg.R_O, cfg.n_occ_levels)
-    dist = occ_dist(scene.occ, cfg.R_O) if use_dist else None
+    RG = cfg.R_O >> dist_level
+    dist = occ_dist(downsample_occ(scene.occ, cfg.R_O, dist_level), RG) if use_dist else None
     return Oracle(cfg, scene.tables if tables is None else tables,
                   scene.coarse if coarse is None else coarse, scene.mlp_w, bits, dist,
-                  attn_inv=getattr(scene, "attn_inv", None), agg_mlp=getattr(scene, "agg_mlp", None))
+                  attn_inv=getattr(scene, "attn_inv", None), agg_mlp=getattr(scene, "agg_mlp", None),
+                  R_G=RG if dist_level else 0)
 
 
 def contract(x: np.ndarray, bounded: bool = False):

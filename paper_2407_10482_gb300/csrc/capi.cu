@@ -98,11 +98,18 @@ int32_t make_occ(const ngprt_occ* o, OccView& v, const char* fn) {
                   fn, o->R_O);
     NGPRT_REQUIRE(o->n_levels >= 1 && o->n_levels <= kMaxOccLevels && (o->R_O >> (o->n_levels - 1)) >= 1,
                   "%s: n_levels=%d", fn, o->n_levels);
+    const int32_t RG = o->R_G == 0 ? o->R_O : o->R_G;
+    int g_shift = -1;
+    for (int k = 0; k < o->n_levels; ++k)
+        if ((o->R_O >> k) == RG) g_shift = k;
+    NGPRT_REQUIRE(g_shift >= 0, "%s: R_G=%d must be R_O >> k for a pyramid level k", fn, o->R_G);
     memset(&v, 0, sizeof v);
     v.bits = o->bits;
     v.dist = o->dist;
     v.R_O = o->R_O;
     v.n_levels = o->n_levels;
+    v.R_G = RG;
+    v.g_shift = g_shift;
     uint32_t off = 0;
     for (int k = 0; k < o->n_levels; ++k) {
         const uint64_t r = (uint64_t)(o->R_O >> k);

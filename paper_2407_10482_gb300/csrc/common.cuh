@@ -61,6 +61,8 @@ struct OccView {
     uint32_t word_off[kMaxOccLevels];  // first word of each pyramid level
     int32_t R_O;
     int32_t n_levels;
+    int32_t R_G;      // resolution of dist: R_O >> g_shift
+    int32_t g_shift;  // G is read when the empty pyramid level is coarser (k > g_shift)
 };
 
 // ------------------------------------------------- exactly rounded FP32 helpers

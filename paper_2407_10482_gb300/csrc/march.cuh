@@ -389,7 +389,8 @@ __device__ __forceinline__ bool march_advance(const MarchParams& p, const float 
     const float B = bounded ? 1.0f : 2.0f;
     const float dt0 = fmul(op.step_base, op.step_gamma);
     const int R_O = p.occ.R_O;
-    const float vG = fdiv(2.0f * B, (float)R_O);
+    const int R_G = p.occ.R_G;
+    const float vG = fdiv(2.0f * B, (float)R_G);
     const bool snap = op.lattice_snap && bounded;
     float t = st.t;
     while (t < st.t_out && st.n_march < op.max_march && st.n_samp < op.max_samples) {
@@ -442,9 +443,9 @@ __device__ __forceinline__ bool march_advance(const MarchParams& p, const float 
         }
         const float s_O = fadd(fmaxf(se, 0.0f), fmul(1e-5f, fmaxf(1.0f, t)));
         float step = s_O;
-        if (op.use_dist && p.occ.dist && empty_level >= 1) {
-            const int g0 = occ_vox(u[0], R_O), g1 = occ_vox(u[1], R_O), g2 = occ_vox(u[2], R_O);
-            const int gv = __ldg(p.occ.dist + ((size_t)g0 + (size_t)R_O * ((size_t)g1 + (size_t)R_O * g2)));
+        if (op.use_dist && p.occ.dist && empty_level > p.occ.g_shift) {
+            const int g0 = occ_vox(u[0], R_G), g1 = occ_vox(u[1], R_G), g2 = occ_vox(u[2], R_G);
+            const int gv = __ldg(p.occ.dist + ((size_t)g0 + (size_t)R_G * ((size_t)g1 + (size_t)R_G * g2)));
             if (gv > 0) {
                 const float sg = dist_step(bounded, x, d, r, fmul((float)gv, vG));
                 step = op.dist_rule == 1 ? fmaxf(sg, s_O) : sg;

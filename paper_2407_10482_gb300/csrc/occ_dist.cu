@@ -84,6 +84,14 @@ __global__ void edt_pass_kernel(const uint8_t* __restrict__ occ, const int32_t* 
     }
 }
 
+// Unpack one pyramid level (n voxels) to one byte per voxel, the input of the
+// distance transform when G sits on a coarser level than the finest.
+__global__ void unpack_bits_kernel(const uint32_t* __restrict__ bits, size_t n, uint8_t* __restrict__ out) {
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    out[i] = (uint8_t)((bits[i >> 5] >> (i & 31)) & 1u);
+}
+
 __global__ void finish_dist_kernel(const int32_t* __restrict__ d2, size_t n, uint8_t* __restrict__ dist) {
     size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -123,24 +131,28 @@ extern "C" size_t ngprt_build_occ_dist_workspace_bytes(int32_t R) {
     return 2 * ((n * sizeof(int32_t) + 255) / 256 * 256);
 }
 
-extern "C" int32_t ngprt_build_occ_dist(const uint8_t* occ, int32_t R, int32_t n_levels, uint32_t* occ_bits_out,
-                                        uint8_t* dist_out, void* workspace, size_t ws_bytes, void* stream) {
+extern "C" int32_t ngprt_build_occ_dist(const uint8_t* occ, int32_t R, int32_t n_levels, int32_t dist_level,
+                                        uint32_t* occ_bits_out, uint8_t* dist_out, void* workspace, size_t ws_bytes,
+                                        void* stream) {
     NGPRT_REQUIRE(occ != nullptr, "ngprt_build_occ_dist: occ is NULL");
     NGPRT_REQUIRE(occ_bits_out != nullptr, "ngprt_build_occ_dist: occ_bits_out is NULL");
     NGPRT_REQUIRE(R >= 2 && R <= 1024 && (R & (R - 1)) == 0, "ngprt_build_occ_dist: R=%d must be a power of two in [2, 1024]", R);
     NGPRT_REQUIRE(n_levels >= 1 && n_levels <= kMaxOccLevels && (R >> (n_levels - 1)) >= 1,
                   "ngprt_build_occ_dist: n_levels=%d invalid for R=%d", n_levels, R);
+    NGPRT_REQUIRE(dist_level >= 0 && dist_level < n_levels, "ngprt_build_occ_dist: dist_level=%d not in [0, %d)",
+                  dist_level, n_levels);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const size_t n = (size_t)R * R * R;
     // pyramid
     size_t w0 = words(n);
     pack_bits_kernel<<<(unsigned)((w0 + 255) / 256), 256, 0, st>>>(occ, n, occ_bits_out, w0);
-    size_t off_prev = 0, off = w0;
+    size_t off_prev = 0, off = w0, dist_off = 0;
     for (int k = 1; k < n_levels; ++k) {
         int rf = R >> (k - 1), rc = R >> k;
         size_t wk = words((size_t)rc * rc * rc);
         downsample_kernel<<<(unsigned)((wk + 127) / 128), 128, 0, st>>>(occ_bits_out + off_prev, rf,
                                                                          occ_bits_out + off, rc, wk);
+        if (k == dist_level) dist_off = off;
         off_prev = off;
         off += wk;
     }
@@ -151,15 +163,26 @@ extern "C" int32_t ngprt_build_occ_dist(const uint8_t* occ, int32_t R, int32_t n
             return NGPRT_ERR_WORKSPACE;
         }
         NGPRT_REQUIRE(((uintptr_t)workspace & 255) == 0, "ngprt_build_occ_dist: workspace not 256-byte aligned");
+        // G on level dist_level: its voxels' occupancy (finest occ, or the level's
+        // pyramid bits unpacked into the second half of the workspace)
+        const int Rg = R >> dist_level;
+        const size_t ng = (size_t)Rg * Rg * Rg;
         int32_t* a = static_cast<int32_t*>(workspace);
         int32_t* b = reinterpret_cast<int32_t*>(static_cast<char*>(workspace) + need / 2);
-        const unsigned lines = (unsigned)((size_t)R * R);
-        const int threads = std::min(R, 256);
-        const size_t shm = (size_t)R * sizeof(int32_t);
-        edt_pass_kernel<<<lines, threads, shm, st>>>(occ, nullptr, a, R, 0);
-        edt_pass_kernel<<<lines, threads, shm, st>>>(nullptr, a, b, R, 1);
-        edt_pass_kernel<<<lines, threads, shm, st>>>(nullptr, b, a, R, 2);
-        finish_dist_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a, n, dist_out);
+        const uint8_t* src = occ;
+        if (dist_level > 0) {
+            // (R/2)^3 bytes fit after a's (R/2)^3 ints in the first half (R^3 ints)
+            uint8_t* u8 = reinterpret_cast<uint8_t*>(a + ng);
+            unpack_bits_kernel<<<(unsigned)((ng + 255) / 256), 256, 0, st>>>(occ_bits_out + dist_off, ng, u8);
+            src = u8;
+        }
+        const unsigned lines = (unsigned)((size_t)Rg * Rg);
+        const int threads = std::min(Rg, 256);
+        const size_t shm = (size_t)Rg * sizeof(int32_t);
+        edt_pass_kernel<<<lines, threads, shm, st>>>(src, nullptr, b, Rg, 0);
+        edt_pass_kernel<<<lines, threads, shm, st>>>(nullptr, b, a, Rg, 1);
+        edt_pass_kernel<<<lines, threads, shm, st>>>(nullptr, a, b, Rg, 2);
+        finish_dist_kernel<<<(unsigned)((ng + 255) / 256), 256, 0, st>>>(b, ng, dist_out);
     }
     return cuda_status("ngprt_build_occ_dist");
 }

@@ -40,7 +40,8 @@ class ngprt_scene(C.Structure):
 
 
 class ngprt_occ(C.Structure):
-    _fields_ = [("R_O", C.c_int32), ("n_levels", C.c_int32), ("bits", C.c_void_p), ("dist", C.c_void_p)]
+    _fields_ = [("R_O", C.c_int32), ("n_levels", C.c_int32), ("bits", C.c_void_p), ("dist", C.c_void_p),
+                ("R_G", C.c_int32)]
 
 
 class ngprt_camera(C.Structure):
@@ -59,7 +60,7 @@ _P = C.c_void_p
 _SIGS = {
     "ngprt_occ_bits_words": (C.c_size_t, [C.c_int32, C.c_int32]),
     "ngprt_build_occ_dist_workspace_bytes": (C.c_size_t, [C.c_int32]),
-    "ngprt_build_occ_dist": (C.c_int32, [_P, C.c_int32, C.c_int32, _P, _P, _P, C.c_size_t, _P]),
+    "ngprt_build_occ_dist": (C.c_int32, [_P, C.c_int32, C.c_int32, C.c_int32, _P, _P, _P, C.c_size_t, _P]),
     "ngprt_table_entries": (C.c_int64, [_P]),
     "ngprt_coarse_channels": (C.c_int32, [C.c_int32, C.c_int32]),
     "ngprt_occupancy_from_density": (C.c_int32, [_P, _P, C.c_int32, C.c_float, _P, _P, _P]),
@@ -158,10 +159,11 @@ def ngprt_build_occ_dist_workspace_bytes(R: int) -> int:
     return int(lib().ngprt_build_occ_dist_workspace_bytes(R))
 
 
-def ngprt_build_occ_dist(occ, R, n_levels, occ_bits_out, dist_out, workspace, stream=None) -> None:
+def ngprt_build_occ_dist(occ, R, n_levels, occ_bits_out, dist_out, workspace, stream=None, dist_level=0) -> None:
     ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
     _check("ngprt_build_occ_dist", lib().ngprt_build_occ_dist(
-        _ptr(occ), R, n_levels, _ptr(occ_bits_out), _ptr(dist_out), _ptr(workspace), ws_bytes, _stream(stream)))
+        _ptr(occ), R, n_levels, dist_level, _ptr(occ_bits_out), _ptr(dist_out), _ptr(workspace), ws_bytes,
+        _stream(stream)))
 
 
 def ngprt_table_entries(scene: ngprt_scene) -> int:
@@ -391,18 +393,18 @@ class DeviceScene:
 class DeviceOcc:
     """Occupancy pyramid and distance grid built on the GPU by ngprt_build_occ_dist."""
 
-    def __init__(self, occ: np.ndarray, R: int, n_levels: int, with_dist: bool = True, device="cuda"):
+    def __init__(self, occ: np.ndarray, R: int, n_levels: int, with_dist: bool = True, device="cuda",
+                 dist_level: int = 0):
         self.R, self.n_levels = R, n_levels
+        self.R_G = R >> dist_level
         self.occ = (occ.to(device=device, dtype=torch.uint8) if isinstance(occ, torch.Tensor)
                     else torch.as_tensor(np.asarray(occ, np.uint8)).to(device)).contiguous()
         self.bits = torch.empty(ngprt_occ_bits_words(R, n_levels), dtype=torch.int32, device=device)
-        self.dist = torch.empty(R ** 3, dtype=torch.uint8, device=device) if with_dist else None
+        self.dist = torch.empty(self.R_G ** 3, dtype=torch.uint8, device=device) if with_dist else None
         ws = torch.empty(ngprt_build_occ_dist_workspace_bytes(R), dtype=torch.uint8, device=device)
-        ngprt_build_occ_dist(self.occ, R, n_levels, self.bits, self.dist, ws)
-        o = ngprt_occ()
-        o.R_O, o.n_levels, o.bits, o.dist = R, n_levels, _ptr(self.bits), _ptr(self.dist)
-        self.struct = o
-        self.struct_nodist = ngprt_occ(R, n_levels, _ptr(self.bits), None)
+        ngprt_build_occ_dist(self.occ, R, n_levels, self.bits, self.dist, ws, dist_level=dist_level)
+        self.struct = ngprt_occ(R, n_levels, _ptr(self.bits), _ptr(self.dist), self.R_G)
+        self.struct_nodist = ngprt_occ(R, n_levels, _ptr(self.bits), None, self.R_G)
 
 
 class Renderer:

@@ -63,6 +63,7 @@ class SceneConfig:
     blob_std: tuple = (0.08, 0.25)
     blob_peak: tuple = (5.0, 50.0)
     aggregation: int = 0    # level fusion (Eq. 8 = 0; the Table 3 variants 1..5, see coarse_channels)
+    dist_level: int = 0     # G on occupancy pyramid level k (resolution R_O >> k)
 
 
 def level_resolutions(n_min: int, n_max: int, L: int) -> list:
@@ -326,9 +327,9 @@ def paper_config(L: int = 2, **kw) -> SceneConfig:
     """The paper's render-time shape (Sec. S2.1, S2.5; Tables 2 and 4): L fine levels
     at 1024 * 2^l with T = 2^22, a 512^3 coarse grid (8 + 2L channels; the paper's is
     sparse, this one dense), a 512^3 occupancy grid with 5 levels down to 32^3 and the
-    distance grid at the occupancy resolution; hd's unbounded blob scene and orbit."""
+    distance grid G at 256^3 (Sec. 3.3); hd's unbounded blob scene and orbit."""
     c = hd_config(name=f"paper_L{L}", L=L, N=[1024 * 2 ** l for l in range(L)], T_log2=22, R_C=512, R_O=512,
-                  n_occ_levels=5, seed=7)
+                  n_occ_levels=5, seed=7, dist_level=1)
     return replace(c, **kw)
 
 

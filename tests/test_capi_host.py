@@ -58,7 +58,7 @@ def test_argument_errors_are_reported_without_a_launch(ng):
     assert rc == ng.ERR_INVALID_ARG
     assert b"scene is NULL" in lib.ngprt_last_error()
     # R not a power of two
-    rc = lib.ngprt_build_occ_dist(C.c_void_p(256), 12, 2, C.c_void_p(256), None, None, 0, None)
+    rc = lib.ngprt_build_occ_dist(C.c_void_p(256), 12, 2, 0, C.c_void_p(256), None, None, 0, None)
     assert rc == ng.ERR_INVALID_ARG and b"power of two" in lib.ngprt_last_error()
     # an L without a kernel
     cfg = S.small_config()

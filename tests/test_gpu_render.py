@@ -26,13 +26,15 @@ def ng():
     return ngprt
 
 
-def _occ_check(ng, occ, R, n_levels):
-    d = ng.DeviceOcc(occ, R, n_levels)
+def _occ_check(ng, occ, R, n_levels, dist_level=0):
+    d = ng.DeviceOcc(occ, R, n_levels, dist_level=dist_level)
     torch.cuda.synchronize()
     bits = d.bits.cpu().numpy().view(np.uint32)
     dist = d.dist.cpu().numpy()
     assert np.array_equal(bits, O.build_pyramid(occ, R, n_levels))
-    ref = O.occ_dist_brute(occ, R) if R <= 12 else O.occ_dist(occ, R)
+    Rg = R >> dist_level
+    lvl = O.downsample_occ(occ, R, dist_level)
+    ref = O.occ_dist_brute(lvl, Rg) if Rg <= 12 else O.occ_dist(lvl, Rg)
     assert np.array_equal(dist, ref)
 
 
@@ -40,7 +42,8 @@ def _occ_check(ng, occ, R, n_levels):
                                                     (16, 4, 0.01, 3), (32, 3, 0.002, 4), (64, 5, 0.03, 5)])
 def test_occupancy_pyramid_and_distance_bit_exact(ng, R, n_levels, frac, seed):
     occ = (np.random.default_rng(seed).uniform(size=R ** 3) < frac).astype(np.uint8)
-    _occ_check(ng, occ, R, n_levels)
+    for k in range(min(n_levels, 3)):
+        _occ_check(ng, occ, R, n_levels, dist_level=k)
 
 
 def test_occupancy_of_the_hd_scene_bit_exact(ng):
@@ -300,7 +303,7 @@ def test_paper_shape_sampled_parity(ng, L):
     cfg = S.paper_config(L, R_C=128, R_O=128, T_log2=20)
     sc = S.make_scene_torch(cfg, device="cuda")
     ds = ng.DeviceScene(cfg, sc.tables, sc.coarse, sc.mlp_w)
-    docc = ng.DeviceOcc(sc.occ, cfg.R_O, cfg.n_occ_levels)
+    docc = ng.DeviceOcc(sc.occ, cfg.R_O, cfg.n_occ_levels, dist_level=cfg.dist_level)
     rend = ng.Renderer(ds, docc)
     opts = S.default_options(cfg)
     cams = S.orbit_cameras(cfg, 1, azimuth0=60.0)
@@ -308,8 +311,10 @@ def test_paper_shape_sampled_parity(ng, L):
     r = rend.render(opts, cams=cams, W=cfg.W, H=cfg.H, pixel_ids=torch.as_tensor(pix).cuda(), stats=True)
     torch.cuda.synchronize()
     occ = sc.occ.cpu().numpy()
+    Rg = cfg.R_O >> cfg.dist_level
     orc = O.Oracle(cfg, sc.tables.cpu().numpy(), sc.coarse.cpu().numpy(), sc.mlp_w,
-                   O.build_pyramid(occ, cfg.R_O, cfg.n_occ_levels), O.occ_dist(occ, cfg.R_O))
+                   O.build_pyramid(occ, cfg.R_O, cfg.n_occ_levels),
+                   O.occ_dist(O.downsample_occ(occ, cfg.R_O, cfg.dist_level), Rg), R_G=Rg)
     _compare(r, orc.render(opts, cams=cams, pix=pix))
     assert r["stats"][:, 1].float().mean() > 3
 
@@ -356,3 +361,27 @@ def test_aggregation_variant_rejects_unbuilt_requests(ng):
     docc = ng.DeviceOcc(sc.occ, cfg.R_O, cfg.n_occ_levels)
     with pytest.raises(ng.NgprtError, match="not built for L=3"):
         ng.Renderer(ds, docc).render(S.default_options(cfg), cams=S.orbit_cameras(cfg, 1), W=cfg.W, H=cfg.H)
+
+
+@pytest.mark.parametrize("bounded", [True, False])
+def test_coarse_distance_grid_parity(ng, bounded):
+    """G one pyramid level coarser than the finest occupancy (the paper's 256^3 beside
+    512^3), read only where the empty level is coarser still: same counts and values
+    as the oracle."""
+    if bounded:
+        cfg = S.small_config(blob_std=(0.05, 0.15), R_O=64, n_occ_levels=4, dist_level=1)
+    else:
+        cfg = S.small_config(bounded=False, R_O=64, n_occ_levels=4, t_min=0.05, r_far=16.0, shell=True,
+                             mlp_layers=3, mlp_width=64, step_base=2 * 3 ** 0.5 / 256, blob_std=(0.05, 0.15),
+                             density_bias=3.0, dist_level=1)
+    sc = S.make_scene(cfg)
+    ds = ng.DeviceScene(cfg, sc.tables, sc.coarse, sc.mlp_w)
+    docc = ng.DeviceOcc(sc.occ, cfg.R_O, cfg.n_occ_levels, dist_level=1)
+    rend = ng.Renderer(ds, docc)
+    orc = O.oracle_for_scene(sc, dist_level=1)
+    for kw in (dict(), dict(dist_rule=1)):
+        opts = S.default_options(cfg, **kw)
+        cams = S.orbit_cameras(cfg, 1, azimuth0=50.0)
+        r = rend.render(opts, cams=cams, W=cfg.W, H=cfg.H, stats=True)
+        torch.cuda.synchronize()
+        _compare(r, orc.render(opts, cams=cams))

@@ -341,19 +341,36 @@ def test_early_termination_after_an_opaque_sample():
     assert r["opacity"][0] > 1 - 2e-3
 
 
-def test_lattice_snap_makes_distance_grid_invisible():
+@pytest.mark.parametrize("dist_level", [0, 1])
+def test_lattice_snap_makes_distance_grid_invisible(dist_level):
     """With samples snapped to the uniform lattice, skipping with G changes only the
     marching points, never the sample set: renders are identical (the exact form of
-    Table 4's unchanged '# Occupied')."""
+    Table 4's unchanged '# Occupied'), with G at the finest occupancy resolution or
+    one level coarser (read only where the empty level is coarser still)."""
     cfg = S.small_config(blob_std=(0.05, 0.12))
     sc = S.make_scene(cfg)
-    orc = O.oracle_for_scene(sc)
+    orc = O.oracle_for_scene(sc, dist_level=dist_level)
     cams = S.orbit_cameras(cfg, 1)
     a = orc.render(S.default_options(cfg, lattice_snap=True, use_dist=True), cams=cams)
     b = orc.render(S.default_options(cfg, lattice_snap=True, use_dist=False), cams=cams)
     assert np.array_equal(a["rgb"], b["rgb"])
     assert np.array_equal(a["stats"][:, 1], b["stats"][:, 1])
     assert a["stats"][:, 0].sum() < b["stats"][:, 0].sum()
+
+
+def test_downsampled_occupancy_is_the_pyramid_level():
+    cfg = S.small_config()
+    sc = S.make_scene(cfg)
+    R, n_levels = cfg.R_O, cfg.n_occ_levels
+    bits = O.build_pyramid(sc.occ, R, n_levels)
+    off = 0
+    for k in range(n_levels):
+        r = R >> k
+        level = O.downsample_occ(sc.occ, R, k)
+        words = bits[off:off + (r ** 3 + 31) // 32]
+        unpacked = ((words[np.arange(r ** 3) >> 5] >> (np.arange(r ** 3) & 31).astype(np.uint32)) & 1).astype(np.uint8)
+        assert np.array_equal(level, unpacked)
+        off += (r ** 3 + 31) // 32
 
 
 def test_distance_grid_cuts_marching_points_not_samples():
