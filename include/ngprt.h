@@ -433,13 +433,14 @@ int32_t ngprt_grid_indices(const ngprt_scene* scene, const float* u, int64_t n, 
                            void* stream);
 
 /* Measured ceiling of the render's gathers: n_threads threads each load per_thread
- * random whole entries (rows drawn by a counter-based hash of seed, thread and step)
- * of an [n_rows][8] table of dtype F32 (one 32-byte load each) or F16 (16 bytes).
+ * random whole entries (rows from a counter-based sequence of seed, thread and step)
+ * of an [n_rows][8] table of dtype F32 (one 32-byte load each) or F16 (16 bytes);
+ * flags = 1 reads FP32 entries without L1 allocation (the march's large levels).
  * Bytes moved = n_threads * per_thread * entry size; time it on `stream`.
  * n_rows a power of two, n_threads a multiple of 256, per_thread of 8; sink: one
- * device float (written only in a case that cannot occur with finite tables). */
+ * device float (written only in a case that practically cannot occur). */
 int32_t ngprt_gather_bench(const void* table, int32_t dtype, int64_t n_rows, int64_t n_threads, int32_t per_thread,
-                           uint32_t seed, float* sink, void* stream);
+                           uint32_t seed, int32_t flags, float* sink, void* stream);
 
 /* 1 if a tensor-core MLP kernel (mlp_dtype F16) ever gave up waiting for its MMAs
  * (it then frees its tensor memory and leaves its rays unwritten), 0 if not, -1 if

@@ -98,7 +98,8 @@ _SIGS = {
     "ngprt_render_noalloc": (C.c_int32, [_P, _P, _P, C.c_int32, _P, _P, _P, C.c_int64, _P, _P, _P, _P, _P, _P,
                                          _P]),
     "ngprt_tensor_core_error": (C.c_int32, []),
-    "ngprt_gather_bench": (C.c_int32, [_P, C.c_int32, C.c_int64, C.c_int64, C.c_int32, C.c_uint32, _P, _P]),
+    "ngprt_gather_bench": (C.c_int32, [_P, C.c_int32, C.c_int64, C.c_int64, C.c_int32, C.c_uint32, C.c_int32, _P,
+                                       _P]),
     "ngprt_last_error": (C.c_char_p, []),
     "ngprt_version": (C.c_int32, []),
 }
@@ -323,9 +324,9 @@ def ngprt_render_noalloc(scene, occ, cams, n_cams, pixel_ids, rays_o, rays_d, n_
         _ptr(t_interval), C.byref(opts), _ptr(rgb), _ptr(depth), _ptr(opacity), _ptr(ray_stats), _stream(stream)))
 
 
-def ngprt_gather_bench(table, dtype, n_rows, n_threads, per_thread, seed, sink, stream=None) -> None:
+def ngprt_gather_bench(table, dtype, n_rows, n_threads, per_thread, seed, sink, stream=None, flags=0) -> None:
     _check("ngprt_gather_bench", lib().ngprt_gather_bench(_ptr(table), dtype, n_rows, n_threads, per_thread, seed,
-                                                          _ptr(sink), _stream(stream)))
+                                                          flags, _ptr(sink), _stream(stream)))
 
 
 def ngprt_grid_indices(scene, u, n, idx_out, stream=None) -> None:
