@@ -3,8 +3,8 @@
 // Kernel 1 (shade_backward_kernel): per ray, the deferred MLP_psi and colour
 // sigmoid again from the stored composite state, then their reverse pass: the
 // cotangents of C_d, F, A and depth go to a per-ray record, and the MLP weight
-// gradients are summed over the warp's rays with shuffles, over the block in shared
-// memory, and added to g_mlp once per block.
+// gradients, sums over rays of outer products, are formed tile by tile from shared
+// memory and added to g_mlp once per block.
 // Kernel 2 (march_backward_kernel): per ray, the same march as the forward (same
 // decisions: march_loop), and at each sample i the derivative of the composite
 // sums Q = sum_j w_j q_j:
@@ -32,168 +32,237 @@ struct ShadeBwdParams {
     float* g_mlp;
 };
 
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
+// Shared-memory layout of the tiled deferred-MLP reverse pass: the weights, then
+// per tile of 128 rays the inputs X [128][25] and the hidden activations (later
+// their gradients) H1, H2 [128][W + 1] (odd row strides: a thread reading its own
+// row and a thread reading one column of all rows are both bank-conflict free), and
+// the colour-logit gradients GZ [128][4].
+template <int WIDTH, int LAYERS>
+struct ShadeTile {
+    static constexpr int n_w0 = WIDTH * kMlpIn;
+    static constexpr int n_mid = (LAYERS - 2) * WIDTH * WIDTH;
+    static constexpr int n_last = 3 * WIDTH;
+    static constexpr int n_all = n_w0 + n_mid + n_last;
+    static constexpr int kRays = 128;
+    static constexpr int kXs = 25;
+    static constexpr int kHs = WIDTH + 1;
+    static constexpr int n_smem = n_all + kRays * kXs + kRays * kHs * (LAYERS - 1) + kRays * 4;
+    static constexpr int TO = WIDTH / 16, TI = WIDTH / 8;  // dW_mid tile per thread (16 x 8 tiles)
+    static constexpr int T0 = WIDTH / 16;                  // dW0 tile per thread: T0 outputs x 3 inputs
+};
 
+// Kernel 1: per ray (one thread), the deferred MLP_psi and colour sigmoid again from
+// the stored composite state, then their reverse pass; the cotangents of C_d, F, A
+// and depth go to a per-ray record.  The weight gradients are sums over rays of
+// outer products, dW = sum_r g_r h_r^T: after each layer's per-ray phase the block
+// multiplies the tile's gradients and activations from shared memory, each thread
+// accumulating a fixed tile of dW in registers over all the block's ray tiles, and
+// adds it to g_mlp once at the end.
 template <int WIDTH, int LAYERS>
 __global__ void __launch_bounds__(128) shade_backward_kernel(const __grid_constant__ ShadeBwdParams p) {
-    constexpr int n_w0 = WIDTH * kMlpIn;
-    constexpr int n_mid = (LAYERS - 2) * WIDTH * WIDTH;
-    constexpr int n_last = 3 * WIDTH;
-    constexpr int n_all = n_w0 + n_mid + n_last;
-    __shared__ __align__(16) float ws[n_all];
-    __shared__ float gw[n_all];
-    for (int i = threadIdx.x; i < n_all; i += blockDim.x) {
-        ws[i] = p.w[i];
-        gw[i] = 0.0f;
-    }
-    __syncthreads();
-    const int64_t ray = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool active = ray < p.n;
-    // ---- forward again (inactive lanes carry zeros so that warp sums stay valid)
-    float x[24];
-    float A = 0.0f;
-    float Cd[3] = {0, 0, 0}, F[4] = {0, 0, 0, 0}, depth = 0.0f;
+    using K = ShadeTile<WIDTH, LAYERS>;
+    extern __shared__ __align__(16) float sm[];
+    float* ws = sm;
+    float* X = ws + K::n_all;
+    float* H1 = X + K::kRays * K::kXs;
+    float* H2 = H1 + K::kRays * K::kHs;  // used when LAYERS == 3
+    float* GZ = H1 + K::kRays * K::kHs * (LAYERS - 1);
+    float* Hl = LAYERS == 3 ? H2 : H1;   // input of the last layer
+    for (int i = threadIdx.x; i < K::n_all; i += blockDim.x) ws[i] = p.w[i];
+    const float* w0 = ws;
+    const float* wm = ws + K::n_w0;
+    const float* wl = ws + K::n_w0 + K::n_mid;
+    const int t = threadIdx.x;
+    const int ob = t >> 3, ib = t & 7;
+    float dmid[K::TO][K::TI];
+    float d0[K::T0][3];
+    float dl[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
-    for (int i = 0; i < 24; ++i) x[i] = 0.0f;
-    if (active) {
-        const float4* s4 = reinterpret_cast<const float4*>(p.state + ray * NGPRT_STATE_FLOATS);
-        const float4 q0 = s4[0], q1 = s4[1], q2 = s4[2];
-        Cd[0] = q0.x; Cd[1] = q0.y; Cd[2] = q0.z;
-        F[0] = q0.w; F[1] = q1.x; F[2] = q1.y; F[3] = q1.z;
-        A = q1.w;
-        depth = q2.x;
-        x[0] = Cd[0]; x[1] = Cd[1]; x[2] = Cd[2];
-        x[3] = F[0]; x[4] = F[1]; x[5] = F[2]; x[6] = F[3];
-        sh16(q2.y, q2.z, q2.w, x + 7);
-    }
-    float a1[WIDTH];  // pre-activation of hidden layer 1
+    for (int a = 0; a < K::TO; ++a)
 #pragma unroll
-    for (int o = 0; o < WIDTH; ++o) {
-        float acc = 0.0f;
+        for (int b = 0; b < K::TI; ++b) dmid[a][b] = 0.0f;
 #pragma unroll
-        for (int i = 0; i < 23; ++i) acc = fmaf(ws[o * kMlpIn + i], x[i], acc);
-        a1[o] = acc;
-    }
-    const float* wl = ws + n_w0 + n_mid;
-    float a2[LAYERS == 3 ? WIDTH : 1];
-    float out[3] = {0.0f, 0.0f, 0.0f};
-    if constexpr (LAYERS == 3) {
-        const float* wm = ws + n_w0;
+    for (int a = 0; a < K::T0; ++a) d0[a][0] = d0[a][1] = d0[a][2] = 0.0f;
+    const int64_t n_tiles = (p.n + K::kRays - 1) / K::kRays;
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        __syncthreads();  // weights loaded; the previous tile's readers are done
+        const int64_t ray = tile * K::kRays + t;
+        const bool active = ray < p.n;
+        // ---- forward again (inactive rays carry zeros: they add nothing to dW)
+        float x[23];
+        float A = 0.0f, depth = 0.0f;
+        float Cd[3] = {0.0f, 0.0f, 0.0f}, F[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int i = 0; i < 23; ++i) x[i] = 0.0f;
+        if (active) {
+            const float4* s4 = reinterpret_cast<const float4*>(p.state + ray * NGPRT_STATE_FLOATS);
+            const float4 q0 = s4[0], q1 = s4[1], q2 = s4[2];
+            Cd[0] = q0.x; Cd[1] = q0.y; Cd[2] = q0.z;
+            F[0] = q0.w; F[1] = q1.x; F[2] = q1.y; F[3] = q1.z;
+            A = q1.w;
+            depth = q2.x;
+            x[0] = Cd[0]; x[1] = Cd[1]; x[2] = Cd[2];
+            x[3] = F[0]; x[4] = F[1]; x[5] = F[2]; x[6] = F[3];
+            sh16(q2.y, q2.z, q2.w, x + 7);
+        }
+#pragma unroll
+        for (int i = 0; i < 23; ++i) X[t * K::kXs + i] = x[i];
+        float h[WIDTH];
+#pragma unroll
+        for (int o = 0; o < WIDTH; ++o) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int i = 0; i < 23; ++i) acc = fmaf(w0[o * kMlpIn + i], x[i], acc);
+            h[o] = fmaxf(acc, 0.0f);
+            H1[t * K::kHs + o] = h[o];
+        }
+        float out[3] = {0.0f, 0.0f, 0.0f};
+        if constexpr (LAYERS == 3) {
 #pragma unroll 4
-        for (int o = 0; o < WIDTH; ++o) {
-            float acc = 0.0f;
+            for (int o = 0; o < WIDTH; ++o) {
+                float acc = 0.0f;
 #pragma unroll
-            for (int i = 0; i < WIDTH; ++i) acc = fmaf(wm[o * WIDTH + i], fmaxf(a1[i], 0.0f), acc);
-            a2[o] = acc;
+                for (int i = 0; i < WIDTH; ++i) acc = fmaf(wm[o * WIDTH + i], h[i], acc);
+                const float h2 = fmaxf(acc, 0.0f);
+                H2[t * K::kHs + o] = h2;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) out[k] = fmaf(wl[k * WIDTH + o], h2, out[k]);
+            }
+        } else {
+#pragma unroll
+            for (int o = 0; o < WIDTH; ++o)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) out[k] = fmaf(wl[k * WIDTH + o], h[o], out[k]);
         }
+        // ---- colour: rgb = A sigmoid(z) + (1 - A) bg, z = C_d + out
+        float gz[3] = {0.0f, 0.0f, 0.0f}, gA = 0.0f;
+        if (active) {
+            gA = p.d_opacity ? p.d_opacity[ray] : 0.0f;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            float acc = 0.0f;
-#pragma unroll
-            for (int i = 0; i < WIDTH; ++i) acc = fmaf(wl[k * WIDTH + i], fmaxf(a2[i], 0.0f), acc);
-            out[k] = acc;
-        }
-    } else {
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            float acc = 0.0f;
-#pragma unroll
-            for (int i = 0; i < WIDTH; ++i) acc = fmaf(wl[k * WIDTH + i], fmaxf(a1[i], 0.0f), acc);
-            out[k] = acc;
-        }
-    }
-    // ---- colour: rgb = A sigmoid(z) + (1 - A) bg, z = C_d + out
-    float gz[3], gA = 0.0f;
-    if (active) {
-        gA = p.d_opacity ? p.d_opacity[ray] : 0.0f;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const float sg = sigmoidf_(Cd[k] + out[k]);
-            const float gr = p.d_rgb[3 * ray + k];
-            gz[k] = gr * A * sg * (1.0f - sg);
-            gA += gr * (sg - p.bg[k]);
-        }
-    } else {
-        gz[0] = gz[1] = gz[2] = 0.0f;
-    }
-    // ---- last layer: dW_last[k][i] = gz[k] h_last[i]; g_h = W_last^T gz
-    float* gwl = gw + n_w0 + n_mid;
-    const int lane = threadIdx.x & 31;
-    float gh[WIDTH];
-#pragma unroll
-    for (int i = 0; i < WIDTH; ++i) {
-        float pre;
-        if constexpr (LAYERS == 3) pre = a2[i];
-        else pre = a1[i];
-        const float hi = fmaxf(pre, 0.0f);
-        float g = 0.0f;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const float s = warp_sum(gz[k] * hi);
-            if (lane == 0) atomicAdd(&gwl[k * WIDTH + i], s);
-            g = fmaf(wl[k * WIDTH + i], gz[k], g);
-        }
-        gh[i] = pre > 0.0f ? g : 0.0f;  // gradient of the pre-activation
-    }
-    if constexpr (LAYERS == 3) {
-        // middle layer: dW1[o][i] = gh[o] relu(a1[i]); g_a1 = (W1^T gh) * [a1 > 0]
-        const float* wm = ws + n_w0;
-        float* gwm = gw + n_w0;
-#pragma unroll 2
-        for (int o = 0; o < WIDTH; ++o) {
-#pragma unroll
-            for (int i = 0; i < WIDTH; ++i) {
-                const float s = warp_sum(gh[o] * fmaxf(a1[i], 0.0f));
-                if (lane == 0) atomicAdd(&gwm[o * WIDTH + i], s);
+            for (int k = 0; k < 3; ++k) {
+                const float sg = sigmoidf_(Cd[k] + out[k]);
+                const float gr = p.d_rgb[3 * ray + k];
+                gz[k] = gr * A * sg * (1.0f - sg);
+                gA += gr * (sg - p.bg[k]);
             }
         }
-        float g1[WIDTH];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) GZ[t * 4 + k] = gz[k];
+        __syncthreads();
+        // ---- dW_last[k][i] += sum_r gz_r[k] h_r[i] (thread i < WIDTH owns column i)
+        if (t < WIDTH) {
+#pragma unroll 4
+            for (int r = 0; r < K::kRays; ++r) {
+                const float hv = Hl[r * K::kHs + t];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) dl[k] = fmaf(GZ[r * 4 + k], hv, dl[k]);
+            }
+        }
+        __syncthreads();
+        // ---- gradient of the last hidden pre-activation, into the thread's own row
+        float g[WIDTH];
 #pragma unroll
         for (int i = 0; i < WIDTH; ++i) {
             float acc = 0.0f;
 #pragma unroll
-            for (int o = 0; o < WIDTH; ++o) acc = fmaf(wm[o * WIDTH + i], gh[o], acc);
-            g1[i] = a1[i] > 0.0f ? acc : 0.0f;
+            for (int k = 0; k < 3; ++k) acc = fmaf(wl[k * WIDTH + i], gz[k], acc);
+            g[i] = Hl[t * K::kHs + i] > 0.0f ? acc : 0.0f;
         }
+        if constexpr (LAYERS == 3) {
 #pragma unroll
-        for (int i = 0; i < WIDTH; ++i) gh[i] = g1[i];
-    }
-    // first layer: dW0[o][i] = gh[o] x[i] (i < 23; padding columns get zero); g_x = W0^T gh
+            for (int i = 0; i < WIDTH; ++i) H2[t * K::kHs + i] = g[i];
+            __syncthreads();
+            // dW_mid[o][i] += sum_r g2_r[o] h1_r[i] over this thread's TO x TI tile
 #pragma unroll 2
-    for (int o = 0; o < WIDTH; ++o) {
+            for (int r = 0; r < K::kRays; ++r) {
+                float go[K::TO], hi[K::TI];
 #pragma unroll
-        for (int i = 0; i < 23; ++i) {
-            const float s = warp_sum(gh[o] * x[i]);
-            if (lane == 0) atomicAdd(&gw[o * kMlpIn + i], s);
+                for (int a = 0; a < K::TO; ++a) go[a] = H2[r * K::kHs + ob * K::TO + a];
+#pragma unroll
+                for (int b = 0; b < K::TI; ++b) hi[b] = H1[r * K::kHs + ib * K::TI + b];
+#pragma unroll
+                for (int a = 0; a < K::TO; ++a)
+#pragma unroll
+                    for (int b = 0; b < K::TI; ++b) dmid[a][b] = fmaf(go[a], hi[b], dmid[a][b]);
+            }
+            __syncthreads();
+            // g1 = (W_mid^T g2) * [a1 > 0]
+            float g1[WIDTH];
+#pragma unroll
+            for (int i = 0; i < WIDTH; ++i) g1[i] = 0.0f;
+#pragma unroll 4
+            for (int o = 0; o < WIDTH; ++o)
+#pragma unroll
+                for (int i = 0; i < WIDTH; ++i) g1[i] = fmaf(wm[o * WIDTH + i], g[o], g1[i]);
+#pragma unroll
+            for (int i = 0; i < WIDTH; ++i) g[i] = H1[t * K::kHs + i] > 0.0f ? g1[i] : 0.0f;
+        }
+        // first-layer gradient into the thread's own H1 row (its readers passed a barrier)
+#pragma unroll
+        for (int i = 0; i < WIDTH; ++i) H1[t * K::kHs + i] = g[i];
+        if (active) {
+            float gx[7];
+#pragma unroll
+            for (int i = 0; i < 7; ++i) {
+                float acc = 0.0f;
+#pragma unroll
+                for (int o = 0; o < WIDTH; ++o) acc = fmaf(w0[o * kMlpIn + i], g[o], acc);
+                gx[i] = acc;
+            }
+            const float gCd[3] = {gz[0] + gx[0], gz[1] + gx[1], gz[2] + gx[2]};
+            const float gD = p.d_depth ? p.d_depth[ray] : 0.0f;
+            const float S = gCd[0] * Cd[0] + gCd[1] * Cd[1] + gCd[2] * Cd[2] + gx[3] * F[0] + gx[4] * F[1] +
+                            gx[5] * F[2] + gx[6] * F[3] + gA * A + gD * depth;
+            float4* c4 = reinterpret_cast<float4*>(p.cot + ray * kCotFloats);
+            c4[0] = make_float4(gCd[0], gCd[1], gCd[2], gx[3]);
+            c4[1] = make_float4(gx[4], gx[5], gx[6], gA);
+            c4[2] = make_float4(gD, S, 0.0f, 0.0f);
+        }
+        __syncthreads();
+        // ---- dW0[o][i] += sum_r g1_r[o] x_r[i], i < 23 (T0 outputs x 3 inputs per thread)
+#pragma unroll 2
+        for (int r = 0; r < K::kRays; ++r) {
+            float go[K::T0];
+#pragma unroll
+            for (int a = 0; a < K::T0; ++a) go[a] = H1[r * K::kHs + ob * K::T0 + a];
+            const float x0 = X[r * K::kXs + ib * 3], x1 = X[r * K::kXs + ib * 3 + 1],
+                        x2 = X[r * K::kXs + ib * 3 + 2];
+#pragma unroll
+            for (int a = 0; a < K::T0; ++a) {
+                d0[a][0] = fmaf(go[a], x0, d0[a][0]);
+                d0[a][1] = fmaf(go[a], x1, d0[a][1]);
+                d0[a][2] = fmaf(go[a], x2, d0[a][2]);
+            }
         }
     }
-    if (active) {
-        float gx[7];
+    // ---- the block's sums into g_mlp
+    if constexpr (LAYERS == 3) {
 #pragma unroll
-        for (int i = 0; i < 7; ++i) {
-            float acc = 0.0f;
+        for (int a = 0; a < K::TO; ++a)
 #pragma unroll
-            for (int o = 0; o < WIDTH; ++o) acc = fmaf(ws[o * kMlpIn + i], gh[o], acc);
-            gx[i] = acc;
-        }
-        const float gCd[3] = {gz[0] + gx[0], gz[1] + gx[1], gz[2] + gx[2]};
-        const float gD = p.d_depth ? p.d_depth[ray] : 0.0f;
-        const float S = gCd[0] * Cd[0] + gCd[1] * Cd[1] + gCd[2] * Cd[2] + gx[3] * F[0] + gx[4] * F[1] +
-                        gx[5] * F[2] + gx[6] * F[3] + gA * A + gD * depth;
-        float4* c4 = reinterpret_cast<float4*>(p.cot + ray * kCotFloats);
-        c4[0] = make_float4(gCd[0], gCd[1], gCd[2], gx[3]);
-        c4[1] = make_float4(gx[4], gx[5], gx[6], gA);
-        c4[2] = make_float4(gD, S, 0.0f, 0.0f);
+            for (int b = 0; b < K::TI; ++b)
+                atomicAdd(&p.g_mlp[K::n_w0 + (ob * K::TO + a) * WIDTH + ib * K::TI + b], dmid[a][b]);
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < n_all; i += blockDim.x) {
-        const float v = gw[i];
-        if (v != 0.0f) atomicAdd(&p.g_mlp[i], v);
+#pragma unroll
+    for (int a = 0; a < K::T0; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+            if (ib * 3 + b < 23) atomicAdd(&p.g_mlp[(ob * K::T0 + a) * kMlpIn + ib * 3 + b], d0[a][b]);
+    if (t < WIDTH) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) atomicAdd(&p.g_mlp[K::n_w0 + K::n_mid + k * WIDTH + t], dl[k]);
     }
+}
+
+template <int WIDTH, int LAYERS>
+void launch_shade_bwd(const ShadeBwdParams& s, cudaStream_t st) {
+    using K = ShadeTile<WIDTH, LAYERS>;
+    const size_t smem = (size_t)K::n_smem * sizeof(float);
+    // the opt-in shared-memory size (over 48 KB) is a per-device function attribute
+    cudaFuncSetAttribute(shade_backward_kernel<WIDTH, LAYERS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int64_t tiles = (s.n + K::kRays - 1) / K::kRays;
+    const unsigned blocks = (unsigned)(tiles < 152 * 2 ? tiles : 152 * 2);
+    shade_backward_kernel<WIDTH, LAYERS><<<blocks, 128, smem, st>>>(s);
 }
 
 struct MarchBwdParams {
@@ -413,16 +482,15 @@ extern "C" int32_t ngprt_render_backward(const ngprt_scene* scene, const ngprt_o
     s.n = n_rays;
     s.cot = cot;
     s.g_mlp = g_mlp;
-    const unsigned sb = (unsigned)((n_rays + 127) / 128);
     const int W = scene->mlp_width, Ly = scene->mlp_layers;
     if (Ly == 2) {
-        if (W == 16) shade_backward_kernel<16, 2><<<sb, 128, 0, st>>>(s);
-        else if (W == 32) shade_backward_kernel<32, 2><<<sb, 128, 0, st>>>(s);
-        else shade_backward_kernel<64, 2><<<sb, 128, 0, st>>>(s);
+        if (W == 16) launch_shade_bwd<16, 2>(s, st);
+        else if (W == 32) launch_shade_bwd<32, 2>(s, st);
+        else launch_shade_bwd<64, 2>(s, st);
     } else {
-        if (W == 16) shade_backward_kernel<16, 3><<<sb, 128, 0, st>>>(s);
-        else if (W == 32) shade_backward_kernel<32, 3><<<sb, 128, 0, st>>>(s);
-        else shade_backward_kernel<64, 3><<<sb, 128, 0, st>>>(s);
+        if (W == 16) launch_shade_bwd<16, 3>(s, st);
+        else if (W == 32) launch_shade_bwd<32, 3>(s, st);
+        else launch_shade_bwd<64, 3>(s, st);
     }
     p.m.opts = *opts;
     p.m.t_interval = nullptr;
