@@ -67,6 +67,23 @@ def initial_scene(cfg: S.SceneConfig, fc: FitConfig, device="cuda"):
     return tables, coarse, mlp_w
 
 
+def tile_order(pixel_ids: torch.Tensor, W: int, H: int, tile: int = 32):
+    """(perm, inv): the permutation that groups a minibatch's pixel ids by view and
+    tile x tile image tile (row-major inside a tile), and its inverse.  The render
+    runs fastest on rays in this order (neighbouring lanes sample neighbouring
+    points); the reverse pass runs fastest in the drawn random order (neighbouring
+    lanes then rarely add gradients to the same entries), so the state moves back
+    through inv between the two."""
+    p = pixel_ids.long()
+    v, rem = p // (W * H), p % (W * H)
+    row, col = rem // W, rem % W
+    key = (v << 40) | ((row // tile) << 28) | ((col // tile) << 16) | ((row % tile) << 8) | (col % tile)
+    perm = torch.argsort(key)
+    inv = torch.empty_like(perm)
+    inv[perm] = torch.arange(len(perm), device=perm.device)
+    return perm, inv
+
+
 def _lr_factor(step: int, fc: FitConfig) -> float:
     f = min(1.0, step / max(1, fc.warmup))
     s0 = fc.decay_from * fc.steps
@@ -108,19 +125,21 @@ def fit(scene: ng.DeviceScene, occ: ng.DeviceOcc, opts, cams: np.ndarray, W: int
     for step in range(1, fc.steps + 1):
         idx = torch.randint(0, n_pix, (B,), device=dev, generator=gen)
         pix = idx.to(torch.int32)
-        tg = targets[idx].contiguous()
+        perm, inv = tile_order(pix, W, H)
+        pix_f = pix[perm].contiguous()
+        tg = targets[idx[perm]].contiguous()
         logging = bool(log_every) and (step % log_every == 0 or step == fc.steps)
         if logging:
             loss.zero_()
         o_step = replace(opts, step_gamma=gamma) if fc.autotune else opts
-        rend.render(o_step, cams=cams, W=W, H=H, pixel_ids=pix, state=True, out=out)
+        rend.render(o_step, cams=cams, W=W, H=H, pixel_ids=pix_f, state=True, out=out)
         if fc.huber_delta > 0:
             ng.ngprt_huber_loss(out["rgb"], tg, 3 * B, fc.huber_delta, 1.0 / (3 * B), loss if logging else None,
                                 d_rgb, stream=stream)
         else:
             ng.ngprt_l2_loss(out["rgb"], tg, 3 * B, 1.0 / (3 * B), loss if logging else None, d_rgb, stream=stream)
-        rend.backward(o_step, out["state"], d_rgb, None, None, grads[0], grads[1], grads[2], cams=cams, W=W, H=H,
-                      pixel_ids=pix)
+        rend.backward(o_step, out["state"][inv].contiguous(), d_rgb[inv].contiguous(), None, None, grads[0],
+                      grads[1], grads[2], cams=cams, W=W, H=H, pixel_ids=pix)
         if fc.eta > 0:
             ro = ng.render_opts(o_step)
             ng.ngprt_distortion_loss(scene.struct, occ.struct, cam_arr, n_cams, pix, None, None, B, ro, fc.eta / B,

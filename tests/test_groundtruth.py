@@ -120,3 +120,16 @@ def test_bounded_field_is_clipped_to_the_box():
     _, a = GT.render_rays(b, o, d, shell=False, n_steps=32, bounded=True)
     tau = 20.0 * 0.1 * math.sqrt(2.0 * math.pi) / 2.0
     assert abs(float(a[0]) - (1.0 - math.exp(-tau))) < 1e-9
+
+
+def test_tile_order_is_a_grouping_permutation():
+    from paper_2407_10482_gb300 import fit as F
+    W, H = 100, 70
+    pix = torch.as_tensor(S.random_pixels(5000, 3, W, H, 1))
+    perm, inv = F.tile_order(pix, W, H, tile=32)
+    assert torch.equal(torch.sort(perm).values, torch.arange(5000))
+    assert torch.equal(perm[inv], torch.arange(5000))
+    q = pix[perm].long()
+    v, rem = q // (W * H), q % (W * H)
+    key = v * 1000 + (rem // W // 32) * 10 + (rem % W) // 32
+    assert torch.all(key[1:] >= key[:-1])          # views, then tile rows, then tile columns
