@@ -31,7 +31,8 @@ typedef enum {
     NGPRT_ERR_INVALID_ARG = -1, /* bad size, null pointer, misaligned pointer, bad enum */
     NGPRT_ERR_UNSUPPORTED = -2, /* valid request this build does not implement (e.g. an L without a kernel) */
     NGPRT_ERR_CUDA = -3,        /* a CUDA launch or query failed */
-    NGPRT_ERR_WORKSPACE = -4    /* workspace missing or smaller than the query asked for */
+    NGPRT_ERR_WORKSPACE = -4,   /* workspace missing or smaller than the query asked for */
+    NGPRT_ERR_TIMEOUT = -5      /* a bounded device-side wait expired (reported by ngprt_sync_status) */
 } ngprt_status;
 
 typedef enum { NGPRT_F32 = 0, NGPRT_F16 = 1, NGPRT_BF16 = 2 } ngprt_dtype;
@@ -301,10 +302,13 @@ int32_t ngprt_render_backward(const ngprt_scene* scene, const ngprt_occ* occ, co
 int32_t ngprt_proposal_param_count(void);
 
 /* Interval per ray, t_interval_out [n][2] = (t_near - margin_near, t_far + margin_far)
+ * from prop_w in prop_dtype (F32, or F16 copies of the FP32 master widened to FP32 in
+ * shared memory; the per-ray arithmetic is FP32)
  * (margin_far = +inf: no far clip, early termination ends the ray); a ray with
  * A^ < a_min gets an empty interval (+inf, -inf) (nothing is marched), a ray with
  * t_far <= t_near gets (-inf, +inf) (the whole ray).  a_hat_out [n] (NULL allowed). */
-int32_t ngprt_propose(const float* prop_w, const ngprt_camera* cams, int32_t n_cams, const int32_t* pixel_ids,
+int32_t ngprt_propose(const void* prop_w, int32_t prop_dtype, const ngprt_camera* cams, int32_t n_cams,
+                      const int32_t* pixel_ids,
                       const float* rays_o, const float* rays_d, int64_t n_rays, float in_scale, float t_scale,
                       float margin_near, float margin_far, float a_min, float* t_interval_out, float* a_hat_out,
                       void* stream);
@@ -441,6 +445,24 @@ int32_t ngprt_grid_indices(const ngprt_scene* scene, const float* u, int64_t n, 
  * device float (written only in a case that practically cannot occur). */
 int32_t ngprt_gather_bench(const void* table, int32_t dtype, int64_t n_rows, int64_t n_threads, int32_t per_thread,
                            uint32_t seed, int32_t flags, float* sink, void* stream);
+
+/* Waits for `stream` and reports what went wrong on the device since the last
+ * report: NGPRT_ERR_CUDA (with the CUDA message) if the stream holds a failed
+ * launch, NGPRT_ERR_TIMEOUT if a tensor-core MLP kernel gave up waiting for its MMAs
+ * (its rays were left unshaded; the flag is cleared by this report), else NGPRT_OK. */
+int32_t ngprt_sync_status(void* stream);
+
+/* Test hook of the timeout path (no counterpart in the paper): one block waits, with
+ * at most `limit` polls (1..2^20), on an mbarrier nothing arrives at, the same
+ * bounded wait the tensor-core MLP uses; it gives up, sets the flag and exits, so the
+ * next ngprt_sync_status returns NGPRT_ERR_TIMEOUT.  Nothing faults or stays
+ * running. */
+int32_t ngprt_test_bounded_wait(int32_t limit, void* stream);
+
+/* Writes to the device int *count the number of NaN or infinite values among x[0..n)
+ * (a check after fault injection: a NaN in the tables makes the affected rays' colour
+ * NaN; the march still ends at its caps). */
+int32_t ngprt_count_nonfinite(const float* x, int64_t n, int32_t* count, void* stream);
 
 /* 1 if a tensor-core MLP kernel (mlp_dtype F16) ever gave up waiting for its MMAs
  * (it then frees its tensor memory and leaves its rays unwritten), 0 if not, -1 if

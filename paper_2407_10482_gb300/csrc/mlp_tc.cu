@@ -66,8 +66,8 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar) {
 }
 
 // Bounded wait for the mbarrier phase with the given parity; false on expiry.
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-    for (int i = 0; i < (1 << 24); ++i) {
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, int limit = 1 << 24) {
+    for (int i = 0; i < limit; ++i) {
         uint32_t ok;
         asm volatile(
             "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -257,6 +257,22 @@ void launch_tc(const MlpTcParams& p, cudaStream_t st) {
     mlp_tc_kernel<WIDTH, LAYERS><<<(unsigned)grid, 128, shm, st>>>(p);
 }
 
+// A bounded wait that nothing completes: the MLP kernel's mbarrier wait with a
+// caller-chosen poll limit on a barrier no thread arrives at.  When it gives up it
+// sets the tensor-core error flag, which ngprt_sync_status then reports; the
+// timeout path is exercised without the tensor cores and nothing is left running.
+__global__ void wait_probe_kernel(int limit) {
+    __shared__ __align__(8) uint64_t bar;
+    const uint32_t mbar = smem_u32(&bar);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(1) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const bool ok = mbar_wait(mbar, 0, limit);
+    if (!ok && threadIdx.x == 0) atomicExch(&g_tc_error, 1);
+}
+
 }  // namespace
 
 bool mlp_tc_supports(int width, int layers) {
@@ -292,4 +308,27 @@ extern "C" int32_t ngprt_tensor_core_error(void) {
     int v = 0;
     if (cudaMemcpyFromSymbol(&v, ngprt::g_tc_error, sizeof v) != cudaSuccess) return -1;
     return v;
+}
+
+extern "C" int32_t ngprt_sync_status(void* stream) {
+    const cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) {
+        ngprt::set_error("ngprt_sync_status: %s", cudaGetErrorString(e));
+        return NGPRT_ERR_CUDA;
+    }
+    int v = 0;
+    if (cudaMemcpyFromSymbol(&v, ngprt::g_tc_error, sizeof v) != cudaSuccess) return ngprt::cuda_status("ngprt_sync_status");
+    if (v) {
+        const int zero = 0;
+        cudaMemcpyToSymbol(ngprt::g_tc_error, &zero, sizeof zero);  // reported once
+        ngprt::set_error("ngprt_sync_status: a tensor-core MLP gave up waiting for its MMAs; its rays were not shaded");
+        return NGPRT_ERR_TIMEOUT;
+    }
+    return NGPRT_OK;
+}
+
+extern "C" int32_t ngprt_test_bounded_wait(int32_t limit, void* stream) {
+    NGPRT_REQUIRE(limit >= 1 && limit <= (1 << 20), "ngprt_test_bounded_wait: limit=%d not in [1, 2^20]", limit);
+    ngprt::wait_probe_kernel<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(limit);
+    return ngprt::cuda_status("ngprt_test_bounded_wait");
 }

@@ -18,6 +18,7 @@ constexpr int kPParams = kPW * kPIn + kPW + kPW * kPW + kPW + 3 * kPW + 3;
 struct PropParams {
     MarchParams m;  // ray source only
     const float* w;
+    const __half* w16;  // propose with FP16 weights (widened to FP32 in shared memory)
     float in_scale, t_scale, margin_near, margin_far, a_min;
     float* interval;
     float* a_hat;
@@ -75,7 +76,7 @@ __device__ __forceinline__ void prop_mlp(const float* w, const float e[kPIn], fl
 
 __global__ void __launch_bounds__(128) propose_kernel(const __grid_constant__ PropParams p) {
     __shared__ float ws[kPParams];
-    for (int i = threadIdx.x; i < kPParams; i += blockDim.x) ws[i] = p.w[i];
+    for (int i = threadIdx.x; i < kPParams; i += blockDim.x) ws[i] = p.w16 ? __half2float(p.w16[i]) : p.w[i];
     __syncthreads();
     int64_t ray;
     float e[kPIn];
@@ -207,7 +208,7 @@ using namespace ngprt;
 
 extern "C" int32_t ngprt_proposal_param_count(void) { return kPParams; }
 
-extern "C" int32_t ngprt_propose(const float* prop_w, const ngprt_camera* cams, int32_t n_cams,
+extern "C" int32_t ngprt_propose(const void* prop_w, int32_t prop_dtype, const ngprt_camera* cams, int32_t n_cams,
                                  const int32_t* pixel_ids, const float* rays_o, const float* rays_d, int64_t n_rays,
                                  float in_scale, float t_scale, float margin_near, float margin_far, float a_min,
                                  float* t_interval_out, float* a_hat_out, void* stream) {
@@ -215,6 +216,8 @@ extern "C" int32_t ngprt_propose(const float* prop_w, const ngprt_camera* cams, 
     PropParams p;
     memset(&p, 0, sizeof p);
     NGPRT_REQUIRE(prop_w != nullptr, "%s: prop_w is NULL", fn);
+    NGPRT_REQUIRE(prop_dtype == NGPRT_F32 || prop_dtype == NGPRT_F16, "%s: prop_dtype=%d (F32 or F16)", fn,
+                  prop_dtype);
     NGPRT_REQUIRE(n_rays >= 0 && in_scale > 0.0f && t_scale > 0.0f && margin_near >= 0.0f && margin_far >= 0.0f,
                   "%s: bad scalar argument", fn);
     dim3 grid;
@@ -222,7 +225,8 @@ extern "C" int32_t ngprt_propose(const float* prop_w, const ngprt_camera* cams, 
     if ((rc = setup_rays(p.m, cams, n_cams, pixel_ids, rays_o, rays_d, n_rays, grid, fn)) != NGPRT_OK) return rc;
     if (n_rays == 0) return NGPRT_OK;
     NGPRT_REQUIRE(t_interval_out != nullptr, "%s: t_interval_out is NULL", fn);
-    p.w = prop_w;
+    p.w = prop_dtype == NGPRT_F32 ? static_cast<const float*>(prop_w) : nullptr;
+    p.w16 = prop_dtype == NGPRT_F16 ? static_cast<const __half*>(prop_w) : nullptr;
     p.in_scale = in_scale;
     p.t_scale = t_scale;
     p.margin_near = margin_near;

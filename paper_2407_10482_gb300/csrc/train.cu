@@ -63,6 +63,16 @@ __global__ void mean_samples_kernel(const int2* __restrict__ stats, int64_t n, f
     if ((threadIdx.x & 31) == 0 && acc) atomicAdd(out, (float)((double)acc / (double)n));
 }
 
+// Count of the values that are NaN or infinite (the guard after fault injection).
+__global__ void nonfinite_kernel(const float* __restrict__ x, int64_t n, int32_t* __restrict__ count) {
+    int c = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        c += isfinite(x[i]) ? 0 : 1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
+}
+
 __global__ void adam_kernel(float* __restrict__ p, float* __restrict__ g, float* __restrict__ m,
                             float* __restrict__ v, int64_t n, float lr, float b1, float b2, float eps, float c1,
                             float c2, int zero_grad) {
@@ -154,4 +164,13 @@ extern "C" float ngprt_step_autotune(float gamma, float n_mean, float n_min, flo
     // per ray on average, else shrink it by (1 - kappa) down to gamma_min
     if (n_mean >= n_min) return fminf(1.0f, (1.0f + kappa) * gamma);
     return fmaxf(gamma_min, (1.0f - kappa) * gamma);
+}
+
+extern "C" int32_t ngprt_count_nonfinite(const float* x, int64_t n, int32_t* count, void* stream) {
+    const char* fn = "ngprt_count_nonfinite";
+    NGPRT_REQUIRE(n >= 0 && count != nullptr && (n == 0 || x != nullptr), "%s: bad arguments", fn);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(count, 0, sizeof(int32_t), st) != cudaSuccess) return cuda_status(fn);
+    if (n > 0) nonfinite_kernel<<<grid_for(n, 256), 256, 0, st>>>(x, n, count);
+    return cuda_status(fn);
 }

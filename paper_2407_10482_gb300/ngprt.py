@@ -22,7 +22,7 @@ STATE_FLOATS = 12
 F32, F16, BF16 = 0, 1, 2
 _TORCH_DT = {F32: torch.float32, F16: torch.float16, BF16: torch.bfloat16}
 
-OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_CUDA, ERR_WORKSPACE = 0, -1, -2, -3, -4
+OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_CUDA, ERR_WORKSPACE, ERR_TIMEOUT = 0, -1, -2, -3, -4, -5
 
 
 class NgprtError(RuntimeError):
@@ -87,8 +87,8 @@ _SIGS = {
     "ngprt_adam_step": (C.c_int32, [_P, _P, _P, _P, C.c_int64, C.c_float, C.c_float, C.c_float, C.c_float,
                                     C.c_int32, C.c_int32, _P]),
     "ngprt_proposal_param_count": (C.c_int32, []),
-    "ngprt_propose": (C.c_int32, [_P, _P, C.c_int32, _P, _P, _P, C.c_int64, C.c_float, C.c_float, C.c_float,
-                                  C.c_float, C.c_float, _P, _P, _P]),
+    "ngprt_propose": (C.c_int32, [_P, C.c_int32, _P, C.c_int32, _P, _P, _P, C.c_int64, C.c_float, C.c_float,
+                                  C.c_float, C.c_float, C.c_float, _P, _P, _P]),
     "ngprt_propose_backward": (C.c_int32, [_P, _P, C.c_int32, _P, _P, _P, C.c_int64, C.c_float, C.c_float, _P, _P,
                                            _P, _P]),
     "ngprt_proposal_targets": (C.c_int32, [_P, _P, _P, C.c_int32, _P, _P, _P, C.c_int64, _P, _P, _P, _P]),
@@ -98,6 +98,9 @@ _SIGS = {
     "ngprt_render_noalloc": (C.c_int32, [_P, _P, _P, C.c_int32, _P, _P, _P, C.c_int64, _P, _P, _P, _P, _P, _P,
                                          _P]),
     "ngprt_tensor_core_error": (C.c_int32, []),
+    "ngprt_sync_status": (C.c_int32, [_P]),
+    "ngprt_test_bounded_wait": (C.c_int32, [C.c_int32, _P]),
+    "ngprt_count_nonfinite": (C.c_int32, [_P, C.c_int64, _P, _P]),
     "ngprt_gather_bench": (C.c_int32, [_P, C.c_int32, C.c_int64, C.c_int64, C.c_int32, C.c_uint32, C.c_int32, _P,
                                        _P]),
     "ngprt_last_error": (C.c_char_p, []),
@@ -214,6 +217,19 @@ def ngprt_step_autotune(gamma, n_mean, n_min=3.0, kappa=1e-3, gamma_min=0.2217) 
     return float(lib().ngprt_step_autotune(gamma, n_mean, n_min, kappa, gamma_min))
 
 
+def ngprt_sync_status(stream=None) -> None:
+    """Raises NgprtError (code ERR_TIMEOUT or ERR_CUDA) for a device-side failure."""
+    _check("ngprt_sync_status", lib().ngprt_sync_status(_stream(stream)))
+
+
+def ngprt_test_bounded_wait(limit, stream=None) -> None:
+    _check("ngprt_test_bounded_wait", lib().ngprt_test_bounded_wait(limit, _stream(stream)))
+
+
+def ngprt_count_nonfinite(x, n, count, stream=None) -> None:
+    _check("ngprt_count_nonfinite", lib().ngprt_count_nonfinite(_ptr(x), n, _ptr(count), _stream(stream)))
+
+
 def ngprt_dilate_workspace_bytes(R: int) -> int:
     return int(lib().ngprt_dilate_workspace_bytes(R))
 
@@ -285,8 +301,10 @@ def ngprt_proposal_param_count() -> int:
 
 def ngprt_propose(prop_w, cams, n_cams, pixel_ids, rays_o, rays_d, n_rays, in_scale, t_scale, margin_near,
                   margin_far, a_min, t_interval_out, a_hat_out=None, stream=None) -> None:
+    """prop_w: float32 or float16 device tensor (the dtype is passed on)."""
+    dt = F16 if prop_w.dtype == torch.float16 else F32
     _check("ngprt_propose", lib().ngprt_propose(
-        _ptr(prop_w), cams, n_cams, _ptr(pixel_ids), _ptr(rays_o), _ptr(rays_d), n_rays, in_scale, t_scale,
+        _ptr(prop_w), dt, cams, n_cams, _ptr(pixel_ids), _ptr(rays_o), _ptr(rays_d), n_rays, in_scale, t_scale,
         margin_near, margin_far, a_min, _ptr(t_interval_out), _ptr(a_hat_out), _stream(stream)))
 
 

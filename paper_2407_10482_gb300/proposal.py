@@ -88,14 +88,16 @@ def train(cams: np.ndarray, W: int, H: int, pixel_ids: torch.Tensor, targets: to
 
 
 class FastRenderer:
-    """FP16 tables + tensor-core FP16 MLP + learned proposal with fallback.
+    """FP16 tables + tensor-core FP16 MLP + learned proposal (FP16 weights) with
+    fallback.
 
     ``render`` writes rgb/depth/opacity for one batch of camera rays; all buffers
     are allocated once per ray count."""
 
     def __init__(self, scene: ng.DeviceScene, occ: ng.DeviceOcc, prop_w: torch.Tensor,
                  cfg: ProposalConfig = ProposalConfig(), device="cuda"):
-        self.scene, self.occ, self.w, self.cfg, self.device = scene, occ, prop_w, cfg, device
+        self.scene, self.occ, self.cfg, self.device = scene, occ, cfg, device
+        self.w = prop_w.to(torch.float16).contiguous()  # FP16 copy of the trained FP32 master
         self._n = -1
 
     def _buffers(self, n: int):

@@ -23,12 +23,17 @@ def _w(seed, std=0.4):
     return np.random.default_rng(seed).normal(0, std, O.prop_param_count(32)).astype(np.float32)
 
 
-def test_propose_forward(ng):
+@pytest.mark.parametrize("half", [False, True])
+def test_propose_forward(ng, half):
+    """FP32 weights, and FP16 copies (the oracle takes the same rounded values)."""
     w = _w(0)
+    if half:
+        w = w.astype(np.float16).astype(np.float32)
+    wt = torch.as_tensor(w).cuda()
     o, d = S.random_rays(5000, 1, False)
     iv = torch.empty(5000, 2, device="cuda")
     ah = torch.empty(5000, device="cuda")
-    ng.ngprt_propose(torch.as_tensor(w).cuda(), None, 0, None, torch.as_tensor(o).cuda(), torch.as_tensor(d).cuda(),
+    ng.ngprt_propose(wt.half() if half else wt, None, 0, None, torch.as_tensor(o).cuda(), torch.as_tensor(d).cuda(),
                      5000, IN_SCALE, T_SCALE, 0.0, 0.0, 0.0, iv, ah)
     torch.cuda.synchronize()
     ref = O.prop_forward(w, o, d, IN_SCALE, T_SCALE)
