@@ -385,3 +385,21 @@ def test_coarse_distance_grid_parity(ng, bounded):
         r = rend.render(opts, cams=cams, W=cfg.W, H=cfg.H, stats=True)
         torch.cuda.synchronize()
         _compare(r, orc.render(opts, cams=cams))
+
+
+def test_maximum_view_batch(ng):
+    """NGPRT_MAX_CAMERAS (64) views in one call: each view's sampled pixels match the
+    oracle; 65 views are refused before any launch."""
+    cfg = S.small_config(blob_std=(0.05, 0.15), W=24, H=16)
+    sc, rend, orc = _pair(ng, cfg)
+    opts = S.default_options(cfg)
+    cams = S.orbit_cameras(cfg, 64, azimuth0=3.0, step_deg=5.625)
+    r = rend.render(opts, cams=cams, W=cfg.W, H=cfg.H, stats=True)
+    torch.cuda.synchronize()
+    n = cfg.W * cfg.H
+    pix = np.concatenate([v * n + np.random.default_rng(v).choice(n, 12, replace=False) for v in range(64)])
+    pix = pix.astype(np.int32)
+    sub = {k: v[torch.as_tensor(pix, dtype=torch.long).cuda()] for k, v in r.items()}
+    _compare(sub, orc.render(opts, cams=cams, pix=pix))
+    with pytest.raises(ng.NgprtError, match="n_cams"):
+        rend.render(opts, cams=S.orbit_cameras(cfg, 65), W=cfg.W, H=cfg.H)
