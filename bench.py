@@ -267,33 +267,15 @@ def other_forms(args, cfg, scene, ds, docc, cams, opts, dev, stream, flush, plai
     tgt = rend32.render(opts, cams=cams8, W=cfg.W, H=cfg.H)["rgb"]
     student_t = ds.tables + 0.02 * torch.randn_like(ds.tables)
     dss = ng.DeviceScene(cfg, student_t.cpu().numpy(), scene.coarse, scene.mlp_w, device=dev)
-    rs = ng.Renderer(dss, docc, device=dev)
-    from paper_2407_10482_gb300 import fit as F
+    from paper_2407_10482_gb300 import train_step as TS
     pix8 = torch.as_tensor(S.random_pixels(1 << 18, 8, cfg.W, cfg.H, 3)).to(dev)
     tg = tgt[pix8.long()].contiguous()
-    params = [dss.tables, dss.coarse, dss.mlp_w]
-    grads = [torch.zeros_like(t) for t in params]
-    moms = [(torch.zeros_like(t), torch.zeros_like(t)) for t in params]
-    loss = torch.zeros(1, device=dev)
-    d_rgb = torch.empty(1 << 18, 3, device=dev)
-    step_no = [0]
-
-    def train_step():
-        # render in pixel-tile order, reverse pass in the drawn order (fit.tile_order)
-        perm, inv = F.tile_order(pix8, cfg.W, cfg.H)
-        o = rs.render(opts, cams=cams8, W=cfg.W, H=cfg.H, pixel_ids=pix8[perm].contiguous(), state=True)
-        ng.ngprt_l2_loss(o["rgb"], tg[perm].contiguous(), 3 * (1 << 18), 1.0 / (3 * (1 << 18)), loss, d_rgb,
-                         stream=stream)
-        rs.backward(opts, o["state"][inv].contiguous(), d_rgb[inv].contiguous(), None, None, grads[0], grads[1],
-                    grads[2], cams=cams8, W=cfg.W, H=cfg.H, pixel_ids=pix8)
-        step_no[0] += 1
-        for t, g, (m, v) in zip(params, grads, moms):
-            ng.ngprt_adam_step(t, g, m, v, 1e-3, 0.9, 0.99, 1e-8, step_no[0], True, stream=stream)
+    train_step, _ = TS.make_step(cfg, dss, docc, cams8, tg, pix8, stream=stream)
     ms_train = _timed(train_step, stream, flush, 5, 3)
     res["train_step"] = {"rays": 1 << 18, "ms": ms_train, "rays_per_s": (1 << 18) / ms_train * 1e3,
                          "parts": "render (with state, rays in pixel-tile order) + L2 loss + reverse pass (rays in drawn "
                                   "order) + Adam on 50.5M table, grid and MLP parameters"}
-    del dss, rs, params, grads, moms
+    del dss
     # gather ceiling: random whole-entry gathers at three footprints, FP32 with and
     # without L1 allocation (the march reads its large levels without it)
     sink = torch.zeros(1, device=dev)

@@ -394,8 +394,15 @@ struct BackwardSampler {
     }
 };
 
+// Resident blocks the reverse march's register allocation must allow.  1 lets it
+// take 255 registers (about 7 warps per SM) and was the fastest measured: 4..8
+// blocks (fewer registers, more warps) made a 2^18-ray training step 5-10% slower.
+#ifndef NGPRT_BWD_MIN_BLOCKS
+#define NGPRT_BWD_MIN_BLOCKS 1
+#endif
+
 template <int L>
-__global__ void __launch_bounds__(128) march_backward_kernel(const __grid_constant__ MarchBwdParams p) {
+__global__ void __launch_bounds__(128, NGPRT_BWD_MIN_BLOCKS) march_backward_kernel(const __grid_constant__ MarchBwdParams p) {
     extern __shared__ float gate_smem[];
     int64_t ray;
     float o[3], d[3], t, t_out;
