@@ -385,6 +385,10 @@ def main():
     ap.add_argument("--engine", default="fused", choices=["wavefront", "fused"])
     ap.add_argument("--plain-only", action="store_true", help="time only the plain FP32 frame")
     ap.add_argument("--no-paper-shape", action="store_true", help="skip the paper-shaped L = 2, 3, 4 frames")
+    ap.add_argument("--workload", default="hd", choices=["hd", "paper2", "paper3", "paper4"],
+                    help="the timed frame: the hd scene, or the paper-shaped scene with L = 2, 3 or 4 "
+                         "(those run the plain frame only, without the CPU baseline)")
+    ap.add_argument("--coarse-res", type=int, default=512, help="coarse-grid resolution of the paper-shaped scenes")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -402,13 +406,18 @@ def main():
     dev = torch.device("cuda", local)
     ng.lib()
 
-    cfg = S.hd_config()
-    scene = S.make_scene(cfg)
+    if args.workload == "hd":
+        cfg = S.hd_config()
+        scene = S.make_scene(cfg)
+    else:
+        # the paper-shaped scenes are drawn on the GPU (their grids are too large for numpy)
+        cfg = S.paper_config(int(args.workload[-1]), R_C=args.coarse_res)
+        scene = S.make_scene_torch(cfg, device=dev)
     cams = S.orbit_cameras(cfg, 1, azimuth0=rank_views(rank)[0])
     opts = S.default_options(cfg)
     ds = ng.DeviceScene(cfg, scene.tables, scene.coarse, scene.mlp_w, table_dtype=args.table_dtype, device=dev,
                         mlp_dtype=args.mlp_dtype)
-    docc = ng.DeviceOcc(scene.occ, cfg.R_O, cfg.n_occ_levels, device=dev)
+    docc = ng.DeviceOcc(scene.occ, cfg.R_O, cfg.n_occ_levels, device=dev, dist_level=cfg.dist_level)
     rend = ng.Renderer(ds, docc, device=dev)
     n = cfg.W * cfg.H
     cam_arr, n_cams = ng.cameras_struct(cams, cfg.W, cfg.H)
@@ -515,14 +524,19 @@ def main():
 
     # ---------------------------------------------------------------- other forms
     extra = {}
-    if not args.plain_only:
+    hd = args.workload == "hd"
+    if not args.plain_only and hd:
         extra = other_forms(args, cfg, scene, ds, docc, cams, opts, dev, stream, flush, rgb)
+    workload = WORKLOAD if hd else (f"paper-shaped 1920x1080 scene, L={cfg.L} (N_l = 1024*2^l), T=2^22, "
+                                    f"{cfg.R_C}^3 dense coarse grid, 512^3 occupancy (5 levels), G at 256^3, "
+                                    f"MLP 23-64-64-3")
+    measured_here = hd and args.table_dtype == 0 and args.engine == "fused"
 
     peaks = _peaks()
     L = cfg.L
     entry_b = 32 if args.table_dtype == 0 else 16
     ch_b = 4 if args.table_dtype == 0 else 2
-    bytes_per_sample = L * 8 * entry_b + 8 * (8 + 2 * L) * ch_b
+    bytes_per_sample = L * 8 * entry_b + 8 * S.coarse_channels(cfg) * ch_b
     alg_bytes = samples * bytes_per_sample + marching * 2 + n * ng.STATE_FLOATS * 4
     t_march_avg = statistics.mean(t_march)
     achieved = alg_bytes / (t_march_avg * 1e-3) / 1e9
@@ -531,7 +545,7 @@ def main():
         "metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {0: "f32", 1: "f16", 2: "bf16"}[args.table_dtype], "data": "synthetic",
-        "config": {"workload": WORKLOAD, "views_per_step": 1, "rays_per_step": n, "l2_flush": True,
+        "config": {"workload": workload, "views_per_step": 1, "rays_per_step": n, "l2_flush": True,
                    "parallelism": f"replicas x{world}", "table_dtype": args.table_dtype},
         "grays_per_s": fps * n / 1e9,
         "kernels_ms": {"march": t_march_avg, "shade_mlp": statistics.mean(t_shade),
@@ -539,8 +553,10 @@ def main():
         "march_stats": march_stats,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"],
-                     "traffic": MARCH_DRAM_BYTES if (args.table_dtype == 0 and args.engine == "fused") else None,
-                     "traffic_unit": "bytes per launch (ncu dram__bytes_read + write)", "kernel": "march_kernel<16,F32> (fused march: occupancy, coarse fetch, 16-level gathers, attention, compositing)",
+                     "traffic": MARCH_DRAM_BYTES if measured_here else None,
+                     "traffic_unit": "bytes per launch (ncu dram__bytes_read + write)",
+                     "kernel": f"march_kernel<{L},{['F32', 'F16', 'BF16'][args.table_dtype]}> (fused march: occupancy, "
+                               f"coarse fetch, {L}-level gathers, attention, compositing)",
                      "peak_source": peaks["source"],
                      "bytes_per_sample": bytes_per_sample,
                      "note": "algorithmic gather bytes (L*8 entries + 8 coarse vertices per sample, 2 B per "
@@ -548,7 +564,7 @@ def main():
                              "served by L1/L2 (DRAM traffic is the 'traffic' figure), and lanes of a pixel tile "
                              "share the coarse levels' entries, so they also exceed the per-lane random-gather "
                              "microbenchmark; the bound is the L1 load pipe (l1_lsu_pct_ncu)",
-                     "l1_lsu_pct_ncu": L1_LSU_PCT if (args.table_dtype == 0 and args.engine == "fused") else None},
+                     "l1_lsu_pct_ncu": L1_LSU_PCT if measured_here else None},
         "e2e": {"value": e2e_fps, "unit": "frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": (2 if args.engine == "fused" else 2 * 8 + 3) * args.steps,
         "clocks": clk,
@@ -565,7 +581,7 @@ def main():
             ceil = max(gc["l1_resident_f16_GBps"], gc["l2_resident_f16_GBps"])
         line["roofline"]["gather_ceiling_GBps"] = ceil
         line["roofline"]["gather_frac"] = achieved / ceil
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and hd:
         line["cpu_baseline"] = cpu_baseline(cfg, scene, cams, opts)
     if rank == 0:
         print(json.dumps(line), flush=True)
