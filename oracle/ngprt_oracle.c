@@ -786,12 +786,12 @@ void or_render_backward(const or_scene* s, const or_occ* oc, const or_opts* op,
                         const float* cams, int n_cams, int W, int H, const int32_t* pix,
                         const float* rays_o, const float* rays_d, int n,
                         const double* d_rgb, const double* d_depth, const double* d_opacity,
-                        double* g_tables, double* g_coarse, double* g_mlp) {
-    if (s->aggregation != 0) return; /* the reverse pass covers Eq. 8 only (oracle.py refuses the rest) */
+                        double* g_tables, double* g_coarse, double* g_mlp, double* g_attn_inv) {
+    if (s->aggregation > 4) return; /* the tiny-MLP aggregation has no reverse pass (oracle.py refuses it) */
     int cap = op->max_samples > 0 ? op->max_samples : 1;
     or_sample* sm = (or_sample*)malloc(sizeof(or_sample) * (size_t)cap);
     double* qg = (double*)malloc(sizeof(double) * (size_t)cap);
-    int nch = OR_NFEAT + 2 * s->L;
+    int nch = or_coarse_channels(s->L, s->aggregation);
     uint32_t T = 1u << s->T_log2;
     for (int i = 0; i < n; ++i) {
         float o[3], dv[3], d[3];
@@ -875,11 +875,22 @@ void or_render_backward(const or_scene* s, const or_occ* oc, const or_opts* op,
             }
             for (int ch = 0; ch < OR_NFEAT; ++ch) g_coarse_v[ch] = g_f[ch];
             for (int l = 0; l < s->L; ++l) {
-                double om, be;
-                double lo = coarse[OR_NFEAT + 2 * l], lb = coarse[OR_NFEAT + 2 * l + 1];
-                if (op->attn_mode == 1) { om = 1.0; be = 1.0; }
-                else if (op->attn_mode == 2) { om = or_sigmoid(lo); be = om; }
-                else { om = or_sigmoid(lo); be = or_sigmoid(lb); }
+                /* the gates of this level and whether each is shared by both modalities */
+                double om = 1.0, be = 1.0;
+                int shared = 0;
+                switch (s->aggregation) {
+                    case 0:
+                        if (op->attn_mode == 2) { om = or_sigmoid(coarse[OR_NFEAT + 2 * l]); be = om; shared = 1; }
+                        else if (op->attn_mode == 0) {
+                            om = or_sigmoid(coarse[OR_NFEAT + 2 * l]);
+                            be = or_sigmoid(coarse[OR_NFEAT + 2 * l + 1]);
+                        }
+                        break;
+                    case 1: om = or_sigmoid(coarse[OR_NFEAT + l]); be = om; shared = 1; break;
+                    case 2: om = or_sigmoid(s->attn_inv[2 * l]); be = or_sigmoid(s->attn_inv[2 * l + 1]); break;
+                    case 3: om = or_sigmoid(s->attn_inv[l]); be = om; shared = 1; break;
+                    default: break; /* 4: plain sum */
+                }
                 int bl[3];
                 double wl[3];
                 or_cell(sp->u, s->N[l], bl, wl);
@@ -896,11 +907,21 @@ void or_render_backward(const or_scene* s, const or_occ* oc, const or_opts* op,
                 }
                 double g_om = fl[0] * g_f[0], g_be = 0.0;
                 for (int ch = 1; ch < OR_NFEAT; ++ch) g_be += fl[ch] * g_f[ch];
-                if (op->attn_mode == 0) {
-                    g_coarse_v[OR_NFEAT + 2 * l] += g_om * om * (1.0 - om);
-                    g_coarse_v[OR_NFEAT + 2 * l + 1] += g_be * be * (1.0 - be);
-                } else if (op->attn_mode == 2) {
-                    g_coarse_v[OR_NFEAT + 2 * l] += (g_om + g_be) * om * (1.0 - om);
+                /* gate gradients through the sigmoid, to the logit they come from */
+                double lo_g = shared ? (g_om + g_be) * om * (1.0 - om) : g_om * om * (1.0 - om);
+                double lb_g = shared ? 0.0 : g_be * be * (1.0 - be);
+                if (s->aggregation == 0 && op->attn_mode == 0) {
+                    g_coarse_v[OR_NFEAT + 2 * l] += lo_g;
+                    g_coarse_v[OR_NFEAT + 2 * l + 1] += lb_g;
+                } else if (s->aggregation == 0 && op->attn_mode == 2) {
+                    g_coarse_v[OR_NFEAT + 2 * l] += lo_g;
+                } else if (s->aggregation == 1) {
+                    g_coarse_v[OR_NFEAT + l] += lo_g;
+                } else if (s->aggregation == 2 && g_attn_inv) {
+                    g_attn_inv[2 * l] += lo_g;
+                    g_attn_inv[2 * l + 1] += lb_g;
+                } else if (s->aggregation == 3 && g_attn_inv) {
+                    g_attn_inv[l] += lo_g;
                 }
                 for (int c = 0; c < 8; ++c) {
                     g_tables[ent[c] * OR_NFEAT + 0] += ew[c] * om * g_f[0];

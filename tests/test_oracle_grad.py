@@ -102,3 +102,48 @@ def test_reverse_pass_per_output(which):
         fd = _fd(orc, opts, o, d, one, arr, None, v0)
         an = float(gr @ v0)
         assert abs(fd - an) <= 1e-7 + 1e-4 * abs(an), (which, name, "sigma", fd, an)
+
+
+@pytest.mark.parametrize("agg", [1, 2, 3, 4])
+def test_reverse_pass_of_aggregation_variants(agg):
+    """Table 3's gate forms: a per-level logit in the coarse grid (Shared (V)), constant
+    logits (both Inv forms, gradient into attn_inv) and the plain sum (no logits)."""
+    cfg = S.small_config(blob_std=(0.05, 0.15), aggregation=agg)
+    sc = S.make_scene(cfg)
+    if sc.coarse.shape[1] > 8:
+        sc.coarse[:, 8:] *= 10.0
+    if sc.attn_inv is not None:
+        sc.attn_inv = sc.attn_inv * 20.0
+    orc = O.oracle_for_scene(sc)
+    opts = S.default_options(cfg, t_term=0.0)
+    o, d = S.random_rays(12, 11, True)
+    rng = np.random.default_rng(21)
+    cot = dict(d_rgb=rng.normal(size=(len(o), 3)), d_depth=rng.normal(size=len(o)) * 0.3,
+               d_opacity=rng.normal(size=len(o)))
+    g = orc.render_backward(opts, rays_o=o, rays_d=d, **cot)
+    # the MLP's reverse pass does not depend on the gate form (pinned above); only the
+    # parameters that feed the gated features are checked here
+    names = [("tables", orc.tables), ("coarse", orc.coarse)]
+    if orc.attn_inv is not None:
+        names.append(("attn_inv", orc.attn_inv))
+    else:
+        assert g["attn_inv"] is None
+    for name, arr in names:
+        gr = g[name].reshape(-1)
+        nz = np.nonzero(np.abs(gr) > 1e-8)[0]
+        assert len(nz) > 0, name
+        for k in rng.choice(nz, min(12, len(nz)), replace=False):
+            fd = _fd(orc, opts, o, d, cot, arr, k)
+            assert abs(fd - gr[k]) <= 1e-6 + 1e-4 * abs(gr[k]), (name, k, fd, gr[k])
+        v = rng.normal(size=arr.size)
+        v /= np.linalg.norm(v)
+        fd = _fd(orc, opts, o, d, cot, arr, None, v)
+        an = float(gr @ v)
+        assert abs(fd - an) <= 1e-6 + 1e-4 * abs(an), (name, fd, an)
+    if agg == 1:
+        # one logit per level: the channels past 8 + L do not exist, and every level's
+        # logit receives gradient somewhere
+        assert g["coarse"].shape[1] == 8 + cfg.L
+        assert np.all(np.abs(g["coarse"][:, 8:]).sum(0) > 0)
+    if agg == 4:
+        assert g["coarse"].shape[1] == 8
