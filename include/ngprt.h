@@ -277,9 +277,14 @@ int32_t ngprt_shade(const ngprt_scene* scene, const float* ray_state, int64_t n_
  * Reverse pass of ngprt_render (F32 tables and F32 MLP): given dL/d rgb, depth,
  * opacity of the same rays (same cams/pixel_ids or rays, same opts, and the
  * ray_state a forward call wrote), ACCUMULATE (+=) dL/d tables into g_tables
- * ([n_entries][8] float), dL/d coarse into g_coarse ([R_C^3][8+2L] float) and
- * dL/d mlp_w into g_mlp (float, mlp_w's layout).  Each ray is marched again; the
- * sample set is the forward's.  Table and grid gradients are atomic adds, so their
+ * ([n_entries][8] float), dL/d coarse into g_coarse ([R_C^3][ngprt_coarse_channels]
+ * float), dL/d mlp_w into g_mlp (float, mlp_w's layout) and, for the spatially
+ * invariant gate forms (SEPARATE_INV, SHARED_INV), dL/d attn_inv into g_attn_inv
+ * (float, attn_inv's layout; ignored, and may be NULL, for the other forms).
+ * Aggregations: SEPARATE_V (Eq. 8, any attn_mode; L = 1, 2, 4, 16), and SHARED_V,
+ * SEPARATE_INV, SHARED_INV, SUM (Table 3; L = 2, 4, 16); the MLP form has no reverse
+ * pass (NGPRT_ERR_UNSUPPORTED).  Each ray is marched again; the sample set is the
+ * forward's.  Table, grid and invariant-logit gradients are atomic adds, so their
  * float summation order varies from run to run.
  *   d_rgb [n][3]; d_depth, d_opacity [n] or NULL (zero).
  */
@@ -288,7 +293,7 @@ int32_t ngprt_render_backward(const ngprt_scene* scene, const ngprt_occ* occ, co
                               const float* rays_d, int64_t n_rays, const ngprt_render_opts* opts,
                               const float* ray_state, const float* d_rgb, const float* d_depth,
                               const float* d_opacity, float* g_tables, float* g_coarse, float* g_mlp,
-                              void* workspace, size_t ws_bytes, void* stream);
+                              float* g_attn_inv, void* workspace, size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------------------
  * Learned proposal (not in the paper, which leaves adaptive sampling aside in

@@ -5,20 +5,13 @@
 // cotangents of C_d, F, A and depth go to a per-ray record, and the MLP weight
 // gradients, sums over rays of outer products, are formed tile by tile from shared
 // memory and added to g_mlp once per block.
-// Kernel 2 (march_backward_kernel): per ray, the same march as the forward (same
-// decisions: march_loop), and at each sample i the derivative of the composite
-// sums Q = sum_j w_j q_j:
-//     dQ/dq_i = w_i,   dQ/dsigma_i = delta_i (T_{i+1} q_i - sum_{j>i} w_j q_j),
-// where the suffix sum is the stored total minus the running prefix.  The density
-// activation exp has the truncated derivative exp(min(sigma_raw, 15)).  Through
-// the attention (Eq. 8) and the trilinear weights the gradient reaches 8 entries
-// of each fine level and 8 coarse vertices; it is added with 16-byte vector atomics.
-#include "march.cuh"
+// Kernel 2 (march_backward_kernel, backward_march.cuh): per ray, the march again
+// and the reverse of compositing, gates and trilinear gathers, added atomically to
+// the table, coarse-grid and invariant-logit gradients.
+#include "backward_march.cuh"
 
 namespace ngprt {
 namespace {
-
-constexpr int kCotFloats = 12;  // g_Cd(3), g_F(4), g_A, g_depth, S_total, pad(2)
 
 struct ShadeBwdParams {
     const float* state;
@@ -265,164 +258,6 @@ void launch_shade_bwd(const ShadeBwdParams& s, cudaStream_t st) {
     shade_backward_kernel<WIDTH, LAYERS><<<blocks, 128, smem, st>>>(s);
 }
 
-struct MarchBwdParams {
-    MarchParams m;
-    const float* state;
-    const float* cot;
-    float* g_tables;
-    float* g_coarse;
-};
-
-__device__ __forceinline__ void atomic_add4(float* p, float a, float b, float c, float d) {
-#ifdef NGPRT_SCALAR_ATOMICS
-    atomicAdd(p, a);
-    atomicAdd(p + 1, b);
-    atomicAdd(p + 2, c);
-    atomicAdd(p + 3, d);
-#else
-    atomicAdd(reinterpret_cast<float4*>(p), make_float4(a, b, c, d));
-#endif
-}
-
-// Reverse of sample_features at u.  The sample's feature cotangent is
-// gf = [gs, w gq] (gs = dL/dsigma_raw, w the sample's weight, gq the ray's colour
-// cotangents); the forward half of the sampler left in the thread's slots the gates
-// omega^l, beta^l ([0, 2L)) and sigma^l, q^l = f^l[1..7] . gq ([2L, 4L)), so no
-// entry is read again: each level only recomputes its 8 corner rows and adds
-//     d entry = cw [omega^l gs, beta^l w gq],
-// and the logit gradients d omega-logit = sigma^l gs omega (1 - omega), d beta-logit =
-// w q^l beta (1 - beta) (both on omega for the shared mode) go to the slots [0, 2L)
-// and then, with gf, to the 8 coarse vertices.
-template <int L>
-__device__ __forceinline__ void scatter_features(const Grid& g, const float u[3], int attn_mode, float gs, float w,
-                                                 const float gq[7], float* slots, int stride, float* g_tables,
-                                                 float* g_coarse) {
-    constexpr int NC = kNFeat + 2 * L;
-    float gw[7];
-#pragma unroll
-    for (int k = 0; k < 7; ++k) gw[k] = w * gq[k];
-#pragma unroll kLevelUnroll
-    for (int l = 0; l < L; ++l) {
-        const float om = slots[(2 * l) * stride], be = slots[(2 * l + 1) * stride];
-        const float sh = slots[(2 * L + 2 * l) * stride], q = slots[(2 * L + 2 * l + 1) * stride];
-        int bl[3];
-        float wl[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) grid_cell(u[a], g.N[l], bl[a], wl[a]);
-        const float s0 = om * gs;
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const uint32_t row = level_row(g, l, (uint32_t)(bl[0] + (c & 1)), (uint32_t)(bl[1] + ((c >> 1) & 1)),
-                                           (uint32_t)(bl[2] + ((c >> 2) & 1)));
-            const float cw = corner_w(wl, c);
-            const float cb = cw * be;
-            float* gp = g_tables + (size_t)row * 8;
-            atomic_add4(gp, cw * s0, cb * gw[0], cb * gw[1], cb * gw[2]);
-            atomic_add4(gp + 4, cb * gw[3], cb * gw[4], cb * gw[5], cb * gw[6]);
-        }
-        float go = 0.0f, gb = 0.0f;
-        if (attn_mode == 0) {
-            go = sh * gs * om * (1.0f - om);
-            gb = w * q * be * (1.0f - be);
-        } else if (attn_mode == 2) {
-            go = (sh * gs + w * q) * om * (1.0f - om);
-        }
-        slots[(2 * l) * stride] = go;
-        slots[(2 * l + 1) * stride] = gb;
-    }
-    // coarse vertices: [gf(8), logit grads(2L)] times the corner weight
-    int b[3];
-    float wc[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) grid_cell(u[a], g.R_C, b[a], wc[a]);
-    const uint32_t R = (uint32_t)g.R_C;
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        const uint32_t cv = (uint32_t)(b[0] + (c & 1)) + R * ((uint32_t)(b[1] + ((c >> 1) & 1)) + R * (uint32_t)(b[2] + ((c >> 2) & 1)));
-        const float cw = corner_w(wc, c);
-        float* gp = g_coarse + (size_t)cv * NC;
-        if constexpr (NC % 4 == 0) {
-            atomic_add4(gp, cw * gs, cw * gw[0], cw * gw[1], cw * gw[2]);
-            atomic_add4(gp + 4, cw * gw[3], cw * gw[4], cw * gw[5], cw * gw[6]);
-            if (attn_mode != 1) {
-#pragma unroll 4
-                for (int k = 0; k < 2 * L; k += 4)
-                    atomic_add4(gp + 8 + k, cw * slots[k * stride], cw * slots[(k + 1) * stride],
-                                cw * slots[(k + 2) * stride], cw * slots[(k + 3) * stride]);
-            }
-        } else {
-            atomicAdd(gp, cw * gs);
-#pragma unroll
-            for (int ch = 0; ch < 7; ++ch) atomicAdd(gp + 1 + ch, cw * gw[ch]);
-            if (attn_mode != 1) {
-#pragma unroll
-                for (int k = 0; k < 2 * L; ++k) atomicAdd(gp + 8 + k, cw * slots[k * stride]);
-            }
-        }
-    }
-}
-
-template <int L>
-struct BackwardSampler {
-    const Grid& g;
-    int attn_mode;
-    float t_term;
-    float T, S_le, S_tot;
-    float gCd[3], gF[4], gA, gD;
-    float* g_tables;
-    float* g_coarse;
-    float* gates;
-    __device__ __forceinline__ bool sample(const float u[3], float t, float delta) {
-        float f[8];
-        const float gq[7] = {gCd[0], gCd[1], gCd[2], gF[0], gF[1], gF[2], gF[3]};
-        sample_features<L, NGPRT_F32, NGPRT_AGG_SEPARATE_V, true>(g, u, attn_mode, f, gates, blockDim.x, gq);
-        const float sigma = expf(f[0]);
-        const float trans = expf(-sigma * delta);
-        const float w = T * (1.0f - trans);
-        const float T_next = T * trans;
-        float qg = fmaf(gD, t, gA);
-#pragma unroll
-        for (int k = 0; k < 3; ++k) qg = fmaf(gCd[k], f[1 + k], qg);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) qg = fmaf(gF[k], f[4 + k], qg);
-        S_le = fmaf(w, qg, S_le);
-        const float g_sigma = delta * (T_next * qg - (S_tot - S_le));
-        const float gs = g_sigma * expf(fminf(f[0], 15.0f));
-        scatter_features<L>(g, u, attn_mode, gs, w, gq, gates, blockDim.x, g_tables, g_coarse);
-        T = T_next;
-        return T < t_term;
-    }
-};
-
-// Resident blocks the reverse march's register allocation must allow.  1 lets it
-// take 255 registers (about 7 warps per SM) and was the fastest measured: 4..8
-// blocks (fewer registers, more warps) made a 2^18-ray training step 5-10% slower.
-#ifndef NGPRT_BWD_MIN_BLOCKS
-#define NGPRT_BWD_MIN_BLOCKS 1
-#endif
-
-template <int L>
-__global__ void __launch_bounds__(128, NGPRT_BWD_MIN_BLOCKS) march_backward_kernel(const __grid_constant__ MarchBwdParams p) {
-    extern __shared__ float gate_smem[];
-    int64_t ray;
-    float o[3], d[3], t, t_out;
-    bool hit;
-    if (!ray_setup(p.m, ray, o, d, t, t_out, hit)) return;
-    if (!hit) return;
-    const float4* c4 = reinterpret_cast<const float4*>(p.cot + ray * kCotFloats);
-    const float4 q0 = c4[0], q1 = c4[1], q2 = c4[2];
-    BackwardSampler<L> smp{p.m.g, p.m.opts.attn_mode, p.m.opts.t_term, 1.0f, 0.0f, q2.y,
-                           {q0.x, q0.y, q0.z}, {q0.w, q1.x, q1.y, q1.z}, q1.w, q2.x, p.g_tables, p.g_coarse,
-                           gate_smem + threadIdx.x};
-    int n_march = 0, n_samp = 0;
-    march_loop(p.m, o, d, t, t_out, smp, n_march, n_samp);
-}
-
-template <int L>
-void launch_bwd(const MarchBwdParams& p, dim3 grid, cudaStream_t st) {
-    march_backward_kernel<L><<<grid, 128, (size_t)4 * L * 128 * sizeof(float), st>>>(p);
-}
-
 }  // namespace
 
 int32_t make_grid(const ngprt_scene* s, Grid& g, const char* fn);
@@ -431,7 +266,6 @@ int32_t check_opts(const ngprt_render_opts* o, const char* fn);
 int32_t setup_rays(MarchParams& p, const ngprt_camera* cams, int32_t n_cams, const int32_t* pixel_ids,
                    const float* rays_o, const float* rays_d, int64_t n_rays, dim3& grid, const char* fn);
 bool march_supports(int L);
-int32_t check_agg(const ngprt_scene* s, const ngprt_render_opts* o, bool forward_only_ok, const char* fn);
 bool mlp_supports(int width, int layers);
 
 }  // namespace ngprt
@@ -443,7 +277,7 @@ extern "C" int32_t ngprt_render_backward(const ngprt_scene* scene, const ngprt_o
                                          const float* rays_d, int64_t n_rays, const ngprt_render_opts* opts,
                                          const float* ray_state, const float* d_rgb, const float* d_depth,
                                          const float* d_opacity, float* g_tables, float* g_coarse, float* g_mlp,
-                                         void* workspace, size_t ws_bytes, void* stream) {
+                                         float* g_attn_inv, void* workspace, size_t ws_bytes, void* stream) {
     const char* fn = "ngprt_render_backward";
     MarchBwdParams p;
     memset(&p, 0, sizeof p);
@@ -451,13 +285,26 @@ extern "C" int32_t ngprt_render_backward(const ngprt_scene* scene, const ngprt_o
     if ((rc = make_grid(scene, p.m.g, fn)) != NGPRT_OK) return rc;
     if ((rc = make_occ(occ, p.m.occ, fn)) != NGPRT_OK) return rc;
     if ((rc = check_opts(opts, fn)) != NGPRT_OK) return rc;
-    if ((rc = check_agg(scene, opts, false, fn)) != NGPRT_OK) return rc;
     NGPRT_REQUIRE(n_rays >= 0, "%s: n_rays=%lld", fn, (long long)n_rays);
     NGPRT_REQUIRE(scene->table_dtype == NGPRT_F32 && scene->mlp_dtype == NGPRT_F32,
                   "%s: gradients need F32 tables and F32 MLP weights", fn);
-    if (!march_supports(scene->L) || !(scene->L == 1 || scene->L == 2 || scene->L == 4 || scene->L == 16)) {
-        set_error("%s: no backward kernel for L=%d (built: 1, 2, 4, 16)", fn, scene->L);
-        return NGPRT_ERR_UNSUPPORTED;
+    const int agg = scene->aggregation;
+    if (agg == NGPRT_AGG_SEPARATE_V) {
+        if (!march_supports(scene->L) || !(scene->L == 1 || scene->L == 2 || scene->L == 4 || scene->L == 16)) {
+            set_error("%s: no backward kernel for L=%d (built: 1, 2, 4, 16)", fn, scene->L);
+            return NGPRT_ERR_UNSUPPORTED;
+        }
+    } else {
+        NGPRT_REQUIRE(opts->attn_mode == 0, "%s: attn_mode=%d applies to the SEPARATE_V aggregation only", fn,
+                      opts->attn_mode);
+        if (agg == NGPRT_AGG_MLP) {
+            set_error("%s: the MLP aggregation has no reverse pass", fn);
+            return NGPRT_ERR_UNSUPPORTED;
+        }
+        if (!march_bwd_agg_supports(scene->L)) {
+            set_error("%s: aggregation %d has no backward kernel for L=%d (built: 2, 4, 16)", fn, agg, scene->L);
+            return NGPRT_ERR_UNSUPPORTED;
+        }
     }
     if (!mlp_supports(scene->mlp_width, scene->mlp_layers)) {
         set_error("%s: MLP %d layers x %d not built", fn, scene->mlp_layers, scene->mlp_width);
@@ -467,6 +314,8 @@ extern "C" int32_t ngprt_render_backward(const ngprt_scene* scene, const ngprt_o
     if ((rc = setup_rays(p.m, cams, n_cams, pixel_ids, rays_o, rays_d, n_rays, grid, fn)) != NGPRT_OK) return rc;
     if (n_rays == 0) return NGPRT_OK;
     NGPRT_REQUIRE(ray_state && d_rgb && g_tables && g_coarse && g_mlp, "%s: NULL buffer", fn);
+    const bool inv = agg == NGPRT_AGG_SEPARATE_INV || agg == NGPRT_AGG_SHARED_INV;
+    NGPRT_REQUIRE(!inv || g_attn_inv, "%s: g_attn_inv is NULL (aggregation %d)", fn, agg);
     NGPRT_REQUIRE(((uintptr_t)g_tables & 15) == 0 && ((uintptr_t)g_coarse & 15) == 0 && ((uintptr_t)ray_state & 15) == 0,
                   "%s: g_tables, g_coarse, ray_state must be 16-byte aligned", fn);
     const size_t need = ngprt_render_workspace_bytes(scene, n_rays);
@@ -505,11 +354,16 @@ extern "C" int32_t ngprt_render_backward(const ngprt_scene* scene, const ngprt_o
     p.cot = cot;
     p.g_tables = g_tables;
     p.g_coarse = g_coarse;
+    p.g_attn_inv = inv ? g_attn_inv : nullptr;
+    if (agg != NGPRT_AGG_SEPARATE_V) {
+        launch_bwd_agg(scene->L, agg, p, grid, st);
+        return cuda_status(fn);
+    }
     switch (scene->L) {
-        case 1: launch_bwd<1>(p, grid, st); break;
-        case 2: launch_bwd<2>(p, grid, st); break;
-        case 4: launch_bwd<4>(p, grid, st); break;
-        default: launch_bwd<16>(p, grid, st); break;
+        case 1: launch_bwd<1, NGPRT_AGG_SEPARATE_V>(p, grid, st); break;
+        case 2: launch_bwd<2, NGPRT_AGG_SEPARATE_V>(p, grid, st); break;
+        case 4: launch_bwd<4, NGPRT_AGG_SEPARATE_V>(p, grid, st); break;
+        default: launch_bwd<16, NGPRT_AGG_SEPARATE_V>(p, grid, st); break;
     }
     return cuda_status(fn);
 }

@@ -53,7 +53,7 @@ def initial_scene(cfg: S.SceneConfig, fc: FitConfig, device="cuda"):
     g = torch.Generator(device=device)
     g.manual_seed(fc.seed)
     tables = torch.randn(S.table_entries(cfg), S.N_FEAT, generator=g, device=device) * fc.table_std
-    coarse = torch.randn(cfg.R_C ** 3, S.N_FEAT + 2 * cfg.L, generator=g, device=device) * fc.table_std
+    coarse = torch.randn(cfg.R_C ** 3, S.coarse_channels(cfg), generator=g, device=device) * fc.table_std
     coarse[:, 0] += fc.density_init
     rng = np.random.default_rng(fc.seed)
     ws = []
@@ -65,6 +65,18 @@ def initial_scene(cfg: S.SceneConfig, fc: FitConfig, device="cuda"):
         ws.append(w.reshape(-1))
     mlp_w = torch.as_tensor(np.concatenate(ws)).to(device)
     return tables, coarse, mlp_w
+
+
+def initial_attn_inv(cfg: S.SceneConfig, fc: FitConfig, device="cuda"):
+    """The constant gate logits of the spatially invariant forms (2L for separate
+    gates, L for shared ones), drawn like the coarse grid's spatial logits; None for
+    the other forms."""
+    agg = cfg.aggregation
+    if agg not in (2, 3):
+        return None
+    g = torch.Generator(device=device)
+    g.manual_seed(fc.seed + 1)
+    return torch.randn((2 if agg == 2 else 1) * cfg.L, generator=g, device=device) * fc.table_std
 
 
 def tile_order(pixel_ids: torch.Tensor, W: int, H: int, tile: int = 32):
@@ -95,15 +107,19 @@ def _lr_factor(step: int, fc: FitConfig) -> float:
 
 def fit(scene: ng.DeviceScene, occ: ng.DeviceOcc, opts, cams: np.ndarray, W: int, H: int,
         targets: torch.Tensor, fc: FitConfig = FitConfig(), log_every: int = 0, stream=None):
-    """Fit ``scene`` (FP32 tables, coarse grid and MLP, updated in place) to the images
-    ``targets`` [n_views * H * W, 3] of the cameras ``cams``.  Returns the loss history
-    [(step, loss)] and the wall time in seconds; with ``autotune`` the final gamma is
-    left in ``fit.last_gamma``."""
+    """Fit ``scene`` (FP32 tables, coarse grid, MLP and any constant gate logits, updated
+    in place) to the images ``targets`` [n_views * H * W, 3] of the cameras ``cams``.
+    Returns the loss history [(step, loss)] and the wall time in seconds; with
+    ``autotune`` the final gamma is left in ``fit.last_gamma``."""
     from dataclasses import replace
     dev = scene.tables.device
     rend = ng.Renderer(scene, occ, device=dev)
     params = [scene.tables, scene.coarse, scene.mlp_w]
     lrs = [fc.lr, fc.lr, fc.lr_mlp]
+    inv = scene.attn_inv is not None and scene.cfg.aggregation in (2, 3)   # constant gate logits
+    if inv:
+        params.append(scene.attn_inv)
+        lrs.append(fc.lr)
     grads = [torch.zeros_like(p) for p in params]
     moms = [(torch.zeros_like(p), torch.zeros_like(p)) for p in params]
     n_pix = len(cams) * W * H
@@ -125,7 +141,7 @@ def fit(scene: ng.DeviceScene, occ: ng.DeviceOcc, opts, cams: np.ndarray, W: int
     for step in range(1, fc.steps + 1):
         idx = torch.randint(0, n_pix, (B,), device=dev, generator=gen)
         pix = idx.to(torch.int32)
-        perm, inv = tile_order(pix, W, H)
+        perm, back = tile_order(pix, W, H)
         pix_f = pix[perm].contiguous()
         tg = targets[idx[perm]].contiguous()
         logging = bool(log_every) and (step % log_every == 0 or step == fc.steps)
@@ -138,8 +154,8 @@ def fit(scene: ng.DeviceScene, occ: ng.DeviceOcc, opts, cams: np.ndarray, W: int
                                 d_rgb, stream=stream)
         else:
             ng.ngprt_l2_loss(out["rgb"], tg, 3 * B, 1.0 / (3 * B), loss if logging else None, d_rgb, stream=stream)
-        rend.backward(o_step, out["state"][inv].contiguous(), d_rgb[inv].contiguous(), None, None, grads[0],
-                      grads[1], grads[2], cams=cams, W=W, H=H, pixel_ids=pix)
+        rend.backward(o_step, out["state"][back].contiguous(), d_rgb[back].contiguous(), None, None, grads[0],
+                      grads[1], grads[2], cams=cams, W=W, H=H, pixel_ids=pix, g_attn_inv=grads[3] if inv else None)
         if fc.eta > 0:
             ro = ng.render_opts(o_step)
             ng.ngprt_distortion_loss(scene.struct, occ.struct, cam_arr, n_cams, pix, None, None, B, ro, fc.eta / B,

@@ -80,7 +80,7 @@ _SIGS = {
     "ngprt_render": (C.c_int32, [_P, _P, _P, C.c_int32, _P, _P, _P, C.c_int64, _P, _P, _P, _P, _P, _P, _P,
                                  _P, C.c_size_t, _P]),
     "ngprt_render_backward": (C.c_int32, [_P, _P, _P, C.c_int32, _P, _P, _P, C.c_int64, _P, _P, _P, _P, _P,
-                                          _P, _P, _P, _P, C.c_size_t, _P]),
+                                          _P, _P, _P, _P, _P, C.c_size_t, _P]),
     "ngprt_grid_indices": (C.c_int32, [_P, _P, C.c_int64, _P, _P]),
     "ngprt_shade": (C.c_int32, [_P, _P, C.c_int64, _P, _P, _P, _P, _P]),
     "ngprt_l2_loss": (C.c_int32, [_P, _P, C.c_int64, C.c_float, _P, _P, _P]),
@@ -270,12 +270,13 @@ def ngprt_render(scene, occ, cams, n_cams, pixel_ids, rays_o, rays_d, n_rays, t_
 
 
 def ngprt_render_backward(scene, occ, cams, n_cams, pixel_ids, rays_o, rays_d, n_rays, opts, ray_state, d_rgb,
-                          d_depth, d_opacity, g_tables, g_coarse, g_mlp, workspace=None, stream=None) -> None:
+                          d_depth, d_opacity, g_tables, g_coarse, g_mlp, workspace=None, stream=None,
+                          g_attn_inv=None) -> None:
     ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
     _check("ngprt_render_backward", lib().ngprt_render_backward(
         C.byref(scene), C.byref(occ), cams, n_cams, _ptr(pixel_ids), _ptr(rays_o), _ptr(rays_d), n_rays,
         C.byref(opts), _ptr(ray_state), _ptr(d_rgb), _ptr(d_depth), _ptr(d_opacity), _ptr(g_tables),
-        _ptr(g_coarse), _ptr(g_mlp), _ptr(workspace), ws_bytes, _stream(stream)))
+        _ptr(g_coarse), _ptr(g_mlp), _ptr(g_attn_inv), _ptr(workspace), ws_bytes, _stream(stream)))
 
 
 def ngprt_shade(scene, ray_state, n_rays, bg, rgb, depth=None, opacity=None, stream=None) -> None:
@@ -463,14 +464,16 @@ class Renderer:
 
 
 class RenderFunction(torch.autograd.Function):
-    """Differentiable render: (tables, coarse, mlp_w) -> (rgb, depth, opacity) through
-    ngprt_render and ngprt_render_backward (gradients accumulate with atomics)."""
+    """Differentiable render: (tables, coarse, mlp_w[, attn_inv]) -> (rgb, depth, opacity)
+    through ngprt_render and ngprt_render_backward (gradients accumulate with atomics).
+    attn_inv is the scene's constant gate logits (the spatially invariant gate forms)."""
 
     @staticmethod
-    def forward(ctx, tables, coarse, mlp_w, renderer, opts, rays):
+    def forward(ctx, tables, coarse, mlp_w, renderer, opts, rays, attn_inv=None):
         scene = renderer.scene
         assert tables.data_ptr() == scene.tables.data_ptr() and coarse.data_ptr() == scene.coarse.data_ptr()
         assert mlp_w.data_ptr() == scene.mlp_w.data_ptr()
+        assert attn_inv is None or attn_inv.data_ptr() == scene.attn_inv.data_ptr()
         out = renderer.render(opts, state=True, **rays)
         ctx.renderer, ctx.opts, ctx.rays = renderer, opts, rays
         ctx.save_for_backward(out["state"])
@@ -484,13 +487,15 @@ class RenderFunction(torch.autograd.Function):
         g_t = torch.zeros_like(s.tables)
         g_c = torch.zeros_like(s.coarse)
         g_m = torch.zeros_like(s.mlp_w)
+        g_i = torch.zeros_like(s.attn_inv) if s.attn_inv is not None else None
         r.backward(ctx.opts, state, d_rgb.contiguous(), None if d_depth is None else d_depth.contiguous(),
-                   None if d_opacity is None else d_opacity.contiguous(), g_t, g_c, g_m, **ctx.rays)
-        return g_t, g_c, g_m, None, None, None
+                   None if d_opacity is None else d_opacity.contiguous(), g_t, g_c, g_m, g_attn_inv=g_i,
+                   **ctx.rays)
+        return g_t, g_c, g_m, None, None, None, g_i
 
 
 def _renderer_backward(self, opts, state, d_rgb, d_depth, d_opacity, g_tables, g_coarse, g_mlp, cams=None, W=None,
-                       H=None, pixel_ids=None, rays_o=None, rays_d=None, t_interval=None):
+                       H=None, pixel_ids=None, rays_o=None, rays_d=None, t_interval=None, g_attn_inv=None):
     if cams is not None:
         cam_arr, n_cams = cameras_struct(cams, W, H)
         n = len(pixel_ids) if pixel_ids is not None else n_cams * W * H
@@ -499,7 +504,7 @@ def _renderer_backward(self, opts, state, d_rgb, d_depth, d_opacity, g_tables, g
         n = rays_o.shape[0]
     ngprt_render_backward(self.scene.struct, self.occ.struct, cam_arr, n_cams, pixel_ids, rays_o, rays_d, n,
                           render_opts(opts), state, d_rgb, d_depth, d_opacity, g_tables, g_coarse, g_mlp,
-                          self.workspace(n))
+                          self.workspace(n), g_attn_inv=g_attn_inv)
 
 
 Renderer.backward = _renderer_backward

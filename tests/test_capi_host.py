@@ -121,11 +121,18 @@ def test_aggregation_layouts_and_validation(ng):
     opts.attn_mode = 0
     s.L = 3                                 # no variant kernel for L = 3
     assert render() == ng.ERR_UNSUPPORTED and b"L=3" in lib.ngprt_last_error()
-    s.L = 4                                 # variants are forward-only
-    rc = lib.ngprt_render_backward(C.byref(s), C.byref(o), None, 0, None, C.c_void_p(256), C.c_void_p(256), 4,
-                                   C.byref(opts), C.c_void_p(256), C.c_void_p(256), None, None, C.c_void_p(256),
-                                   C.c_void_p(256), C.c_void_p(256), None, 0, None)
-    assert rc == ng.ERR_UNSUPPORTED and b"forward render only" in lib.ngprt_last_error()
+    s.L = 4
+
+    def backward(g_inv=None):
+        return lib.ngprt_render_backward(C.byref(s), C.byref(o), None, 0, None, C.c_void_p(256), C.c_void_p(256),
+                                         4, C.byref(opts), C.c_void_p(256), C.c_void_p(256), None, None,
+                                         C.c_void_p(256), C.c_void_p(256), C.c_void_p(256), g_inv, None, 0, None)
+    s.aggregation, s.agg_mlp = 5, 256  # the MLP form has no reverse pass
+    assert backward() == ng.ERR_UNSUPPORTED and b"no reverse pass" in lib.ngprt_last_error()
+    s.aggregation, s.agg_mlp, s.attn_inv = 2, None, 256
+    assert backward() == ng.ERR_INVALID_ARG and b"g_attn_inv" in lib.ngprt_last_error()
+    s.L = 3                                 # no variant reverse pass for L = 3
+    assert backward(C.c_void_p(256)) == ng.ERR_UNSUPPORTED and b"L=3" in lib.ngprt_last_error()
 
 
 def test_step_autotune_matches_oracle(ng):

@@ -89,3 +89,89 @@ def test_autograd_function_matches_direct_call(ng):
     loss.backward()
     for a, b in zip((t.grad, c.grad, m.grad), grads):
         np.testing.assert_allclose(a.cpu().numpy(), b.cpu().numpy(), rtol=1e-4, atol=1e-6)
+
+
+def _run_agg(ng, cfg, opts, n_rays, seed=5):
+    sc = S.make_scene(cfg)
+    if sc.coarse.shape[1] > 8:
+        sc.coarse[:, 8:] *= 10.0
+    if sc.attn_inv is not None:
+        sc.attn_inv = sc.attn_inv * 20.0
+    ds = ng.DeviceScene(cfg, sc.tables, sc.coarse, sc.mlp_w, attn_inv=sc.attn_inv)
+    docc = ng.DeviceOcc(sc.occ, cfg.R_O, cfg.n_occ_levels)
+    rend = ng.Renderer(ds, docc)
+    o, d = S.random_rays(n_rays, seed, cfg.bounded)
+    rng = np.random.default_rng(seed + 1)
+    d_rgb = rng.normal(size=(n_rays, 3)).astype(np.float32)
+    d_dep = (0.3 * rng.normal(size=n_rays)).astype(np.float32)
+    d_op = rng.normal(size=n_rays).astype(np.float32)
+    rays = dict(rays_o=torch.as_tensor(o).cuda(), rays_d=torch.as_tensor(d).cuda())
+    out = rend.render(opts, state=True, **rays)
+    g_t = torch.zeros_like(ds.tables)
+    g_c = torch.zeros_like(ds.coarse)
+    g_m = torch.zeros_like(ds.mlp_w)
+    g_i = torch.zeros_like(ds.attn_inv) if ds.attn_inv is not None else None
+    rend.backward(opts, out["state"], torch.as_tensor(d_rgb).cuda(), torch.as_tensor(d_dep).cuda(),
+                  torch.as_tensor(d_op).cuda(), g_t, g_c, g_m, g_attn_inv=g_i, **rays)
+    torch.cuda.synchronize()
+    ref = O.oracle_for_scene(sc).render_backward(opts, d_rgb=d_rgb, d_depth=d_dep, d_opacity=d_op, rays_o=o,
+                                                 rays_d=d)
+    _close("tables", g_t.cpu().numpy(), ref["tables"])
+    _close("coarse", g_c.cpu().numpy(), ref["coarse"])
+    _close("mlp_w", g_m.cpu().numpy(), ref["mlp_w"])
+    if g_i is not None:
+        _close("attn_inv", g_i.cpu().numpy(), ref["attn_inv"])
+    return g_c
+
+
+@pytest.mark.parametrize("L", [2, 4])
+@pytest.mark.parametrize("agg", [1, 2, 3, 4])
+def test_backward_aggregation_variants(ng, agg, L):
+    """Table 3's gate forms in their own layouts (one spatial logit per level, constant
+    logits, no logits); 2500 rays span 20 blocks and a ragged last one."""
+    cfg = S.small_config(L=L, N=[16, 32, 64, 128][:L] if L == 4 else [24, 96], blob_std=(0.05, 0.15),
+                         aggregation=agg)
+    g_c = _run_agg(ng, cfg, S.default_options(cfg, t_term=0.0), n_rays=2500)
+    assert g_c.shape[1] == S.coarse_channels(cfg)
+
+
+@pytest.mark.parametrize("agg", [1, 3])
+def test_backward_aggregation_variants_hd_levels(ng, agg):
+    """16 levels (the hd workload's, T = 2^19): 24 coarse channels (SHARED_V) and the
+    16 shared constant logits summed over the block."""
+    cfg = S.hd_config(density_bias=0.5, aggregation=agg)
+    _run_agg(ng, cfg, S.default_options(cfg, t_term=0.0, max_samples=64), n_rays=384)
+
+
+def test_backward_refuses_the_mlp_aggregation(ng):
+    cfg = S.small_config(aggregation=5)
+    sc = S.make_scene(cfg)
+    ds = ng.DeviceScene(cfg, sc.tables, sc.coarse, sc.mlp_w, agg_mlp=sc.agg_mlp)
+    docc = ng.DeviceOcc(sc.occ, cfg.R_O, cfg.n_occ_levels)
+    rend = ng.Renderer(ds, docc)
+    o, d = S.random_rays(64, 1, cfg.bounded)
+    rays = dict(rays_o=torch.as_tensor(o).cuda(), rays_d=torch.as_tensor(d).cuda())
+    opts = S.default_options(cfg)
+    out = rend.render(opts, state=True, **rays)
+    with pytest.raises(RuntimeError, match="no reverse pass"):
+        rend.backward(opts, out["state"], torch.zeros(64, 3, device="cuda"), None, None,
+                      torch.zeros_like(ds.tables), torch.zeros_like(ds.coarse), torch.zeros_like(ds.mlp_w), **rays)
+
+
+def test_autograd_function_returns_the_invariant_logits_gradient(ng):
+    cfg = S.small_config(blob_std=(0.05, 0.15), aggregation=2)
+    sc = S.make_scene(cfg)
+    ds = ng.DeviceScene(cfg, sc.tables, sc.coarse, sc.mlp_w, attn_inv=sc.attn_inv)
+    docc = ng.DeviceOcc(sc.occ, cfg.R_O, cfg.n_occ_levels)
+    rend = ng.Renderer(ds, docc)
+    o, d = S.random_rays(300, 2, cfg.bounded)
+    rays = dict(rays_o=torch.as_tensor(o).cuda(), rays_d=torch.as_tensor(d).cuda())
+    opts = S.default_options(cfg, t_term=0.0)
+    params = [ds.tables.requires_grad_(), ds.coarse.requires_grad_(), ds.mlp_w.requires_grad_(),
+              ds.attn_inv.requires_grad_()]
+    rgb, dep, opa = ng.RenderFunction.apply(params[0], params[1], params[2], rend, opts, rays, params[3])
+    (rgb.sum() + 0.1 * opa.sum()).backward()
+    cot = dict(d_rgb=np.ones((300, 3)), d_depth=np.zeros(300), d_opacity=np.full(300, 0.1))
+    ref = O.oracle_for_scene(sc).render_backward(opts, rays_o=o, rays_d=d, **cot)
+    _close("attn_inv", ds.attn_inv.grad.cpu().numpy(), ref["attn_inv"])
+    _close("coarse", ds.coarse.grad.cpu().numpy(), ref["coarse"])

@@ -1,6 +1,8 @@
 """Fitting the small scene's model to ground-truth images of its analytic field with
 the library's forward, reverse pass and Adam kernels: the photometric error must
 fall by a wide margin, on the training views and on a view between them."""
+from dataclasses import replace
+
 import numpy as np
 import pytest
 import torch
@@ -88,25 +90,29 @@ def test_fit_with_huber_distortion_and_autotune(ng):
 
 def test_attention_fits_better_than_sum(ng):
     """Table 3's quality order on synthetic data: the same collision-heavy model
-    (T = 2^12, so the fine levels share entries) fitted with the level fusion of Eq. 8
-    (separate gates per modality), one shared gate per level, or the plain sum; the
-    attention forms reach a higher PSNR on the training views and on views between
-    them.  Prints the table (run with -s)."""
-    cfg = S.small_config()
-    blobs = S._blobs(cfg, np.random.default_rng(cfg.seed))
-    occ = S._occupancy(cfg, blobs)
-    cams = S.orbit_cameras(cfg, 32, step_deg=360.0 / 32)
-    targets = GT.render_views(cfg, blobs, cams, device="cuda", n_steps=512)
-    held = S.orbit_cameras(cfg, 4, azimuth0=360.0 / 64, step_deg=90.0)
-    held_t = GT.render_views(cfg, blobs, held, device="cuda", n_steps=512)
-    docc = ng.DeviceOcc(occ, cfg.R_O, cfg.n_occ_levels)
+    (T = 2^12, so the fine levels share entries) fitted with each gated level fusion in
+    its own layout (separate or shared gates per level, spatially variant in the coarse
+    grid or invariant constants) or the plain sum; every gated form reaches a higher
+    PSNR than the sum between the training views, the spatially variant ones on them
+    too.  Prints the table (run with -s)."""
+    base = S.small_config()
+    blobs = S._blobs(base, np.random.default_rng(base.seed))
+    occ = S._occupancy(base, blobs)
+    cams = S.orbit_cameras(base, 32, step_deg=360.0 / 32)
+    targets = GT.render_views(base, blobs, cams, device="cuda", n_steps=512)
+    held = S.orbit_cameras(base, 4, azimuth0=360.0 / 64, step_deg=90.0)
+    held_t = GT.render_views(base, blobs, held, device="cuda", n_steps=512)
+    docc = ng.DeviceOcc(occ, base.R_O, base.n_occ_levels)
     res = {}
-    for mode, label in ((1, "SUM"), (2, "Shared-Att (V)"), (0, "Separate-Att (V)")):
+    forms = ((4, "SUM"), (3, "Shared-Att (Inv)"), (2, "Separate-Att (Inv)"), (1, "Shared-Att (V)"),
+             (0, "Separate-Att (V)"))
+    for agg, label in forms:
+        cfg = replace(base, aggregation=agg)
+        opts = S.default_options(cfg)
         runs = []
         for seed in (5, 6):
             fc = F.FitConfig(steps=1500, batch=1 << 14, seed=seed)
-            ds = ng.DeviceScene(cfg, *F.initial_scene(cfg, fc, "cuda"))
-            opts = S.default_options(cfg, attn_mode=mode)
+            ds = ng.DeviceScene(cfg, *F.initial_scene(cfg, fc, "cuda"), attn_inv=F.initial_attn_inv(cfg, fc, "cuda"))
             F.fit(ds, docc, opts, cams, cfg.W, cfg.H, targets, fc)
             r = ng.Renderer(ds, docc)
             runs.append((P.psnr(r.render(opts, cams=cams, W=cfg.W, H=cfg.H)["rgb"], targets),
@@ -118,3 +124,5 @@ def test_attention_fits_better_than_sum(ng):
     for att in ("Separate-Att (V)", "Shared-Att (V)"):
         assert res[att][1] > res["SUM"][1] + 0.2      # between the training views
         assert res[att][0] > res["SUM"][0]            # on them
+    for att in ("Separate-Att (Inv)", "Shared-Att (Inv)"):
+        assert res[att][1] > res["SUM"][1]
