@@ -67,6 +67,13 @@ typedef enum {
 
 #define NGPRT_AGG_MLP_HIDDEN 64
 
+/* Sparse coarse grid (the block-indexed storage of the baked 512^3 grid, Sec. 3.1,
+ * Eq. S1): cells are grouped in blocks of 8^3; a stored block holds the 9^3 vertices
+ * of its cells (neighbouring blocks repeat their shared face), so one index lookup
+ * serves all 8 corners of a sample. */
+#define NGPRT_COARSE_BLOCK 8
+#define NGPRT_COARSE_BLOCK_ROWS 729
+
 /*
  * Render-time scene (Sec. 3.1, Eq. 6): L fine levels of explicit deferred features
  * and a coarse grid holding the coarse feature and the attention logits.
@@ -93,6 +100,16 @@ typedef enum {
  *   agg_mlp: device FP32 weights of the MLP form, W1 [64][8L] then W2 [8][64]
  *            ([out][in] row-major; input = level 1's 8 channels, then level 2's, ...),
  *            16-byte aligned; NULL otherwise.
+ *   coarse_index: NULL = coarse is the dense [R_C^3] grid above.  Else coarse is
+ *            sparse: [coarse_blocks][NGPRT_COARSE_BLOCK_ROWS][channels], block s
+ *            row i + 9 j + 81 k = vertex (8 bx + i, 8 by + j, 8 bz + k) of the block
+ *            (bx, by, bz) whose index entry is s, and coarse_index is int32
+ *            [NB^3] (NB = ceil((R_C - 1) / 8), entry bx + NB (by + NB bz)).  Slot 0
+ *            conventionally holds zeros and serves the empty blocks.  Slots outside
+ *            [0, coarse_blocks) are clamped into it.  Render paths only
+ *            (ngprt_render, the occupancy builders); the reverse passes need the
+ *            dense grid.  Built by ngprt_coarse_block_mask + ngprt_coarse_sparsify.
+ *   coarse_blocks: stored blocks (>= 1) when coarse_index != NULL.
  * Vertex grids of N per axis cover the unit cube coordinate u in [0,1]^3 with
  * p = u (N - 1) (trilinear interpolation, Eq. 6).
  */
@@ -112,10 +129,13 @@ typedef struct {
     int32_t aggregation;
     const float* attn_inv;
     const float* agg_mlp;
+    const int32_t* coarse_index;
+    int64_t coarse_blocks;
 } ngprt_scene;
 
 /* Channels per coarse-grid vertex for L levels under `aggregation` (0 if invalid). */
 int32_t ngprt_coarse_channels(int32_t L, int32_t aggregation);
+
 
 /*
  * Occupancy (Sec. 3.3; Sec. S2.5).  bits: n_levels bit-packed grids, finest
@@ -133,6 +153,33 @@ typedef struct {
     const uint8_t* dist;
     int32_t R_G;
 } ngprt_occ;
+
+/*
+ * Coarse blocks a render can read: block_mask (uint8 [NB^3], NB = ceil((R_C - 1) / 8),
+ * written 0/1 in full) marks every block holding a cell that an occupied voxel of
+ * the finest occupancy level (occ->bits, R_O^3) overlaps, widened by one cell on
+ * each side.  Voxel x covers u in [x / R_O, (x + 1) / R_O] and so the coarse cells
+ * floor(x (R_C - 1) / R_O) - 1 ... floor((x + 1) (R_C - 1) / R_O) + 1 (clamped to
+ * [0, R_C - 2]) per axis: samples are only taken in occupied voxels, so a sparse
+ * grid of the marked blocks renders exactly like the dense grid.  occ->dist unused.
+ */
+int32_t ngprt_coarse_block_mask(const ngprt_occ* occ, int32_t R_C, uint8_t* block_mask, void* stream);
+
+/*
+ * Sparse coarse grid from a dense one.  block_mask: device uint8 [NB^3] (e.g. from
+ * ngprt_coarse_block_mask).  Writes the device index (int32 [NB^3]: marked blocks
+ * numbered 1, 2, ... in index order, unmarked ones 0) and the host count
+ * *n_blocks = 1 + marked blocks (slot 0 = zeros).  With blocks != NULL (device,
+ * room for max_blocks blocks of NGPRT_COARSE_BLOCK_ROWS rows of row_bytes) the
+ * blocks are filled from dense ([R_C^3] rows of row_bytes = channels x element
+ * size, a multiple of 4; vertices past R_C - 1 are zero).  NULL blocks only counts.
+ * Synchronises `stream` (the count comes back to the host).  workspace: device,
+ * ngprt_coarse_sparsify_workspace_bytes(R_C) bytes, 16-byte aligned.
+ */
+size_t ngprt_coarse_sparsify_workspace_bytes(int32_t R_C);
+int32_t ngprt_coarse_sparsify(const void* dense, int32_t R_C, int32_t row_bytes, const uint8_t* block_mask,
+                              int32_t* index, void* blocks, int64_t max_blocks, int64_t* n_blocks, void* workspace,
+                              size_t ws_bytes, void* stream);
 
 /* Pinhole camera, OpenCV axes (x right, y down, z forward).  c2w: 3x4 row-major
  * camera-to-world.  Pixel (col, row) looks through (col + 0.5, row + 0.5). */

@@ -377,6 +377,52 @@ def downsample_occ(occ: np.ndarray, R: int, k: int) -> np.ndarray:
     return np.ascontiguousarray(g.reshape(r, f, r, f, r, f).max(axis=(1, 3, 5)).reshape(-1))
 
 
+COARSE_BLOCK = 8
+
+
+def coarse_block_mask(occ: np.ndarray, R_O: int, R_C: int) -> np.ndarray:
+    """Blocks of the sparse coarse grid a render can reach (the baked grid is stored
+    sparse, Sec. 3.1 and Eq. S1; which vertices to keep is this build's reading):
+    occupied finest voxel x covers u in [x / R_O, (x + 1) / R_O], so the cells
+    floor(x (R_C - 1) / R_O) ... floor((x + 1) (R_C - 1) / R_O) per axis, widened by one
+    cell and clamped to [0, R_C - 2]; a block of 8^3 cells is kept when it holds one
+    of them.  uint8 [NB^3], NB = ceil((R_C - 1) / 8), entry bx + NB (by + NB bz)."""
+    nb = (R_C - 1 + COARSE_BLOCK - 1) // COARSE_BLOCK
+    g = np.asarray(occ, np.uint8).reshape(R_O, R_O, R_O)       # [z][y][x]
+    z, y, x = np.nonzero(g)
+    mask = np.zeros((nb, nb, nb), np.uint8)                     # [bz][by][bx]
+    ranges = []
+    for v in (x, y, z):
+        v = v.astype(np.int64)
+        lo = np.maximum(v * (R_C - 1) // R_O - 1, 0) // COARSE_BLOCK
+        hi = np.minimum((v + 1) * (R_C - 1) // R_O + 1, R_C - 2) // COARSE_BLOCK
+        ranges.append((lo, hi))
+    for i in range(len(x)):
+        (x0, x1), (y0, y1), (z0, z1) = [(lo[i], hi[i]) for lo, hi in ranges]
+        mask[z0:z1 + 1, y0:y1 + 1, x0:x1 + 1] = 1
+    return mask.reshape(-1)
+
+
+def sparse_coarse(dense: np.ndarray, R_C: int, mask: np.ndarray):
+    """(index, blocks) of the sparse coarse grid: marked blocks numbered 1, 2, ... in
+    index order (0 = the all-zero slot 0); block s holds the 9^3 vertices
+    (8 bx + i, 8 by + j, 8 bz + k), row i + 9 j + 81 k, zero past vertex R_C - 1."""
+    nb = (R_C - 1 + COARSE_BLOCK - 1) // COARSE_BLOCK
+    mask = np.asarray(mask, np.uint8).reshape(-1)
+    nch = dense.shape[-1]
+    d = np.asarray(dense).reshape(R_C, R_C, R_C, nch)          # [z][y][x][ch]
+    index = np.zeros(nb ** 3, np.int32)
+    marked = np.nonzero(mask)[0]
+    index[marked] = np.arange(1, len(marked) + 1, dtype=np.int32)
+    blocks = np.zeros((1 + len(marked), 9, 9, 9, nch), d.dtype)  # [s][k][j][i][ch]
+    for s, e in enumerate(marked, start=1):
+        bx, by, bz = e % nb, (e // nb) % nb, e // (nb * nb)
+        x0, y0, z0 = COARSE_BLOCK * bx, COARSE_BLOCK * by, COARSE_BLOCK * bz
+        part = d[z0:z0 + 9, y0:y0 + 9, x0:x0 + 9]
+        blocks[s, :part.shape[0], :part.shape[1], :part.shape[2]] = part
+    return index, blocks.reshape(1 + len(marked), 729, nch)
+
+
 def oracle_for_scene(scene, tables=None, coarse=None, use_dist=True, dist_level=0) -> Oracle:
     """Oracle over a generated scene: builds the pyramid and distance grid itself (G
     on pyramid level dist_level)."""

@@ -283,6 +283,7 @@ extern "C" int32_t ngprt_render_backward(const ngprt_scene* scene, const ngprt_o
     memset(&p, 0, sizeof p);
     int32_t rc;
     if ((rc = make_grid(scene, p.m.g, fn)) != NGPRT_OK) return rc;
+    NGPRT_REQUIRE(scene->coarse_index == nullptr, "%s: gradients need the dense coarse grid (coarse_index is set)", fn);
     if ((rc = make_occ(occ, p.m.occ, fn)) != NGPRT_OK) return rc;
     if ((rc = check_opts(opts, fn)) != NGPRT_OK) return rc;
     NGPRT_REQUIRE(n_rays >= 0, "%s: n_rays=%lld", fn, (long long)n_rays);

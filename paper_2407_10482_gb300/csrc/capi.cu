@@ -68,7 +68,17 @@ int32_t make_grid(const ngprt_scene* s, Grid& g, const char* fn) {
     NGPRT_REQUIRE(!inv || s->attn_inv != nullptr, "%s: the invariant aggregations need attn_inv", fn);
     NGPRT_REQUIRE(s->aggregation != NGPRT_AGG_MLP || (s->agg_mlp != nullptr && ((uintptr_t)s->agg_mlp % 16) == 0),
                   "%s: the MLP aggregation needs 16-byte aligned agg_mlp", fn);
+    if (s->coarse_index) {
+        NGPRT_REQUIRE(s->coarse_blocks >= 1 && s->coarse_blocks <= (int64_t)(0xFFFFFFFFu / NGPRT_COARSE_BLOCK_ROWS),
+                      "%s: coarse_blocks=%lld", fn, (long long)s->coarse_blocks);
+        NGPRT_REQUIRE(((uintptr_t)s->coarse_index & 3) == 0, "%s: coarse_index must be 4-byte aligned", fn);
+    }
     memset(&g, 0, sizeof g);
+    if (s->coarse_index) {
+        g.coarse_index = s->coarse_index;
+        g.coarse_nb = (uint32_t)((s->R_C - 1 + NGPRT_COARSE_BLOCK - 1) / NGPRT_COARSE_BLOCK);
+        g.coarse_last = (uint32_t)(s->coarse_blocks - 1);
+    }
     g.agg = s->aggregation;
     g.attn_inv = s->attn_inv;
     g.agg_mlp = s->agg_mlp;

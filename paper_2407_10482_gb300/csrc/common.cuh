@@ -48,6 +48,9 @@ struct Grid {
     int32_t agg;                 // ngprt_aggregation
     const float* attn_inv;       // invariant attention logits
     const float* agg_mlp;        // MLP aggregation weights
+    const int32_t* coarse_index; // sparse coarse grid: block slots [nb^3]; NULL = dense
+    uint32_t coarse_nb;          // blocks per axis
+    uint32_t coarse_last;        // last stored block slot
 };
 
 // Coarse-grid channels per vertex under an aggregation (f~ plus the variant's logits).
@@ -163,6 +166,27 @@ __device__ __forceinline__ void grid_cell(float u, int N, int& base, float& w) {
     bf = fminf(fmaxf(bf, 0.0f), (float)(N - 2));
     base = (int)bf;
     w = fadd(fsub(pf, bf), __fmaf_rn(u, nm1, -pf));
+}
+
+// Row of the coarse vertex at the base corner of cell b and the row strides of
+// its y and z neighbours: dense [R_C^3] rows, or the 9^3-vertex block of the cell's
+// 8^3-cell block in the sparse grid (one index lookup for all 8 corners).
+__device__ __forceinline__ void coarse_base(const Grid& g, const int b[3], uint32_t& base, uint32_t& sy,
+                                            uint32_t& sz) {
+    if (g.coarse_index) {
+        const uint32_t nb = g.coarse_nb;
+        const uint32_t blk = ((uint32_t)b[0] >> 3) + nb * (((uint32_t)b[1] >> 3) + nb * ((uint32_t)b[2] >> 3));
+        const uint32_t slot = min((uint32_t)__ldg(g.coarse_index + blk), g.coarse_last);
+        base = slot * (uint32_t)NGPRT_COARSE_BLOCK_ROWS + (uint32_t)(b[0] & 7) +
+               9u * ((uint32_t)(b[1] & 7) + 9u * (uint32_t)(b[2] & 7));
+        sy = 9u;
+        sz = 81u;
+    } else {
+        const uint32_t R = (uint32_t)g.R_C;
+        base = (uint32_t)b[0] + R * ((uint32_t)b[1] + R * (uint32_t)b[2]);
+        sy = R;
+        sz = R * R;
+    }
 }
 
 // Absolute table row of vertex (x, y, z) of level l: dense row-major or the

@@ -192,6 +192,7 @@ static int32_t run_distortion(bool backward, const ngprt_scene* scene, const ngp
     memset(&p, 0, sizeof p);
     int32_t rc;
     if ((rc = make_grid(scene, p.m.g, fn)) != NGPRT_OK) return rc;
+    NGPRT_REQUIRE(scene->coarse_index == nullptr, "%s: gradients need the dense coarse grid (coarse_index is set)", fn);
     if ((rc = make_occ(occ, p.m.occ, fn)) != NGPRT_OK) return rc;
     if ((rc = check_opts(opts, fn)) != NGPRT_OK) return rc;
     if ((rc = check_agg(scene, opts, false, fn)) != NGPRT_OK) return rc;

@@ -155,7 +155,8 @@ __device__ __forceinline__ void sample_features(const Grid& g, const float u[3],
 #pragma unroll
     for (int a = 0; a < 3; ++a) grid_cell(u[a], g.R_C, b[a], w[a]);
     float2 acc[NC / 2];
-    const uint32_t R = (uint32_t)g.R_C;
+    uint32_t cb, sy, sz;
+    coarse_base(g, b, cb, sy, sz);
     if constexpr (DT == NGPRT_F16) {
         // FP16 tables: trilinear sums in packed half2 FMAs, converted once
         __half2 hacc[NC / 2];
@@ -163,7 +164,7 @@ __device__ __forceinline__ void sample_features(const Grid& g, const float u[3],
         for (int ch = 0; ch < NC / 2; ++ch) hacc[ch] = __float2half2_rn(0.0f);
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-            const uint32_t v = (uint32_t)(b[0] + (c & 1)) + R * ((uint32_t)(b[1] + ((c >> 1) & 1)) + R * (uint32_t)(b[2] + ((c >> 2) & 1)));
+            const uint32_t v = cb + (uint32_t)(c & 1) + sy * (uint32_t)((c >> 1) & 1) + sz * (uint32_t)((c >> 2) & 1);
             uint32_t q[NC / 2];
             load_pairs<NC>(static_cast<const uint16_t*>(g.coarse) + (size_t)v * NC, q);
             const __half2 cw2 = __float2half2_rn(corner_w(w, c));
@@ -178,7 +179,7 @@ __device__ __forceinline__ void sample_features(const Grid& g, const float u[3],
         for (int ch = 0; ch < NC / 2; ++ch) acc[ch] = make_float2(0.0f, 0.0f);
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-            const uint32_t v = (uint32_t)(b[0] + (c & 1)) + R * ((uint32_t)(b[1] + ((c >> 1) & 1)) + R * (uint32_t)(b[2] + ((c >> 2) & 1)));
+            const uint32_t v = cb + (uint32_t)(c & 1) + sy * (uint32_t)((c >> 1) & 1) + sz * (uint32_t)((c >> 2) & 1);
             float val[NC];
             load_channels<DT, NC>(g.coarse, v, val);
             const float cw = corner_w(w, c);

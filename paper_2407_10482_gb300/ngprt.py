@@ -19,6 +19,8 @@ from . import build as _build
 MAX_LEVELS = 32
 MAX_CAMERAS = 64
 STATE_FLOATS = 12
+COARSE_BLOCK = 8  # cells per axis of a sparse coarse-grid block
+COARSE_BLOCK_ROWS = 729  # its 9^3 stored vertices
 F32, F16, BF16 = 0, 1, 2
 _TORCH_DT = {F32: torch.float32, F16: torch.float16, BF16: torch.bfloat16}
 
@@ -36,7 +38,8 @@ class ngprt_scene(C.Structure):
                 ("table_dtype", C.c_int32), ("R_C", C.c_int32), ("mlp_layers", C.c_int32),
                 ("mlp_width", C.c_int32), ("mlp_dtype", C.c_int32), ("bounded", C.c_int32),
                 ("tables", C.c_void_p), ("coarse", C.c_void_p), ("mlp_w", C.c_void_p),
-                ("aggregation", C.c_int32), ("attn_inv", C.c_void_p), ("agg_mlp", C.c_void_p)]
+                ("aggregation", C.c_int32), ("attn_inv", C.c_void_p), ("agg_mlp", C.c_void_p),
+                ("coarse_index", C.c_void_p), ("coarse_blocks", C.c_int64)]
 
 
 class ngprt_occ(C.Structure):
@@ -76,6 +79,10 @@ _SIGS = {
     "ngprt_dilate_workspace_bytes": (C.c_size_t, [C.c_int32]),
     "ngprt_dilate": (C.c_int32, [_P, C.c_int32, C.c_int32, _P, _P, _P, C.c_size_t, _P]),
     "ngprt_render_workspace_bytes": (C.c_size_t, [_P, C.c_int64]),
+    "ngprt_coarse_block_mask": (C.c_int32, [_P, C.c_int32, _P, _P]),
+    "ngprt_coarse_sparsify_workspace_bytes": (C.c_size_t, [C.c_int32]),
+    "ngprt_coarse_sparsify": (C.c_int32, [_P, C.c_int32, C.c_int32, _P, _P, _P, C.c_int64, _P, _P, C.c_size_t,
+                                          _P]),
     "ngprt_wavefront_workspace_bytes": (C.c_size_t, [_P, C.c_int64]),
     "ngprt_render": (C.c_int32, [_P, _P, _P, C.c_int32, _P, _P, _P, C.c_int64, _P, _P, _P, _P, _P, _P, _P,
                                  _P, C.c_size_t, _P]),
@@ -279,6 +286,31 @@ def ngprt_render_backward(scene, occ, cams, n_cams, pixel_ids, rays_o, rays_d, n
         _ptr(g_coarse), _ptr(g_mlp), _ptr(g_attn_inv), _ptr(workspace), ws_bytes, _stream(stream)))
 
 
+def coarse_blocks_per_axis(R_C: int) -> int:
+    return (R_C - 1 + COARSE_BLOCK - 1) // COARSE_BLOCK
+
+
+def ngprt_coarse_block_mask(occ, R_C, block_mask, stream=None) -> None:
+    _check("ngprt_coarse_block_mask", lib().ngprt_coarse_block_mask(C.byref(occ), R_C, _ptr(block_mask),
+                                                                    _stream(stream)))
+
+
+def ngprt_coarse_sparsify_workspace_bytes(R_C) -> int:
+    return int(lib().ngprt_coarse_sparsify_workspace_bytes(R_C))
+
+
+def ngprt_coarse_sparsify(dense, R_C, row_bytes, block_mask, index, blocks, max_blocks, workspace,
+                          stream=None) -> int:
+    """Index (and, with `blocks`, the blocks) of the sparse coarse grid; returns the
+    stored block count (slot 0 = zeros included)."""
+    n = C.c_int64(0)
+    ws_bytes = workspace.numel() * workspace.element_size()
+    _check("ngprt_coarse_sparsify", lib().ngprt_coarse_sparsify(
+        _ptr(dense), R_C, row_bytes, _ptr(block_mask), _ptr(index), _ptr(blocks), max_blocks, C.byref(n),
+        _ptr(workspace), ws_bytes, _stream(stream)))
+    return int(n.value)
+
+
 def ngprt_shade(scene, ray_state, n_rays, bg, rgb, depth=None, opacity=None, stream=None) -> None:
     bgv = (C.c_float * 3)(*[float(b) for b in bg])
     _check("ngprt_shade", lib().ngprt_shade(C.byref(scene), _ptr(ray_state), n_rays, bgv, _ptr(rgb), _ptr(depth),
@@ -393,6 +425,29 @@ class DeviceScene:
         self.mlp_w = _device_array(mlp_w, _TORCH_DT[mlp_dtype], device)
         self.attn_inv = None if attn_inv is None else _device_array(attn_inv, torch.float32, device)
         self.agg_mlp = None if agg_mlp is None else _device_array(agg_mlp, torch.float32, device)
+        self.coarse_index = None
+        self.coarse_blocks = 0
+        self.refresh()
+
+    def sparsify_coarse(self, occ: "DeviceOcc") -> None:
+        """Replace the dense coarse grid by its block-indexed sparse form: the 8^3-cell
+        blocks that the occupied voxels of ``occ`` reach (ngprt_coarse_block_mask), each
+        stored as its 9^3 vertices.  Renders are unchanged; the reverse passes then
+        refuse the scene."""
+        assert self.coarse_index is None, "already sparse"
+        R_C = self.cfg.R_C
+        nb = coarse_blocks_per_axis(R_C)
+        dev = self.coarse.device
+        mask = torch.empty(nb ** 3, dtype=torch.uint8, device=dev)
+        ngprt_coarse_block_mask(occ.struct, R_C, mask)
+        index = torch.empty(nb ** 3, dtype=torch.int32, device=dev)
+        ws = torch.empty(ngprt_coarse_sparsify_workspace_bytes(R_C), dtype=torch.uint8, device=dev)
+        nch = self.coarse.shape[1]
+        row_bytes = nch * self.coarse.element_size()
+        n = ngprt_coarse_sparsify(self.coarse, R_C, row_bytes, mask, index, None, 0, ws)
+        blocks = torch.empty(n, COARSE_BLOCK_ROWS, nch, dtype=self.coarse.dtype, device=dev)
+        ngprt_coarse_sparsify(self.coarse, R_C, row_bytes, mask, index, blocks, n, ws)
+        self.coarse, self.coarse_index, self.coarse_blocks = blocks, index, n
         self.refresh()
 
     def refresh(self) -> None:
@@ -407,6 +462,7 @@ class DeviceScene:
         s.tables, s.coarse, s.mlp_w = _ptr(self.tables), _ptr(self.coarse), _ptr(self.mlp_w)
         s.aggregation = self.aggregation
         s.attn_inv, s.agg_mlp = _ptr(self.attn_inv), _ptr(self.agg_mlp)
+        s.coarse_index, s.coarse_blocks = _ptr(self.coarse_index), self.coarse_blocks
         self.struct = s
 
 

@@ -325,8 +325,9 @@ def default_options(cfg: SceneConfig, **kw) -> RenderOptions:
 
 def paper_config(L: int = 2, **kw) -> SceneConfig:
     """The paper's render-time shape (Sec. S2.1, S2.5; Tables 2 and 4): L fine levels
-    at 1024 * 2^l with T = 2^22, a 512^3 coarse grid (8 + 2L channels; the paper's is
-    sparse, this one dense), a 512^3 occupancy grid with 5 levels down to 32^3 and the
+    at 1024 * 2^l with T = 2^22, a 512^3 coarse grid (8 + 2L channels; drawn dense,
+    DeviceScene.sparsify_coarse stores it block-sparse as the paper does), a 512^3
+    occupancy grid with 5 levels down to 32^3 and the
     distance grid G at 256^3 (Sec. 3.3); hd's unbounded blob scene and orbit."""
     c = hd_config(name=f"paper_L{L}", L=L, N=[1024 * 2 ** l for l in range(L)], T_log2=22, R_C=512, R_O=512,
                   n_occ_levels=5, seed=7, dist_level=1)

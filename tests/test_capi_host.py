@@ -146,3 +146,37 @@ def test_step_autotune_matches_oracle(ng):
         want = O.step_autotune(g, n_mean, 3.0, 1e-3, float(np.float32(0.2217)))
         got = ng.ngprt_step_autotune(g, n_mean, 3.0, 1e-3, 0.2217)
         assert abs(got - want) <= 1e-6 * want
+
+
+def test_sparse_coarse_grid_validation(ng):
+    """The sparse coarse grid's fields are checked before any launch."""
+    lib = ng.lib()
+    s = ng.ngprt_scene()
+    s.L, s.T_log2, s.R_C, s.mlp_layers, s.mlp_width = 4, 12, 16, 2, 16
+    for i in range(4):
+        s.N[i] = 16 << i
+    s.tables = s.coarse = s.mlp_w = 256
+    o = ng.ngprt_occ(32, 3, 256, None)
+    opts = ng.render_opts(S.default_options(S.small_config()))
+
+    def render():
+        return lib.ngprt_render(C.byref(s), C.byref(o), None, 0, None, C.c_void_p(256), C.c_void_p(256), 4, None,
+                                C.byref(opts), C.c_void_p(256), None, None, None, None, None, 0, None)
+    s.coarse_index, s.coarse_blocks = 256, 0
+    assert render() == ng.ERR_INVALID_ARG and b"coarse_blocks" in lib.ngprt_last_error()
+    s.coarse_index, s.coarse_blocks = 258, 3
+    assert render() == ng.ERR_INVALID_ARG and b"coarse_index" in lib.ngprt_last_error()
+    s.coarse_index = 256
+    rc = lib.ngprt_render_backward(C.byref(s), C.byref(o), None, 0, None, C.c_void_p(256), C.c_void_p(256), 4,
+                                   C.byref(opts), C.c_void_p(256), C.c_void_p(256), None, None, C.c_void_p(256),
+                                   C.c_void_p(256), C.c_void_p(256), None, None, 0, None)
+    assert rc == ng.ERR_INVALID_ARG and b"dense coarse grid" in lib.ngprt_last_error()
+    assert ng.ngprt_coarse_sparsify_workspace_bytes(512) >= 16 + 2 * 4 * 256
+    assert ng.ngprt_coarse_sparsify_workspace_bytes(1) == 0
+    n = C.c_int64(0)
+    rc = lib.ngprt_coarse_sparsify(None, 512, 6, C.c_void_p(256), C.c_void_p(256), None, 0, C.byref(n),
+                                   C.c_void_p(256), 1 << 20, None)
+    assert rc == ng.ERR_INVALID_ARG and b"row_bytes" in lib.ngprt_last_error()
+    rc = lib.ngprt_coarse_sparsify(None, 512, 48, C.c_void_p(256), C.c_void_p(256), None, 0, C.byref(n),
+                                   C.c_void_p(256), 8, None)
+    assert rc == ng.ERR_WORKSPACE
