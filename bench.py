@@ -358,7 +358,18 @@ def paper_shape(args, dev, stream, flush):
             rend = ng.Renderer(ds, docc, device=dev)
             o = rend.render(opts, cams=cams, W=cfg.W, H=cfg.H, stats=True)
             ms = _timed(lambda: rend.render(opts, cams=cams, W=cfg.W, H=cfg.H, out=o), stream, flush, 5, 3)
-            row["fp32" if dt == 0 else "fp16_tc"] = {"ms_per_frame": ms, "frames_per_s": 1000.0 / ms}
+            key = "fp32" if dt == 0 else "fp16_tc"
+            row[key] = {"ms_per_frame": ms, "frames_per_s": 1000.0 / ms}
+            ref_rgb = o["rgb"].clone()
+            # the same frame through the block-sparse coarse grid (identical pixels)
+            ds.sparsify_coarse(docc)
+            o_s = rend.render(opts, cams=cams, W=cfg.W, H=cfg.H)
+            ms_s = _timed(lambda: rend.render(opts, cams=cams, W=cfg.W, H=cfg.H, out=o_s), stream, flush, 5, 3)
+            row[key + "_sparse_coarse"] = {"ms_per_frame": ms_s, "frames_per_s": 1000.0 / ms_s,
+                                           "blocks": ds.coarse_blocks,
+                                           "grid_bytes": ds.coarse.numel() * ds.coarse.element_size(),
+                                           "identical_to_dense": bool(torch.equal(o_s["rgb"], ref_rgb))}
+            del o_s, ref_rgb
             if dt == 0:
                 st = o["stats"].float().mean(0)
                 st0 = rend.render(opts, cams=cams, W=cfg.W, H=cfg.H, stats=True, use_dist=False)["stats"].float().mean(0)
@@ -368,7 +379,8 @@ def paper_shape(args, dev, stream, flush):
         out[f"L{L}"] = row
         del sc, docc
         torch.cuda.empty_cache()
-    out["config"] = "N_l = 1024 * 2^l, T = 2^22, R_C = 512 dense (8 + 2L channels), R_O = 512 (5 levels), G at 256^3"
+    out["config"] = ("N_l = 1024 * 2^l, T = 2^22, R_C = 512 dense (8 + 2L channels; *_sparse_coarse: 8^3-cell "
+                     "blocks of 9^3 vertices reached by the occupancy), R_O = 512 (5 levels), G at 256^3")
     return out
 
 
