@@ -328,7 +328,7 @@ int32_t ngprt_shade(const ngprt_scene* scene, const float* ray_state, int64_t n_
  * float), dL/d mlp_w into g_mlp (float, mlp_w's layout) and, for the spatially
  * invariant gate forms (SEPARATE_INV, SHARED_INV), dL/d attn_inv into g_attn_inv
  * (float, attn_inv's layout; ignored, and may be NULL, for the other forms).
- * Aggregations: SEPARATE_V (Eq. 8, any attn_mode; L = 1, 2, 4, 16), and SHARED_V,
+ * Aggregations: SEPARATE_V (Eq. 8, any attn_mode; L = 1, 2, 3, 4, 8, 16), and SHARED_V,
  * SEPARATE_INV, SHARED_INV, SUM (Table 3; L = 2, 4, 16); the MLP form has no reverse
  * pass (NGPRT_ERR_UNSUPPORTED).  Each ray is marched again; the sample set is the
  * forward's.  Table, grid and invariant-logit gradients are atomic adds, so their
@@ -421,7 +421,7 @@ int32_t ngprt_huber_loss(const float* rgb, const float* target, int64_t n, float
  * ngprt_distortion_backward ACCUMULATES scale * dL_dist/d(parameters) into g_tables
  * and g_coarse (FP32, layouts of the scene) from that dist_state: the density path
  * only (sigma~, the omega logits and the fine density channel).  Both need F32
- * tables, the Eq. 8 aggregation and L in {1, 2, 4, 16}; rays as for ngprt_render.
+ * tables, the Eq. 8 aggregation and L in {1, 2, 3, 4, 8, 16}; rays as for ngprt_render.
  */
 int32_t ngprt_distortion_loss(const ngprt_scene* scene, const ngprt_occ* occ, const ngprt_camera* cams,
                               int32_t n_cams, const int32_t* pixel_ids, const float* rays_o, const float* rays_d,

@@ -291,8 +291,8 @@ extern "C" int32_t ngprt_render_backward(const ngprt_scene* scene, const ngprt_o
                   "%s: gradients need F32 tables and F32 MLP weights", fn);
     const int agg = scene->aggregation;
     if (agg == NGPRT_AGG_SEPARATE_V) {
-        if (!march_supports(scene->L) || !(scene->L == 1 || scene->L == 2 || scene->L == 4 || scene->L == 16)) {
-            set_error("%s: no backward kernel for L=%d (built: 1, 2, 4, 16)", fn, scene->L);
+        if (!march_supports(scene->L)) {
+            set_error("%s: no backward kernel for L=%d (built: 1, 2, 3, 4, 8, 16)", fn, scene->L);
             return NGPRT_ERR_UNSUPPORTED;
         }
     } else {
@@ -363,7 +363,9 @@ extern "C" int32_t ngprt_render_backward(const ngprt_scene* scene, const ngprt_o
     switch (scene->L) {
         case 1: launch_bwd<1, NGPRT_AGG_SEPARATE_V>(p, grid, st); break;
         case 2: launch_bwd<2, NGPRT_AGG_SEPARATE_V>(p, grid, st); break;
+        case 3: launch_bwd<3, NGPRT_AGG_SEPARATE_V>(p, grid, st); break;
         case 4: launch_bwd<4, NGPRT_AGG_SEPARATE_V>(p, grid, st); break;
+        case 8: launch_bwd<8, NGPRT_AGG_SEPARATE_V>(p, grid, st); break;
         default: launch_bwd<16, NGPRT_AGG_SEPARATE_V>(p, grid, st); break;
     }
     return cuda_status(fn);

@@ -199,8 +199,8 @@ static int32_t run_distortion(bool backward, const ngprt_scene* scene, const ngp
     NGPRT_REQUIRE(n_rays >= 0, "%s: n_rays=%lld", fn, (long long)n_rays);
     NGPRT_REQUIRE(scene->table_dtype == NGPRT_F32, "%s: needs F32 tables", fn);
     const int L = scene->L;
-    if (!(L == 1 || L == 2 || L == 4 || L == 16)) {
-        set_error("%s: no kernel for L=%d (built: 1, 2, 4, 16)", fn, L);
+    if (!(L == 1 || L == 2 || L == 3 || L == 4 || L == 8 || L == 16)) {
+        set_error("%s: no kernel for L=%d (built: 1, 2, 3, 4, 8, 16)", fn, L);
         return NGPRT_ERR_UNSUPPORTED;
     }
     dim3 grid;
@@ -220,7 +220,9 @@ static int32_t run_distortion(bool backward, const ngprt_scene* scene, const ngp
     switch (L) {
         case 1: launch_dist<1>(backward, p, grid, st); break;
         case 2: launch_dist<2>(backward, p, grid, st); break;
+        case 3: launch_dist<3>(backward, p, grid, st); break;
         case 4: launch_dist<4>(backward, p, grid, st); break;
+        case 8: launch_dist<8>(backward, p, grid, st); break;
         default: launch_dist<16>(backward, p, grid, st); break;
     }
     return cuda_status(fn);

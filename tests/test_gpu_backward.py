@@ -64,6 +64,13 @@ def test_backward_small_bounded(ng, attn_mode):
     _run(ng, cfg, S.default_options(cfg, t_term=0.0, attn_mode=attn_mode))
 
 
+@pytest.mark.parametrize("L,N", [(3, [16, 40, 100]), (8, [16 + 12 * l for l in range(8)])])
+def test_backward_three_and_eight_levels(ng, L, N):
+    """The paper's L = 3 shape and an 8-level stack (dense and hashed levels mixed)."""
+    cfg = S.small_config(L=L, N=N, blob_std=(0.05, 0.15))
+    _run(ng, cfg, S.default_options(cfg, t_term=0.0))
+
+
 def test_backward_unbounded_wide_mlp(ng):
     cfg = S.small_config(bounded=False, R_O=32, n_occ_levels=4, t_min=0.05, r_far=16.0, shell=True, mlp_layers=3,
                          mlp_width=64, step_base=2 * 3 ** 0.5 / 256, blob_std=(0.05, 0.15))

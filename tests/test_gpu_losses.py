@@ -82,9 +82,10 @@ def test_distortion_loss_per_ray(ng, cfg_name):
     assert (ref[:, 0] > 0).sum() > n // 10
 
 
-@pytest.mark.parametrize("attn_mode", [0, 1, 2])
-def test_distortion_backward(ng, attn_mode):
-    cfg = S.small_config(blob_std=(0.05, 0.15))
+@pytest.mark.parametrize("attn_mode,L", [(0, 4), (1, 4), (2, 4), (0, 3), (0, 8)])
+def test_distortion_backward(ng, attn_mode, L):
+    N = {3: [16, 40, 100], 4: [16, 32, 64, 128], 8: [16 + 12 * l for l in range(8)]}[L]
+    cfg = S.small_config(blob_std=(0.05, 0.15), L=L, N=N)
     sc, ds, docc, orc = _scene(ng, cfg)
     opts = S.default_options(cfg, t_term=0.0, attn_mode=attn_mode)
     o, d = S.random_rays(4096, 21, True)
