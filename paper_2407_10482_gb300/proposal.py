@@ -25,7 +25,11 @@ from . import ngprt as ng
 class ProposalConfig:
     in_scale: float = 3.0      # origins are divided by this (the orbit radius)
     t_scale: float = 16.0      # t_near, t_far = t_scale * sigmoid(.)
-    margin_near: float = 0.5   # world units the march starts before t_near
+    # world units the march starts before t_near.  The rays the proposal gets wrong
+    # are opaque ones started behind their surface, which the opacity fallback cannot
+    # see; on the hd scene a margin of 1.0 against 0.5 lifts the worst of 8 views
+    # from 45.9 to 48.4 dB against the plain render for 1% more frame time
+    margin_near: float = 1.0
     margin_far: float = float("inf")  # after t_far (inf: no far clip, termination ends the ray)
     a_min: float = 0.01        # predicted opacity below which nothing is marched
     fallback: float = 0.01     # re-march when a_hat - A(interval) exceeds this
