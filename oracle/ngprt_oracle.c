@@ -786,8 +786,8 @@ void or_render_backward(const or_scene* s, const or_occ* oc, const or_opts* op,
                         const float* cams, int n_cams, int W, int H, const int32_t* pix,
                         const float* rays_o, const float* rays_d, int n,
                         const double* d_rgb, const double* d_depth, const double* d_opacity,
-                        double* g_tables, double* g_coarse, double* g_mlp, double* g_attn_inv) {
-    if (s->aggregation > 4) return; /* the tiny-MLP aggregation has no reverse pass (oracle.py refuses it) */
+                        double* g_tables, double* g_coarse, double* g_mlp, double* g_attn_inv,
+                        double* g_agg_mlp) {
     int cap = op->max_samples > 0 ? op->max_samples : 1;
     or_sample* sm = (or_sample*)malloc(sizeof(or_sample) * (size_t)cap);
     double* qg = (double*)malloc(sizeof(double) * (size_t)cap);
@@ -874,7 +874,58 @@ void or_render_backward(const or_scene* s, const or_occ* oc, const or_opts* op,
                 for (int ch = 0; ch < nch; ++ch) coarse[ch] += cwt[c] * s->coarse[cv[c] * nch + ch];
             }
             for (int ch = 0; ch < OR_NFEAT; ++ch) g_coarse_v[ch] = g_f[ch];
-            for (int l = 0; l < s->L; ++l) {
+            if (s->aggregation == 5) {
+                /* Instant-NGP's tiny MLP in place of the attention: f = f~ + W2 relu(W1 x),
+                 * x = [f^1, ..., f^L].  Its reverse: dW2 += g_f relu(h)^T, g_h = (W2^T g_f)
+                 * where h > 0, dW1 += g_h x^T, g_x = W1^T g_h, then each level's entries. */
+                int nx = OR_NFEAT * s->L;
+                const double* w1 = s->agg_mlp;
+                const double* w2 = s->agg_mlp + (size_t)OR_AGG_HIDDEN * nx;
+                double xs[OR_NFEAT * OR_MAXL], h[OR_AGG_HIDDEN], gh[OR_AGG_HIDDEN], gx[OR_NFEAT * OR_MAXL];
+                uint64_t ents[OR_MAXL][8];
+                double ews[OR_MAXL][8];
+                memset(xs, 0, sizeof xs);
+                for (int l = 0; l < s->L; ++l) {
+                    int bl[3];
+                    double wl[3];
+                    or_cell(sp->u, s->N[l], bl, wl);
+                    uint64_t off = or_level_offset(s->N, s->L, s->T_log2, l);
+                    for (int c = 0; c < 8; ++c) {
+                        int xx = bl[0] + (c & 1), yy = bl[1] + ((c >> 1) & 1), zz = bl[2] + ((c >> 2) & 1);
+                        ents[l][c] = off + or_level_entry(s->N[l], T, xx, yy, zz);
+                        ews[l][c] = or_corner_weight(wl, c);
+                        for (int ch = 0; ch < OR_NFEAT; ++ch)
+                            xs[OR_NFEAT * l + ch] += ews[l][c] * s->tables[ents[l][c] * OR_NFEAT + ch];
+                    }
+                }
+                for (int j = 0; j < OR_AGG_HIDDEN; ++j) {
+                    double acc = 0.0;
+                    for (int q = 0; q < nx; ++q) acc += w1[(size_t)j * nx + q] * xs[q];
+                    h[j] = acc;
+                }
+                for (int j = 0; j < OR_AGG_HIDDEN; ++j) {
+                    double ga = 0.0;
+                    for (int k = 0; k < OR_NFEAT; ++k) ga += w2[k * OR_AGG_HIDDEN + j] * g_f[k];
+                    gh[j] = h[j] > 0.0 ? ga : 0.0;
+                }
+                if (g_agg_mlp) {
+                    double* gw2 = g_agg_mlp + (size_t)OR_AGG_HIDDEN * nx;
+                    for (int k = 0; k < OR_NFEAT; ++k)
+                        for (int j = 0; j < OR_AGG_HIDDEN; ++j) gw2[k * OR_AGG_HIDDEN + j] += g_f[k] * fmax(h[j], 0.0);
+                    for (int j = 0; j < OR_AGG_HIDDEN; ++j)
+                        for (int q = 0; q < nx; ++q) g_agg_mlp[(size_t)j * nx + q] += gh[j] * xs[q];
+                }
+                for (int q = 0; q < nx; ++q) {
+                    double acc = 0.0;
+                    for (int j = 0; j < OR_AGG_HIDDEN; ++j) acc += w1[(size_t)j * nx + q] * gh[j];
+                    gx[q] = acc;
+                }
+                for (int l = 0; l < s->L; ++l)
+                    for (int c = 0; c < 8; ++c)
+                        for (int ch = 0; ch < OR_NFEAT; ++ch)
+                            g_tables[ents[l][c] * OR_NFEAT + ch] += ews[l][c] * gx[OR_NFEAT * l + ch];
+            }
+            for (int l = 0; l < (s->aggregation == 5 ? 0 : s->L); ++l) {
                 /* the gates of this level and whether each is shared by both modalities */
                 double om = 1.0, be = 1.0;
                 int shared = 0;

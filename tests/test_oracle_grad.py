@@ -31,7 +31,7 @@ def _setup(attn_mode=0, bounded=True):
     return sc, orc, opts, o, d, cot
 
 
-def _fd(orc, opts, o, d, cot, arr, flat_idx, direction=None):
+def _fd(orc, opts, o, d, cot, arr, flat_idx, direction=None, H=H):
     base = arr.reshape(-1)
     keep = base.copy()
     if direction is None:
@@ -104,10 +104,11 @@ def test_reverse_pass_per_output(which):
         assert abs(fd - an) <= 1e-7 + 1e-4 * abs(an), (which, name, "sigma", fd, an)
 
 
-@pytest.mark.parametrize("agg", [1, 2, 3, 4])
+@pytest.mark.parametrize("agg", [1, 2, 3, 4, 5])
 def test_reverse_pass_of_aggregation_variants(agg):
-    """Table 3's gate forms: a per-level logit in the coarse grid (Shared (V)), constant
-    logits (both Inv forms, gradient into attn_inv) and the plain sum (no logits)."""
+    """Table 3's forms: a per-level logit in the coarse grid (Shared (V)), constant
+    logits (both Inv forms, gradient into attn_inv), the plain sum (no logits) and the
+    tiny MLP (gradient into its weights W1, W2 and, through them, every level)."""
     cfg = S.small_config(blob_std=(0.05, 0.15), aggregation=agg)
     sc = S.make_scene(cfg)
     if sc.coarse.shape[1] > 8:
@@ -128,16 +129,20 @@ def test_reverse_pass_of_aggregation_variants(agg):
         names.append(("attn_inv", orc.attn_inv))
     else:
         assert g["attn_inv"] is None
+    if orc.agg_mlp is not None:
+        names.append(("agg_mlp", orc.agg_mlp))
     for name, arr in names:
         gr = g[name].reshape(-1)
         nz = np.nonzero(np.abs(gr) > 1e-8)[0]
         assert len(nz) > 0, name
+        # the MLP form's ReLUs put kinks within 1e-3 of some weights: a smaller step
+        h = 1e-4 if agg == 5 else H
         for k in rng.choice(nz, min(12, len(nz)), replace=False):
-            fd = _fd(orc, opts, o, d, cot, arr, k)
+            fd = _fd(orc, opts, o, d, cot, arr, k, H=h)
             assert abs(fd - gr[k]) <= 1e-6 + 1e-4 * abs(gr[k]), (name, k, fd, gr[k])
         v = rng.normal(size=arr.size)
         v /= np.linalg.norm(v)
-        fd = _fd(orc, opts, o, d, cot, arr, None, v)
+        fd = _fd(orc, opts, o, d, cot, arr, None, v, H=h)
         an = float(gr @ v)
         assert abs(fd - an) <= 1e-6 + 1e-4 * abs(an), (name, fd, an)
     if agg == 1:
