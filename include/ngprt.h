@@ -327,20 +327,27 @@ int32_t ngprt_shade(const ngprt_scene* scene, const float* ray_state, int64_t n_
  * ([n_entries][8] float), dL/d coarse into g_coarse ([R_C^3][ngprt_coarse_channels]
  * float), dL/d mlp_w into g_mlp (float, mlp_w's layout) and, for the spatially
  * invariant gate forms (SEPARATE_INV, SHARED_INV), dL/d attn_inv into g_attn_inv
- * (float, attn_inv's layout; ignored, and may be NULL, for the other forms).
+ * (float, attn_inv's layout; ignored, and may be NULL, for the other forms) and, for
+ * the MLP form, dL/d agg_mlp into g_agg_mlp (float, agg_mlp's layout; ignored, and
+ * may be NULL, otherwise).
  * Aggregations: SEPARATE_V (Eq. 8, any attn_mode; L = 1, 2, 3, 4, 8, 16), and SHARED_V,
- * SEPARATE_INV, SHARED_INV, SUM (Table 3; L = 2, 4, 16); the MLP form has no reverse
- * pass (NGPRT_ERR_UNSUPPORTED).  Each ray is marched again; the sample set is the
- * forward's.  Table, grid and invariant-logit gradients are atomic adds, so their
- * float summation order varies from run to run.
+ * SEPARATE_INV, SHARED_INV, SUM and MLP (Table 3; L = 2, 4, 16).  Each ray is marched
+ * again; the sample set is the forward's.  Table, grid, logit and weight gradients
+ * are atomic adds, so their float summation order varies from run to run.
  *   d_rgb [n][3]; d_depth, d_opacity [n] or NULL (zero).
+ *   workspace: ngprt_render_backward_workspace_bytes(scene, opts, n_rays) bytes,
+ *              16-byte aligned (the MLP form keeps one (f^1..f^L, g_f) record per
+ *              sample there: n_rays x opts->max_samples x (8L + 8) floats).
  */
+size_t ngprt_render_backward_workspace_bytes(const ngprt_scene* scene, const ngprt_render_opts* opts,
+                                             int64_t n_rays);
 int32_t ngprt_render_backward(const ngprt_scene* scene, const ngprt_occ* occ, const ngprt_camera* cams,
                               int32_t n_cams, const int32_t* pixel_ids, const float* rays_o,
                               const float* rays_d, int64_t n_rays, const ngprt_render_opts* opts,
                               const float* ray_state, const float* d_rgb, const float* d_depth,
                               const float* d_opacity, float* g_tables, float* g_coarse, float* g_mlp,
-                              float* g_attn_inv, void* workspace, size_t ws_bytes, void* stream);
+                              float* g_attn_inv, float* g_agg_mlp, void* workspace, size_t ws_bytes,
+                              void* stream);
 
 /* ------------------------------------------------------------------------------
  * Learned proposal (not in the paper, which leaves adaptive sampling aside in

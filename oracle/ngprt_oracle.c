@@ -787,7 +787,7 @@ void or_render_backward(const or_scene* s, const or_occ* oc, const or_opts* op,
                         const float* rays_o, const float* rays_d, int n,
                         const double* d_rgb, const double* d_depth, const double* d_opacity,
                         double* g_tables, double* g_coarse, double* g_mlp, double* g_attn_inv,
-                        double* g_agg_mlp) {
+                        double* g_agg_mlp, int32_t* kink) {
     int cap = op->max_samples > 0 ? op->max_samples : 1;
     or_sample* sm = (or_sample*)malloc(sizeof(or_sample) * (size_t)cap);
     double* qg = (double*)malloc(sizeof(double) * (size_t)cap);
@@ -899,9 +899,15 @@ void or_render_backward(const or_scene* s, const or_occ* oc, const or_opts* op,
                     }
                 }
                 for (int j = 0; j < OR_AGG_HIDDEN; ++j) {
-                    double acc = 0.0;
-                    for (int q = 0; q < nx; ++q) acc += w1[(size_t)j * nx + q] * xs[q];
+                    double acc = 0.0, mag = 0.0;
+                    for (int q = 0; q < nx; ++q) {
+                        acc += w1[(size_t)j * nx + q] * xs[q];
+                        mag += fabs(w1[(size_t)j * nx + q] * xs[q]);
+                    }
                     h[j] = acc;
+                    /* a unit this close to its ReLU kink may switch sides in FP32: the
+                     * ray's gradient is then not comparable element by element */
+                    if (kink && fabs(acc) <= 1e-5 * mag) kink[i] = 1;
                 }
                 for (int j = 0; j < OR_AGG_HIDDEN; ++j) {
                     double ga = 0.0;

@@ -318,6 +318,9 @@ class Oracle:
 
     def render_backward(self, opts, d_rgb=None, d_depth=None, d_opacity=None, cams=None, pix=None,
                         rays_o=None, rays_d=None, W=None, H=None):
+        """Gradients (+ for the MLP form, "kink": per ray 1 when a hidden unit of one
+        of its samples lies within 1e-5 relative of its ReLU kink, where FP32 may take
+        the other side)."""
         W = W or self.cfg.W
         H = H or self.cfg.H
         cams, pix, ro, rd, n = self._rays(cams, pix, rays_o, rays_d)
@@ -326,6 +329,7 @@ class Oracle:
         g_m = np.zeros_like(self.mlp_w)
         g_i = np.zeros_like(self.attn_inv) if self.attn_inv is not None else None
         g_a = np.zeros_like(self.agg_mlp) if self.agg_mlp is not None else None
+        kink = np.zeros(n, np.int32)
         op = self._opts(opts)
         # hold the converted cotangents in locals: a temporary freed before the call
         # would hand the C code a dangling pointer
@@ -333,8 +337,8 @@ class Oracle:
         lib().or_render_backward(C.byref(self._s), C.byref(self._o), C.byref(op), _p(cams),
                                  C.c_int(0 if cams is None else len(cams)), C.c_int(W), C.c_int(H),
                                  _p(pix), _p(ro), _p(rd), C.c_int(n), _p(cr), _p(cd), _p(co),
-                                 _p(g_t), _p(g_c), _p(g_m), _p(g_i), _p(g_a))
-        return dict(tables=g_t, coarse=g_c, mlp_w=g_m, attn_inv=g_i, agg_mlp=g_a)
+                                 _p(g_t), _p(g_c), _p(g_m), _p(g_i), _p(g_a), _p(kink))
+        return dict(tables=g_t, coarse=g_c, mlp_w=g_m, attn_inv=g_i, agg_mlp=g_a, kink=kink)
 
     def render_dot(self, opts, d_rgb=None, d_depth=None, d_opacity=None, cams=None, pix=None,
                    rays_o=None, rays_d=None, W=None, H=None) -> float:

@@ -272,12 +272,30 @@ bool mlp_supports(int width, int layers);
 
 using namespace ngprt;
 
+// Per-ray cotangent records at the head of the reverse pass's workspace (256-byte
+// rounded, plus 256 bytes of slack as for the forward's state).
+static size_t cot_bytes(int64_t n) {
+    return ((size_t)n * kCotFloats * sizeof(float) + 255) / 256 * 256 + 256;
+}
+
+extern "C" size_t ngprt_render_backward_workspace_bytes(const ngprt_scene* scene, const ngprt_render_opts* opts,
+                                                        int64_t n_rays) {
+    if (!scene || n_rays < 0) return 0;
+    size_t b = cot_bytes(n_rays);
+    if (scene->aggregation == NGPRT_AGG_MLP) {
+        const int64_t ms = opts && opts->max_samples > 0 ? opts->max_samples : 0;
+        b += 256 + (size_t)n_rays * (size_t)ms * (size_t)(kNFeat * (scene->L + 1)) * sizeof(float);
+    }
+    return b;
+}
+
 extern "C" int32_t ngprt_render_backward(const ngprt_scene* scene, const ngprt_occ* occ, const ngprt_camera* cams,
                                          int32_t n_cams, const int32_t* pixel_ids, const float* rays_o,
                                          const float* rays_d, int64_t n_rays, const ngprt_render_opts* opts,
                                          const float* ray_state, const float* d_rgb, const float* d_depth,
                                          const float* d_opacity, float* g_tables, float* g_coarse, float* g_mlp,
-                                         float* g_attn_inv, void* workspace, size_t ws_bytes, void* stream) {
+                                         float* g_attn_inv, float* g_agg_mlp, void* workspace, size_t ws_bytes,
+                                         void* stream) {
     const char* fn = "ngprt_render_backward";
     MarchBwdParams p;
     memset(&p, 0, sizeof p);
@@ -298,10 +316,6 @@ extern "C" int32_t ngprt_render_backward(const ngprt_scene* scene, const ngprt_o
     } else {
         NGPRT_REQUIRE(opts->attn_mode == 0, "%s: attn_mode=%d applies to the SEPARATE_V aggregation only", fn,
                       opts->attn_mode);
-        if (agg == NGPRT_AGG_MLP) {
-            set_error("%s: the MLP aggregation has no reverse pass", fn);
-            return NGPRT_ERR_UNSUPPORTED;
-        }
         if (!march_bwd_agg_supports(scene->L)) {
             set_error("%s: aggregation %d has no backward kernel for L=%d (built: 2, 4, 16)", fn, agg, scene->L);
             return NGPRT_ERR_UNSUPPORTED;
@@ -317,9 +331,11 @@ extern "C" int32_t ngprt_render_backward(const ngprt_scene* scene, const ngprt_o
     NGPRT_REQUIRE(ray_state && d_rgb && g_tables && g_coarse && g_mlp, "%s: NULL buffer", fn);
     const bool inv = agg == NGPRT_AGG_SEPARATE_INV || agg == NGPRT_AGG_SHARED_INV;
     NGPRT_REQUIRE(!inv || g_attn_inv, "%s: g_attn_inv is NULL (aggregation %d)", fn, agg);
+    NGPRT_REQUIRE(agg != NGPRT_AGG_MLP || (g_agg_mlp && ((uintptr_t)g_agg_mlp & 3) == 0),
+                  "%s: g_agg_mlp is NULL (the MLP aggregation)", fn);
     NGPRT_REQUIRE(((uintptr_t)g_tables & 15) == 0 && ((uintptr_t)g_coarse & 15) == 0 && ((uintptr_t)ray_state & 15) == 0,
                   "%s: g_tables, g_coarse, ray_state must be 16-byte aligned", fn);
-    const size_t need = ngprt_render_workspace_bytes(scene, n_rays);
+    const size_t need = ngprt_render_backward_workspace_bytes(scene, opts, n_rays);
     if (!workspace || ws_bytes < need) {
         set_error("%s: workspace %zu bytes < %zu needed", fn, ws_bytes, need);
         return NGPRT_ERR_WORKSPACE;
@@ -356,8 +372,18 @@ extern "C" int32_t ngprt_render_backward(const ngprt_scene* scene, const ngprt_o
     p.g_tables = g_tables;
     p.g_coarse = g_coarse;
     p.g_attn_inv = inv ? g_attn_inv : nullptr;
+    if (agg == NGPRT_AGG_MLP) {
+        // after the per-ray cotangents: the record count, then n_rays x max_samples records
+        char* w = static_cast<char*>(workspace) + cot_bytes(n_rays);
+        p.n_records = reinterpret_cast<int32_t*>(w);
+        p.records = reinterpret_cast<float*>(w + 256);
+        p.rec_capacity = n_rays * (int64_t)opts->max_samples;
+        cudaMemsetAsync(p.n_records, 0, sizeof(int32_t), st);
+    }
     if (agg != NGPRT_AGG_SEPARATE_V) {
         launch_bwd_agg(scene->L, agg, p, grid, st);
+        if (agg == NGPRT_AGG_MLP)
+            launch_bwd_agg_mlp_wgrad(scene->L, p, scene->agg_mlp, g_agg_mlp, st);
         return cuda_status(fn);
     }
     switch (scene->L) {

@@ -22,7 +22,17 @@ struct MarchBwdParams {
     float* g_tables;
     float* g_coarse;
     float* g_attn_inv;  // constant gate logits' gradient (SEPARATE_INV, SHARED_INV)
+    float* records;     // MLP form: per-sample (f^1..f^L, g_f) records for the weight gradient
+    int32_t* n_records; // their count (device)
+    int64_t rec_capacity;
 };
+
+// Floats of one MLP-form sample record: the level features x (8L) and the feature
+// cotangent g_f (8).
+template <int L>
+__host__ __device__ constexpr int mlp_record_floats() {
+    return kNFeat * L + kNFeat;
+}
 
 __device__ __forceinline__ void atomic_add4(float* p, float a, float b, float c, float d) {
 #ifdef NGPRT_SCALAR_ATOMICS
@@ -46,7 +56,67 @@ __host__ __device__ constexpr int n_inv_logits() {
 // ([0, 2L)), sigma^l and q^l ([2L, 4L)) and the invariant logits' sums.
 template <int L, int AGG>
 __host__ __device__ constexpr int bwd_slots() {
-    return 4 * L + n_inv_logits<L, AGG>();
+    return AGG == NGPRT_AGG_MLP ? kNFeat * L + NGPRT_AGG_MLP_HIDDEN : 4 * L + n_inv_logits<L, AGG>();
+}
+
+// Reverse of the tiny-MLP aggregation f = f~ + W2 relu(W1 x) at one sample, x =
+// [f^1..f^L] and the pre-activations h left in the slots by the forward half:
+// g_h = (W2^T g_f) where h > 0 (written over h), then each level's g_x^l = W1^T g_h
+// restricted to its 8 inputs, added to its 8 corner entries times the corner weight.
+template <int L>
+__device__ __forceinline__ void scatter_mlp_levels(const Grid& g, const float u[3], const float gf[8], float* slots,
+                                                   int stride, float* g_tables) {
+    constexpr int kHid = NGPRT_AGG_MLP_HIDDEN;
+    constexpr int NX = kNFeat * L;
+    const float4* w2 = reinterpret_cast<const float4*>(g.agg_mlp + (size_t)kHid * NX);
+#pragma unroll 2
+    for (int j4 = 0; j4 < kHid / 4; ++j4) {
+        float4 ga = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll
+        for (int k = 0; k < kNFeat; ++k) {
+            const float4 a = __ldg(w2 + k * (kHid / 4) + j4);
+            ga.x = fmaf(a.x, gf[k], ga.x);
+            ga.y = fmaf(a.y, gf[k], ga.y);
+            ga.z = fmaf(a.z, gf[k], ga.z);
+            ga.w = fmaf(a.w, gf[k], ga.w);
+        }
+        float* hp = slots + (size_t)(NX + 4 * j4) * stride;
+        hp[0] = hp[0] > 0.0f ? ga.x : 0.0f;
+        hp[stride] = hp[stride] > 0.0f ? ga.y : 0.0f;
+        hp[2 * stride] = hp[2 * stride] > 0.0f ? ga.z : 0.0f;
+        hp[3 * stride] = hp[3 * stride] > 0.0f ? ga.w : 0.0f;
+    }
+    const float4* w1 = reinterpret_cast<const float4*>(g.agg_mlp);
+#pragma unroll 1
+    for (int l = 0; l < L; ++l) {
+        float gx[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll 4
+        for (int j = 0; j < kHid; ++j) {
+            const float gh = slots[(NX + j) * stride];
+            const float4 a = __ldg(w1 + 2 * (L * j + l)), b = __ldg(w1 + 2 * (L * j + l) + 1);
+            gx[0] = fmaf(a.x, gh, gx[0]);
+            gx[1] = fmaf(a.y, gh, gx[1]);
+            gx[2] = fmaf(a.z, gh, gx[2]);
+            gx[3] = fmaf(a.w, gh, gx[3]);
+            gx[4] = fmaf(b.x, gh, gx[4]);
+            gx[5] = fmaf(b.y, gh, gx[5]);
+            gx[6] = fmaf(b.z, gh, gx[6]);
+            gx[7] = fmaf(b.w, gh, gx[7]);
+        }
+        int bl[3];
+        float wl[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) grid_cell(u[a], g.N[l], bl[a], wl[a]);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const uint32_t row = level_row(g, l, (uint32_t)(bl[0] + (c & 1)), (uint32_t)(bl[1] + ((c >> 1) & 1)),
+                                           (uint32_t)(bl[2] + ((c >> 2) & 1)));
+            const float cw = corner_w(wl, c);
+            float* gp = g_tables + (size_t)row * 8;
+            atomic_add4(gp, cw * gx[0], cw * gx[1], cw * gx[2], cw * gx[3]);
+            atomic_add4(gp + 4, cw * gx[4], cw * gx[5], cw * gx[6], cw * gx[7]);
+        }
+    }
 }
 
 // Reverse of sample_features at u.  The sample's feature cotangent is
@@ -69,8 +139,12 @@ __device__ __forceinline__ void scatter_features(const Grid& g, const float u[3]
     float gw[7];
 #pragma unroll
     for (int k = 0; k < 7; ++k) gw[k] = w * gq[k];
+    if constexpr (AGG == NGPRT_AGG_MLP) {
+        const float gf[8] = {gs, gw[0], gw[1], gw[2], gw[3], gw[4], gw[5], gw[6]};
+        scatter_mlp_levels<L>(g, u, gf, slots, stride, g_tables);
+    }
 #pragma unroll kLevelUnroll
-    for (int l = 0; l < L; ++l) {
+    for (int l = 0; l < (AGG == NGPRT_AGG_MLP ? 0 : L); ++l) {
         float om = 1.0f, be = 1.0f;
         if constexpr (AGG != NGPRT_AGG_SUM) {
             om = slots[(2 * l) * stride];
@@ -155,6 +229,9 @@ struct BackwardSampler {
     float* g_tables;
     float* g_coarse;
     float* gates;
+    float* records;
+    int32_t* n_records;
+    int64_t rec_capacity;
     __device__ __forceinline__ bool sample(const float u[3], float t, float delta) {
         float f[8];
         const float gq[7] = {gCd[0], gCd[1], gCd[2], gF[0], gF[1], gF[2], gF[3]};
@@ -172,6 +249,21 @@ struct BackwardSampler {
         const float g_sigma = delta * (T_next * qg - (S_tot - S_le));
         const float gs = g_sigma * expf(fminf(f[0], 15.0f));
         scatter_features<L, AGG>(g, u, attn_mode, gs, w, gq, gates, blockDim.x, g_tables, g_coarse);
+        if constexpr (AGG == NGPRT_AGG_MLP) {
+            // (x, g_f) of this sample for the weight gradient; capacity n_rays x
+            // max_samples is never exceeded, the bound only guards the buffer
+            const int64_t r = atomicAdd(n_records, 1);
+            if (r < rec_capacity) {
+                float4* rp = reinterpret_cast<float4*>(records + r * mlp_record_floats<L>());
+                const int st = blockDim.x;
+#pragma unroll 4
+                for (int q = 0; q < 2 * L; ++q)
+                    rp[q] = make_float4(gates[(4 * q) * st], gates[(4 * q + 1) * st], gates[(4 * q + 2) * st],
+                                        gates[(4 * q + 3) * st]);
+                rp[2 * L] = make_float4(gs, w * gq[0], w * gq[1], w * gq[2]);
+                rp[2 * L + 1] = make_float4(w * gq[3], w * gq[4], w * gq[5], w * gq[6]);
+            }
+        }
         T = T_next;
         return T < t_term;
     }
@@ -206,7 +298,7 @@ __global__ void __launch_bounds__(128, NGPRT_BWD_MIN_BLOCKS) march_backward_kern
         const float4 q0 = c4[0], q1 = c4[1], q2 = c4[2];
         BackwardSampler<L, AGG> smp{p.m.g, p.m.opts.attn_mode, p.m.opts.t_term, 1.0f, 0.0f, q2.y,
                                     {q0.x, q0.y, q0.z}, {q0.w, q1.x, q1.y, q1.z}, q1.w, q2.x, p.g_tables,
-                                    p.g_coarse, slots};
+                                    p.g_coarse, slots, p.records, p.n_records, p.rec_capacity};
         int n_march = 0, n_samp = 0;
         march_loop(p.m, o, d, t, t_out, smp, n_march, n_samp);
     }
@@ -223,6 +315,105 @@ __global__ void __launch_bounds__(128, NGPRT_BWD_MIN_BLOCKS) march_backward_kern
     }
 }
 
+// Weight gradient of the tiny-MLP aggregation from the sample records: per record
+// h = W1 x, a = relu(h), g_h = (W2^T g_f) on h > 0, then dW1 += g_h x^T and dW2 +=
+// g_f a^T.  Each block takes tiles of 128 records (one per thread), stages x, g_f,
+// a, g_h in shared memory and sums its share of the outputs over the tile in
+// registers (thread t owns outputs t, t + 128, ...); one atomic per output and block.
+template <int L>
+__global__ void __launch_bounds__(128) agg_mlp_wgrad_kernel(const float* __restrict__ records,
+                                                            const int32_t* __restrict__ n_records, int64_t capacity,
+                                                            const float* __restrict__ w, float* __restrict__ g_w) {
+    constexpr int kHid = NGPRT_AGG_MLP_HIDDEN;
+    constexpr int NX = kNFeat * L;
+    constexpr int RF = mlp_record_floats<L>();
+    constexpr int NOUT = kHid * NX + kNFeat * kHid;
+    constexpr int PER = (NOUT + 127) / 128;
+    extern __shared__ float sm[];
+    float* X = sm;                  // [128][NX + 1]
+    float* GF = X + 128 * (NX + 1);  // [128][9]
+    float* A = GF + 128 * 9;         // [128][kHid + 1]
+    float* GH = A + 128 * (kHid + 1); // [128][kHid + 1]
+    const int64_t n = min((int64_t)*n_records, capacity);
+    float acc[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) acc[k] = 0.0f;
+    const int t = threadIdx.x;
+    for (int64_t base = (int64_t)blockIdx.x * 128; base < n; base += (int64_t)gridDim.x * 128) {
+        const int64_t r = base + t;
+        // this thread's record into its rows of X and GF (zeros past the last record)
+        float* xr = X + t * (NX + 1);
+        float* gr = GF + t * 9;
+        const float4* rp = reinterpret_cast<const float4*>(records + r * RF);
+#pragma unroll 4
+        for (int q = 0; q < NX / 4; ++q) {
+            const float4 v = r < n ? rp[q] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            xr[4 * q] = v.x; xr[4 * q + 1] = v.y; xr[4 * q + 2] = v.z; xr[4 * q + 3] = v.w;
+        }
+        float gf[kNFeat];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const float4 v = r < n ? rp[NX / 4 + q] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            gf[4 * q] = v.x; gf[4 * q + 1] = v.y; gf[4 * q + 2] = v.z; gf[4 * q + 3] = v.w;
+        }
+#pragma unroll
+        for (int k = 0; k < kNFeat; ++k) gr[k] = gf[k];
+        const float4* w1 = reinterpret_cast<const float4*>(w);
+        const float* w2 = w + (size_t)kHid * NX;
+#pragma unroll 1
+        for (int j = 0; j < kHid; ++j) {
+            float h = 0.0f;
+#pragma unroll 4
+            for (int q = 0; q < NX / 4; ++q) {
+                const float4 a = __ldg(w1 + j * (NX / 4) + q);
+                h = fmaf(a.x, xr[4 * q], h);
+                h = fmaf(a.y, xr[4 * q + 1], h);
+                h = fmaf(a.z, xr[4 * q + 2], h);
+                h = fmaf(a.w, xr[4 * q + 3], h);
+            }
+            float ga = 0.0f;
+#pragma unroll
+            for (int k = 0; k < kNFeat; ++k) ga = fmaf(__ldg(w2 + k * kHid + j), gf[k], ga);
+            A[t * (kHid + 1) + j] = fmaxf(h, 0.0f);
+            GH[t * (kHid + 1) + j] = h > 0.0f ? ga : 0.0f;
+        }
+        __syncthreads();
+        // one pass over the tile per owned output (acc may live in local memory: it
+        // is touched once per 128 multiply-adds)
+#pragma unroll 1
+        for (int k = 0; k < PER; ++k) {
+            const int o = t + 128 * k;
+            if (o < NOUT) {
+                float s = acc[k];
+                if (o < kHid * NX) {
+                    const int j = o / NX, q = o - j * NX;
+                    for (int rr = 0; rr < 128; ++rr) s = fmaf(GH[rr * (kHid + 1) + j], X[rr * (NX + 1) + q], s);
+                } else {
+                    const int o2 = o - kHid * NX, k2 = o2 / kHid, j = o2 - k2 * kHid;
+                    for (int rr = 0; rr < 128; ++rr) s = fmaf(GF[rr * 9 + k2], A[rr * (kHid + 1) + j], s);
+                }
+                acc[k] = s;
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int o = t + 128 * k;
+        if (o < NOUT && acc[k] != 0.0f) atomicAdd(g_w + o, acc[k]);
+    }
+}
+
+template <int L>
+void launch_agg_mlp_wgrad(const MarchBwdParams& p, const float* w, float* g_w, cudaStream_t st) {
+    constexpr int NX = kNFeat * L;
+    const size_t smem = (size_t)128 * ((NX + 1) + 9 + 2 * (NGPRT_AGG_MLP_HIDDEN + 1)) * sizeof(float);
+    cudaFuncSetAttribute(agg_mlp_wgrad_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int64_t tiles = (p.rec_capacity + 127) / 128;
+    const unsigned blocks = (unsigned)(tiles < 152 * 2 ? (tiles < 1 ? 1 : tiles) : 152 * 2);
+    agg_mlp_wgrad_kernel<L><<<blocks, 128, smem, st>>>(p.records, p.n_records, p.rec_capacity, w, g_w);
+}
+
 template <int L, int AGG>
 void launch_bwd(const MarchBwdParams& p, dim3 grid, cudaStream_t st) {
     const size_t smem = (size_t)bwd_slots<L, AGG>() * 128 * sizeof(float);
@@ -231,8 +422,9 @@ void launch_bwd(const MarchBwdParams& p, dim3 grid, cudaStream_t st) {
     march_backward_kernel<L, AGG><<<grid, 128, smem, st>>>(p);
 }
 
-// The gate forms other than Eq. 8 (backward_agg.cu): L = 2, 4, 16.
+// The gate forms other than Eq. 8 and the tiny MLP (backward_agg.cu): L = 2, 4, 16.
 bool march_bwd_agg_supports(int L);
 void launch_bwd_agg(int L, int agg, const MarchBwdParams& p, dim3 grid, cudaStream_t st);
+void launch_bwd_agg_mlp_wgrad(int L, const MarchBwdParams& p, const float* w, float* g_w, cudaStream_t st);
 
 }  // namespace ngprt

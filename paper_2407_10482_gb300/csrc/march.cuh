@@ -143,7 +143,8 @@ constexpr int kLevelUnroll = NGPRT_LEVEL_UNROLL;
 // units level by level (W1 columns of level l against f^l), then applies W2.
 // With kKeep (reverse pass), level l also leaves sigma^l and q^l = sum over the
 // colour channels of f^l times gq (the ray's colour cotangents) in the slots
-// gates[(2L + 2l) * stride] and gates[(2L + 2l + 1) * stride].
+// gates[(2L + 2l) * stride] and gates[(2L + 2l + 1) * stride]; the MLP form leaves
+// f^l in the slots [8l, 8l + 8) and its 64 hidden pre-activations in [8L, 8L + 64).
 template <int L, int DT, int AGG = NGPRT_AGG_SEPARATE_V, bool kKeep = false>
 __device__ __forceinline__ void sample_features(const Grid& g, const float u[3], int attn_mode, float f[8],
                                                 float* gates, int stride, const float* gq = nullptr) {
@@ -279,7 +280,13 @@ __device__ __forceinline__ void sample_features(const Grid& g, const float u[3],
                 for (int ch = 0; ch < 4; ++ch) fl[ch] = ffma2(cw2, make_float2(e[c][2 * ch], e[c][2 * ch + 1]), fl[ch]);
             }
         }
-        if constexpr (kKeep) {
+        if constexpr (kKeep && AGG == NGPRT_AGG_MLP) {
+#pragma unroll
+            for (int ch = 0; ch < 4; ++ch) {
+                gates[(kNFeat * l + 2 * ch) * stride] = fl[ch].x;
+                gates[(kNFeat * l + 2 * ch + 1) * stride] = fl[ch].y;
+            }
+        } else if constexpr (kKeep) {
             float q = fl[0].y * gq[0];
             q = fmaf(fl[1].x, gq[1], q);
             q = fmaf(fl[1].y, gq[2], q);
@@ -325,6 +332,10 @@ __device__ __forceinline__ void sample_features(const Grid& g, const float u[3],
         }
     }
     if constexpr (AGG == NGPRT_AGG_MLP) {
+        if constexpr (kKeep) {
+#pragma unroll
+            for (int j = 0; j < kHid; ++j) gates[(kNFeat * L + j) * stride] = hid[j];
+        }
         const float4* w2 = reinterpret_cast<const float4*>(g.agg_mlp + (size_t)kHid * kNFeat * L);
 #pragma unroll
         for (int k = 0; k < kNFeat; ++k) {

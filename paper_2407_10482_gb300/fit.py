@@ -67,6 +67,18 @@ def initial_scene(cfg: S.SceneConfig, fc: FitConfig, device="cuda"):
     return tables, coarse, mlp_w
 
 
+def initial_agg_mlp(cfg: S.SceneConfig, fc: FitConfig, device="cuda"):
+    """Weights of the tiny-MLP aggregation (W1 [64][8L] ~ N(0, 1/(8L)), W2 [8][64] ~
+    N(0, 1/64), no biases) for the MLP form; None for the other forms."""
+    if cfg.aggregation != 5:
+        return None
+    rng = np.random.default_rng(fc.seed + 2)
+    nx = S.N_FEAT * cfg.L
+    w1 = rng.normal(0.0, 1.0 / math.sqrt(nx), (64, nx))
+    w2 = rng.normal(0.0, 1.0 / math.sqrt(64), (S.N_FEAT, 64))
+    return torch.as_tensor(np.concatenate([w1.reshape(-1), w2.reshape(-1)]).astype(np.float32)).to(device)
+
+
 def initial_attn_inv(cfg: S.SceneConfig, fc: FitConfig, device="cuda"):
     """The constant gate logits of the spatially invariant forms (2L for separate
     gates, L for shared ones), drawn like the coarse grid's spatial logits; None for
@@ -116,10 +128,15 @@ def fit(scene: ng.DeviceScene, occ: ng.DeviceOcc, opts, cams: np.ndarray, W: int
     rend = ng.Renderer(scene, occ, device=dev)
     params = [scene.tables, scene.coarse, scene.mlp_w]
     lrs = [fc.lr, fc.lr, fc.lr_mlp]
-    inv = scene.attn_inv is not None and scene.cfg.aggregation in (2, 3)   # constant gate logits
-    if inv:
+    extra = {}                           # the aggregation's own parameters, by backward keyword
+    if scene.attn_inv is not None and scene.cfg.aggregation in (2, 3):       # constant gate logits
+        extra["g_attn_inv"] = len(params)
         params.append(scene.attn_inv)
         lrs.append(fc.lr)
+    if scene.agg_mlp is not None and scene.cfg.aggregation == 5:             # tiny-MLP weights
+        extra["g_agg_mlp"] = len(params)
+        params.append(scene.agg_mlp)
+        lrs.append(fc.lr_mlp)
     grads = [torch.zeros_like(p) for p in params]
     moms = [(torch.zeros_like(p), torch.zeros_like(p)) for p in params]
     n_pix = len(cams) * W * H
@@ -155,7 +172,8 @@ def fit(scene: ng.DeviceScene, occ: ng.DeviceOcc, opts, cams: np.ndarray, W: int
         else:
             ng.ngprt_l2_loss(out["rgb"], tg, 3 * B, 1.0 / (3 * B), loss if logging else None, d_rgb, stream=stream)
         rend.backward(o_step, out["state"][back].contiguous(), d_rgb[back].contiguous(), None, None, grads[0],
-                      grads[1], grads[2], cams=cams, W=W, H=H, pixel_ids=pix, g_attn_inv=grads[3] if inv else None)
+                      grads[1], grads[2], cams=cams, W=W, H=H, pixel_ids=pix,
+                      **{k: grads[i] for k, i in extra.items()})
         if fc.eta > 0:
             ro = ng.render_opts(o_step)
             ng.ngprt_distortion_loss(scene.struct, occ.struct, cam_arr, n_cams, pix, None, None, B, ro, fc.eta / B,

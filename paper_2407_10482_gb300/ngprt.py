@@ -87,7 +87,8 @@ _SIGS = {
     "ngprt_render": (C.c_int32, [_P, _P, _P, C.c_int32, _P, _P, _P, C.c_int64, _P, _P, _P, _P, _P, _P, _P,
                                  _P, C.c_size_t, _P]),
     "ngprt_render_backward": (C.c_int32, [_P, _P, _P, C.c_int32, _P, _P, _P, C.c_int64, _P, _P, _P, _P, _P,
-                                          _P, _P, _P, _P, _P, C.c_size_t, _P]),
+                                          _P, _P, _P, _P, _P, _P, C.c_size_t, _P]),
+    "ngprt_render_backward_workspace_bytes": (C.c_size_t, [_P, _P, C.c_int64]),
     "ngprt_grid_indices": (C.c_int32, [_P, _P, C.c_int64, _P, _P]),
     "ngprt_shade": (C.c_int32, [_P, _P, C.c_int64, _P, _P, _P, _P, _P]),
     "ngprt_l2_loss": (C.c_int32, [_P, _P, C.c_int64, C.c_float, _P, _P, _P]),
@@ -278,12 +279,17 @@ def ngprt_render(scene, occ, cams, n_cams, pixel_ids, rays_o, rays_d, n_rays, t_
 
 def ngprt_render_backward(scene, occ, cams, n_cams, pixel_ids, rays_o, rays_d, n_rays, opts, ray_state, d_rgb,
                           d_depth, d_opacity, g_tables, g_coarse, g_mlp, workspace=None, stream=None,
-                          g_attn_inv=None) -> None:
+                          g_attn_inv=None, g_agg_mlp=None) -> None:
     ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
     _check("ngprt_render_backward", lib().ngprt_render_backward(
         C.byref(scene), C.byref(occ), cams, n_cams, _ptr(pixel_ids), _ptr(rays_o), _ptr(rays_d), n_rays,
         C.byref(opts), _ptr(ray_state), _ptr(d_rgb), _ptr(d_depth), _ptr(d_opacity), _ptr(g_tables),
-        _ptr(g_coarse), _ptr(g_mlp), _ptr(g_attn_inv), _ptr(workspace), ws_bytes, _stream(stream)))
+        _ptr(g_coarse), _ptr(g_mlp), _ptr(g_attn_inv), _ptr(g_agg_mlp), _ptr(workspace), ws_bytes,
+        _stream(stream)))
+
+
+def ngprt_render_backward_workspace_bytes(scene, opts, n_rays) -> int:
+    return int(lib().ngprt_render_backward_workspace_bytes(C.byref(scene), C.byref(opts), n_rays))
 
 
 def coarse_blocks_per_axis(R_C: int) -> int:
@@ -489,6 +495,7 @@ class Renderer:
     def __init__(self, scene: DeviceScene, occ: DeviceOcc, device="cuda"):
         self.scene, self.occ, self.device = scene, occ, device
         self._ws = None
+        self._bws = None  # the reverse pass's workspace
 
     def workspace(self, n_rays: int):
         need = ngprt_render_workspace_bytes(self.scene.struct, n_rays)
@@ -525,11 +532,12 @@ class RenderFunction(torch.autograd.Function):
     attn_inv is the scene's constant gate logits (the spatially invariant gate forms)."""
 
     @staticmethod
-    def forward(ctx, tables, coarse, mlp_w, renderer, opts, rays, attn_inv=None):
+    def forward(ctx, tables, coarse, mlp_w, renderer, opts, rays, attn_inv=None, agg_mlp=None):
         scene = renderer.scene
         assert tables.data_ptr() == scene.tables.data_ptr() and coarse.data_ptr() == scene.coarse.data_ptr()
         assert mlp_w.data_ptr() == scene.mlp_w.data_ptr()
         assert attn_inv is None or attn_inv.data_ptr() == scene.attn_inv.data_ptr()
+        assert agg_mlp is None or agg_mlp.data_ptr() == scene.agg_mlp.data_ptr()
         out = renderer.render(opts, state=True, **rays)
         ctx.renderer, ctx.opts, ctx.rays = renderer, opts, rays
         ctx.save_for_backward(out["state"])
@@ -544,23 +552,29 @@ class RenderFunction(torch.autograd.Function):
         g_c = torch.zeros_like(s.coarse)
         g_m = torch.zeros_like(s.mlp_w)
         g_i = torch.zeros_like(s.attn_inv) if s.attn_inv is not None else None
+        g_a = torch.zeros_like(s.agg_mlp) if s.agg_mlp is not None else None
         r.backward(ctx.opts, state, d_rgb.contiguous(), None if d_depth is None else d_depth.contiguous(),
                    None if d_opacity is None else d_opacity.contiguous(), g_t, g_c, g_m, g_attn_inv=g_i,
-                   **ctx.rays)
-        return g_t, g_c, g_m, None, None, None, g_i
+                   g_agg_mlp=g_a, **ctx.rays)
+        return g_t, g_c, g_m, None, None, None, g_i, g_a
 
 
 def _renderer_backward(self, opts, state, d_rgb, d_depth, d_opacity, g_tables, g_coarse, g_mlp, cams=None, W=None,
-                       H=None, pixel_ids=None, rays_o=None, rays_d=None, t_interval=None, g_attn_inv=None):
+                       H=None, pixel_ids=None, rays_o=None, rays_d=None, t_interval=None, g_attn_inv=None,
+                       g_agg_mlp=None):
     if cams is not None:
         cam_arr, n_cams = cameras_struct(cams, W, H)
         n = len(pixel_ids) if pixel_ids is not None else n_cams * W * H
     else:
         cam_arr, n_cams = None, 0
         n = rays_o.shape[0]
+    ro = render_opts(opts)
+    need = ngprt_render_backward_workspace_bytes(self.scene.struct, ro, n)
+    if self._bws is None or self._bws.numel() < need:
+        self._bws = torch.empty(need, dtype=torch.uint8, device=self.device)
     ngprt_render_backward(self.scene.struct, self.occ.struct, cam_arr, n_cams, pixel_ids, rays_o, rays_d, n,
-                          render_opts(opts), state, d_rgb, d_depth, d_opacity, g_tables, g_coarse, g_mlp,
-                          self.workspace(n), g_attn_inv=g_attn_inv)
+                          ro, state, d_rgb, d_depth, d_opacity, g_tables, g_coarse, g_mlp, self._bws,
+                          g_attn_inv=g_attn_inv, g_agg_mlp=g_agg_mlp)
 
 
 Renderer.backward = _renderer_backward

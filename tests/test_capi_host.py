@@ -126,9 +126,10 @@ def test_aggregation_layouts_and_validation(ng):
     def backward(g_inv=None):
         return lib.ngprt_render_backward(C.byref(s), C.byref(o), None, 0, None, C.c_void_p(256), C.c_void_p(256),
                                          4, C.byref(opts), C.c_void_p(256), C.c_void_p(256), None, None,
-                                         C.c_void_p(256), C.c_void_p(256), C.c_void_p(256), g_inv, None, 0, None)
-    s.aggregation, s.agg_mlp = 5, 256  # the MLP form has no reverse pass
-    assert backward() == ng.ERR_UNSUPPORTED and b"no reverse pass" in lib.ngprt_last_error()
+                                         C.c_void_p(256), C.c_void_p(256), C.c_void_p(256), g_inv, None, None, 0,
+                                         None)
+    s.aggregation, s.agg_mlp = 5, 256  # the MLP form needs its weight gradient buffer
+    assert backward() == ng.ERR_INVALID_ARG and b"g_agg_mlp" in lib.ngprt_last_error()
     s.aggregation, s.agg_mlp, s.attn_inv = 2, None, 256
     assert backward() == ng.ERR_INVALID_ARG and b"g_attn_inv" in lib.ngprt_last_error()
     s.L = 3                                 # no variant reverse pass for L = 3
@@ -169,7 +170,7 @@ def test_sparse_coarse_grid_validation(ng):
     s.coarse_index = 256
     rc = lib.ngprt_render_backward(C.byref(s), C.byref(o), None, 0, None, C.c_void_p(256), C.c_void_p(256), 4,
                                    C.byref(opts), C.c_void_p(256), C.c_void_p(256), None, None, C.c_void_p(256),
-                                   C.c_void_p(256), C.c_void_p(256), None, None, 0, None)
+                                   C.c_void_p(256), C.c_void_p(256), None, None, None, 0, None)
     assert rc == ng.ERR_INVALID_ARG and b"dense coarse grid" in lib.ngprt_last_error()
     assert ng.ngprt_coarse_sparsify_workspace_bytes(512) >= 16 + 2 * 4 * 256
     assert ng.ngprt_coarse_sparsify_workspace_bytes(1) == 0

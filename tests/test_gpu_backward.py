@@ -98,13 +98,17 @@ def test_autograd_function_matches_direct_call(ng):
         np.testing.assert_allclose(a.cpu().numpy(), b.cpu().numpy(), rtol=1e-4, atol=1e-6)
 
 
+def agg_kinks_excluded(cfg):
+    return cfg.aggregation == 5
+
+
 def _run_agg(ng, cfg, opts, n_rays, seed=5):
     sc = S.make_scene(cfg)
     if sc.coarse.shape[1] > 8:
         sc.coarse[:, 8:] *= 10.0
     if sc.attn_inv is not None:
         sc.attn_inv = sc.attn_inv * 20.0
-    ds = ng.DeviceScene(cfg, sc.tables, sc.coarse, sc.mlp_w, attn_inv=sc.attn_inv)
+    ds = ng.DeviceScene(cfg, sc.tables, sc.coarse, sc.mlp_w, attn_inv=sc.attn_inv, agg_mlp=sc.agg_mlp)
     docc = ng.DeviceOcc(sc.occ, cfg.R_O, cfg.n_occ_levels)
     rend = ng.Renderer(ds, docc)
     o, d = S.random_rays(n_rays, seed, cfg.bounded)
@@ -112,57 +116,55 @@ def _run_agg(ng, cfg, opts, n_rays, seed=5):
     d_rgb = rng.normal(size=(n_rays, 3)).astype(np.float32)
     d_dep = (0.3 * rng.normal(size=n_rays)).astype(np.float32)
     d_op = rng.normal(size=n_rays).astype(np.float32)
+    orc = O.oracle_for_scene(sc)
+    if agg_kinks_excluded(cfg):
+        # the MLP form's ReLU decisions: rays with a unit at its kink within FP32's
+        # reach are compared by neither side (5% of the rays at L = 2, 4; about 20%
+        # with 16 levels and 64-sample rays)
+        kink = orc.render_backward(opts, d_rgb=d_rgb, rays_o=o, rays_d=d)["kink"].astype(bool)
+        assert kink.mean() < 0.5, kink.mean()
+        o, d, d_rgb, d_dep, d_op = (np.ascontiguousarray(a[~kink]) for a in (o, d, d_rgb, d_dep, d_op))
     rays = dict(rays_o=torch.as_tensor(o).cuda(), rays_d=torch.as_tensor(d).cuda())
     out = rend.render(opts, state=True, **rays)
     g_t = torch.zeros_like(ds.tables)
     g_c = torch.zeros_like(ds.coarse)
     g_m = torch.zeros_like(ds.mlp_w)
     g_i = torch.zeros_like(ds.attn_inv) if ds.attn_inv is not None else None
+    g_a = torch.zeros_like(ds.agg_mlp) if ds.agg_mlp is not None else None
     rend.backward(opts, out["state"], torch.as_tensor(d_rgb).cuda(), torch.as_tensor(d_dep).cuda(),
-                  torch.as_tensor(d_op).cuda(), g_t, g_c, g_m, g_attn_inv=g_i, **rays)
+                  torch.as_tensor(d_op).cuda(), g_t, g_c, g_m, g_attn_inv=g_i, g_agg_mlp=g_a, **rays)
     torch.cuda.synchronize()
-    ref = O.oracle_for_scene(sc).render_backward(opts, d_rgb=d_rgb, d_depth=d_dep, d_opacity=d_op, rays_o=o,
-                                                 rays_d=d)
+    ref = orc.render_backward(opts, d_rgb=d_rgb, d_depth=d_dep, d_opacity=d_op, rays_o=o, rays_d=d)
+    if agg_kinks_excluded(cfg):
+        assert not ref["kink"].any()
     _close("tables", g_t.cpu().numpy(), ref["tables"])
     _close("coarse", g_c.cpu().numpy(), ref["coarse"])
     _close("mlp_w", g_m.cpu().numpy(), ref["mlp_w"])
     if g_i is not None:
         _close("attn_inv", g_i.cpu().numpy(), ref["attn_inv"])
+    if g_a is not None:
+        _close("agg_mlp", g_a.cpu().numpy(), ref["agg_mlp"])
     return g_c
 
 
 @pytest.mark.parametrize("L", [2, 4])
-@pytest.mark.parametrize("agg", [1, 2, 3, 4])
+@pytest.mark.parametrize("agg", [1, 2, 3, 4, 5])
 def test_backward_aggregation_variants(ng, agg, L):
-    """Table 3's gate forms in their own layouts (one spatial logit per level, constant
-    logits, no logits); 2500 rays span 20 blocks and a ragged last one."""
+    """Table 3's forms in their own layouts (one spatial logit per level, constant
+    logits, no logits, the tiny MLP with its weight gradient); 2500 rays span 20
+    blocks and a ragged last one."""
     cfg = S.small_config(L=L, N=[16, 32, 64, 128][:L] if L == 4 else [24, 96], blob_std=(0.05, 0.15),
                          aggregation=agg)
     g_c = _run_agg(ng, cfg, S.default_options(cfg, t_term=0.0), n_rays=2500)
     assert g_c.shape[1] == S.coarse_channels(cfg)
 
 
-@pytest.mark.parametrize("agg", [1, 3])
+@pytest.mark.parametrize("agg", [1, 3, 5])
 def test_backward_aggregation_variants_hd_levels(ng, agg):
-    """16 levels (the hd workload's, T = 2^19): 24 coarse channels (SHARED_V) and the
-    16 shared constant logits summed over the block."""
+    """16 levels (the hd workload's, T = 2^19): 24 coarse channels (SHARED_V), the 16
+    shared constant logits summed over the block, and the tiny MLP's 128 inputs."""
     cfg = S.hd_config(density_bias=0.5, aggregation=agg)
     _run_agg(ng, cfg, S.default_options(cfg, t_term=0.0, max_samples=64), n_rays=384)
-
-
-def test_backward_refuses_the_mlp_aggregation(ng):
-    cfg = S.small_config(aggregation=5)
-    sc = S.make_scene(cfg)
-    ds = ng.DeviceScene(cfg, sc.tables, sc.coarse, sc.mlp_w, agg_mlp=sc.agg_mlp)
-    docc = ng.DeviceOcc(sc.occ, cfg.R_O, cfg.n_occ_levels)
-    rend = ng.Renderer(ds, docc)
-    o, d = S.random_rays(64, 1, cfg.bounded)
-    rays = dict(rays_o=torch.as_tensor(o).cuda(), rays_d=torch.as_tensor(d).cuda())
-    opts = S.default_options(cfg)
-    out = rend.render(opts, state=True, **rays)
-    with pytest.raises(RuntimeError, match="no reverse pass"):
-        rend.backward(opts, out["state"], torch.zeros(64, 3, device="cuda"), None, None,
-                      torch.zeros_like(ds.tables), torch.zeros_like(ds.coarse), torch.zeros_like(ds.mlp_w), **rays)
 
 
 def test_autograd_function_returns_the_invariant_logits_gradient(ng):

@@ -92,9 +92,9 @@ def test_attention_fits_better_than_sum(ng):
     """Table 3's quality order on synthetic data: the same collision-heavy model
     (T = 2^12, so the fine levels share entries) fitted with each gated level fusion in
     its own layout (separate or shared gates per level, spatially variant in the coarse
-    grid or invariant constants) or the plain sum; every gated form reaches a higher
-    PSNR than the sum between the training views, the spatially variant ones on them
-    too.  Prints the table (run with -s)."""
+    grid or invariant constants), the plain sum, or Instant-NGP's tiny MLP; every
+    gated form and the MLP reach a higher PSNR than the sum between the training
+    views, the spatially variant gates on them too.  Prints the table (run with -s)."""
     base = S.small_config()
     blobs = S._blobs(base, np.random.default_rng(base.seed))
     occ = S._occupancy(base, blobs)
@@ -105,14 +105,15 @@ def test_attention_fits_better_than_sum(ng):
     docc = ng.DeviceOcc(occ, base.R_O, base.n_occ_levels)
     res = {}
     forms = ((4, "SUM"), (3, "Shared-Att (Inv)"), (2, "Separate-Att (Inv)"), (1, "Shared-Att (V)"),
-             (0, "Separate-Att (V)"))
+             (0, "Separate-Att (V)"), (5, "MLP"))
     for agg, label in forms:
         cfg = replace(base, aggregation=agg)
         opts = S.default_options(cfg)
         runs = []
         for seed in (5, 6):
             fc = F.FitConfig(steps=1500, batch=1 << 14, seed=seed)
-            ds = ng.DeviceScene(cfg, *F.initial_scene(cfg, fc, "cuda"), attn_inv=F.initial_attn_inv(cfg, fc, "cuda"))
+            ds = ng.DeviceScene(cfg, *F.initial_scene(cfg, fc, "cuda"), attn_inv=F.initial_attn_inv(cfg, fc, "cuda"),
+                                agg_mlp=F.initial_agg_mlp(cfg, fc, "cuda"))
             F.fit(ds, docc, opts, cams, cfg.W, cfg.H, targets, fc)
             r = ng.Renderer(ds, docc)
             runs.append((P.psnr(r.render(opts, cams=cams, W=cfg.W, H=cfg.H)["rgb"], targets),
@@ -124,5 +125,5 @@ def test_attention_fits_better_than_sum(ng):
     for att in ("Separate-Att (V)", "Shared-Att (V)"):
         assert res[att][1] > res["SUM"][1] + 0.2      # between the training views
         assert res[att][0] > res["SUM"][0]            # on them
-    for att in ("Separate-Att (Inv)", "Shared-Att (Inv)"):
+    for att in ("Separate-Att (Inv)", "Shared-Att (Inv)", "MLP"):
         assert res[att][1] > res["SUM"][1]
