@@ -36,9 +36,9 @@ METRIC = "1080p frames/s & Grays/s, plain FP32 vs FP16+proposal at ≤0.1 dB PSN
 # DRAM bytes (read + write) of one march_kernel<16,F32> launch on this frame, from the
 # ncu capture summarised in profiles/march_kernel_hd_1080p_fp32.md; None while the
 # kernel has changed since the counters were taken
-MARCH_DRAM_BYTES = 2.332612e9  # 2.024988 GB read + 0.307624 GB written
+MARCH_DRAM_BYTES = 2.545277e9  # 2.187119 GB read + 0.358158 GB written
 # l1tex__data_pipe_lsu_wavefronts.avg.pct_of_peak_sustained_elapsed of the same capture
-L1_LSU_PCT = 80.15
+L1_LSU_PCT = 80.34
 WORKLOAD = "hd 1920x1080 unbounded-360 synthetic scene, L=16 (16..4096), T=2^19, 128^3 occupancy+G, MLP 23-64-64-3"
 
 
