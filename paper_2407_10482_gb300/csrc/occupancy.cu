@@ -2,69 +2,9 @@
 // model's own density at voxel centres, visibility marking by training rays (the
 // voxels of samples whose weight passes a threshold), and box dilation.  The
 // pyramid and the distance grid G of the result then come from ngprt_build_occ_dist.
-#include "march.cuh"
+#include "occupancy.cuh"
 
 namespace ngprt {
-
-struct DensityOccParams {
-    Grid g;
-    int32_t R;
-    int32_t attn_mode;
-    float sigma_thr;
-    uint8_t* occ;
-    float* sigma;
-};
-
-// One voxel per thread: sigma = exp(sigma_raw) at the voxel centre (Eq. 6-8).
-template <int L, int DT>
-__global__ void __launch_bounds__(128) density_occ_kernel(const __grid_constant__ DensityOccParams p) {
-    extern __shared__ float gate_smem[];
-    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t R = p.R;
-    if (v >= R * R * R) return;
-    const int i = (int)(v % R), j = (int)((v / R) % R), k = (int)(v / (R * R));
-    const float inv = fdiv(1.0f, (float)R);  // R is a power of two: exact
-    const float u[3] = {fmul(fadd((float)i, 0.5f), inv), fmul(fadd((float)j, 0.5f), inv),
-                        fmul(fadd((float)k, 0.5f), inv)};
-    float f[8];
-    sample_features<L, DT>(p.g, u, p.attn_mode, f, gate_smem + threadIdx.x, blockDim.x);
-    const float sg = expf(f[0]);
-    p.occ[v] = sg > p.sigma_thr ? 1 : 0;
-    if (p.sigma) p.sigma[v] = sg;
-}
-
-// Composites like the forward render and marks the voxel (R^3 grid) of every sample
-// whose weight exceeds w_thr.  All writers store 1, so concurrent marks agree.
-template <int L, int DT>
-struct VisibilitySampler {
-    ForwardSampler<L, DT> fw;
-    float w_thr;
-    int32_t R;
-    uint8_t* vis;
-    __device__ __forceinline__ bool sample(const float u[3], float t, float delta) {
-        const bool stop = fw.sample(u, t, delta);
-        if (fw.w_last > w_thr) {
-            const uint32_t v = (uint32_t)occ_vox(u[0], R) +
-                               (uint32_t)R * ((uint32_t)occ_vox(u[1], R) + (uint32_t)R * (uint32_t)occ_vox(u[2], R));
-            vis[v] = 1;
-        }
-        return stop;
-    }
-};
-
-template <int L, int DT>
-__global__ void __launch_bounds__(128, march_min_blocks<L, DT>())
-    visibility_kernel(const __grid_constant__ MarchParams p, float w_thr, int32_t R, uint8_t* vis) {
-    int64_t ray;
-    float o[3], d[3], t, t_out;
-    bool hit;
-    extern __shared__ float gate_smem[];
-    if (!ray_setup(p, ray, o, d, t, t_out, hit)) return;
-    VisibilitySampler<L, DT> smp{ForwardSampler<L, DT>(p.g, p.opts.attn_mode, p.opts.t_term, gate_smem + threadIdx.x),
-                                 w_thr, R, vis};
-    int n_march = 0, n_samp = 0;
-    if (hit) march_loop(p, o, d, t, t_out, smp, n_march, n_samp);
-}
 
 // One pass of the separable box dilation along `axis`: out = max over +-r voxels.
 __global__ void dilate_pass_kernel(const uint8_t* __restrict__ in, uint8_t* __restrict__ out, int32_t R, int32_t r,
@@ -93,25 +33,6 @@ int32_t setup_rays(MarchParams& p, const ngprt_camera* cams, int32_t n_cams, con
 
 static bool pow2_in(int32_t R) { return R >= 2 && R <= 1024 && (R & (R - 1)) == 0; }
 
-template <int L>
-static void launch_density(int dt, const DensityOccParams& p, cudaStream_t st) {
-    const int64_t n = (int64_t)p.R * p.R * p.R;
-    const unsigned blocks = (unsigned)((n + 127) / 128);
-    const size_t shm = (size_t)2 * L * 128 * sizeof(float);
-    if (dt == NGPRT_F32) density_occ_kernel<L, NGPRT_F32><<<blocks, 128, shm, st>>>(p);
-    else if (dt == NGPRT_F16) density_occ_kernel<L, NGPRT_F16><<<blocks, 128, shm, st>>>(p);
-    else density_occ_kernel<L, NGPRT_BF16><<<blocks, 128, shm, st>>>(p);
-}
-
-template <int L>
-static void launch_visibility(int dt, const MarchParams& p, dim3 grid, float w_thr, int32_t R, uint8_t* vis,
-                              cudaStream_t st) {
-    const size_t shm = (size_t)2 * L * 128 * sizeof(float);
-    if (dt == NGPRT_F32) visibility_kernel<L, NGPRT_F32><<<grid, 128, shm, st>>>(p, w_thr, R, vis);
-    else if (dt == NGPRT_F16) visibility_kernel<L, NGPRT_F16><<<grid, 128, shm, st>>>(p, w_thr, R, vis);
-    else visibility_kernel<L, NGPRT_BF16><<<grid, 128, shm, st>>>(p, w_thr, R, vis);
-}
-
 }  // namespace ngprt
 
 using namespace ngprt;
@@ -124,7 +45,7 @@ extern "C" int32_t ngprt_occupancy_from_density(const ngprt_scene* scene, const 
     int32_t rc;
     if ((rc = make_grid(scene, p.g, fn)) != NGPRT_OK) return rc;
     if ((rc = check_opts(opts, fn)) != NGPRT_OK) return rc;
-    if ((rc = check_agg(scene, opts, false, fn)) != NGPRT_OK) return rc;
+    if ((rc = check_agg(scene, opts, true, fn)) != NGPRT_OK) return rc;
     NGPRT_REQUIRE(pow2_in(R), "%s: R=%d must be a power of two in [2, 1024]", fn, R);
     NGPRT_REQUIRE(occ_out != nullptr, "%s: occ_out is NULL", fn);
     p.R = R;
@@ -133,13 +54,18 @@ extern "C" int32_t ngprt_occupancy_from_density(const ngprt_scene* scene, const 
     p.occ = occ_out;
     p.sigma = sigma_out;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (scene->aggregation != NGPRT_AGG_SEPARATE_V) {
+        NGPRT_REQUIRE(scene->table_dtype == NGPRT_F32, "%s: the Table 3 forms are built here for F32 tables", fn);
+        launch_density_agg(scene->L, scene->aggregation, scene->table_dtype, p, st);
+        return cuda_status(fn);
+    }
     switch (scene->L) {
-        case 1: launch_density<1>(scene->table_dtype, p, st); break;
-        case 2: launch_density<2>(scene->table_dtype, p, st); break;
-        case 3: launch_density<3>(scene->table_dtype, p, st); break;
-        case 4: launch_density<4>(scene->table_dtype, p, st); break;
-        case 8: launch_density<8>(scene->table_dtype, p, st); break;
-        case 16: launch_density<16>(scene->table_dtype, p, st); break;
+        case 1: launch_density<1, NGPRT_AGG_SEPARATE_V>(scene->table_dtype, p, st); break;
+        case 2: launch_density<2, NGPRT_AGG_SEPARATE_V>(scene->table_dtype, p, st); break;
+        case 3: launch_density<3, NGPRT_AGG_SEPARATE_V>(scene->table_dtype, p, st); break;
+        case 4: launch_density<4, NGPRT_AGG_SEPARATE_V>(scene->table_dtype, p, st); break;
+        case 8: launch_density<8, NGPRT_AGG_SEPARATE_V>(scene->table_dtype, p, st); break;
+        case 16: launch_density<16, NGPRT_AGG_SEPARATE_V>(scene->table_dtype, p, st); break;
         default: set_error("%s: no kernel for L=%d", fn, scene->L); return NGPRT_ERR_UNSUPPORTED;
     }
     return cuda_status(fn);
@@ -157,7 +83,7 @@ extern "C" int32_t ngprt_occupancy_visibility(const ngprt_scene* scene, const ng
     if ((rc = make_grid(scene, p.g, fn)) != NGPRT_OK) return rc;
     if ((rc = make_occ(occ, p.occ, fn)) != NGPRT_OK) return rc;
     if ((rc = check_opts(opts, fn)) != NGPRT_OK) return rc;
-    if ((rc = check_agg(scene, opts, false, fn)) != NGPRT_OK) return rc;
+    if ((rc = check_agg(scene, opts, true, fn)) != NGPRT_OK) return rc;
     NGPRT_REQUIRE(pow2_in(R), "%s: R=%d must be a power of two in [2, 1024]", fn, R);
     NGPRT_REQUIRE(n_rays >= 0, "%s: n_rays=%lld", fn, (long long)n_rays);
     dim3 grid;
@@ -166,13 +92,18 @@ extern "C" int32_t ngprt_occupancy_visibility(const ngprt_scene* scene, const ng
     NGPRT_REQUIRE(vis != nullptr, "%s: vis is NULL", fn);
     p.opts = *opts;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (scene->aggregation != NGPRT_AGG_SEPARATE_V) {
+        NGPRT_REQUIRE(scene->table_dtype == NGPRT_F32, "%s: the Table 3 forms are built here for F32 tables", fn);
+        launch_visibility_agg(scene->L, scene->aggregation, scene->table_dtype, p, grid, w_thr, R, vis, st);
+        return cuda_status(fn);
+    }
     switch (scene->L) {
-        case 1: launch_visibility<1>(scene->table_dtype, p, grid, w_thr, R, vis, st); break;
-        case 2: launch_visibility<2>(scene->table_dtype, p, grid, w_thr, R, vis, st); break;
-        case 3: launch_visibility<3>(scene->table_dtype, p, grid, w_thr, R, vis, st); break;
-        case 4: launch_visibility<4>(scene->table_dtype, p, grid, w_thr, R, vis, st); break;
-        case 8: launch_visibility<8>(scene->table_dtype, p, grid, w_thr, R, vis, st); break;
-        case 16: launch_visibility<16>(scene->table_dtype, p, grid, w_thr, R, vis, st); break;
+        case 1: launch_visibility<1, NGPRT_AGG_SEPARATE_V>(scene->table_dtype, p, grid, w_thr, R, vis, st); break;
+        case 2: launch_visibility<2, NGPRT_AGG_SEPARATE_V>(scene->table_dtype, p, grid, w_thr, R, vis, st); break;
+        case 3: launch_visibility<3, NGPRT_AGG_SEPARATE_V>(scene->table_dtype, p, grid, w_thr, R, vis, st); break;
+        case 4: launch_visibility<4, NGPRT_AGG_SEPARATE_V>(scene->table_dtype, p, grid, w_thr, R, vis, st); break;
+        case 8: launch_visibility<8, NGPRT_AGG_SEPARATE_V>(scene->table_dtype, p, grid, w_thr, R, vis, st); break;
+        case 16: launch_visibility<16, NGPRT_AGG_SEPARATE_V>(scene->table_dtype, p, grid, w_thr, R, vis, st); break;
         default: set_error("%s: no kernel for L=%d", fn, scene->L); return NGPRT_ERR_UNSUPPORTED;
     }
     return cuda_status(fn);

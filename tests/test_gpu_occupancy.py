@@ -22,7 +22,7 @@ def ng():
 
 
 def _device_scene(ng, sc):
-    return ng.DeviceScene(sc.cfg, sc.tables, sc.coarse, sc.mlp_w)
+    return ng.DeviceScene(sc.cfg, sc.tables, sc.coarse, sc.mlp_w, attn_inv=sc.attn_inv, agg_mlp=sc.agg_mlp)
 
 
 @pytest.mark.parametrize("cfg_name,R", [("small", 32), ("small", 64), ("hd", 64)])
@@ -46,8 +46,29 @@ def test_density_occupancy_matches_oracle(ng, cfg_name, R):
     assert np.array_equal(occ.cpu().numpy()[sure], occ_ref[sure])
 
 
-def test_visibility_marks_match_oracle(ng):
-    cfg = S.small_config()
+@pytest.mark.parametrize("agg", [1, 2, 3, 4, 5])
+def test_density_occupancy_of_the_aggregation_forms(ng, agg):
+    """Table 3's other forms: each feeds its own density into the occupancy."""
+    cfg = S.small_config(aggregation=agg)
+    sc = S.make_scene(cfg)
+    ds = _device_scene(ng, sc)
+    opts = S.default_options(cfg)
+    R = 32
+    _, sig_ref = O.oracle_for_scene(sc).occupancy_density(opts, R, 1.0)
+    thr = float(np.median(sig_ref))
+    occ = torch.empty(R ** 3, dtype=torch.uint8, device="cuda")
+    sig = torch.empty(R ** 3, device="cuda")
+    ng.ngprt_occupancy_from_density(ds.struct, ng.render_opts(opts), R, thr, occ, sig)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(sig.cpu().numpy().astype(np.float64), sig_ref, rtol=2e-5)
+    sure = np.abs(sig_ref - thr) > 5e-5 * thr
+    assert (~sure).sum() <= max(2, R ** 3 // 500)
+    assert np.array_equal(occ.cpu().numpy()[sure], (sig_ref > thr).astype(np.uint8)[sure])
+
+
+@pytest.mark.parametrize("agg", [0, 1, 3, 5])
+def test_visibility_marks_match_oracle(ng, agg):
+    cfg = S.small_config(aggregation=agg)
     sc = S.make_scene(cfg)
     ds = _device_scene(ng, sc)
     docc = ng.DeviceOcc(sc.occ, cfg.R_O, cfg.n_occ_levels)
