@@ -771,6 +771,147 @@ int or_ray_samples(const or_scene* s, const or_occ* oc, const or_opts* op, const
 
 /* ------------------------------------------------------------ reverse pass */
 
+/* Reverse of Eq. 6-8 (and of Table 3's other forms) at one sample u: given the
+ * sample's feature cotangent g_f = dL/d f (f = [sigma_raw, c_d(3), v_s(4)]), add the
+ * gradients of the coarse vertices, the gate logits (coarse channels or the constant
+ * logits) or the tiny MLP's weights, and the fine entries.  kink (may be NULL) is set
+ * when a hidden unit of the MLP form lies within 1e-5 relative of its ReLU kink. */
+static void or_feature_reverse(const or_scene* s, const or_opts* op, const float u[3], const double g_f[OR_NFEAT],
+                               double* g_tables, double* g_coarse, double* g_attn_inv, double* g_agg_mlp,
+                               int32_t* kink) {
+    int nch = or_coarse_channels(s->L, s->aggregation);
+    uint32_t T = 1u << s->T_log2;
+    /* Eq. 6-8 reverse: coarse part, attention logits, fine levels */
+    double coarse[OR_NFEAT + 2 * OR_MAXL], g_coarse_v[OR_NFEAT + 2 * OR_MAXL];
+    int base[3];
+    double wc[3];
+    memset(coarse, 0, sizeof coarse);
+    memset(g_coarse_v, 0, sizeof g_coarse_v);
+    or_cell(u, s->R_C, base, wc);
+    size_t cv[8];
+    double cwt[8];
+    for (int c = 0; c < 8; ++c) {
+        int xx = base[0] + (c & 1), yy = base[1] + ((c >> 1) & 1), zz = base[2] + ((c >> 2) & 1);
+        cv[c] = (size_t)xx + (size_t)s->R_C * ((size_t)yy + (size_t)s->R_C * zz);
+        cwt[c] = or_corner_weight(wc, c);
+        for (int ch = 0; ch < nch; ++ch) coarse[ch] += cwt[c] * s->coarse[cv[c] * nch + ch];
+    }
+    for (int ch = 0; ch < OR_NFEAT; ++ch) g_coarse_v[ch] = g_f[ch];
+    if (s->aggregation == 5) {
+        /* Instant-NGP's tiny MLP in place of the attention: f = f~ + W2 relu(W1 x),
+         * x = [f^1, ..., f^L].  Its reverse: dW2 += g_f relu(h)^T, g_h = (W2^T g_f)
+         * where h > 0, dW1 += g_h x^T, g_x = W1^T g_h, then each level's entries. */
+        int nx = OR_NFEAT * s->L;
+        const double* w1 = s->agg_mlp;
+        const double* w2 = s->agg_mlp + (size_t)OR_AGG_HIDDEN * nx;
+        double xs[OR_NFEAT * OR_MAXL], h[OR_AGG_HIDDEN], gh[OR_AGG_HIDDEN], gx[OR_NFEAT * OR_MAXL];
+        uint64_t ents[OR_MAXL][8];
+        double ews[OR_MAXL][8];
+        memset(xs, 0, sizeof xs);
+        for (int l = 0; l < s->L; ++l) {
+            int bl[3];
+            double wl[3];
+            or_cell(u, s->N[l], bl, wl);
+            uint64_t off = or_level_offset(s->N, s->L, s->T_log2, l);
+            for (int c = 0; c < 8; ++c) {
+                int xx = bl[0] + (c & 1), yy = bl[1] + ((c >> 1) & 1), zz = bl[2] + ((c >> 2) & 1);
+                ents[l][c] = off + or_level_entry(s->N[l], T, xx, yy, zz);
+                ews[l][c] = or_corner_weight(wl, c);
+                for (int ch = 0; ch < OR_NFEAT; ++ch)
+                    xs[OR_NFEAT * l + ch] += ews[l][c] * s->tables[ents[l][c] * OR_NFEAT + ch];
+            }
+        }
+        for (int j = 0; j < OR_AGG_HIDDEN; ++j) {
+            double acc = 0.0, mag = 0.0;
+            for (int q = 0; q < nx; ++q) {
+                acc += w1[(size_t)j * nx + q] * xs[q];
+                mag += fabs(w1[(size_t)j * nx + q] * xs[q]);
+            }
+            h[j] = acc;
+            /* a unit this close to its ReLU kink may switch sides in FP32: the
+             * ray's gradient is then not comparable element by element */
+            if (kink && fabs(acc) <= 1e-5 * mag) *kink = 1;
+        }
+        for (int j = 0; j < OR_AGG_HIDDEN; ++j) {
+            double ga = 0.0;
+            for (int k = 0; k < OR_NFEAT; ++k) ga += w2[k * OR_AGG_HIDDEN + j] * g_f[k];
+            gh[j] = h[j] > 0.0 ? ga : 0.0;
+        }
+        if (g_agg_mlp) {
+            double* gw2 = g_agg_mlp + (size_t)OR_AGG_HIDDEN * nx;
+            for (int k = 0; k < OR_NFEAT; ++k)
+                for (int j = 0; j < OR_AGG_HIDDEN; ++j) gw2[k * OR_AGG_HIDDEN + j] += g_f[k] * fmax(h[j], 0.0);
+            for (int j = 0; j < OR_AGG_HIDDEN; ++j)
+                for (int q = 0; q < nx; ++q) g_agg_mlp[(size_t)j * nx + q] += gh[j] * xs[q];
+        }
+        for (int q = 0; q < nx; ++q) {
+            double acc = 0.0;
+            for (int j = 0; j < OR_AGG_HIDDEN; ++j) acc += w1[(size_t)j * nx + q] * gh[j];
+            gx[q] = acc;
+        }
+        for (int l = 0; l < s->L; ++l)
+            for (int c = 0; c < 8; ++c)
+                for (int ch = 0; ch < OR_NFEAT; ++ch)
+                    g_tables[ents[l][c] * OR_NFEAT + ch] += ews[l][c] * gx[OR_NFEAT * l + ch];
+    }
+    for (int l = 0; l < (s->aggregation == 5 ? 0 : s->L); ++l) {
+        /* the gates of this level and whether each is shared by both modalities */
+        double om = 1.0, be = 1.0;
+        int shared = 0;
+        switch (s->aggregation) {
+            case 0:
+                if (op->attn_mode == 2) { om = or_sigmoid(coarse[OR_NFEAT + 2 * l]); be = om; shared = 1; }
+                else if (op->attn_mode == 0) {
+                    om = or_sigmoid(coarse[OR_NFEAT + 2 * l]);
+                    be = or_sigmoid(coarse[OR_NFEAT + 2 * l + 1]);
+                }
+                break;
+            case 1: om = or_sigmoid(coarse[OR_NFEAT + l]); be = om; shared = 1; break;
+            case 2: om = or_sigmoid(s->attn_inv[2 * l]); be = or_sigmoid(s->attn_inv[2 * l + 1]); break;
+            case 3: om = or_sigmoid(s->attn_inv[l]); be = om; shared = 1; break;
+            default: break; /* 4: plain sum */
+        }
+        int bl[3];
+        double wl[3];
+        or_cell(u, s->N[l], bl, wl);
+        uint64_t off = or_level_offset(s->N, s->L, s->T_log2, l);
+        double fl[OR_NFEAT];
+        memset(fl, 0, sizeof fl);
+        uint64_t ent[8];
+        double ew[8];
+        for (int c = 0; c < 8; ++c) {
+            int xx = bl[0] + (c & 1), yy = bl[1] + ((c >> 1) & 1), zz = bl[2] + ((c >> 2) & 1);
+            ent[c] = off + or_level_entry(s->N[l], T, xx, yy, zz);
+            ew[c] = or_corner_weight(wl, c);
+            for (int ch = 0; ch < OR_NFEAT; ++ch) fl[ch] += ew[c] * s->tables[ent[c] * OR_NFEAT + ch];
+        }
+        double g_om = fl[0] * g_f[0], g_be = 0.0;
+        for (int ch = 1; ch < OR_NFEAT; ++ch) g_be += fl[ch] * g_f[ch];
+        /* gate gradients through the sigmoid, to the logit they come from */
+        double lo_g = shared ? (g_om + g_be) * om * (1.0 - om) : g_om * om * (1.0 - om);
+        double lb_g = shared ? 0.0 : g_be * be * (1.0 - be);
+        if (s->aggregation == 0 && op->attn_mode == 0) {
+            g_coarse_v[OR_NFEAT + 2 * l] += lo_g;
+            g_coarse_v[OR_NFEAT + 2 * l + 1] += lb_g;
+        } else if (s->aggregation == 0 && op->attn_mode == 2) {
+            g_coarse_v[OR_NFEAT + 2 * l] += lo_g;
+        } else if (s->aggregation == 1) {
+            g_coarse_v[OR_NFEAT + l] += lo_g;
+        } else if (s->aggregation == 2 && g_attn_inv) {
+            g_attn_inv[2 * l] += lo_g;
+            g_attn_inv[2 * l + 1] += lb_g;
+        } else if (s->aggregation == 3 && g_attn_inv) {
+            g_attn_inv[l] += lo_g;
+        }
+        for (int c = 0; c < 8; ++c) {
+            g_tables[ent[c] * OR_NFEAT + 0] += ew[c] * om * g_f[0];
+            for (int ch = 1; ch < OR_NFEAT; ++ch) g_tables[ent[c] * OR_NFEAT + ch] += ew[c] * be * g_f[ch];
+        }
+    }
+    for (int c = 0; c < 8; ++c)
+        for (int ch = 0; ch < nch; ++ch) g_coarse[cv[c] * nch + ch] += cwt[c] * g_coarse_v[ch];
+}
+
 /* Reverse-mode derivative of or_render with respect to the fine tables, the coarse
  * grid and the MLP weights, accumulated (+=) into g_tables, g_coarse, g_mlp.
  *
@@ -791,8 +932,6 @@ void or_render_backward(const or_scene* s, const or_occ* oc, const or_opts* op,
     int cap = op->max_samples > 0 ? op->max_samples : 1;
     or_sample* sm = (or_sample*)malloc(sizeof(or_sample) * (size_t)cap);
     double* qg = (double*)malloc(sizeof(double) * (size_t)cap);
-    int nch = or_coarse_channels(s->L, s->aggregation);
-    uint32_t T = 1u << s->T_log2;
     for (int i = 0; i < n; ++i) {
         float o[3], dv[3], d[3];
         or_ray_input(cams, n_cams, W, H, pix, rays_o, rays_d, i, o, dv);
@@ -858,135 +997,7 @@ void or_render_backward(const or_scene* s, const or_occ* oc, const or_opts* op,
             g_f[0] = g_sigma * exp(fmin(sp->sigma_raw, 15.0));
             for (int k = 0; k < 3; ++k) g_f[1 + k] = w * g_Cd[k];
             for (int k = 0; k < 4; ++k) g_f[4 + k] = w * g_F[k];
-            /* Eq. 6-8 reverse: coarse part, attention logits, fine levels */
-            double coarse[OR_NFEAT + 2 * OR_MAXL], g_coarse_v[OR_NFEAT + 2 * OR_MAXL];
-            int base[3];
-            double wc[3];
-            memset(coarse, 0, sizeof coarse);
-            memset(g_coarse_v, 0, sizeof g_coarse_v);
-            or_cell(sp->u, s->R_C, base, wc);
-            size_t cv[8];
-            double cwt[8];
-            for (int c = 0; c < 8; ++c) {
-                int xx = base[0] + (c & 1), yy = base[1] + ((c >> 1) & 1), zz = base[2] + ((c >> 2) & 1);
-                cv[c] = (size_t)xx + (size_t)s->R_C * ((size_t)yy + (size_t)s->R_C * zz);
-                cwt[c] = or_corner_weight(wc, c);
-                for (int ch = 0; ch < nch; ++ch) coarse[ch] += cwt[c] * s->coarse[cv[c] * nch + ch];
-            }
-            for (int ch = 0; ch < OR_NFEAT; ++ch) g_coarse_v[ch] = g_f[ch];
-            if (s->aggregation == 5) {
-                /* Instant-NGP's tiny MLP in place of the attention: f = f~ + W2 relu(W1 x),
-                 * x = [f^1, ..., f^L].  Its reverse: dW2 += g_f relu(h)^T, g_h = (W2^T g_f)
-                 * where h > 0, dW1 += g_h x^T, g_x = W1^T g_h, then each level's entries. */
-                int nx = OR_NFEAT * s->L;
-                const double* w1 = s->agg_mlp;
-                const double* w2 = s->agg_mlp + (size_t)OR_AGG_HIDDEN * nx;
-                double xs[OR_NFEAT * OR_MAXL], h[OR_AGG_HIDDEN], gh[OR_AGG_HIDDEN], gx[OR_NFEAT * OR_MAXL];
-                uint64_t ents[OR_MAXL][8];
-                double ews[OR_MAXL][8];
-                memset(xs, 0, sizeof xs);
-                for (int l = 0; l < s->L; ++l) {
-                    int bl[3];
-                    double wl[3];
-                    or_cell(sp->u, s->N[l], bl, wl);
-                    uint64_t off = or_level_offset(s->N, s->L, s->T_log2, l);
-                    for (int c = 0; c < 8; ++c) {
-                        int xx = bl[0] + (c & 1), yy = bl[1] + ((c >> 1) & 1), zz = bl[2] + ((c >> 2) & 1);
-                        ents[l][c] = off + or_level_entry(s->N[l], T, xx, yy, zz);
-                        ews[l][c] = or_corner_weight(wl, c);
-                        for (int ch = 0; ch < OR_NFEAT; ++ch)
-                            xs[OR_NFEAT * l + ch] += ews[l][c] * s->tables[ents[l][c] * OR_NFEAT + ch];
-                    }
-                }
-                for (int j = 0; j < OR_AGG_HIDDEN; ++j) {
-                    double acc = 0.0, mag = 0.0;
-                    for (int q = 0; q < nx; ++q) {
-                        acc += w1[(size_t)j * nx + q] * xs[q];
-                        mag += fabs(w1[(size_t)j * nx + q] * xs[q]);
-                    }
-                    h[j] = acc;
-                    /* a unit this close to its ReLU kink may switch sides in FP32: the
-                     * ray's gradient is then not comparable element by element */
-                    if (kink && fabs(acc) <= 1e-5 * mag) kink[i] = 1;
-                }
-                for (int j = 0; j < OR_AGG_HIDDEN; ++j) {
-                    double ga = 0.0;
-                    for (int k = 0; k < OR_NFEAT; ++k) ga += w2[k * OR_AGG_HIDDEN + j] * g_f[k];
-                    gh[j] = h[j] > 0.0 ? ga : 0.0;
-                }
-                if (g_agg_mlp) {
-                    double* gw2 = g_agg_mlp + (size_t)OR_AGG_HIDDEN * nx;
-                    for (int k = 0; k < OR_NFEAT; ++k)
-                        for (int j = 0; j < OR_AGG_HIDDEN; ++j) gw2[k * OR_AGG_HIDDEN + j] += g_f[k] * fmax(h[j], 0.0);
-                    for (int j = 0; j < OR_AGG_HIDDEN; ++j)
-                        for (int q = 0; q < nx; ++q) g_agg_mlp[(size_t)j * nx + q] += gh[j] * xs[q];
-                }
-                for (int q = 0; q < nx; ++q) {
-                    double acc = 0.0;
-                    for (int j = 0; j < OR_AGG_HIDDEN; ++j) acc += w1[(size_t)j * nx + q] * gh[j];
-                    gx[q] = acc;
-                }
-                for (int l = 0; l < s->L; ++l)
-                    for (int c = 0; c < 8; ++c)
-                        for (int ch = 0; ch < OR_NFEAT; ++ch)
-                            g_tables[ents[l][c] * OR_NFEAT + ch] += ews[l][c] * gx[OR_NFEAT * l + ch];
-            }
-            for (int l = 0; l < (s->aggregation == 5 ? 0 : s->L); ++l) {
-                /* the gates of this level and whether each is shared by both modalities */
-                double om = 1.0, be = 1.0;
-                int shared = 0;
-                switch (s->aggregation) {
-                    case 0:
-                        if (op->attn_mode == 2) { om = or_sigmoid(coarse[OR_NFEAT + 2 * l]); be = om; shared = 1; }
-                        else if (op->attn_mode == 0) {
-                            om = or_sigmoid(coarse[OR_NFEAT + 2 * l]);
-                            be = or_sigmoid(coarse[OR_NFEAT + 2 * l + 1]);
-                        }
-                        break;
-                    case 1: om = or_sigmoid(coarse[OR_NFEAT + l]); be = om; shared = 1; break;
-                    case 2: om = or_sigmoid(s->attn_inv[2 * l]); be = or_sigmoid(s->attn_inv[2 * l + 1]); break;
-                    case 3: om = or_sigmoid(s->attn_inv[l]); be = om; shared = 1; break;
-                    default: break; /* 4: plain sum */
-                }
-                int bl[3];
-                double wl[3];
-                or_cell(sp->u, s->N[l], bl, wl);
-                uint64_t off = or_level_offset(s->N, s->L, s->T_log2, l);
-                double fl[OR_NFEAT];
-                memset(fl, 0, sizeof fl);
-                uint64_t ent[8];
-                double ew[8];
-                for (int c = 0; c < 8; ++c) {
-                    int xx = bl[0] + (c & 1), yy = bl[1] + ((c >> 1) & 1), zz = bl[2] + ((c >> 2) & 1);
-                    ent[c] = off + or_level_entry(s->N[l], T, xx, yy, zz);
-                    ew[c] = or_corner_weight(wl, c);
-                    for (int ch = 0; ch < OR_NFEAT; ++ch) fl[ch] += ew[c] * s->tables[ent[c] * OR_NFEAT + ch];
-                }
-                double g_om = fl[0] * g_f[0], g_be = 0.0;
-                for (int ch = 1; ch < OR_NFEAT; ++ch) g_be += fl[ch] * g_f[ch];
-                /* gate gradients through the sigmoid, to the logit they come from */
-                double lo_g = shared ? (g_om + g_be) * om * (1.0 - om) : g_om * om * (1.0 - om);
-                double lb_g = shared ? 0.0 : g_be * be * (1.0 - be);
-                if (s->aggregation == 0 && op->attn_mode == 0) {
-                    g_coarse_v[OR_NFEAT + 2 * l] += lo_g;
-                    g_coarse_v[OR_NFEAT + 2 * l + 1] += lb_g;
-                } else if (s->aggregation == 0 && op->attn_mode == 2) {
-                    g_coarse_v[OR_NFEAT + 2 * l] += lo_g;
-                } else if (s->aggregation == 1) {
-                    g_coarse_v[OR_NFEAT + l] += lo_g;
-                } else if (s->aggregation == 2 && g_attn_inv) {
-                    g_attn_inv[2 * l] += lo_g;
-                    g_attn_inv[2 * l + 1] += lb_g;
-                } else if (s->aggregation == 3 && g_attn_inv) {
-                    g_attn_inv[l] += lo_g;
-                }
-                for (int c = 0; c < 8; ++c) {
-                    g_tables[ent[c] * OR_NFEAT + 0] += ew[c] * om * g_f[0];
-                    for (int ch = 1; ch < OR_NFEAT; ++ch) g_tables[ent[c] * OR_NFEAT + ch] += ew[c] * be * g_f[ch];
-                }
-            }
-            for (int c = 0; c < 8; ++c)
-                for (int ch = 0; ch < nch; ++ch) g_coarse[cv[c] * nch + ch] += cwt[c] * g_coarse_v[ch];
+            or_feature_reverse(s, op, sp->u, g_f, g_tables, g_coarse, g_attn_inv, g_agg_mlp, kink ? kink + i : NULL);
         }
     }
     free(sm);
@@ -1334,12 +1345,9 @@ void or_distortion(const or_scene* s, const or_occ* oc, const or_opts* op,
 void or_distortion_backward(const or_scene* s, const or_occ* oc, const or_opts* op,
                             const float* cams, int n_cams, int W, int H, const int32_t* pix,
                             const float* rays_o, const float* rays_d, int n, double scale,
-                            double* g_tables, double* g_coarse) {
-    if (s->aggregation != 0) return; /* Eq. 8 only (oracle.py refuses the rest) */
+                            double* g_tables, double* g_coarse, double* g_attn_inv, double* g_agg_mlp) {
     or_sample* sm = (or_sample*)malloc(sizeof(or_sample) * (size_t)(op->max_samples > 0 ? op->max_samples : 1));
     double* g = (double*)malloc(sizeof(double) * (size_t)(op->max_samples > 0 ? op->max_samples : 1));
-    int nch = OR_NFEAT + 2 * s->L;
-    uint32_t T = 1u << s->T_log2;
     for (int r = 0; r < n; ++r) {
         float o[3], dv[3];
         or_ray_input(cams, n_cams, W, H, pix, rays_o, rays_d, r, o, dv);
@@ -1361,38 +1369,9 @@ void or_distortion_backward(const or_scene* s, const or_occ* oc, const or_opts* 
             double T_next = sp->T_before * (1.0 - sp->alpha);
             double d_sigma = (double)sp->delta * T_next * g[i];
             for (int j = i + 1; j < ns; ++j) d_sigma -= (double)sp->delta * sm[j].T_before * sm[j].alpha * g[j];
-            double gs = scale * d_sigma * exp(fmin(sp->sigma_raw, 15.0));
-            int base[3];
-            double wc[3];
-            or_cell(sp->u, s->R_C, base, wc);
-            size_t cv[8];
-            double cwt[8], logit_om[OR_MAXL];
-            for (int l = 0; l < s->L; ++l) logit_om[l] = 0.0;
-            for (int c = 0; c < 8; ++c) {
-                int xx = base[0] + (c & 1), yy = base[1] + ((c >> 1) & 1), zz = base[2] + ((c >> 2) & 1);
-                cv[c] = (size_t)xx + (size_t)s->R_C * ((size_t)yy + (size_t)s->R_C * zz);
-                cwt[c] = or_corner_weight(wc, c);
-                for (int l = 0; l < s->L; ++l) logit_om[l] += cwt[c] * s->coarse[cv[c] * nch + OR_NFEAT + 2 * l];
-            }
-            for (int c = 0; c < 8; ++c) g_coarse[cv[c] * nch] += cwt[c] * gs;
-            for (int l = 0; l < s->L; ++l) {
-                double om = op->attn_mode == 1 ? 1.0 : or_sigmoid(logit_om[l]);
-                int bl[3];
-                double wl[3];
-                or_cell(sp->u, s->N[l], bl, wl);
-                uint64_t off = or_level_offset(s->N, s->L, s->T_log2, l);
-                double sh = 0.0;
-                for (int c = 0; c < 8; ++c) {
-                    int xx = bl[0] + (c & 1), yy = bl[1] + ((c >> 1) & 1), zz = bl[2] + ((c >> 2) & 1);
-                    uint64_t e = off + or_level_entry(s->N[l], T, xx, yy, zz);
-                    double ew = or_corner_weight(wl, c);
-                    sh += ew * s->tables[e * OR_NFEAT];
-                    g_tables[e * OR_NFEAT] += ew * om * gs;
-                }
-                if (op->attn_mode != 1)
-                    for (int c = 0; c < 8; ++c)
-                        g_coarse[cv[c] * nch + OR_NFEAT + 2 * l] += cwt[c] * gs * sh * om * (1.0 - om);
-            }
+            /* the regulariser sees the density only: f's cotangent is [dL/d sigma_raw, 0, ...] */
+            double g_f[OR_NFEAT] = {scale * d_sigma * exp(fmin(sp->sigma_raw, 15.0)), 0, 0, 0, 0, 0, 0, 0};
+            or_feature_reverse(s, op, sp->u, g_f, g_tables, g_coarse, g_attn_inv, g_agg_mlp, NULL);
         }
     }
     free(g);

@@ -301,19 +301,24 @@ class Oracle:
                             _p(rd), C.c_int(n), _p(out))
         return out
 
-    def distortion_backward(self, opts, scale=1.0, cams=None, pix=None, rays_o=None, rays_d=None, W=None, H=None):
-        """Gradients of scale * sum over rays of L_dist: (g_tables, g_coarse)."""
-        if int(getattr(self.cfg, "aggregation", 0)) != 0:
-            raise NotImplementedError("the reverse pass follows Eq. 8 (aggregation 0) only")
+    def distortion_backward(self, opts, scale=1.0, cams=None, pix=None, rays_o=None, rays_d=None, W=None, H=None,
+                            full=False):
+        """Gradients of scale * sum over rays of L_dist: (g_tables, g_coarse), or with
+        full=True a dict that adds the constant logits' and the tiny MLP's gradients."""
         W = W or self.cfg.W
         H = H or self.cfg.H
         cams, pix, ro, rd, n = self._rays(cams, pix, rays_o, rays_d)
         g_t = np.zeros_like(self.tables)
         g_c = np.zeros_like(self.coarse)
+        g_i = np.zeros_like(self.attn_inv) if self.attn_inv is not None else None
+        g_a = np.zeros_like(self.agg_mlp) if self.agg_mlp is not None else None
         op = self._opts(opts)
         lib().or_distortion_backward(C.byref(self._s), C.byref(self._o), C.byref(op), _p(cams),
                                      C.c_int(0 if cams is None else len(cams)), C.c_int(W), C.c_int(H), _p(pix),
-                                     _p(ro), _p(rd), C.c_int(n), C.c_double(scale), _p(g_t), _p(g_c))
+                                     _p(ro), _p(rd), C.c_int(n), C.c_double(scale), _p(g_t), _p(g_c), _p(g_i),
+                                     _p(g_a))
+        if full:
+            return dict(tables=g_t, coarse=g_c, attn_inv=g_i, agg_mlp=g_a)
         return g_t, g_c
 
     def render_backward(self, opts, d_rgb=None, d_depth=None, d_opacity=None, cams=None, pix=None,

@@ -123,3 +123,54 @@ def test_distortion_gradient_matches_central_differences(attn_mode):
     assert checked >= 20
     # colour channels get no distortion gradient
     assert np.all(g_t[:, 1:] == 0) and np.all(g_c[:, 1:8] == 0)
+
+
+@pytest.mark.parametrize("agg", [1, 2, 3, 4, 5])
+def test_distortion_gradient_of_the_aggregation_forms(agg):
+    """Eq. S2's gradient through Table 3's other forms (the density path of each: its
+    gate logits, constant logits or the tiny MLP), by central differences along random
+    directions and on single coordinates."""
+    cfg = S.small_config(blob_std=(0.05, 0.15), aggregation=agg)
+    sc = S.make_scene(cfg)
+    if sc.coarse.shape[1] > 8:
+        sc.coarse[:, 8:] *= 10.0
+    if sc.attn_inv is not None:
+        sc.attn_inv = sc.attn_inv * 20.0
+    orc = O.oracle_for_scene(sc)
+    opts = S.default_options(cfg, t_term=0.0)
+    o, d = S.random_rays(10, 13, True)
+    scale = 0.7
+    h = 1e-4 if agg == 5 else H     # the MLP's ReLU kinks: a smaller step
+
+    def loss():
+        return scale * orc.distortion(opts, rays_o=o, rays_d=d)[:, 0].sum()
+    g = orc.distortion_backward(opts, scale, rays_o=o, rays_d=d, full=True)
+    rng = np.random.default_rng(agg)
+    names = [("tables", orc.tables), ("coarse", orc.coarse)]
+    names += [(k, getattr(orc, k)) for k in ("attn_inv", "agg_mlp") if getattr(orc, k) is not None]
+    for name, arr in names:
+        flat = arr.reshape(-1)
+        gr = g[name].reshape(-1)
+        nz = np.flatnonzero(np.abs(gr) > 1e-7)
+        assert len(nz) > 0, name
+        for i in rng.choice(nz, min(8, len(nz)), replace=False):
+            keep = flat[i]
+            flat[i] = keep + h
+            fp = loss()
+            flat[i] = keep - h
+            fm = loss()
+            flat[i] = keep
+            fd = (fp - fm) / (2 * h)
+            assert abs(fd - gr[i]) < 1e-5 + 1e-4 * abs(fd), (name, i, fd, gr[i])
+        v = rng.normal(size=flat.size)
+        v /= np.linalg.norm(v)
+        keep = flat.copy()
+        flat[:] = keep + h * v
+        fp = loss()
+        flat[:] = keep - h * v
+        fm = loss()
+        flat[:] = keep
+        an = float(gr @ v)
+        assert abs((fp - fm) / (2 * h) - an) < 1e-5 + 1e-4 * abs(an), (name, an)
+    if agg != 5:       # only the density channels carry the regulariser's gradient
+        assert np.all(g["tables"][:, 1:] == 0) and np.all(g["coarse"][:, 1:8] == 0)
