@@ -427,9 +427,16 @@ int32_t ngprt_huber_loss(const float* rgb, const float* target, int64_t n, float
  * scale * sum over rays of L_dist to *loss (NULL to skip).
  * ngprt_distortion_backward ACCUMULATES scale * dL_dist/d(parameters) into g_tables
  * and g_coarse (FP32, layouts of the scene) from that dist_state: the density path
- * only (sigma~, the omega logits and the fine density channel).  Both need F32
- * tables, the Eq. 8 aggregation and L in {1, 2, 3, 4, 8, 16}; rays as for ngprt_render.
+ * only (sigma~, the density logits and the fine density channel; for the tiny-MLP
+ * form every channel it mixes), and for SEPARATE_INV / SHARED_INV into g_attn_inv,
+ * for the MLP form into g_agg_mlp (NULL otherwise).  Both need F32 tables; L in
+ * {1, 2, 3, 4, 8, 16} for Eq. 8, {2, 4, 16} for the other forms; rays as for
+ * ngprt_render.  workspace: ngprt_distortion_backward_workspace_bytes(scene, opts,
+ * n_rays) bytes, 16-byte aligned (0, and NULL allowed, except for the MLP form, which
+ * keeps one record per sample there).
  */
+size_t ngprt_distortion_backward_workspace_bytes(const ngprt_scene* scene, const ngprt_render_opts* opts,
+                                                 int64_t n_rays);
 int32_t ngprt_distortion_loss(const ngprt_scene* scene, const ngprt_occ* occ, const ngprt_camera* cams,
                               int32_t n_cams, const int32_t* pixel_ids, const float* rays_o, const float* rays_d,
                               int64_t n_rays, const ngprt_render_opts* opts, float scale, float* dist_state,
@@ -437,7 +444,8 @@ int32_t ngprt_distortion_loss(const ngprt_scene* scene, const ngprt_occ* occ, co
 int32_t ngprt_distortion_backward(const ngprt_scene* scene, const ngprt_occ* occ, const ngprt_camera* cams,
                                   int32_t n_cams, const int32_t* pixel_ids, const float* rays_o, const float* rays_d,
                                   int64_t n_rays, const ngprt_render_opts* opts, const float* dist_state, float scale,
-                                  float* g_tables, float* g_coarse, void* stream);
+                                  float* g_tables, float* g_coarse, float* g_attn_inv, float* g_agg_mlp,
+                                  void* workspace, size_t ws_bytes, void* stream);
 
 /*
  * Step-size auto-tuning of training (Eq. S3).  ngprt_mean_samples writes to the

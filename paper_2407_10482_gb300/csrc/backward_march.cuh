@@ -25,6 +25,8 @@ struct MarchBwdParams {
     float* records;     // MLP form: per-sample (f^1..f^L, g_f) records for the weight gradient
     int32_t* n_records; // their count (device)
     int64_t rec_capacity;
+    const float* dist_state;  // distortion mode: per ray (L_dist, W, S, 0) of the forward
+    float dist_scale;         // distortion mode: dL_total / dL_dist
 };
 
 // Floats of one MLP-form sample record: the level features x (8L) and the feature
@@ -130,7 +132,10 @@ __device__ __forceinline__ void scatter_mlp_levels(const Grid& g, const float u[
 // summed onto one logit where omega and beta are one gate.  Spatial logits go with gf
 // to the 8 coarse vertices (Eq. 8: slots [0, 2L) -> channels 8 + [0, 2L); one gate per
 // level: slot l -> channel 8 + l); invariant ones add to the thread's sums.
-template <int L, int AGG>
+// kDensityOnly (the distortion regulariser, whose cotangent is [gs, 0, ...]): the
+// gated forms and the sum add nothing to the colour channels, so only the density
+// channel of each entry and vertex (and the logits) are written.
+template <int L, int AGG, bool kDensityOnly = false>
 __device__ __forceinline__ void scatter_features(const Grid& g, const float u[3], int attn_mode, float gs, float w,
                                                  const float gq[7], float* slots, int stride, float* g_tables,
                                                  float* g_coarse) {
@@ -163,8 +168,12 @@ __device__ __forceinline__ void scatter_features(const Grid& g, const float u[3]
             const float cw = corner_w(wl, c);
             const float cb = cw * be;
             float* gp = g_tables + (size_t)row * 8;
-            atomic_add4(gp, cw * s0, cb * gw[0], cb * gw[1], cb * gw[2]);
-            atomic_add4(gp + 4, cb * gw[3], cb * gw[4], cb * gw[5], cb * gw[6]);
+            if constexpr (kDensityOnly) {
+                atomicAdd(gp, cw * s0);
+            } else {
+                atomic_add4(gp, cw * s0, cb * gw[0], cb * gw[1], cb * gw[2]);
+                atomic_add4(gp + 4, cb * gw[3], cb * gw[4], cb * gw[5], cb * gw[6]);
+            }
         }
         if constexpr (AGG == NGPRT_AGG_SEPARATE_V) {
             float go = 0.0f, gb = 0.0f;
@@ -198,7 +207,13 @@ __device__ __forceinline__ void scatter_features(const Grid& g, const float u[3]
         const uint32_t cv = (uint32_t)(b[0] + (c & 1)) + R * ((uint32_t)(b[1] + ((c >> 1) & 1)) + R * (uint32_t)(b[2] + ((c >> 2) & 1)));
         const float cw = corner_w(wc, c);
         float* gp = g_coarse + (size_t)cv * NC;
-        if constexpr (NC % 4 == 0) {
+        if constexpr (kDensityOnly) {
+            atomicAdd(gp, cw * gs);
+            if (logits) {
+#pragma unroll
+                for (int k = 0; k < NLOG; ++k) atomicAdd(gp + 8 + k, cw * slots[k * stride]);
+            }
+        } else if constexpr (NC % 4 == 0) {
             atomic_add4(gp, cw * gs, cw * gw[0], cw * gw[1], cw * gw[2]);
             atomic_add4(gp + 4, cw * gw[3], cw * gw[4], cw * gw[5], cw * gw[6]);
             if (logits) {
@@ -219,7 +234,10 @@ __device__ __forceinline__ void scatter_features(const Grid& g, const float u[3]
     }
 }
 
-template <int L, int AGG>
+// kDist: the distortion regulariser's reverse pass (Eq. S2): the colour cotangents
+// stay 0 and each sample's dL/dsigma comes from the running sums W, S, G against the
+// ray's totals, as in the regulariser's own reverse pass.
+template <int L, int AGG, bool kDist = false>
 struct BackwardSampler {
     const Grid& g;
     int attn_mode;
@@ -232,6 +250,8 @@ struct BackwardSampler {
     float* records;
     int32_t* n_records;
     int64_t rec_capacity;
+    float dW = 0.0f, dS = 0.0f, dG = 0.0f;                         // distortion running sums
+    float dW_tot = 0.0f, dS_tot = 0.0f, dG_tot = 0.0f, d_scale = 0.0f;  // and the ray's totals
     __device__ __forceinline__ bool sample(const float u[3], float t, float delta) {
         float f[8];
         const float gq[7] = {gCd[0], gCd[1], gCd[2], gF[0], gF[1], gF[2], gF[3]};
@@ -240,15 +260,28 @@ struct BackwardSampler {
         const float trans = expf(-sigma * delta);
         const float w = T * (1.0f - trans);
         const float T_next = T * trans;
-        float qg = fmaf(gD, t, gA);
+        float gs;
+        if constexpr (kDist) {
+            const float m = fmaf(0.5f, delta, t);
+            const float W_lt = dW, S_lt = dS;
+            dW += w;
+            dS = fmaf(w, m, dS);
+            const float gw = 2.0f * (fmaf(m, W_lt, -S_lt) + (dS_tot - dS) - m * (dW_tot - dW)) +
+                             (2.0f / 3.0f) * w * delta;
+            dG = fmaf(w, gw, dG);
+            const float g_sigma = delta * (T_next * gw - (dG_tot - dG));
+            gs = d_scale * g_sigma * expf(fminf(f[0], 15.0f));
+        } else {
+            float qg = fmaf(gD, t, gA);
 #pragma unroll
-        for (int k = 0; k < 3; ++k) qg = fmaf(gCd[k], f[1 + k], qg);
+            for (int k = 0; k < 3; ++k) qg = fmaf(gCd[k], f[1 + k], qg);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) qg = fmaf(gF[k], f[4 + k], qg);
-        S_le = fmaf(w, qg, S_le);
-        const float g_sigma = delta * (T_next * qg - (S_tot - S_le));
-        const float gs = g_sigma * expf(fminf(f[0], 15.0f));
-        scatter_features<L, AGG>(g, u, attn_mode, gs, w, gq, gates, blockDim.x, g_tables, g_coarse);
+            for (int k = 0; k < 4; ++k) qg = fmaf(gF[k], f[4 + k], qg);
+            S_le = fmaf(w, qg, S_le);
+            const float g_sigma = delta * (T_next * qg - (S_tot - S_le));
+            gs = g_sigma * expf(fminf(f[0], 15.0f));
+        }
+        scatter_features<L, AGG, kDist>(g, u, attn_mode, gs, w, gq, gates, blockDim.x, g_tables, g_coarse);
         if constexpr (AGG == NGPRT_AGG_MLP) {
             // (x, g_f) of this sample for the weight gradient; capacity n_rays x
             // max_samples is never exceeded, the bound only guards the buffer
@@ -276,7 +309,7 @@ struct BackwardSampler {
 #define NGPRT_BWD_MIN_BLOCKS 1
 #endif
 
-template <int L, int AGG>
+template <int L, int AGG, bool kDist = false>
 __global__ void __launch_bounds__(128, NGPRT_BWD_MIN_BLOCKS) march_backward_kernel(const __grid_constant__ MarchBwdParams p) {
     extern __shared__ float gate_smem[];
     constexpr int NI = n_inv_logits<L, AGG>();
@@ -294,13 +327,23 @@ __global__ void __launch_bounds__(128, NGPRT_BWD_MIN_BLOCKS) march_backward_kern
         if (!live) return;
     }
     if (live) {
-        const float4* c4 = reinterpret_cast<const float4*>(p.cot + ray * kCotFloats);
-        const float4 q0 = c4[0], q1 = c4[1], q2 = c4[2];
-        BackwardSampler<L, AGG> smp{p.m.g, p.m.opts.attn_mode, p.m.opts.t_term, 1.0f, 0.0f, q2.y,
-                                    {q0.x, q0.y, q0.z}, {q0.w, q1.x, q1.y, q1.z}, q1.w, q2.x, p.g_tables,
-                                    p.g_coarse, slots, p.records, p.n_records, p.rec_capacity};
         int n_march = 0, n_samp = 0;
-        march_loop(p.m, o, d, t, t_out, smp, n_march, n_samp);
+        if constexpr (kDist) {
+            const float4 ds = reinterpret_cast<const float4*>(p.dist_state)[ray];
+            BackwardSampler<L, AGG, true> smp{p.m.g, p.m.opts.attn_mode, p.m.opts.t_term, 1.0f, 0.0f, 0.0f,
+                                              {0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f, 0.0f}, 0.0f, 0.0f,
+                                              p.g_tables, p.g_coarse, slots, p.records, p.n_records,
+                                              p.rec_capacity, 0.0f, 0.0f, 0.0f, ds.y, ds.z, 2.0f * ds.x,
+                                              p.dist_scale};
+            march_loop(p.m, o, d, t, t_out, smp, n_march, n_samp);
+        } else {
+            const float4* c4 = reinterpret_cast<const float4*>(p.cot + ray * kCotFloats);
+            const float4 q0 = c4[0], q1 = c4[1], q2 = c4[2];
+            BackwardSampler<L, AGG> smp{p.m.g, p.m.opts.attn_mode, p.m.opts.t_term, 1.0f, 0.0f, q2.y,
+                                        {q0.x, q0.y, q0.z}, {q0.w, q1.x, q1.y, q1.z}, q1.w, q2.x, p.g_tables,
+                                        p.g_coarse, slots, p.records, p.n_records, p.rec_capacity};
+            march_loop(p.m, o, d, t, t_out, smp, n_march, n_samp);
+        }
     }
     if constexpr (NI > 0) {
         // the block's sums of the invariant logits' gradients: thread k < NI adds
@@ -414,12 +457,13 @@ void launch_agg_mlp_wgrad(const MarchBwdParams& p, const float* w, float* g_w, c
     agg_mlp_wgrad_kernel<L><<<blocks, 128, smem, st>>>(p.records, p.n_records, p.rec_capacity, w, g_w);
 }
 
-template <int L, int AGG>
+template <int L, int AGG, bool kDist = false>
 void launch_bwd(const MarchBwdParams& p, dim3 grid, cudaStream_t st) {
     const size_t smem = (size_t)bwd_slots<L, AGG>() * 128 * sizeof(float);
     if (smem > 48 * 1024)
-        cudaFuncSetAttribute(march_backward_kernel<L, AGG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    march_backward_kernel<L, AGG><<<grid, 128, smem, st>>>(p);
+        cudaFuncSetAttribute(march_backward_kernel<L, AGG, kDist>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    march_backward_kernel<L, AGG, kDist><<<grid, 128, smem, st>>>(p);
 }
 
 // The gate forms other than Eq. 8 and the tiny MLP (backward_agg.cu): L = 2, 4, 16.

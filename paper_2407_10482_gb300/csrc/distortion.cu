@@ -13,61 +13,10 @@
 // sum_j w_j g_j = 2 L_dist because L_dist is homogeneous of degree 2 in w.  Only
 // the density path carries a gradient: sigma~ of the coarse grid, the omega logits
 // and the density channel of each fine level.
-#include "march.cuh"
+#include "distortion.cuh"
 
 namespace ngprt {
 namespace {
-
-struct DistParams {
-    MarchParams m;
-    float* dist_state;       // forward: [n][4] = (L_dist, W, S, 0) out; backward: in
-    float scale;             // forward: loss += scale L_dist; backward: dL_total/dL_dist per ray
-    float* loss;
-    float* g_tables;
-    float* g_coarse;
-};
-
-template <int L>
-struct DistSampler {
-    ForwardSampler<L, NGPRT_F32> fw;
-    float W, S, Lp, Ls;
-    __device__ __forceinline__ bool sample(const float u[3], float t, float delta) {
-        const bool stop = fw.sample(u, t, delta);
-        const float w = fw.w_last;
-        const float m = fmaf(0.5f, delta, t);
-        Lp = fmaf(2.0f * w, fmaf(m, W, -S), Lp);
-        Ls = fmaf(w * w, delta * (1.0f / 3.0f), Ls);
-        W += w;
-        S = fmaf(w, m, S);
-        return stop;
-    }
-};
-
-template <int L>
-__global__ void __launch_bounds__(128) distortion_kernel(const __grid_constant__ DistParams p) {
-    extern __shared__ float gate_smem[];
-    int64_t ray = 0;
-    float o[3], d[3], t, t_out;
-    bool hit = false;
-    const bool has_ray = ray_setup(p.m, ray, o, d, t, t_out, hit);
-    float Ld = 0.0f;
-    if (has_ray) {
-        DistSampler<L> smp{ForwardSampler<L, NGPRT_F32>(p.m.g, p.m.opts.attn_mode, p.m.opts.t_term,
-                                                        gate_smem + threadIdx.x),
-                           0.0f, 0.0f, 0.0f, 0.0f};
-        int n_march = 0, n_samp = 0;
-        if (hit) march_loop(p.m, o, d, t, t_out, smp, n_march, n_samp);
-        Ld = smp.Lp + smp.Ls;
-        reinterpret_cast<float4*>(p.dist_state)[ray] = make_float4(Ld, smp.W, smp.S, 0.0f);
-    }
-    if (p.loss) {
-        __syncwarp();
-        float v = Ld;
-#pragma unroll
-        for (int k = 16; k > 0; k >>= 1) v += __shfl_xor_sync(0xffffffffu, v, k);
-        if ((threadIdx.x & 31) == 0 && v != 0.0f) atomicAdd(p.loss, p.scale * v);
-    }
-}
 
 // Density-only reverse of sample_features (Eq. 6-8) for d(loss)/d(sigma_raw) = gs.
 template <int L>
@@ -172,7 +121,7 @@ template <int L>
 void launch_dist(bool backward, const DistParams& p, dim3 grid, cudaStream_t st) {
     const size_t shm = (size_t)2 * L * 128 * sizeof(float);
     if (backward) distortion_backward_kernel<L><<<grid, 128, shm, st>>>(p);
-    else distortion_kernel<L><<<grid, 128, shm, st>>>(p);
+    else distortion_kernel<L, NGPRT_AGG_SEPARATE_V><<<grid, 128, shm, st>>>(p);
 }
 
 }  // namespace
@@ -187,7 +136,8 @@ int32_t setup_rays(MarchParams& p, const ngprt_camera* cams, int32_t n_cams, con
 static int32_t run_distortion(bool backward, const ngprt_scene* scene, const ngprt_occ* occ, const ngprt_camera* cams,
                               int32_t n_cams, const int32_t* pixel_ids, const float* rays_o, const float* rays_d,
                               int64_t n_rays, const ngprt_render_opts* opts, float* dist_state, float scale,
-                              float* loss, float* g_tables, float* g_coarse, void* stream, const char* fn) {
+                              float* loss, float* g_tables, float* g_coarse, float* g_attn_inv, float* g_agg_mlp,
+                              void* workspace, size_t ws_bytes, void* stream, const char* fn) {
     DistParams p;
     memset(&p, 0, sizeof p);
     int32_t rc;
@@ -195,11 +145,13 @@ static int32_t run_distortion(bool backward, const ngprt_scene* scene, const ngp
     NGPRT_REQUIRE(scene->coarse_index == nullptr, "%s: gradients need the dense coarse grid (coarse_index is set)", fn);
     if ((rc = make_occ(occ, p.m.occ, fn)) != NGPRT_OK) return rc;
     if ((rc = check_opts(opts, fn)) != NGPRT_OK) return rc;
-    if ((rc = check_agg(scene, opts, false, fn)) != NGPRT_OK) return rc;
+    if ((rc = check_agg(scene, opts, true, fn)) != NGPRT_OK) return rc;
     NGPRT_REQUIRE(n_rays >= 0, "%s: n_rays=%lld", fn, (long long)n_rays);
     NGPRT_REQUIRE(scene->table_dtype == NGPRT_F32, "%s: needs F32 tables", fn);
+    const int agg = scene->aggregation;
     const int L = scene->L;
-    if (!(L == 1 || L == 2 || L == 3 || L == 4 || L == 8 || L == 16)) {
+    if (!(L == 1 || L == 2 || L == 3 || L == 4 || L == 8 || L == 16) ||
+        (agg != NGPRT_AGG_SEPARATE_V && !(L == 2 || L == 4 || L == 16))) {
         set_error("%s: no kernel for L=%d (built: 1, 2, 3, 4, 8, 16)", fn, L);
         return NGPRT_ERR_UNSUPPORTED;
     }
@@ -208,8 +160,17 @@ static int32_t run_distortion(bool backward, const ngprt_scene* scene, const ngp
     if (n_rays == 0) return NGPRT_OK;
     NGPRT_REQUIRE(dist_state != nullptr && ((uintptr_t)dist_state & 15) == 0,
                   "%s: dist_state must be a 16-byte aligned [n][4] buffer", fn);
-    if (backward)
+    const bool inv = agg == NGPRT_AGG_SEPARATE_INV || agg == NGPRT_AGG_SHARED_INV;
+    if (backward) {
         NGPRT_REQUIRE(g_tables && g_coarse, "%s: g_tables and g_coarse are required", fn);
+        NGPRT_REQUIRE(!inv || g_attn_inv, "%s: g_attn_inv is NULL (aggregation %d)", fn, agg);
+        NGPRT_REQUIRE(agg != NGPRT_AGG_MLP || g_agg_mlp, "%s: g_agg_mlp is NULL (the MLP aggregation)", fn);
+        const size_t need = ngprt_distortion_backward_workspace_bytes(scene, opts, n_rays);
+        if (need > 0 && (!workspace || ws_bytes < need || ((uintptr_t)workspace & 15) != 0)) {
+            set_error("%s: workspace %zu bytes < %zu needed (16-byte aligned)", fn, ws_bytes, need);
+            return NGPRT_ERR_WORKSPACE;
+        }
+    }
     p.m.opts = *opts;
     p.dist_state = dist_state;
     p.scale = scale;
@@ -217,6 +178,31 @@ static int32_t run_distortion(bool backward, const ngprt_scene* scene, const ngp
     p.g_tables = g_tables;
     p.g_coarse = g_coarse;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (agg != NGPRT_AGG_SEPARATE_V) {
+        if (!backward) {
+            launch_dist_fwd_agg(L, agg, p, grid, st);
+            return cuda_status(fn);
+        }
+        // the reverse march in distortion mode: colour cotangents 0, dL/dsigma from Eq. S2
+        MarchBwdParams b;
+        memset(&b, 0, sizeof b);
+        b.m = p.m;
+        b.g_tables = g_tables;
+        b.g_coarse = g_coarse;
+        b.g_attn_inv = inv ? g_attn_inv : nullptr;
+        b.dist_state = dist_state;
+        b.dist_scale = scale;
+        if (agg == NGPRT_AGG_MLP) {
+            char* w = static_cast<char*>(workspace);
+            b.n_records = reinterpret_cast<int32_t*>(w);
+            b.records = reinterpret_cast<float*>(w + 256);
+            b.rec_capacity = n_rays * (int64_t)opts->max_samples;
+            cudaMemsetAsync(b.n_records, 0, sizeof(int32_t), st);
+        }
+        launch_dist_bwd_agg(L, agg, b, grid, st);
+        if (agg == NGPRT_AGG_MLP) launch_bwd_agg_mlp_wgrad(L, b, scene->agg_mlp, g_agg_mlp, st);
+        return cuda_status(fn);
+    }
     switch (L) {
         case 1: launch_dist<1>(backward, p, grid, st); break;
         case 2: launch_dist<2>(backward, p, grid, st); break;
@@ -237,15 +223,23 @@ extern "C" int32_t ngprt_distortion_loss(const ngprt_scene* scene, const ngprt_o
                                          const float* rays_d, int64_t n_rays, const ngprt_render_opts* opts,
                                          float scale, float* dist_state, float* loss, void* stream) {
     return run_distortion(false, scene, occ, cams, n_cams, pixel_ids, rays_o, rays_d, n_rays, opts, dist_state, scale,
-                          loss, nullptr, nullptr, stream, "ngprt_distortion_loss");
+                          loss, nullptr, nullptr, nullptr, nullptr, nullptr, 0, stream, "ngprt_distortion_loss");
+}
+
+extern "C" size_t ngprt_distortion_backward_workspace_bytes(const ngprt_scene* scene, const ngprt_render_opts* opts,
+                                                            int64_t n_rays) {
+    if (!scene || n_rays < 0 || scene->aggregation != NGPRT_AGG_MLP) return 0;
+    const int64_t ms = opts && opts->max_samples > 0 ? opts->max_samples : 0;
+    return 256 + (size_t)n_rays * (size_t)ms * (size_t)(kNFeat * (scene->L + 1)) * sizeof(float);
 }
 
 extern "C" int32_t ngprt_distortion_backward(const ngprt_scene* scene, const ngprt_occ* occ, const ngprt_camera* cams,
                                              int32_t n_cams, const int32_t* pixel_ids, const float* rays_o,
                                              const float* rays_d, int64_t n_rays, const ngprt_render_opts* opts,
                                              const float* dist_state, float scale, float* g_tables, float* g_coarse,
+                                             float* g_attn_inv, float* g_agg_mlp, void* workspace, size_t ws_bytes,
                                              void* stream) {
     return run_distortion(true, scene, occ, cams, n_cams, pixel_ids, rays_o, rays_d, n_rays, opts,
-                          const_cast<float*>(dist_state), scale, nullptr, g_tables, g_coarse, stream,
-                          "ngprt_distortion_backward");
+                          const_cast<float*>(dist_state), scale, nullptr, g_tables, g_coarse, g_attn_inv, g_agg_mlp,
+                          workspace, ws_bytes, stream, "ngprt_distortion_backward");
 }

@@ -151,6 +151,7 @@ def fit(scene: ng.DeviceScene, occ: ng.DeviceOcc, opts, cams: np.ndarray, W: int
         out["stats"] = torch.empty(B, 2, dtype=torch.int32, device=dev)
         n_mean = torch.empty(1, device=dev)
     dist_state = torch.empty(B, 4, device=dev) if fc.eta > 0 else None
+    dist_ws = None
     cam_arr, n_cams = ng.cameras_struct(cams, W, H)
     gamma = opts.step_gamma
     hist = []
@@ -178,8 +179,13 @@ def fit(scene: ng.DeviceScene, occ: ng.DeviceOcc, opts, cams: np.ndarray, W: int
             ro = ng.render_opts(o_step)
             ng.ngprt_distortion_loss(scene.struct, occ.struct, cam_arr, n_cams, pix, None, None, B, ro, fc.eta / B,
                                      dist_state, loss if logging else None, stream=stream)
+            need = ng.ngprt_distortion_backward_workspace_bytes(scene.struct, ro, B)
+            if need and (dist_ws is None or dist_ws.numel() < need):
+                dist_ws = torch.empty(need, dtype=torch.uint8, device=dev)
             ng.ngprt_distortion_backward(scene.struct, occ.struct, cam_arr, n_cams, pix, None, None, B, ro,
-                                         dist_state, fc.eta / B, grads[0], grads[1], stream=stream)
+                                         dist_state, fc.eta / B, grads[0], grads[1], stream=stream,
+                                         workspace=dist_ws if need else None,
+                                         **{k: grads[i] for k, i in extra.items()})
         if fc.autotune:
             ng.ngprt_mean_samples(out["stats"], B, n_mean, stream=stream)
             gamma = ng.ngprt_step_autotune(gamma, float(n_mean.item()), fc.n_min, fc.kappa, fc.gamma_min)

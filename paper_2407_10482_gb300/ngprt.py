@@ -73,7 +73,8 @@ _SIGS = {
     "ngprt_distortion_loss": (C.c_int32, [_P, _P, _P, C.c_int32, _P, _P, _P, C.c_int64, _P, C.c_float, _P, _P,
                                           _P]),
     "ngprt_distortion_backward": (C.c_int32, [_P, _P, _P, C.c_int32, _P, _P, _P, C.c_int64, _P, _P, C.c_float,
-                                              _P, _P, _P]),
+                                              _P, _P, _P, _P, _P, C.c_size_t, _P]),
+    "ngprt_distortion_backward_workspace_bytes": (C.c_size_t, [_P, _P, C.c_int64]),
     "ngprt_mean_samples": (C.c_int32, [_P, C.c_int64, _P, _P]),
     "ngprt_step_autotune": (C.c_float, [C.c_float, C.c_float, C.c_float, C.c_float, C.c_float]),
     "ngprt_dilate_workspace_bytes": (C.c_size_t, [C.c_int32]),
@@ -211,10 +212,17 @@ def ngprt_distortion_loss(scene, occ, cams, n_cams, pixel_ids, rays_o, rays_d, n
 
 
 def ngprt_distortion_backward(scene, occ, cams, n_cams, pixel_ids, rays_o, rays_d, n_rays, opts, dist_state, scale,
-                              g_tables, g_coarse, stream=None) -> None:
+                              g_tables, g_coarse, stream=None, g_attn_inv=None, g_agg_mlp=None,
+                              workspace=None) -> None:
+    ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
     _check("ngprt_distortion_backward", lib().ngprt_distortion_backward(
         C.byref(scene), C.byref(occ), cams, n_cams, _ptr(pixel_ids), _ptr(rays_o), _ptr(rays_d), n_rays,
-        C.byref(opts), _ptr(dist_state), scale, _ptr(g_tables), _ptr(g_coarse), _stream(stream)))
+        C.byref(opts), _ptr(dist_state), scale, _ptr(g_tables), _ptr(g_coarse), _ptr(g_attn_inv), _ptr(g_agg_mlp),
+        _ptr(workspace), ws_bytes, _stream(stream)))
+
+
+def ngprt_distortion_backward_workspace_bytes(scene, opts, n_rays) -> int:
+    return int(lib().ngprt_distortion_backward_workspace_bytes(C.byref(scene), C.byref(opts), n_rays))
 
 
 def ngprt_mean_samples(ray_stats, n_rays, out, stream=None) -> None:

@@ -104,3 +104,49 @@ def test_distortion_backward(ng, attn_mode, L):
         err = np.abs(got.astype(np.float64) - ref).max()
         assert err <= 2e-4 * np.abs(ref).max() + 1e-9, (err, np.abs(ref).max())
     assert np.abs(rt).max() > 0
+
+
+@pytest.mark.parametrize("agg", [1, 2, 3, 4, 5])
+def test_distortion_loss_and_backward_of_the_aggregation_forms(ng, agg):
+    """Eq. S2 through Table 3's other forms: per-ray values and the density path's
+    gradients (logits, constant logits, the tiny MLP's weights) against the oracle."""
+    cfg = S.small_config(blob_std=(0.05, 0.15), aggregation=agg)
+    sc = S.make_scene(cfg)
+    if sc.coarse.shape[1] > 8:
+        sc.coarse[:, 8:] *= 10.0
+    if sc.attn_inv is not None:
+        sc.attn_inv = sc.attn_inv * 20.0
+    ds = ng.DeviceScene(cfg, sc.tables, sc.coarse, sc.mlp_w, attn_inv=sc.attn_inv, agg_mlp=sc.agg_mlp)
+    docc = ng.DeviceOcc(sc.occ, cfg.R_O, cfg.n_occ_levels)
+    orc = O.oracle_for_scene(sc)
+    opts = S.default_options(cfg, t_term=0.0)
+    o, d = S.random_rays(3000, 23, True)
+    if agg == 5:     # the MLP form's ReLU decisions (see the render's reverse-pass parity)
+        kink = orc.render_backward(opts, d_rgb=np.ones((len(o), 3)), rays_o=o, rays_d=d)["kink"].astype(bool)
+        o, d = np.ascontiguousarray(o[~kink]), np.ascontiguousarray(d[~kink])
+    n = len(o)
+    ot, dt = torch.as_tensor(o).cuda(), torch.as_tensor(d).cuda()
+    ro = ng.render_opts(opts)
+    state = torch.empty(n, 4, device="cuda")
+    ng.ngprt_distortion_loss(ds.struct, docc.struct, None, 0, None, ot, dt, n, ro, 1.0, state)
+    torch.cuda.synchronize()
+    ref_fwd = orc.distortion(opts, rays_o=o, rays_d=d)
+    g_fwd = state.cpu().numpy().astype(np.float64)
+    assert np.abs(g_fwd[:, 0] - ref_fwd[:, 0]).max() <= 1e-4 * max(1.0, np.abs(ref_fwd[:, 0]).max())
+    g_t = torch.zeros_like(ds.tables)
+    g_c = torch.zeros_like(ds.coarse)
+    g_i = torch.zeros_like(ds.attn_inv) if ds.attn_inv is not None else None
+    g_a = torch.zeros_like(ds.agg_mlp) if ds.agg_mlp is not None else None
+    need = ng.ngprt_distortion_backward_workspace_bytes(ds.struct, ro, n)
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda") if need else None
+    scale = 1.0 / n
+    ng.ngprt_distortion_backward(ds.struct, docc.struct, None, 0, None, ot, dt, n, ro, state, scale, g_t, g_c,
+                                 g_attn_inv=g_i, g_agg_mlp=g_a, workspace=ws)
+    torch.cuda.synchronize()
+    ref = orc.distortion_backward(opts, scale, rays_o=o, rays_d=d, full=True)
+    pairs = [(g_t, ref["tables"]), (g_c, ref["coarse"])]
+    pairs += [(g, ref[k]) for g, k in ((g_i, "attn_inv"), (g_a, "agg_mlp")) if g is not None]
+    for got, r in pairs:
+        err = np.abs(got.cpu().numpy().astype(np.float64) - r).max()
+        assert err <= 2e-4 * np.abs(r).max() + 1e-9, (err, np.abs(r).max())
+        assert np.abs(r).max() > 0
