@@ -308,14 +308,14 @@ int32_t setup_rays(MarchParams& p, const ngprt_camera* cams, int32_t n_cams, con
     return NGPRT_OK;
 }
 
-// The aggregation forms other than Eq. 8 take attn_mode 0; callers passing
-// forward_only_ok = false (distortion, occupancy marks, proposal targets) serve Eq. 8
-// only.
+// The aggregation forms other than Eq. 8 take attn_mode 0 and are built for L = 2,
+// 4, 16; callers passing forward_only_ok = false (the proposal's training targets)
+// serve Eq. 8 only.
 int32_t check_agg(const ngprt_scene* s, const ngprt_render_opts* o, bool forward_only_ok, const char* fn) {
     if (s->aggregation == NGPRT_AGG_SEPARATE_V) return NGPRT_OK;
     NGPRT_REQUIRE(o->attn_mode == 0, "%s: attn_mode=%d applies to the SEPARATE_V aggregation only", fn, o->attn_mode);
     if (!forward_only_ok) {
-        set_error("%s: aggregation %d is served by the render and its reverse pass only", fn, s->aggregation);
+        set_error("%s: aggregation %d is not served here (Eq. 8 only)", fn, s->aggregation);
         return NGPRT_ERR_UNSUPPORTED;
     }
     if (!march_supports(s->L, s->aggregation)) {
