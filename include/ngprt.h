@@ -385,7 +385,8 @@ int32_t ngprt_propose_backward(const float* prop_w, const ngprt_camera* cams, in
 /* Proposal targets from a plain render of the same rays (ray_state from ngprt_render
  * without t_interval): targets [n][3] = t of the first sample whose cumulative weight
  * exceeds 0.005 A, t + delta of the first sample whose cumulative weight reaches
- * 0.995 A, and A (0, 0, 0 for rays without samples). */
+ * 0.995 A, and A (0, 0, 0 for rays without samples).  Eq. 8 scenes only
+ * (NGPRT_ERR_UNSUPPORTED for the other aggregation forms). */
 int32_t ngprt_proposal_targets(const ngprt_scene* scene, const ngprt_occ* occ, const ngprt_camera* cams,
                                int32_t n_cams, const int32_t* pixel_ids, const float* rays_o, const float* rays_d,
                                int64_t n_rays, const ngprt_render_opts* opts, const float* ray_state, float* targets,
