@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(128) mlp_tc_kernel(const __grid_constant__ Mlp
                 if (layer == 0) issue_layer(tmem, a0, smem_u32(smem + Lay::w0), kMlpIn, WIDTH, mbar);
                 else issue_layer(tmem, a1, smem_u32(smem + Lay::wm), WIDTH, WIDTH, mbar);
             }
-            ok = __syncthreads_and(mbar_wait(mbar, phase)) != 0;  // one verdict for the whole block
+            ok = __syncthreads_and(mbar_wait(mbar, phase)) != 0;  // one decision for the whole block
             phase ^= 1u;
             fence_after();
             if (!ok) break;
