@@ -96,6 +96,17 @@ def test_struct_layouts_match_the_binding(c_run):
             assert getattr(cls, f).offset == c["fields"][f], (name, f)
 
 
+def test_header_compiles_as_cpp(tmp_path):
+    """The same header from C++ (extern "C" linkage, no C-only constructs)."""
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("g++ not available")
+    src = tmp_path / "abi.cpp"
+    src.write_text('#include "ngprt.h"\nint main() { ngprt_scene s{}; return (int)sizeof(s) > 0 ? 0 : 1; }\n')
+    subprocess.run([gxx, "-std=c++17", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", INCLUDE, "-c", str(src),
+                    "-o", str(tmp_path / "abi.o")], check=True)
+
+
 def test_host_entries_from_c(c_run):
     from paper_2407_10482_gb300 import ngprt as ng
     assert c_run["version"] >= 100
