@@ -9,8 +9,8 @@ Sec. S2.4 with ``huber_delta`` > 0), runs ``ngprt_render_backward`` into the tab
 coarse-grid and MLP gradients, adds eta times the distortion regulariser of Eq. S2
 (``ngprt_distortion_loss`` / ``ngprt_distortion_backward``) when eta > 0, and applies
 ``ngprt_adam_step`` to each parameter array.  With ``autotune`` the step scaler gamma
-follows Eq. S3 from the batch's mean sample count.  torch only holds the buffers
-and draws the minibatch indices.
+follows Eq. S3 from the batch's mean sample count.  torch holds the buffers, draws
+the minibatch indices and permutes the rays between pixel-tile and drawn order.
 """
 from __future__ import annotations
 
@@ -119,8 +119,9 @@ def _lr_factor(step: int, fc: FitConfig) -> float:
 
 def fit(scene: ng.DeviceScene, occ: ng.DeviceOcc, opts, cams: np.ndarray, W: int, H: int,
         targets: torch.Tensor, fc: FitConfig = FitConfig(), log_every: int = 0, stream=None):
-    """Fit ``scene`` (FP32 tables, coarse grid, MLP and any constant gate logits, updated
-    in place) to the images ``targets`` [n_views * H * W, 3] of the cameras ``cams``.
+    """Fit ``scene`` (FP32 tables, coarse grid, MLP and the aggregation form's own
+    parameters: constant gate logits or the tiny MLP's weights; updated in place) to
+    the images ``targets`` [n_views * H * W, 3] of the cameras ``cams``.
     Returns the loss history [(step, loss)] and the wall time in seconds; with
     ``autotune`` the final gamma is left in ``fit.last_gamma``."""
     from dataclasses import replace
