@@ -1,7 +1,8 @@
 """One training step of the render path, timed: render a minibatch of random pixels
 of 8 orbit views (rays in pixel-tile order, keeping the per-ray state), photometric
 L2 loss, reverse pass (rays in the drawn order), Adam on the tables, coarse grid
-and MLP.  Every step runs in the library's kernels.
+and MLP.  Render, loss, reverse pass and Adam run in the library's kernels; torch
+permutes the rays between the two orders.
 
     python -m paper_2407_10482_gb300.train_step --rays 65536 --steps 5
 """
