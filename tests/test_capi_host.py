@@ -181,3 +181,24 @@ def test_sparse_coarse_grid_validation(ng):
     rc = lib.ngprt_coarse_sparsify(None, 512, 48, C.c_void_p(256), C.c_void_p(256), None, 0, C.byref(n),
                                    C.c_void_p(256), 8, None)
     assert rc == ng.ERR_WORKSPACE
+
+
+def test_reverse_pass_workspace_sizes(ng):
+    """The reverse passes' workspace: per-ray cotangents for every form, plus one
+    (f^1..f^L, g_f) record per possible sample for the tiny-MLP form."""
+    lib = ng.lib()
+    s = ng.ngprt_scene()
+    s.L, s.T_log2, s.R_C = 4, 12, 16
+    opts = ng.render_opts(S.default_options(S.small_config(), max_samples=100))
+    n = 1000
+    cot = (n * 12 * 4 + 255) // 256 * 256 + 256
+    for agg in range(5):
+        s.aggregation = agg
+        assert ng.ngprt_render_backward_workspace_bytes(s, opts, n) == cot
+        assert ng.ngprt_distortion_backward_workspace_bytes(s, opts, n) == 0
+    s.aggregation = 5
+    rec = 256 + n * 100 * (8 * 4 + 8) * 4
+    assert ng.ngprt_render_backward_workspace_bytes(s, opts, n) == cot + rec
+    assert ng.ngprt_distortion_backward_workspace_bytes(s, opts, n) == rec
+    assert lib.ngprt_render_backward_workspace_bytes(None, C.byref(opts), n) == 0
+    assert ng.ngprt_render_backward_workspace_bytes(s, opts, -1) == 0
