@@ -202,3 +202,28 @@ def test_reverse_pass_workspace_sizes(ng):
     assert ng.ngprt_distortion_backward_workspace_bytes(s, opts, n) == rec
     assert lib.ngprt_render_backward_workspace_bytes(None, C.byref(opts), n) == 0
     assert ng.ngprt_render_backward_workspace_bytes(s, opts, -1) == 0
+
+
+def test_distortion_reverse_pass_argument_checks(ng):
+    """The regulariser's reverse pass asks each form for its own outputs before any
+    launch: the constant logits' gradient, the tiny MLP's and its record workspace."""
+    lib = ng.lib()
+    s = ng.ngprt_scene()
+    s.L, s.T_log2, s.R_C, s.mlp_layers, s.mlp_width = 4, 12, 16, 2, 16
+    for i in range(4):
+        s.N[i] = 16 << i
+    s.tables = s.coarse = s.mlp_w = 256
+    o = ng.ngprt_occ(32, 3, 256, None)
+    opts = ng.render_opts(S.default_options(S.small_config()))
+    P = C.c_void_p(256)
+
+    def dist_bwd(g_inv=None, g_mlp=None, ws=None, ws_bytes=0):
+        return lib.ngprt_distortion_backward(C.byref(s), C.byref(o), None, 0, None, P, P, 4, C.byref(opts), P,
+                                             C.c_float(1.0), P, P, g_inv, g_mlp, ws, ws_bytes, None)
+    s.aggregation, s.attn_inv = 2, 256
+    assert dist_bwd() == ng.ERR_INVALID_ARG and b"g_attn_inv" in lib.ngprt_last_error()
+    s.aggregation, s.attn_inv, s.agg_mlp = 5, None, 256
+    assert dist_bwd() == ng.ERR_INVALID_ARG and b"g_agg_mlp" in lib.ngprt_last_error()
+    assert dist_bwd(g_mlp=P) == ng.ERR_WORKSPACE
+    s.L = 3                                 # the other forms are built for L = 2, 4, 16
+    assert dist_bwd(g_mlp=P) == ng.ERR_UNSUPPORTED
