@@ -540,7 +540,9 @@ int32_t ngprt_tensor_core_error(void);
 /* Message of the calling thread's last failed call ("" if none). */
 const char* ngprt_last_error(void);
 
-/* ABI version of this header (major*100 + minor). */
+/* ABI version of this header (major*100 + minor); ngprt_version() returns the
+ * library's, so a caller can refuse a library built from another header. */
+#define NGPRT_ABI_VERSION 200
 int32_t ngprt_version(void);
 
 #ifdef __cplusplus

@@ -133,7 +133,7 @@ int32_t make_occ(const ngprt_occ* o, OccView& v, const char* fn) {
 
 extern "C" const char* ngprt_last_error(void) { return ngprt::g_err; }
 
-extern "C" int32_t ngprt_version(void) { return 100; }
+extern "C" int32_t ngprt_version(void) { return NGPRT_ABI_VERSION; }
 
 extern "C" int32_t ngprt_coarse_channels(int32_t L, int32_t aggregation) {
     if (L < 1 || L > ngprt::kMaxL) return 0;

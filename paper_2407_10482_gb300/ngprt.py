@@ -16,6 +16,7 @@ import torch
 
 from . import build as _build
 
+ABI_VERSION = 200  # NGPRT_ABI_VERSION of include/ngprt.h that these structs and signatures follow
 MAX_LEVELS = 32
 MAX_CAMERAS = 64
 STATE_FLOATS = 12
@@ -138,6 +139,8 @@ def lib(build_if_missing: bool = False):
             f = getattr(h, name)
             f.restype = res
             f.argtypes = args
+        if h.ngprt_version() != ABI_VERSION:
+            raise RuntimeError(f"{path} has ABI version {h.ngprt_version()}, this binding {ABI_VERSION}: rebuild it")
         _lib = h
     return _lib
 
