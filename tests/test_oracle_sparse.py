@@ -87,3 +87,32 @@ def test_blocks_read_back_the_dense_grid(R_C, nch):
                         dx, dy, dz = c & 1, (c >> 1) & 1, (c >> 2) & 1
                         row = base + dx + 9 * dy + 81 * dz
                         assert np.array_equal(blocks.reshape(-1, nch)[row], d[cz + dz, cy + dy, cx + dx])
+
+
+@pytest.mark.parametrize("bounded", [True, False])
+def test_vertices_outside_the_kept_blocks_never_reach_a_render(bounded):
+    """The claim the sparse grid rests on, in the oracle: zeroing every coarse vertex
+    that no kept block stores leaves renders (values and counts) unchanged bit for bit."""
+    from paper_2407_10482_gb300 import scenes as S
+    kw = dict(blob_std=(0.05, 0.15), R_C=41)
+    if not bounded:
+        kw.update(bounded=False, R_O=64, n_occ_levels=4, t_min=0.05, r_far=16.0, shell=True,
+                  step_base=2 * 3 ** 0.5 / 256)
+    cfg = S.small_config(**kw)
+    sc = S.make_scene(cfg)
+    mask = O.coarse_block_mask(sc.occ, cfg.R_O, cfg.R_C)
+    nb = (cfg.R_C - 1 + 7) // 8
+    kept = np.zeros((cfg.R_C,) * 3, bool)                      # [z][y][x] vertices some kept block stores
+    for b in np.flatnonzero(mask):
+        bx, by, bz = b % nb, (b // nb) % nb, b // (nb * nb)
+        kept[8 * bz:8 * bz + 9, 8 * by:8 * by + 9, 8 * bx:8 * bx + 9] = True
+    if bounded:
+        assert not kept.all()
+    masked = sc.coarse.copy()
+    masked[~kept.reshape(-1)] = 0.0
+    opts = S.default_options(cfg)
+    cams = S.orbit_cameras(cfg, 1, azimuth0=25.0)
+    a = O.oracle_for_scene(sc).render(opts, cams=cams)
+    b = O.oracle_for_scene(sc, coarse=masked).render(opts, cams=cams)
+    for k in ("rgb", "depth", "opacity", "stats"):
+        assert np.array_equal(a[k], b[k]), k
