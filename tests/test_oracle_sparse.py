@@ -116,3 +116,13 @@ def test_vertices_outside_the_kept_blocks_never_reach_a_render(bounded):
     b = O.oracle_for_scene(sc, coarse=masked).render(opts, cams=cams)
     for k in ("rgb", "depth", "opacity", "stats"):
         assert np.array_equal(a[k], b[k]), k
+    if bounded:
+        # a planted mistake: one kept block fewer must show in the image
+        worst = 0.0
+        for b_drop in np.flatnonzero(mask)[:6]:
+            bx, by, bz = b_drop % nb, (b_drop // nb) % nb, b_drop // (nb * nb)
+            short = masked.reshape(cfg.R_C, cfg.R_C, cfg.R_C, -1).copy()
+            short[8 * bz:8 * bz + 9, 8 * by:8 * by + 9, 8 * bx:8 * bx + 9] = 0.0
+            c = O.oracle_for_scene(sc, coarse=short.reshape(masked.shape)).render(opts, cams=cams)
+            worst = max(worst, float(np.abs(c["rgb"] - a["rgb"]).max()))
+        assert worst > 1e-4
