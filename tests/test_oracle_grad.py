@@ -152,3 +152,21 @@ def test_reverse_pass_of_aggregation_variants(agg):
         assert np.all(np.abs(g["coarse"][:, 8:]).sum(0) > 0)
     if agg == 4:
         assert g["coarse"].shape[1] == 8
+
+
+def test_mlp_form_flags_rays_at_a_relu_kink():
+    """A hidden unit whose W1 row is zero sits exactly at its kink for every sample:
+    every ray with samples is flagged; with the generated weights most rays are not."""
+    cfg = S.small_config(blob_std=(0.05, 0.15), aggregation=5)
+    sc = S.make_scene(cfg)
+    o, d = S.random_rays(200, 3, True)
+    opts = S.default_options(cfg, t_term=0.0)
+    cot = dict(d_rgb=np.ones((len(o), 3)))
+    orc = O.oracle_for_scene(sc)
+    k_gen = orc.render_backward(opts, rays_o=o, rays_d=d, **cot)["kink"]
+    stats = orc.render(opts, rays_o=o, rays_d=d)["stats"]
+    assert k_gen.mean() < 0.2
+    nx = 8 * cfg.L
+    orc.agg_mlp[5 * nx:6 * nx] = 0.0             # hidden unit 5: h = 0 at every sample
+    k_zero = orc.render_backward(opts, rays_o=o, rays_d=d, **cot)["kink"]
+    assert np.array_equal(k_zero.astype(bool), stats[:, 1] > 0)
