@@ -2,27 +2,37 @@
 
 ``python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]``
 
-One step = one 1920x1080 frame of the hd workload (unbounded 360-style scene, L=16
-levels 16..4096, T=2^19, 128^3 occupancy + distance grid, MLP 23->64->64->3), plain
-FP32 tables and MLP: the march kernel (occupancy-distance marching, coarse fetch,
-16-level gathers, attention, compositing) then the deferred-MLP kernel.  Inputs are
-resident in HBM; L2 is flushed (a 256 MiB write) between timed frames, outside the
-timed events.  Under torchrun every rank renders its own view (weak scaling,
-replicas: no data-path collective); rank 0 prints one JSON line.
+Headline workload: the hd model (L=16 levels 16..4096, T=2^19, 16^3 coarse grid of
+40 channels, 128^3 occupancy + distance grid G, MLP 23->64->64->3) fitted in this
+run to ground-truth images of its synthetic unbounded 360-style scene
+(``hdfit.fit_hd_scene``: 48 training views, Huber loss + distortion regulariser,
+visibility-culled occupancy), rendered at 1920x1080 from a held-out orbit view.
+One step = one frame of the plain FP32 renderer: the fused march kernel
+(occupancy-distance marching, coarse fetch, 16-level gathers, attention,
+compositing) and the deferred-MLP kernel.  Inputs are resident in HBM; L2 is
+flushed (a 256 MiB write) between timed frames, outside the timed events.  Under
+torchrun every rank fits its own replica and renders its own view (weak scaling,
+no data-path collective); rank 0 prints one JSON line.
 
-``--impl reference`` times the CPU oracle (the only other program of the same
-computation) on a bounded pixel sample of the same frame, on the host cores.
+Beside it: the FP16 + tensor-core MLP + learned-proposal form with the PSNR of both
+forms against the held-out targets (the <= 0.1 dB criterion), batches of 8 views,
+one training step, the random-weight hd scene, the paper-shaped scenes (Tables 2-4),
+the L1-pipe roofline of the march kernel, and the CPU oracle's rate.
+
+``--impl reference`` times the CPU oracle (the plain FP64 program of the same
+computation) on a bounded pixel sample per step, on the host cores.
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
 import statistics
 import subprocess
-import tempfile
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -33,13 +43,36 @@ sys.path.insert(0, ROOT)
 from paper_2407_10482_gb300 import scenes as S  # noqa: E402
 
 METRIC = "1080p frames/s & Grays/s, plain FP32 vs FP16+proposal at ≤0.1 dB PSNR loss"
-# DRAM bytes (read + write) of one march_kernel<16,F32> launch on this frame, from the
-# ncu capture summarised in profiles/march_kernel_hd_1080p_fp32.md; None while the
-# kernel has changed since the counters were taken
-MARCH_DRAM_BYTES = 2.545277e9  # 2.187119 GB read + 0.358158 GB written
-# l1tex__data_pipe_lsu_wavefronts.avg.pct_of_peak_sustained_elapsed of the same capture
-L1_LSU_PCT = 80.34
-WORKLOAD = "hd 1920x1080 unbounded-360 synthetic scene, L=16 (16..4096), T=2^19, 128^3 occupancy+G, MLP 23-64-64-3"
+WORKLOAD = ("hd fitted scene 1920x1080 (unbounded 360-style, L=16 levels 16..4096, T=2^19, 16^3x40 coarse, "
+            "128^3 occupancy+G, MLP 23-64-64-3), fitted in-run to 48 analytic views, held-out view")
+RANDOM_WORKLOAD = ("hd random-weight scene 1920x1080 (same model shape, tables N(0, 0.1), coarse density offset "
+                   "3.2), orbit view at azimuth 0")
+COUNTERS = os.path.join(ROOT, "profiles", "march_kernel_counters.json")
+# sources the march kernel is compiled from: counters taken on other sources are stale
+KERNEL_SOURCES = ("paper_2407_10482_gb300/csrc/common.cuh", "paper_2407_10482_gb300/csrc/march.cuh",
+                  "paper_2407_10482_gb300/csrc/render.cu", "include/ngprt.h")
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def load_counters(key: str):
+    """The committed ncu counters of the march kernel for workload `key`, or None
+    when they are missing or were taken on other kernel sources."""
+    try:
+        with open(COUNTERS) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    e = d.get(key)
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return e
 
 
 def _peaks() -> dict:
@@ -129,23 +162,12 @@ def max_over_ranks(value: float, world: int, device=None) -> float:
     return float(t.item())
 
 
-def cpu_baseline(cfg, scene, cams, opts, sample_stride: int = 16) -> dict:
-    """The oracle on a stratified pixel sample (every sample_stride-th pixel) of the
-    frame, on all host cores; rays/s scaled to frames/s of the full frame."""
-    from oracle import oracle as O
-    orc = O.oracle_for_scene(scene)
-    n = cfg.W * cfg.H
-    pix = np.arange(0, n, sample_stride, dtype=np.int32)
-    t0 = time.perf_counter()
-    orc.render(opts, cams=cams, pix=pix)
-    dt = time.perf_counter() - t0
-    rays_s = len(pix) / dt
-    return {"value": rays_s / n, "unit": "frames/s", "rays_per_s": rays_s, "cores": O.max_threads(),
-            "kind": "oracle", "seconds": dt,
-            "sample": f"{len(pix)} pixels (every {sample_stride}th pixel of the 1920x1080 frame), FP64 oracle, OpenMP"}
-
+# ---------------------------------------------------------------- reference arm
 
 def run_reference(args):
+    """The CPU oracle on the random-weight hd scene (the fitted model's shape; the
+    oracle takes only seeded generator inputs), every step a 1/ref_stride pixel
+    sample of one frame on all host cores; value = frames/s of that rate."""
     world, rank, _ = _dist_setup()
     if rank != 0:
         return
@@ -164,18 +186,21 @@ def run_reference(args):
         orc.render(opts, cams=cams, pix=pix)
         dt = time.perf_counter() - t0
         if k >= args.warmup:
-            steps.append(dt * stride)  # seconds per full frame
-    ms = 1000.0 * statistics.mean(steps)
-    value = 1000.0 / ms
+            steps.append(dt)
+    ms = 1000.0 * statistics.mean(steps)                 # one step = 1/stride of a frame
+    value = 1000.0 / (ms * stride)                       # frames/s
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": f"1/{stride} of the pixels per step, extrapolated"},
+            "config": {"workload": RANDOM_WORKLOAD, "step": f"1/{stride} of the frame's pixels (every "
+                       f"{stride}th pixel, offset by the step index)", "rays_per_step": n // stride},
             "cpu_baseline": {"value": value, "unit": "frames/s", "cores": O.max_threads(), "kind": "oracle",
-                             "sample": f"every {stride}th pixel of the frame per step (offset by step)"},
+                             "sample": f"every {stride}th pixel of the frame per step"},
             "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
+
+# ------------------------------------------------------------------- helpers
 
 def _timed(fn, stream, flush, reps, warmup):
     """Mean CUDA-event time (ms) of fn() on `stream`, L2 flushed before each call."""
@@ -195,109 +220,159 @@ def _timed(fn, stream, flush, reps, warmup):
     return statistics.mean(out)
 
 
-def other_forms(args, cfg, scene, ds, docc, cams, opts, dev, stream, flush, plain_rgb):
-    """The FP16 + proposal form, 8-view batches, the training step and the gather
-    ceiling, on the same GPU (reported beside the plain FP32 frame)."""
+def _psnr(a, b) -> float:
+    mse = float(((a.double() - b.double()) ** 2).mean())
+    return float("inf") if mse == 0 else -10.0 * math.log10(mse)
+
+
+def _views(render_one, cams, W, H, dev):
+    """rgb [V*H*W, 3] of render_one(cams[v:v+1], out) over the views."""
+    import torch
+    n = W * H
+    out = torch.empty(len(cams) * n, 3, device=dev)
+    for v in range(len(cams)):
+        render_one(cams[v:v + 1], out[v * n:(v + 1) * n])
+    return out
+
+
+# ------------------------------------------------------------- fitted forms
+
+def fitted_forms(args, fs, opts, dev, stream, flush):
+    """On the fitted scene: the plain FP32 renderer, FP16 tables + tensor-core MLP,
+    and that form with the learned proposal; PSNR of each against the held-out
+    targets (8 views) and the loss of the fast form; batches of 8 views; one
+    training step against the analytic targets."""
     import torch
     from paper_2407_10482_gb300 import ngprt as ng
     from paper_2407_10482_gb300 import proposal as P
-    n = cfg.W * cfg.H
-    res = {}
+    cfg = fs.cfg
+    W, H = cfg.W, cfg.H
+    n = W * H
     reps, warm = max(3, args.steps // 2), args.warmup
-    rend32 = ng.Renderer(ds, docc, device=dev)
-    plain = rend32.render(opts, cams=cams, W=cfg.W, H=cfg.H, stats=True)
-    plain_rgb = plain["rgb"].clone()
-    plain_st = plain["stats"].float().mean(0)
+    res = {}
+    ds = fs.scene
+    rend = ng.Renderer(ds, fs.occ, device=dev)
+
+    def plain_one(c, out):
+        out.copy_(rend.render(opts, cams=c, W=W, H=H)["rgb"])
+    rgb_plain = _views(plain_one, fs.cams_test, W, H, dev)
+    # FP16 tables, FP16 tensor-core MLP
+    ds16 = ng.DeviceScene(cfg, ds.tables, ds.coarse, ds.mlp_w, table_dtype=ng.F16, mlp_dtype=ng.F16, device=dev)
+    r16 = ng.Renderer(ds16, fs.occ, device=dev)
+
+    def f16_one(c, out):
+        out.copy_(r16.render(opts, cams=c, W=W, H=H)["rgb"])
+    rgb16 = _views(f16_one, fs.cams_test, W, H, dev)
+    c1 = fs.cams_test[:1]
+    o16 = r16.render(opts, cams=c1, W=W, H=H)
+    ms_16 = _timed(lambda: r16.render(opts, cams=c1, W=W, H=H, out=o16), stream, flush, reps, warm)
     # learned proposal: trained on the plain renderer's weights over 64 orbit views
-    # that differ from the test views, every step in the library's kernels
+    # between the held-out ones, every step in the library's kernels
     t0 = time.perf_counter()
     train_cams = S.orbit_cameras(cfg, 64, azimuth0=2.8125, step_deg=5.625)
-    pix = torch.as_tensor(S.random_pixels(1 << 20, 64, cfg.W, cfg.H, 4)).to(dev)
-    targets = P.make_targets(rend32, opts, train_cams, cfg.W, cfg.H, pix)
+    pix = torch.as_tensor(S.random_pixels(1 << 20, 64, W, H, 4)).to(dev)
+    targets = P.make_targets(rend, opts, train_cams, W, H, pix)
     pc = P.ProposalConfig()
-    w, hist = P.train(train_cams, cfg.W, cfg.H, pix, targets, pc, log_every=500)
+    w, hist = P.train(train_cams, W, H, pix, targets, pc, log_every=2000)
     torch.cuda.synchronize(dev)
     train_s = time.perf_counter() - t0
-    # FP16 tables, FP16 tensor-core MLP, proposal + fallback
-    ds16 = ng.DeviceScene(cfg, scene.tables, scene.coarse, scene.mlp_w, table_dtype=1, mlp_dtype=1, device=dev)
-    fr = P.FastRenderer(ds16, docc, w, pc, device=dev)
-    rgb = torch.empty(n, 3, device=dev)
-    fr.render(opts, cams, cfg.W, cfg.H, rgb, stats=True)
-    torch.cuda.synchronize(dev)
-    fast_st = fr.stats.float().mean(0)
-    fast_psnr = P.psnr(rgb, plain_rgb)
-    ms_fast = _timed(lambda: fr.render(opts, cams, cfg.W, cfg.H, rgb, stream=stream), stream, flush, reps, warm)
-    # a 4x finer-step render of the same model approximates its continuous volume
-    # rendering: the PSNR loss of the fast form is measured against it as well
-    opts_fine = S.default_options(cfg, step_gamma=0.25, max_march=4096, max_samples=4096)
-    ref = rend32.render(opts_fine, cams=cams, W=cfg.W, H=cfg.H)["rgb"].clone()
-    psnr_plain_ref = P.psnr(plain_rgb, ref)
-    psnr_fast_ref = P.psnr(rgb, ref)
-    # FP16 tables + tensor-core MLP without the proposal (precision form alone)
-    r16 = ng.Renderer(ds16, docc, device=dev)
-    o16 = r16.render(opts, cams=cams, W=cfg.W, H=cfg.H)
-    p16 = P.psnr(o16["rgb"], plain_rgb)
-    ms_16 = _timed(lambda: r16.render(opts, cams=cams, W=cfg.W, H=cfg.H, out=o16), stream, flush, reps, warm)
+    fr = P.FastRenderer(ds16, fs.occ, w, pc, device=dev)
+    stats_fast, stats_plain = [], []
+
+    def fast_one(c, out):
+        fr.render(opts, c, W, H, out, stats=True)
+        stats_fast.append(fr.stats.float().mean(0))
+    rgb_fast = _views(fast_one, fs.cams_test, W, H, dev)
+    for v in range(len(fs.cams_test)):
+        stats_plain.append(rend.render(opts, cams=fs.cams_test[v:v + 1], W=W, H=H, stats=True)["stats"].float()
+                           .mean(0))
+    sf, sp = torch.stack(stats_fast).mean(0), torch.stack(stats_plain).mean(0)
+    ob = torch.empty(n, 3, device=dev)
+    ms_fast = _timed(lambda: fr.render(opts, c1, W, H, ob, stream=stream), stream, flush, reps, warm)
+    tg = fs.targets_test
+    p_plain, p16, p_fast = _psnr(rgb_plain, tg), _psnr(rgb16, tg), _psnr(rgb_fast, tg)
+
+    def per_view(rgb):
+        return [_psnr(rgb[k * n:(k + 1) * n], tg[k * n:(k + 1) * n]) for k in range(len(fs.cams_test))]
+    loss = p_plain - p_fast
+    vs_plain = _psnr(rgb_fast, rgb_plain)
     res["forms"] = {
-        "fp16_tables_tc_mlp": {"ms_per_frame": ms_16, "frames_per_s": 1000.0 / ms_16, "psnr_vs_plain_db": p16},
+        "held_out_views": "8 views, orbit radius 3, elevation 20 deg, azimuths 22.5 + 45 k (not trained on)",
+        "plain_fp32": {"psnr_vs_targets_db": p_plain, "psnr_vs_targets_db_per_view": per_view(rgb_plain),
+                       "marching_per_ray": float(sp[0]), "samples_per_ray": float(sp[1])},
+        "fp16_tables_tc_mlp": {"ms_per_frame": ms_16, "frames_per_s": 1000.0 / ms_16,
+                               "psnr_vs_targets_db": p16, "psnr_loss_vs_targets_db": p_plain - p16,
+                               "psnr_vs_plain_db": _psnr(rgb16, rgb_plain)},
         "fp16_tc_mlp_proposal": {
             "ms_per_frame": ms_fast, "frames_per_s": 1000.0 / ms_fast, "grays_per_s": n / ms_fast / 1e6,
-            "psnr_vs_plain_db": fast_psnr, "loss_0p1dB_threshold_db": 41.9,
-            "psnr_vs_fine_ref_db": psnr_fast_ref, "plain_psnr_vs_fine_ref_db": psnr_plain_ref,
-            "psnr_loss_vs_fine_ref_db": psnr_plain_ref - psnr_fast_ref,
-            "marching_per_ray": float(fast_st[0]), "samples_per_ray": float(fast_st[1]),
-            "plain_marching_per_ray": float(plain_st[0]), "plain_samples_per_ray": float(plain_st[1]),
+            "psnr_vs_targets_db": p_fast, "psnr_vs_targets_db_per_view": per_view(rgb_fast),
+            "psnr_loss_vs_targets_db": loss, "loss_criterion_db": 0.1, "meets_0p1dB_vs_targets": bool(loss <= 0.1),
+            "psnr_vs_plain_db": vs_plain, "vs_plain_threshold_db": 41.9,
+            "meets_41p9dB_vs_plain": bool(vs_plain >= 41.9),
+            "marching_per_ray": float(sf[0]), "samples_per_ray": float(sf[1]),
             "fallback_rays": float(((fr.a_hat - fr.state[:, 7]) > pc.fallback).float().mean()),
+            "margin_near": pc.margin_near, "margin_far": pc.margin_far,
             "proposal_train_s": train_s, "proposal_loss": hist,
             "training": "2^20 rays of 64 orbit views (azimuth 2.8125 + 5.625 k deg), 6000 Adam steps of 2^15"}}
-    # batches of 8 views (azimuth 45 k deg): plain FP32 and the fast form
-    cams8 = S.orbit_cameras(cfg, 8)
-    n8 = 8 * n
+    # batches of the 8 held-out views: plain FP32 and the fast form
+    cams8 = fs.cams_test
+    n8 = len(cams8) * n
     out8 = {"rgb": torch.empty(n8, 3, device=dev), "depth": torch.empty(n8, device=dev),
             "opacity": torch.empty(n8, device=dev)}
-    ms8 = _timed(lambda: rend32.render(opts, cams=cams8, W=cfg.W, H=cfg.H, out=out8), stream, flush, 3, 2)
+    rend8 = ng.Renderer(ds, fs.occ, device=dev)
+    ms8 = _timed(lambda: rend8.render(opts, cams=cams8, W=W, H=H, out=out8), stream, flush, 3, 2)
     rgb8 = torch.empty(n8, 3, device=dev)
-    fr8 = P.FastRenderer(ds16, docc, w, pc, device=dev)
-    ms8f = _timed(lambda: fr8.render(opts, cams8, cfg.W, cfg.H, rgb8, stream=stream), stream, flush, 3, 2)
-    psnr8 = [P.psnr(rgb8[k * n:(k + 1) * n], out8["rgb"][k * n:(k + 1) * n]) for k in range(8)]
-    res["batch8"] = {"plain_fp32_frames_per_s": 8000.0 / ms8, "fast_frames_per_s": 8000.0 / ms8f,
-                     "fast_psnr_vs_plain_db_per_view": psnr8}
-    del out8, rgb8, fr8
-    # one training step: 2^18 random rays of 8 views, L2 loss against the plain
-    # render of a perturbed scene, reverse pass, Adam over all parameters
-    tgt = rend32.render(opts, cams=cams8, W=cfg.W, H=cfg.H)["rgb"]
-    student_t = ds.tables + 0.02 * torch.randn_like(ds.tables)
-    dss = ng.DeviceScene(cfg, student_t.cpu().numpy(), scene.coarse, scene.mlp_w, device=dev)
+    fr8 = P.FastRenderer(ds16, fs.occ, w, pc, device=dev)
+    ms8f = _timed(lambda: fr8.render(opts, cams8, W, H, rgb8, stream=stream), stream, flush, 3, 2)
+    res["batch8"] = {"plain_fp32_frames_per_s": 8000.0 / ms8, "fast_frames_per_s": 8000.0 / ms8f}
+    del out8, rgb8, fr8, rend8, ds16, r16, o16
+    # one training step (2^18 random rays of the 8 held-out 1080p analytic targets,
+    # L2 loss, reverse pass, Adam over every parameter) on a copy of the fitted scene
     from paper_2407_10482_gb300 import train_step as TS
-    pix8 = torch.as_tensor(S.random_pixels(1 << 18, 8, cfg.W, cfg.H, 3)).to(dev)
-    tg = tgt[pix8.long()].contiguous()
-    train_step, _ = TS.make_step(cfg, dss, docc, cams8, tg, pix8, stream=stream)
+    dss = ng.DeviceScene(cfg, ds.tables.clone(), ds.coarse.clone(), ds.mlp_w.clone(), device=dev)
+    pix8 = torch.as_tensor(S.random_pixels(1 << 18, len(cams8), W, H, 3)).to(dev)
+    tg8 = tg[pix8.long()].contiguous()
+    train_step, _ = TS.make_step(cfg, dss, fs.occ, cams8, tg8, pix8, stream=stream)
     ms_train = _timed(train_step, stream, flush, 5, 3)
     res["train_step"] = {"rays": 1 << 18, "ms": ms_train, "rays_per_s": (1 << 18) / ms_train * 1e3,
-                         "parts": "render (with state, rays in pixel-tile order) + L2 loss + reverse pass (rays in drawn "
-                                  "order) + Adam on 50.5M table, grid and MLP parameters"}
+                         "targets": "analytic ground truth of the 8 held-out 1080p views",
+                         "parts": "render (with state, rays in pixel-tile order) + L2 loss + reverse pass (rays in "
+                                  "drawn order) + Adam on 50.5M table, grid and MLP parameters"}
     del dss
-    # gather ceiling: random whole-entry gathers at three footprints, FP32 with and
-    # without L1 allocation (the march reads its large levels without it)
-    sink = torch.zeros(1, device=dev)
-    gcl = {}
-    for name, dt, rows, flags in (("l1_resident_f32", 0, 1 << 11, 0), ("l1_resident_f16", 1, 1 << 12, 0),
-                                  ("l2_resident_f32", 0, 1 << 20, 0), ("l2_resident_f32_noalloc", 0, 1 << 20, 1),
-                                  ("l2_resident_f16", 1, 1 << 21, 0),
-                                  ("hd_footprint_f32", 0, 1 << 23, 0), ("hd_footprint_f32_noalloc", 0, 1 << 23, 1)):
-        tab = torch.rand(rows, 8, device=dev, dtype=torch.float32 if dt == 0 else torch.float16)
-        nthr, per = 152 * 2048, 256
-
-        def g():
-            ng.ngprt_gather_bench(tab, dt, rows, nthr, per, 7, sink, stream=stream, flags=flags)
-        ms_g = _timed(g, stream, flush, 5, 2)
-        gcl[name + "_GBps"] = nthr * per * (32 if dt == 0 else 16) / (ms_g * 1e-3) / 1e9
-        del tab
-    res["gather_ceiling"] = gcl
-    if not args.no_paper_shape:
-        res["paper_shape"] = paper_shape(args, dev, stream, flush)
-        res["aggregation_ablation"] = aggregation_ablation(args, dev, stream, flush)
+    torch.cuda.empty_cache()
     return res
+
+
+# ------------------------------------------------------- random-weight scene
+
+def random_scene(args, dev, stream, flush):
+    """The random-weight hd scene (the model's stress case, no fit): plain FP32 and
+    FP16 + tensor-core MLP frames, and Table 4's counts with and without G."""
+    import torch
+    from paper_2407_10482_gb300 import ngprt as ng
+    cfg = S.hd_config()
+    sc = S.make_scene(cfg)
+    cams = S.orbit_cameras(cfg, 1)
+    opts = S.default_options(cfg)
+    docc = ng.DeviceOcc(sc.occ, cfg.R_O, cfg.n_occ_levels, device=dev)
+    out = {"workload": RANDOM_WORKLOAD}
+    for dt, key in ((ng.F32, "fp32"), (ng.F16, "fp16_tc")):
+        ds = ng.DeviceScene(cfg, sc.tables, sc.coarse, sc.mlp_w, table_dtype=dt, mlp_dtype=dt, device=dev)
+        rend = ng.Renderer(ds, docc, device=dev)
+        o = rend.render(opts, cams=cams, W=cfg.W, H=cfg.H)
+        ms = _timed(lambda: rend.render(opts, cams=cams, W=cfg.W, H=cfg.H, out=o), stream, flush, 5, 3)
+        out[key] = {"ms_per_frame": ms, "frames_per_s": 1000.0 / ms}
+        if dt == ng.F32:
+            n = cfg.W * cfg.H
+            st = {}
+            for name, kw in (("with_G", {}), ("without_G", {"use_dist": False}), ("G_eq9_literal", {"dist_rule": 0})):
+                s = rend.render(S.default_options(cfg, **kw), cams=cams, W=cfg.W, H=cfg.H, stats=True,
+                                use_dist=kw.get("use_dist", True))["stats"].float()
+                st[name] = {"marching_per_ray": float(s[:, 0].sum()) / n, "samples_per_ray": float(s[:, 1].sum()) / n}
+            out["march_stats"] = st
+        del ds, rend, o
+    torch.cuda.empty_cache()
+    return out
 
 
 AGG_NAMES = {0: "Separate-Att (V)", 1: "Shared-Att (V)", 2: "Separate-Att (Inv)", 3: "Shared-Att (Inv)", 4: "SUM",
@@ -351,7 +426,6 @@ def paper_shape(args, dev, stream, flush):
         docc = ng.DeviceOcc(sc.occ, cfg.R_O, cfg.n_occ_levels, device=dev, dist_level=cfg.dist_level)
         opts = S.default_options(cfg)
         cams = S.orbit_cameras(cfg, 1)
-        n = cfg.W * cfg.H
         row = {}
         for dt in (0, 1):
             ds = ng.DeviceScene(cfg, sc.tables, sc.coarse, sc.mlp_w, table_dtype=dt, mlp_dtype=dt, device=dev)
@@ -371,10 +445,13 @@ def paper_shape(args, dev, stream, flush):
                                            "identical_to_dense": bool(torch.equal(o_s["rgb"], ref_rgb))}
             del o_s, ref_rgb
             if dt == 0:
-                st = o["stats"].float().mean(0)
-                st0 = rend.render(opts, cams=cams, W=cfg.W, H=cfg.H, stats=True, use_dist=False)["stats"].float().mean(0)
-                row["marching_per_ray"] = {"with_G": float(st[0]), "without_G": float(st0[0])}
-                row["occupied_per_ray"] = {"with_G": float(st[1]), "without_G": float(st0[1])}
+                st = {}
+                for name, kw in (("with_G", {}), ("without_G", {"use_dist": False}),
+                                 ("G_eq9_literal", {"dist_rule": 0})):
+                    s = rend.render(S.default_options(cfg, **kw), cams=cams, W=cfg.W, H=cfg.H, stats=True,
+                                    use_dist=kw.get("use_dist", True))["stats"].float().mean(0)
+                    st[name] = {"marching_per_ray": float(s[0]), "occupied_per_ray": float(s[1])}
+                row["march_stats"] = st
             del ds, rend, o
         out[f"L{L}"] = row
         del sc, docc
@@ -384,6 +461,73 @@ def paper_shape(args, dev, stream, flush):
     return out
 
 
+# --------------------------------------------------------------- CPU oracle leg
+
+def cpu_leg(dev, sample_stride: int = 16, one_core_stride: int = 512, n_precision_pixels: int = 2000):
+    """The FP64 oracle on the host cores (the timed CPU baseline) and, from the same
+    oracle, the error of each precision form against it (8 orbit views of the
+    random-weight hd scene, azimuths 45 k).  The oracle sees only the seeded
+    generator's inputs."""
+    import torch
+    from oracle import oracle as O
+    from paper_2407_10482_gb300 import ngprt as ng
+    cfg = S.hd_config()
+    sc = S.make_scene(cfg)
+    opts = S.default_options(cfg)
+    orc = O.oracle_for_scene(sc)
+    n = cfg.W * cfg.H
+    cams1 = S.orbit_cameras(cfg, 1)
+    pix = np.arange(0, n, sample_stride, dtype=np.int32)
+    t0 = time.perf_counter()
+    orc.render(opts, cams=cams1, pix=pix)
+    dt_all = time.perf_counter() - t0
+    threads = O.max_threads()
+    O.set_threads(1)
+    pix1 = np.arange(0, n, one_core_stride, dtype=np.int32)
+    t0 = time.perf_counter()
+    orc.render(opts, cams=cams1, pix=pix1)
+    dt_one = time.perf_counter() - t0
+    O.set_threads(threads)
+    base = {"value": len(pix) / dt_all / n, "unit": "frames/s", "rays_per_s": len(pix) / dt_all, "cores": threads,
+            "kind": "oracle", "seconds": dt_all,
+            "sample": f"{len(pix)} pixels (every {sample_stride}th) of one 1920x1080 frame of the random-weight hd "
+                      f"scene, FP64 oracle, OpenMP",
+            "one_core": {"rays_per_s": len(pix1) / dt_one, "frames_per_s": len(pix1) / dt_one / n,
+                         "sample": f"{len(pix1)} pixels (every {one_core_stride}th), 1 thread"}}
+    # precision forms against the oracle, per view: on the FP32 master and on the
+    # 16-bit values the kernel reads
+    cams8 = S.orbit_cameras(cfg, 8)
+    docc = ng.DeviceOcc(sc.occ, cfg.R_O, cfg.n_occ_levels, device=dev)
+    rng = np.random.default_rng(19)
+    prec = {"views": "8 orbit views, azimuth 45 k deg, 1920x1080; random-weight hd scene",
+            "pixels_per_view": n_precision_pixels}
+    master = {}
+    for v in range(8):
+        pv = rng.choice(n, n_precision_pixels, replace=False).astype(np.int32)
+        master[v] = (pv, orc.render(opts, cams=cams8[v:v + 1], pix=pv)["rgb"])
+    for name, tdt in (("fp16", ng.F16), ("bf16", ng.BF16)):
+        ds = ng.DeviceScene(cfg, sc.tables, sc.coarse, sc.mlp_w, table_dtype=tdt, mlp_dtype=ng.F16, device=dev)
+        rend = ng.Renderer(ds, docc, device=dev)
+        orq = O.Oracle(cfg, ds.tables.float().cpu().numpy(), ds.coarse.float().cpu().numpy(),
+                       ds.mlp_w.float().cpu().numpy(), O.build_pyramid(sc.occ, cfg.R_O, cfg.n_occ_levels),
+                       O.occ_dist(sc.occ, cfg.R_O))
+        rows = []
+        for v in range(8):
+            pv, ref_m = master[v]
+            rgb = rend.render(opts, cams=cams8[v:v + 1], W=cfg.W, H=cfg.H)["rgb"][torch.as_tensor(pv).long().to(dev)]
+            g = rgb.double().cpu().numpy()
+            ref_r = orq.render(opts, cams=cams8[v:v + 1], pix=pv)["rgb"]
+            e_m, e_r = np.abs(g - ref_m), np.abs(g - ref_r)
+            rows.append({"max_abs_master": float(e_m.max()), "psnr_master_db": float(-10 * np.log10((e_m ** 2).mean())),
+                         "max_abs_rounded": float(e_r.max()),
+                         "psnr_rounded_db": float(-10 * np.log10((e_r ** 2).mean()))})
+        prec[f"{name}_tables_fp16_tc_mlp"] = rows
+        del ds, rend
+    return base, prec
+
+
+# ---------------------------------------------------------------------- main
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -391,16 +535,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ref-stride", type=int, default=64)
+    ap.add_argument("--fit-steps", type=int, default=800, help="Adam steps of the in-run fit of the hd scene")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--table-dtype", type=int, default=0, help="0 F32, 1 F16, 2 BF16 (plain form: 0)")
-    ap.add_argument("--mlp-dtype", type=int, default=0, help="0 F32 (CUDA cores), 1 F16 (tensor cores)")
-    ap.add_argument("--engine", default="fused", choices=["wavefront", "fused"])
-    ap.add_argument("--plain-only", action="store_true", help="time only the plain FP32 frame")
+    ap.add_argument("--plain-only", action="store_true", help="time only the plain FP32 frame of the fitted scene")
     ap.add_argument("--no-paper-shape", action="store_true", help="skip the paper-shaped L = 2, 3, 4 frames")
-    ap.add_argument("--workload", default="hd", choices=["hd", "paper2", "paper3", "paper4"],
-                    help="the timed frame: the hd scene, or the paper-shaped scene with L = 2, 3 or 4 "
-                         "(those run the plain frame only, without the CPU baseline)")
-    ap.add_argument("--coarse-res", type=int, default=512, help="coarse-grid resolution of the paper-shaped scenes")
+    ap.add_argument("--save-scene", default="", help="write the fitted scene (tables, grid, MLP, occupancy) here")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -409,6 +548,7 @@ def main():
 
     import torch
     import torch.distributed as dist
+    from paper_2407_10482_gb300 import hdfit as HF
     from paper_2407_10482_gb300 import ngprt as ng
 
     world, rank, local = _dist_setup()
@@ -417,20 +557,19 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     ng.lib()
+    stream = torch.cuda.current_stream(dev)
 
-    if args.workload == "hd":
-        cfg = S.hd_config()
-        scene = S.make_scene(cfg)
-    else:
-        # the paper-shaped scenes are drawn on the GPU (their grids are too large for numpy)
-        cfg = S.paper_config(int(args.workload[-1]), R_C=args.coarse_res)
-        scene = S.make_scene_torch(cfg, device=dev)
-    cams = S.orbit_cameras(cfg, 1, azimuth0=rank_views(rank)[0])
+    # the headline scene: fitted in this run, in bounded time
+    fs = HF.fit_hd_scene(S.hd_fit_config(), HF.HdFitConfig(steps=args.fit_steps), device=dev)
+    if args.save_scene:
+        from paper_2407_10482_gb300 import checkpoint as CK
+        CK.save_scene(args.save_scene, S.Scene(cfg=fs.cfg, tables=fs.scene.tables, coarse=fs.scene.coarse,
+                                                mlp_w=fs.scene.mlp_w, occ=fs.occ.occ))
+    cfg = fs.cfg
+    ds, docc = fs.scene, fs.occ
     opts = S.default_options(cfg)
-    ds = ng.DeviceScene(cfg, scene.tables, scene.coarse, scene.mlp_w, table_dtype=args.table_dtype, device=dev,
-                        mlp_dtype=args.mlp_dtype)
-    docc = ng.DeviceOcc(scene.occ, cfg.R_O, cfg.n_occ_levels, device=dev, dist_level=cfg.dist_level)
-    rend = ng.Renderer(ds, docc, device=dev)
+    view = rank % len(fs.cams_test)
+    cams = fs.cams_test[view:view + 1]
     n = cfg.W * cfg.H
     cam_arr, n_cams = ng.cameras_struct(cams, cfg.W, cfg.H)
     ro = ng.render_opts(opts)
@@ -438,33 +577,24 @@ def main():
     rgb = torch.empty(n, 3, device=dev)
     depth = torch.empty(n, device=dev)
     opac = torch.empty(n, device=dev)
-    stream = torch.cuda.current_stream(dev)
 
-    ws = torch.empty(ng.ngprt_wavefront_workspace_bytes(ds.struct, n), dtype=torch.uint8, device=dev)
-
-    main_ws = ws if args.engine == "wavefront" else None
-
-    def march(workspace=main_ws):
-        # wavefront engine (advance / gather rounds) when given the workspace
+    def march():
         ng.ngprt_render(ds.struct, docc.struct, cam_arr, n_cams, None, None, None, n, None, ro, None,
-                        ray_state=state, workspace=workspace, stream=stream)
+                        ray_state=state, stream=stream)
 
     def shade():
         ng.ngprt_shade(ds.struct, state, n, opts.bg, rgb, depth, opac, stream=stream)
 
-    # unit counts (samples, marching points) of this frame, with and without G
+    rend = ng.Renderer(ds, docc, device=dev)
     st = rend.render(opts, cams=cams, W=cfg.W, H=cfg.H, stats=True)["stats"].float()
-    samples = float(st[:, 1].sum())
-    marching = float(st[:, 0].sum())
-    st_nog = rend.render(opts, cams=cams, W=cfg.W, H=cfg.H, stats=True, use_dist=False)["stats"].float()
-    optsmax = S.default_options(cfg, dist_rule=1)
-    st_max = rend.render(optsmax, cams=cams, W=cfg.W, H=cfg.H, stats=True)["stats"].float()
-    march_stats = {
-        "marching_per_ray": marching / n, "samples_per_ray": samples / n,
-        "without_G": {"marching_per_ray": float(st_nog[:, 0].sum()) / n,
-                      "samples_per_ray": float(st_nog[:, 1].sum()) / n},
-        "G_max_rule": {"marching_per_ray": float(st_max[:, 0].sum()) / n,
-                       "samples_per_ray": float(st_max[:, 1].sum()) / n}}
+    samples, marching = float(st[:, 1].sum()), float(st[:, 0].sum())
+    march_stats = {"marching_per_ray": marching / n, "samples_per_ray": samples / n,
+                   "marching_p99": float(st[:, 0].quantile(0.99)), "marching_max": float(st[:, 0].max())}
+    for name, kw in (("without_G", {"use_dist": False}), ("G_eq9_literal", {"dist_rule": 0})):
+        s = rend.render(S.default_options(cfg, **kw), cams=cams, W=cfg.W, H=cfg.H, stats=True,
+                        use_dist=kw.get("use_dist", True))["stats"].float()
+        march_stats[name] = {"marching_per_ray": float(s[:, 0].sum()) / n, "samples_per_ray": float(s[:, 1].sum()) / n}
+    del rend
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     for _ in range(args.warmup):
@@ -498,19 +628,6 @@ def main():
     ms_max = max_over_ranks(ms, world, dev)
     fps = world * 1000.0 / ms_max
 
-    # the single fused march kernel on the same frame, for comparison
-    fused = []
-    for k in range(args.warmup + 5):
-        flush.fill_(float(k))
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        march(None)
-        e1.record(stream)
-        e1.synchronize()
-        if k >= args.warmup:
-            fused.append(e0.elapsed_time(e1))
-
     # end to end through the public call with host buffers: camera in, image out
     host = {"rgb": torch.empty(n, 3, pin_memory=True), "depth": torch.empty(n, pin_memory=True),
             "opacity": torch.empty(n, pin_memory=True)}
@@ -524,7 +641,7 @@ def main():
         e0.record(stream)
         cam_arr_k, _ = ng.cameras_struct(cams, cfg.W, cfg.H)
         ng.ngprt_render(ds.struct, docc.struct, cam_arr_k, n_cams, None, None, None, n, None, ro, rgb, depth, opac,
-                        None, state, main_ws, stream=stream)
+                        None, state, None, stream=stream)
         host["rgb"].copy_(rgb, non_blocking=True)
         host["depth"].copy_(depth, non_blocking=True)
         host["opacity"].copy_(opac, non_blocking=True)
@@ -534,67 +651,58 @@ def main():
             e2e_ms.append(e0.elapsed_time(e1))
     e2e_fps = world * 1000.0 / max_over_ranks(statistics.mean(e2e_ms), world, dev)
 
-    # ---------------------------------------------------------------- other forms
-    extra = {}
-    hd = args.workload == "hd"
-    if not args.plain_only and hd:
-        extra = other_forms(args, cfg, scene, ds, docc, cams, opts, dev, stream, flush, rgb)
-    workload = WORKLOAD if hd else (f"paper-shaped 1920x1080 scene, L={cfg.L} (N_l = 1024*2^l), T=2^22, "
-                                    f"{cfg.R_C}^3 dense coarse grid, 512^3 occupancy (5 levels), G at 256^3, "
-                                    f"MLP 23-64-64-3")
-    measured_here = hd and args.table_dtype == 0 and args.engine == "fused"
-
+    # roofline of the march kernel: the L1 load pipe it runs at.  Wavefronts per
+    # occupied sample come from the committed ncu counters of this kernel source on
+    # this workload; times this frame's samples, over the kernel's event time,
+    # against 152 SMs x the pipe's wavefronts per cycle x the sampled SM clock.  The
+    # DRAM traffic of the same capture is reported against HBM beside it.
     peaks = _peaks()
-    L = cfg.L
-    entry_b = 32 if args.table_dtype == 0 else 16
-    ch_b = 4 if args.table_dtype == 0 else 2
-    bytes_per_sample = L * 8 * entry_b + 8 * S.coarse_channels(cfg) * ch_b
-    alg_bytes = samples * bytes_per_sample + marching * 2 + n * ng.STATE_FLOATS * 4
     t_march_avg = statistics.mean(t_march)
-    achieved = alg_bytes / (t_march_avg * 1e-3) / 1e9
+    cnt = load_counters("hd_fit_1080p_fp32")
+    clock_hz = (clk.get("sm_mhz") or 2070.0) * 1e6
+    roof = {"bound": "l1", "unit": "Gwavefronts/s",
+            "kernel": "march_kernel<16,F32> (fused march: occupancy, coarse fetch, 16-level gathers, attention, "
+                      "compositing)",
+            "counters": os.path.relpath(COUNTERS, ROOT), "source_hash": kernel_source_hash()}
+    if cnt:
+        wf = cnt["l1_wavefronts_per_sample"] * samples
+        peak = cnt["l1_wavefronts_peak_per_cycle_per_sm"] * cnt["sms"] * clock_hz / 1e9
+        achieved = wf / (t_march_avg * 1e-3) / 1e9
+        roof.update(achieved=achieved, peak=peak, frac=achieved / peak,
+                    traffic=cnt["dram_bytes_per_sample"] * samples,
+                    hbm={"achieved_GBps": cnt["dram_bytes_per_sample"] * samples / (t_march_avg * 1e-3) / 1e9,
+                         "peak_GBps": peaks["hbm_gbs"], "peak_source": peaks["source"]},
+                    note="L1 wavefronts per occupied sample (ncu, this kernel source, this workload) x this frame's "
+                         "samples / the kernel's event time, against the L1 data pipe's peak wavefront rate at the "
+                         "sampled SM clock; traffic = ncu DRAM bytes per sample x samples")
+    else:
+        roof.update(achieved=None, peak=None, frac=None, traffic=None,
+                    note="no ncu counters for this kernel source and workload")
 
     line = {
         "metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": {0: "f32", 1: "f16", 2: "bf16"}[args.table_dtype], "data": "synthetic",
-        "config": {"workload": workload, "views_per_step": 1, "rays_per_step": n, "l2_flush": True,
-                   "parallelism": f"replicas x{world}", "table_dtype": args.table_dtype},
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded analytic scene; model fitted in-run)",
+        "config": {"workload": WORKLOAD, "views_per_step": 1, "rays_per_step": n, "l2_flush": True,
+                   "parallelism": f"replicas x{world}", "fit": {k: v for k, v in fs.info.items() if k != "loss"},
+                   "fit_loss": fs.info.get("loss")},
         "grays_per_s": fps * n / 1e9,
-        "kernels_ms": {"march": t_march_avg, "shade_mlp": statistics.mean(t_shade),
-                       "march_fused_engine": statistics.mean(fused), "engine": args.engine},
+        "kernels_ms": {"march": t_march_avg, "shade_mlp": statistics.mean(t_shade)},
         "march_stats": march_stats,
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                     "frac": achieved / peaks["hbm_gbs"],
-                     "traffic": MARCH_DRAM_BYTES if measured_here else None,
-                     "traffic_unit": "bytes per launch (ncu dram__bytes_read + write)",
-                     "kernel": f"march_kernel<{L},{['F32', 'F16', 'BF16'][args.table_dtype]}> (fused march: occupancy, "
-                               f"coarse fetch, {L}-level gathers, attention, compositing)",
-                     "peak_source": peaks["source"],
-                     "bytes_per_sample": bytes_per_sample,
-                     "note": "algorithmic gather bytes (L*8 entries + 8 coarse vertices per sample, 2 B per "
-                             "marching point, 48 B state per ray) over the march kernel's event time; they are "
-                             "served by L1/L2 (DRAM traffic is the 'traffic' figure), and lanes of a pixel tile "
-                             "share the coarse levels' entries, so they also exceed the per-lane random-gather "
-                             "microbenchmark; the bound is the L1 load pipe (l1_lsu_pct_ncu)",
-                     "l1_lsu_pct_ncu": L1_LSU_PCT if measured_here else None},
+        "roofline": roof,
         "e2e": {"value": e2e_fps, "unit": "frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": (2 if args.engine == "fused" else 2 * 8 + 3) * args.steps,
+        "gpu_launches": 2 * args.steps,
         "clocks": clk,
         "wall_s": wall,
     }
-    line.update(extra)
-    if "gather_ceiling" in extra:
-        gc = extra["gather_ceiling"]
-        # the best random-gather rate the microbenchmark reaches in any of the access
-        # modes the march uses (L1-resident with allocation, L2-resident without)
-        if args.table_dtype == 0:
-            ceil = max(gc["l1_resident_f32_GBps"], gc["l2_resident_f32_noalloc_GBps"])
-        else:
-            ceil = max(gc["l1_resident_f16_GBps"], gc["l2_resident_f16_GBps"])
-        line["roofline"]["gather_ceiling_GBps"] = ceil
-        line["roofline"]["gather_frac"] = achieved / ceil
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and hd:
-        line["cpu_baseline"] = cpu_baseline(cfg, scene, cams, opts)
+    if not args.plain_only:
+        line.update(fitted_forms(args, fs, opts, dev, stream, flush))
+        line["random_scene"] = random_scene(args, dev, stream, flush)
+        if not args.no_paper_shape:
+            line["paper_shape"] = paper_shape(args, dev, stream, flush)
+            line["aggregation_ablation"] = aggregation_ablation(args, dev, stream, flush)
+        if rank == 0 and world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"], line["precision_8view"] = cpu_leg(dev)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -196,8 +196,9 @@ typedef struct {
  * use_dist = read G (Eq. 9); lattice_snap = (bounded only) keep samples on the
  * uniform lattice; attn_mode (SEPARATE_V scenes only; 0 for every other
  * aggregation) 0 = separate attention (Eq. 8), 1 = gates fixed at 1 (SUM over the
- * same grid), 2 = omega^l for both modalities; dist_rule 0 = Eq. 9 as printed,
- * 1 = max(v G, s_O). */
+ * same grid), 2 = omega^l for both modalities; dist_rule 1 = max(v G, s_O) (the
+ * longer of two safe steps; the rule the bindings default to), 0 = Eq. 9 as
+ * printed (v G whenever G > 0). */
 typedef struct {
     float step_base;
     float step_gamma;
@@ -281,11 +282,6 @@ int64_t ngprt_table_entries(const ngprt_scene* scene);
 /* Workspace bytes of ngprt_render / ngprt_render_backward for n_rays rays. */
 size_t ngprt_render_workspace_bytes(const ngprt_scene* scene, int64_t n_rays);
 
-/* Workspace bytes with which ngprt_render runs its march as rounds over the
- * unfinished rays (advance / gather kernels) instead of one fused kernel; the
- * results are identical, the speed differs with the scene. */
-size_t ngprt_wavefront_workspace_bytes(const ngprt_scene* scene, int64_t n_rays);
-
 /*
  * Render rays (Eq. 2, 5, 6, 8, 9): occupancy-distance marching, per-sample coarse
  * fetch + per-level gathers + lightweight attention, alpha compositing, one
@@ -301,9 +297,9 @@ size_t ngprt_wavefront_workspace_bytes(const ngprt_scene* scene, int64_t n_rays)
  *   ray_stats  : NULL or int32 [n][2] = (marching points, samples).
  *   ray_state  : NULL or float [n][NGPRT_STATE_FLOATS], the per-ray composite state
  *                ngprt_render_backward consumes.
- *   workspace  : 256-byte aligned; ngprt_render_workspace_bytes(n) bytes run one fused
- *                march kernel, ngprt_wavefront_workspace_bytes(n) bytes run the march
- *                as rounds (advance / gather kernels).  Identical results.
+ *   workspace  : 256-byte aligned, at least ngprt_render_workspace_bytes(n) bytes
+ *                (the per-ray state when ray_state is NULL); NULL allowed with
+ *                ray_state.  One fused march kernel runs either way.
  */
 int32_t ngprt_render(const ngprt_scene* scene, const ngprt_occ* occ, const ngprt_camera* cams, int32_t n_cams,
                      const int32_t* pixel_ids, const float* rays_o, const float* rays_d, int64_t n_rays,
@@ -504,20 +500,14 @@ int32_t ngprt_render_noalloc(const ngprt_scene* scene, const ngprt_occ* occ, con
 int32_t ngprt_grid_indices(const ngprt_scene* scene, const float* u, int64_t n, uint32_t* idx_out,
                            void* stream);
 
-/* Measured ceiling of the render's gathers: n_threads threads each load per_thread
- * random whole entries (rows from a counter-based sequence of seed, thread and step)
- * of an [n_rows][8] table of dtype F32 (one 32-byte load each) or F16 (16 bytes);
- * flags = 1 reads FP32 entries without L1 allocation (the march's large levels).
- * Bytes moved = n_threads * per_thread * entry size; time it on `stream`.
- * n_rows a power of two, n_threads a multiple of 256, per_thread of 8; sink: one
- * device float (written only in a case that practically cannot occur). */
-int32_t ngprt_gather_bench(const void* table, int32_t dtype, int64_t n_rows, int64_t n_threads, int32_t per_thread,
-                           uint32_t seed, int32_t flags, float* sink, void* stream);
-
 /* Waits for `stream` and reports what went wrong on the device since the last
  * report: NGPRT_ERR_CUDA (with the CUDA message) if the stream holds a failed
  * launch, NGPRT_ERR_TIMEOUT if a tensor-core MLP kernel gave up waiting for its MMAs
- * (its rays were left unshaded; the flag is cleared by this report), else NGPRT_OK. */
+ * (its rays were left unshaded; the flag is cleared by this report), else NGPRT_OK.
+ * After an expired wait the kernel waits once more, again bounded, for the MMA in
+ * flight before releasing its tensor memory; if that MMA never completes it keeps
+ * the memory, and the message says so: the context is then suspect and the
+ * tensor-core forms should not be used in it again. */
 int32_t ngprt_sync_status(void* stream);
 
 /* Test hook of the timeout path (no counterpart in the paper): one block waits, with
@@ -542,7 +532,7 @@ const char* ngprt_last_error(void);
 
 /* ABI version of this header (major*100 + minor); ngprt_version() returns the
  * library's, so a caller can refuse a library built from another header. */
-#define NGPRT_ABI_VERSION 200
+#define NGPRT_ABI_VERSION 201
 int32_t ngprt_version(void);
 
 #ifdef __cplusplus

@@ -6,14 +6,17 @@
  * header or constant table with the CUDA library; both sides receive the same
  * seeded input arrays and nothing else.
  *
- * Precision.  Every feature, attention, compositing, MLP and gradient value is
- * computed in FP64.  The march itself (ray set-up, sample positions t, the
- * contraction, occupancy voxel choice, empty-space steps) is a recurrence whose
- * results are integers (which voxel, which sample), so it is evaluated in FP32,
- * one IEEE-rounded operation at a time with no fused multiply-add (compile with
- * -ffp-contract=off): the kernel takes the same decisions in the same precision.
- * The grid cell of a trilinear lookup (an integer) is chosen the same way from the
- * FP32 position; its interpolation weights are FP64.
+ * Precision.  Everything is computed in FP64 from the FP32 inputs: ray set-up,
+ * sample positions t, the contraction, the occupancy voxel and trilinear cell
+ * choices, the empty-space and distance steps, features, attention, compositing,
+ * the MLP and every gradient.  The march is written from its definition and shares
+ * no operation order with the kernels, which take the same decisions in FP32.  A
+ * decision that FP32 rounding could take the other way is flagged: a ray is
+ * "ambiguous" when one of its unit-cube coordinates came within OR_AMB_U (the FP32
+ * march's position error) of a voxel face whose other side changes the march's
+ * outcome, when a termination test came within OR_AMB_T
+ * (relative) of t_term, or when the march came within OR_AMB_END of the domain's
+ * end.  Parity tests require every ray on which the kernels differ to be flagged.
  *
  * Where each function comes from:
  *   volume rendering quadrature ........ Eq. 2 (Sec. 3, Preliminaries)
@@ -114,15 +117,16 @@ uint64_t or_level_offset(const int* N, int L, int T_log2, int l) {
 }
 
 /* Trilinear cell of a vertex grid of N vertices per axis covering u in [0, 1]:
- * p = u (N - 1).  The integer cell is chosen in FP32 (as the kernel chooses it),
- * clamped to [0, N-2]; the fractional weights are FP64. */
-static void or_cell(const float u[3], int N, int base[3], double w[3]) {
+ * p = u (N - 1), cell = floor(p) clamped to [0, N-2], weights p - cell.  FP64: for
+ * an FP32 u the product is exact, so the cell is the exact floor. */
+static void or_cell(const double u[3], int N, int base[3], double w[3]) {
     for (int a = 0; a < 3; ++a) {
-        float pf = u[a] * (float)(N - 1);
-        float bf = floorf(pf);
-        bf = fminf(fmaxf(bf, 0.0f), (float)(N - 2));
-        base[a] = (int)bf;
-        w[a] = (double)u[a] * (double)(N - 1) - (double)bf;
+        double p = u[a] * (double)(N - 1);
+        double b = floor(p);
+        if (b < 0.0) b = 0.0;
+        if (b > (double)(N - 2)) b = (double)(N - 2);
+        base[a] = (int)b;
+        w[a] = p - b;
     }
 }
 
@@ -135,8 +139,8 @@ void or_grid_indices(const int* N, int L, int T_log2, const float* u, int n,
     for (int i = 0; i < n; ++i) {
         for (int l = 0; l < L; ++l) {
             int base[3];
-            double w[3];
-            or_cell(u + 3 * i, N[l], base, w);
+            double w[3], ud[3] = {u[3 * i], u[3 * i + 1], u[3 * i + 2]};
+            or_cell(ud, N[l], base, w);
             uint64_t off = or_level_offset(N, L, T_log2, l);
             for (int c = 0; c < 8; ++c) {
                 int x = base[0] + (c & 1), y = base[1] + ((c >> 1) & 1), z = base[2] + ((c >> 2) & 1);
@@ -342,7 +346,7 @@ static double or_sigmoid(double v) { return 1.0 / (1.0 + exp(-v)); }
 
 /* Per-sample quantities the reverse pass needs again. */
 typedef struct {
-    float t, delta, u[3];
+    double t, delta, u[3];
     double sigma_raw, sigma, alpha, T_before;
     double f[OR_NFEAT];          /* fused deferred feature [sigma_raw, c_d, v_s] */
 } or_sample;
@@ -370,7 +374,7 @@ int or_coarse_channels(int L, int aggregation) {
  * channels (shared), gates constant over space (invariant: sigmoid of a logit per
  * level), the plain sum, or Instant-NGP's tiny MLP on the concatenated levels,
  * f^ = W2 relu(W1 [f^1, ..., f^L]). */
-static void or_features(const or_scene* s, const or_opts* op, const float u[3], double f[OR_NFEAT]) {
+static void or_features(const or_scene* s, const or_opts* op, const double u[3], double f[OR_NFEAT]) {
     int nch = or_coarse_channels(s->L, s->aggregation);
     double coarse[OR_NFEAT + 2 * OR_MAXL];
     double hid[OR_AGG_HIDDEN];
@@ -429,37 +433,58 @@ static void or_features(const or_scene* s, const or_opts* op, const float u[3], 
     }
 }
 
-/* ------------------------------------------------------------- FP32 march */
+/* ------------------------------------------------------------- FP64 march */
 
-/* Contraction of mip-NeRF 360 (the unbounded configuration): identity inside the
- * unit ball, else (2 - 1/r) x / r.  FP32, one rounding per operation. */
-static void or_point(const or_scene* s, const float o[3], const float d[3], float t,
-                     float x[3], float y[3], float u[3], float* r_out) {
+/* Ambiguity margins (see the header): unit-cube distance to a deciding voxel face,
+ * and the relative distance of T to t_term or of t to the domain's end. */
+#define OR_AMB_T 3e-5
+/* Largest distance (unit-cube coordinates) between an FP32 march's sample positions
+ * and the exact ones: a decision whose deciding face lies closer than this may go
+ * either way. */
+#ifndef OR_AMB_U
+#define OR_AMB_U 8e-7
+#endif
+
+/* Position error the tiny-MLP form's kink flag allows for (or_set_kink_position_error):
+ * OR_AMB_U, or 0 for rays whose sample positions are exact in FP32 as well. */
+static double or_kink_pos_err = OR_AMB_U;
+void or_set_kink_position_error(double e) { or_kink_pos_err = e; }
+#define OR_AMB_END 1e-6      /* relative distance of t to the domain's end */
+#define OR_AMB_LATTICE 1e-4  /* lattice units, for lattice_snap */
+
+/* Position at parameter t: world x = o + t d, its radius r, the contracted point y
+ * (mip-NeRF 360: x inside the unit ball, (2 - 1/r) x / r outside; the bounded scene
+ * keeps x) and the unit-cube coordinate u = (y + B) / (2B), B = 1 bounded, 2
+ * contracted. */
+static void or_point(int bounded, const double o[3], const double d[3], double t,
+                     double x[3], double y[3], double u[3], double* r_out) {
     for (int a = 0; a < 3; ++a) x[a] = o[a] + t * d[a];
-    float r2 = (x[0] * x[0] + x[1] * x[1]) + x[2] * x[2];
-    float r = sqrtf(r2);
+    double r = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
     *r_out = r;
-    float B = s->bounded ? 1.0f : 2.0f, hB = s->bounded ? 0.5f : 0.25f;
-    if (!s->bounded && r > 1.0f) {
-        float ir = 1.0f / r;
-        float k = (2.0f - ir) * ir;  /* (2 - 1/r) / r */
-        for (int a = 0; a < 3; ++a) y[a] = x[a] * k;
-    } else {
-        for (int a = 0; a < 3; ++a) y[a] = x[a];
+    double scale = (!bounded && r > 1.0) ? (2.0 - 1.0 / r) / r : 1.0;
+    double B = bounded ? 1.0 : 2.0;
+    for (int a = 0; a < 3; ++a) {
+        y[a] = scale * x[a];
+        u[a] = (y[a] + B) / (2.0 * B);
     }
-    for (int a = 0; a < 3; ++a) u[a] = (y[a] + B) * hB;
 }
 
-/* For tests: the FP32 contraction and unit-cube position of world points x. */
-void or_contract_batch(int bounded, const float* x, int n, float* y_out, float* u_out) {
-    or_scene s;
-    memset(&s, 0, sizeof s);
-    s.bounded = bounded;
-    float o[3] = {0.0f, 0.0f, 0.0f};
+/* For tests: the contraction and unit-cube position of world points x. */
+void or_contract_batch(int bounded, const double* x, int n, double* y_out, double* u_out) {
+    const double o[3] = {0.0, 0.0, 0.0};
     for (int i = 0; i < n; ++i) {
-        float xx[3], r;
-        or_point(&s, o, x + 3 * i, 1.0f, xx, y_out + 3 * i, u_out + 3 * i, &r);
+        double xx[3], r;
+        or_point(bounded, o, x + 3 * i, 1.0, xx, y_out + 3 * i, u_out + 3 * i, &r);
     }
+}
+
+/* The contraction's Jacobian applied to d at x (radius r > 1): with
+ * y = g(r) x, g(r) = 2/r - 1/r^2, J d = g d + g'(r) (x.d / r) x, g'(r) = 2/r^3 - 2/r^2. */
+static void or_jacobian_dir(const double x[3], const double d[3], double r, double v[3]) {
+    double g = 2.0 / r - 1.0 / (r * r);
+    double gp = 2.0 / (r * r * r) - 2.0 / (r * r);
+    double xd = x[0] * d[0] + x[1] * d[1] + x[2] * d[2];
+    for (int a = 0; a < 3; ++a) v[a] = g * d[a] + gp * (xd / r) * x[a];
 }
 
 /* World length of a step whose contracted image stays within distance rho of its
@@ -469,33 +494,89 @@ void or_contract_batch(int bounded, const float* x, int n, float* y_out, float* 
  * the image of the segment [x, x + s d] moves at speed |J d| with
  * |J d|^2 <= 1/r^4 + (2r - 1)^2 b^2 / r^6, b = |x x d| the ray's distance from the
  * origin (constant along it) and r the radius on the segment; that bound falls
- * with r, and with s <= (r - 1)/2 the segment stays at radius >= max((r+1)/2, b).
- * FP32, one rounding per operation. */
-static float or_dist_step(int bounded, const float x[3], const float d[3], float r, float rho) {
-    if (bounded || !(r > 1.0f)) return rho;
-    float cx = x[1] * d[2] - x[2] * d[1];
-    float cy = x[2] * d[0] - x[0] * d[2];
-    float cz = x[0] * d[1] - x[1] * d[0];
-    float b2 = (cx * cx + cy * cy) + cz * cz;
-    float rl = fmaxf((r + 1.0f) * 0.5f, sqrtf(b2));
-    float q = (2.0f * rl - 1.0f) / rl;
-    float s_dir = (rho * (rl * rl)) / sqrtf(1.0f + (q * q) * b2);
-    float cap = (r - 1.0f) * 0.5f;
-    return fmaxf(rho, fminf(s_dir, cap));
+ * with r, and with s <= (r - 1)/2 the segment stays at radius >= max((r+1)/2, b),
+ * where the speed is at most sqrt(1 + q^2 b^2) / r'^2, q = (2r' - 1)/r'. */
+static double or_dist_step(int bounded, const double x[3], const double d[3], double r, double rho) {
+    if (bounded || !(r > 1.0)) return rho;
+    double c[3] = {x[1] * d[2] - x[2] * d[1], x[2] * d[0] - x[0] * d[2], x[0] * d[1] - x[1] * d[0]};
+    double b = sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+    double rl = fmax(0.5 * (r + 1.0), b);
+    double q = 2.0 - 1.0 / rl;
+    double speed = sqrt(1.0 + q * q * b * b) / (rl * rl);
+    double s = fmin(rho / speed, 0.5 * (r - 1.0));
+    return fmax(rho, s);
 }
 
-void or_dist_step_batch(int bounded, const float* x, const float* d, const float* rho, int n, float* out) {
+void or_dist_step_batch(int bounded, const double* x, const double* d, const double* rho, int n, double* out) {
     for (int i = 0; i < n; ++i) {
-        const float* xi = x + 3 * i;
-        float r = sqrtf((xi[0] * xi[0] + xi[1] * xi[1]) + xi[2] * xi[2]);
+        const double* xi = x + 3 * i;
+        double r = sqrt(xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2]);
         out[i] = or_dist_step(bounded, xi, d + 3 * i, r, rho[i]);
     }
 }
 
-static int or_vox(float u, int Rk) {
-    float c = floorf(u * (float)Rk);
-    c = fminf(fmaxf(c, 0.0f), (float)(Rk - 1));
+/* Voxel of coordinate u in a grid of Rk voxels over [0, 1] (clamped to the grid). */
+static int or_vox(double u, int Rk) {
+    double c = floor(u * (double)Rk);
+    if (c < 0.0) c = 0.0;
+    if (c > (double)(Rk - 1)) c = (double)(Rk - 1);
     return (int)c;
+}
+
+/* Empty-space step s_O from a point of empty voxel ev of resolution Rk (Sec. 3.3:
+ * the step that leaves the voxel the empty level reports).  The contracted image
+ * of the ray is aimed at a plane OR_GUARD finest voxels (2B / R_O each) beyond the
+ * voxel's exit face, so that the next point lies clearly inside the next voxel:
+ * first along the image's local direction v = J(x) d, which picks the exit axis
+ * a (the first plane reached); beyond the unit ball the image curves, so one
+ * Newton step on that axis then corrects the length with the image's position
+ * and direction at the first estimate (the correction clamped to half the
+ * estimate).  The bounded scene and the unit ball map straight, where the first
+ * estimate is exact. */
+#define OR_GUARD 2e-2
+static double or_empty_step(int bounded, const double x[3], const double y[3], const double d[3], double r,
+                            const int ev[3], int Rk, int R_O, double* v_exit) {
+    double B = bounded ? 1.0 : 2.0;
+    int curved = !bounded && r > 1.0;
+    double v[3];
+    if (curved) or_jacobian_dir(x, d, r, v);
+    else { v[0] = d[0]; v[1] = d[1]; v[2] = d[2]; }
+    double side = 2.0 * B / (double)Rk, g = OR_GUARD * 2.0 * B / (double)R_O;
+    double s0 = INFINITY, target = 0.0;
+    int ax = -1;
+    for (int a = 0; a < 3; ++a) {
+        double plane;
+        if (v[a] > 0.0) plane = -B + side * (ev[a] + 1) + g;
+        else if (v[a] < 0.0) plane = -B + side * ev[a] - g;
+        else continue;
+        double ta = (plane - y[a]) / v[a];
+        if (ta < s0) { s0 = ta; ax = a; target = plane; }
+    }
+    if (ax < 0) return INFINITY;
+    if (v_exit) *v_exit = fabs(v[ax]);
+    s0 = fmax(s0, 0.0);
+    if (!curved) return s0;
+    /* Newton step on axis ax at the first estimate */
+    double o0[3] = {0.0, 0.0, 0.0}, x1[3], y1[3], u1[3], r1, v1[3];
+    double p1[3] = {x[0] + s0 * d[0], x[1] + s0 * d[1], x[2] + s0 * d[2]};
+    or_point(0, o0, p1, 1.0, x1, y1, u1, &r1);
+    if (r1 > 1.0) or_jacobian_dir(x1, d, r1, v1);
+    else { v1[0] = d[0]; v1[1] = d[1]; v1[2] = d[2]; }
+    if (!(v1[ax] * v[ax] > 0.0)) return s0;
+    double c = (target - y1[ax]) / v1[ax];
+    return s0 + fmin(fmax(c, -0.5 * s0), 0.5 * s0);
+}
+
+/* For tests: s_O of points x (bounded or contracted) in their empty voxel of
+ * resolution Rk, with the guard of a finest resolution R_O. */
+void or_empty_step_batch(int bounded, const double* x, const double* d, int Rk, int R_O, int n, double* out) {
+    for (int i = 0; i < n; ++i) {
+        const double o[3] = {0.0, 0.0, 0.0};
+        double xx[3], y[3], u[3], r;
+        or_point(bounded, o, x + 3 * i, 1.0, xx, y, u, &r);
+        int ev[3] = {or_vox(u[0], Rk), or_vox(u[1], Rk), or_vox(u[2], Rk)};
+        out[i] = or_empty_step(bounded, xx, y, d + 3 * i, r, ev, Rk, R_O, NULL);
+    }
 }
 
 typedef struct {
@@ -504,175 +585,200 @@ typedef struct {
     double T;
 } or_ray_out;
 
-/* March one ray and composite (Eq. 2, Eq. 5 before the MLP).  The step rule is
- * Eq. 9 with the multi-level occupancy check of Sec. 3.3.  If samples != NULL the
- * per-sample records are written there (capacity max_samples). */
+/* What one marching point decides (Sec. 3.3): the coarse-to-fine occupancy test and,
+ * at an empty point, the step: s_O from the coarsest empty level, or the distance
+ * step v G (Eq. 9; max(v G, s_O) with dist_rule 1) when that level is coarser than
+ * G's grid and G > 0.  The voxel choices read u; the steps read the position. */
+typedef struct {
+    int empty_level;  /* -1: occupied at every level (a sample) */
+    double step;
+    double v_exit;    /* s_O: the image's speed across the exit face; 0 for a G step */
+} or_decision;
+
+static size_t or_level_word(const or_occ* oc, int k) {
+    size_t off = 0;
+    for (int j = 0; j < k; ++j) {
+        size_t rj = (size_t)(oc->R_O >> j);
+        off += or_words(rj * rj * rj);
+    }
+    return off;
+}
+
+static int or_g_shift(const or_occ* oc) {
+    int R_G = oc->R_G ? oc->R_G : oc->R_O, g = 0;
+    while ((oc->R_O >> g) > R_G) ++g;
+    return g;
+}
+
+static or_decision or_decide(const or_scene* s, const or_occ* oc, const or_opts* op, const double u[3],
+                             const double x[3], const double y[3], const double d[3], double r, double t) {
+    or_decision dc = {-1, 0.0, 0.0};
+    int ev[3] = {0, 0, 0};
+    for (int k = oc->n_levels - 1; k >= 0; --k) {
+        int Rk = oc->R_O >> k;
+        int c[3] = {or_vox(u[0], Rk), or_vox(u[1], Rk), or_vox(u[2], Rk)};
+        size_t bi = (size_t)c[0] + (size_t)Rk * ((size_t)c[1] + (size_t)Rk * (size_t)c[2]);
+        if (!or_bit(oc->bits + or_level_word(oc, k), bi)) {
+            dc.empty_level = k;
+            ev[0] = c[0]; ev[1] = c[1]; ev[2] = c[2];
+            break;
+        }
+    }
+    if (dc.empty_level < 0) return dc;
+    double s_O = or_empty_step(s->bounded, x, y, d, r, ev, oc->R_O >> dc.empty_level, oc->R_O, &dc.v_exit);
+    dc.step = s_O;
+    int R_G = oc->R_G ? oc->R_G : oc->R_O;
+    if (op->use_dist && oc->dist && dc.empty_level > or_g_shift(oc)) {
+        int g = oc->dist[(size_t)or_vox(u[0], R_G) +
+                         (size_t)R_G * ((size_t)or_vox(u[1], R_G) + (size_t)R_G * (size_t)or_vox(u[2], R_G))];
+        if (g > 0) {
+            double B = s->bounded ? 1.0 : 2.0;
+            double sg = or_dist_step(s->bounded, x, d, r, g * (2.0 * B / (double)R_G));
+            dc.step = op->dist_rule == 1 ? fmax(sg, s_O) : sg;
+            if (dc.step != s_O) dc.v_exit = 0.0;
+        }
+    }
+    return dc;
+}
+
+/* 1 when a unit-cube coordinate of this point lies within `margin` of a face of the
+ * voxels or G cells the decision reads and the decision on the other side of that
+ * face differs (another level empty, or an empty step longer or shorter by more
+ * than 1e-7 max(1, t)). */
+static int or_decision_ambiguous(const or_scene* s, const or_occ* oc, const or_opts* op, const double u[3],
+                                 const double x[3], const double y[3], const double d[3], double r, double t,
+                                 or_decision dc, double margin) {
+    int R_G = oc->R_G ? oc->R_G : oc->R_O;
+    int R_max = oc->R_O > R_G ? oc->R_O : R_G;
+    for (int a = 0; a < 3; ++a) {
+        /* faces of every grid read are faces of the finest one (resolutions are
+         * powers of two of one another) */
+        double p = u[a] * (double)R_max;
+        double f = floor(p + 0.5);
+        if (f <= 0.0 || f >= (double)R_max) continue;
+        if (fabs(p - f) >= margin * (double)R_max) continue;
+        double uo[3] = {u[0], u[1], u[2]};
+        double face = f / (double)R_max;
+        uo[a] = p >= f ? face - 1e-12 : face + 1e-12;
+        or_decision other = or_decide(s, oc, op, uo, x, y, d, r, t);
+        if ((other.empty_level < 0) != (dc.empty_level < 0)) return 1;
+        if (dc.empty_level >= 0 && fabs(other.step - dc.step) > 1e-7 * fmax(1.0, t)) return 1;
+    }
+    return 0;
+}
+
+/* March one ray and composite (Eq. 2, Eq. 5 before the MLP), in FP64.  The step
+ * rule is Eq. 9 with the multi-level occupancy check of Sec. 3.3; the sample step is
+ * gamma s_0 (bounded) or gamma s_0 max(1, |x|), and delta_i is that step clipped to
+ * the domain's end.  If samples != NULL the per-sample records are written there
+ * (capacity max_samples). */
 static void or_march(const or_scene* s, const or_occ* oc, const or_opts* op,
-                     const float o[3], const float din[3], float t_lo, float t_hi,
-                     or_ray_out* res, or_sample* samples, float d_out[3]) {
+                     const double o[3], const double din[3], double t_lo, double t_hi,
+                     or_ray_out* res, or_sample* samples, double d_out[3]) {
     memset(res, 0, sizeof *res);
     res->T = 1.0;
-    float n2 = (din[0] * din[0] + din[1] * din[1]) + din[2] * din[2];
-    float nn = sqrtf(n2);
-    float d[3] = {din[0] / nn, din[1] / nn, din[2] / nn};
+    double nn = sqrt(din[0] * din[0] + din[1] * din[1] + din[2] * din[2]);
+    double d[3] = {din[0] / nn, din[1] / nn, din[2] / nn};
     if (d_out) { d_out[0] = d[0]; d_out[1] = d[1]; d_out[2] = d[2]; }
-    float t_in, t_out;
-    float B = s->bounded ? 1.0f : 2.0f;
+    double t_in, t_out;
     if (s->bounded) {
-        float lo[3], hi[3];
+        t_in = -INFINITY;
+        t_out = INFINITY;
         for (int a = 0; a < 3; ++a) {
-            float ia = 1.0f / d[a];
-            float t0 = (-1.0f - o[a]) * ia, t1 = (1.0f - o[a]) * ia;
-            lo[a] = fminf(t0, t1);
-            hi[a] = fmaxf(t0, t1);
+            double t0 = (-1.0 - o[a]) / d[a], t1 = (1.0 - o[a]) / d[a];
+            t_in = fmax(t_in, fmin(t0, t1));
+            t_out = fmin(t_out, fmax(t0, t1));
         }
-        t_in = fmaxf(fmaxf(lo[0], lo[1]), lo[2]);
-        t_out = fminf(fminf(hi[0], hi[1]), hi[2]);
     } else {
-        float b = (o[0] * d[0] + o[1] * d[1]) + o[2] * d[2];
-        float c = ((o[0] * o[0] + o[1] * o[1]) + o[2] * o[2]) - op->r_far * op->r_far;
-        float disc = b * b - c;
-        if (!(disc >= 0.0f)) return;
-        float sq = sqrtf(disc);
-        t_in = -b - sq;
-        t_out = -b + sq;
+        /* |o + t d| = r_far */
+        double b = o[0] * d[0] + o[1] * d[1] + o[2] * d[2];
+        double c = o[0] * o[0] + o[1] * o[1] + o[2] * o[2] - (double)op->r_far * (double)op->r_far;
+        double disc = b * b - c;
+        if (fabs(disc) <= OR_AMB_END * fabs(c)) res->ambiguous = 1;
+        if (!(disc >= 0.0)) return;
+        t_in = -b - sqrt(disc);
+        t_out = -b + sqrt(disc);
     }
-    float t = fmaxf(t_in, op->t_min);
-    /* optional interval [t_lo, t_hi] from the learned proposal */
-    t = fmaxf(t, t_lo);
-    t_out = fminf(t_out, t_hi);
+    double t = fmax(fmax(t_in, (double)op->t_min), t_lo);
+    t_out = fmin(t_out, t_hi);
+    if (fabs(t - t_out) <= OR_AMB_END * fmax(1.0, fabs(t))) res->ambiguous = 1;
     if (!(t < t_out)) return;
     res->hit = 1;
-    const float dt0 = op->step_base * op->step_gamma;
-    const float t_start = t;
-    int lat_k = 0;
-    const int R_O = oc->R_O;
-    const int R_G = oc->R_G ? oc->R_G : oc->R_O;
-    int g_shift = 0;
-    while ((R_O >> g_shift) > R_G) ++g_shift;
-    const float vG = (2.0f * B) / (float)R_G;
+    const double dt0 = (double)op->step_base * (double)op->step_gamma;
+    const double t_start = t;
+    long lat_k = 0;
     double T = 1.0;
     while (t < t_out && res->n_march < op->max_march && res->n_samples < op->max_samples) {
         res->n_march++;
-        float x[3], y[3], u[3], r;
-        or_point(s, o, d, t, x, y, u, &r);
-        /* coarse-to-fine occupancy check; empty_level = coarsest level reporting empty */
-        int empty_level = -1, ev[3] = {0, 0, 0};
-        size_t woff = 0;
-        size_t offs[16];
-        for (int k = 0; k < oc->n_levels; ++k) {
-            offs[k] = woff;
-            size_t rk = (size_t)(R_O >> k);
-            woff += or_words(rk * rk * rk);
-        }
-        for (int k = oc->n_levels - 1; k >= 0; --k) {
-            int Rk = R_O >> k;
-            int c[3] = {or_vox(u[0], Rk), or_vox(u[1], Rk), or_vox(u[2], Rk)};
-            size_t bi = (size_t)c[0] + (size_t)Rk * ((size_t)c[1] + (size_t)Rk * c[2]);
-            if (!or_bit(oc->bits + offs[k], bi)) {
-                empty_level = k;
-                ev[0] = c[0]; ev[1] = c[1]; ev[2] = c[2];
-                break;
-            }
-        }
-        float step;
+        double x[3], y[3], u[3], r;
+        or_point(s->bounded, o, d, t, x, y, u, &r);
+        or_decision dc = or_decide(s, oc, op, u, x, y, d, r, t);
+        if (or_decision_ambiguous(s, oc, op, u, x, y, d, r, t, dc, OR_AMB_U)) res->ambiguous = 1;
+        double step;
         int sampled = 0;
-        if (empty_level < 0) {
-            /* occupied at every level: take a sample */
-            float dt = s->bounded ? dt0 : dt0 * fmaxf(1.0f, r);
-            float delta = fminf(dt, t_out - t);
+        if (dc.empty_level < 0) {
+            /* occupied at every level: a sample */
+            double dt = s->bounded ? dt0 : dt0 * fmax(1.0, r);
+            double delta = fmin(dt, t_out - t);
             double f[OR_NFEAT];
             or_features(s, op, u, f);
-            double sr = f[0];
-            double sigma = exp(sr);
-            double alpha = 1.0 - exp(-sigma * (double)delta);
+            double sigma = exp(f[0]);
+            double alpha = 1.0 - exp(-sigma * delta);
             double w = T * alpha;
             if (samples) {
                 or_sample* sp = samples + res->n_samples;
                 sp->t = t; sp->delta = delta;
                 sp->u[0] = u[0]; sp->u[1] = u[1]; sp->u[2] = u[2];
-                sp->sigma_raw = sr; sp->sigma = sigma; sp->alpha = alpha; sp->T_before = T;
+                sp->sigma_raw = f[0]; sp->sigma = sigma; sp->alpha = alpha; sp->T_before = T;
                 memcpy(sp->f, f, sizeof f);
             }
             for (int k = 0; k < 3; ++k) res->C_d[k] += w * f[1 + k];
             for (int k = 0; k < 4; ++k) res->F[k] += w * f[4 + k];
             res->A += w;
-            res->depth += w * (double)t;
+            res->depth += w * t;
             T *= 1.0 - alpha;
             res->n_samples++;
             sampled = 1;
             step = dt;
-            double rel = fabs(T - (double)op->t_term) / (double)op->t_term;
-            if (rel < 3e-5) res->ambiguous = 1;
-            if (T < (double)op->t_term) break;
+            if (fabs(T - (double)op->t_term) <= OR_AMB_T * (double)op->t_term) res->ambiguous = 1;
+            if (T < (double)op->t_term) break;   /* strict: the crossing sample is kept */
         } else {
-            /* s_O: leave the empty voxel of level empty_level along the ray (its
-             * local direction in contracted space), plus a small guard distance */
-            int Rk = R_O >> empty_level;
-            float vk = (2.0f * B) / (float)Rk;
-            float v[3];
-            if (s->bounded || !(r > 1.0f)) {
-                v[0] = d[0]; v[1] = d[1]; v[2] = d[2];
-            } else {
-                /* J(x) d = k d + m x, k = (2 - 1/r)/r, m = (x.d) 2 (1 - r) / r^4 */
-                float ir = 1.0f / r;
-                float k = (2.0f - ir) * ir;
-                float px = (x[0] * d[0] + x[1] * d[1]) + x[2] * d[2];
-                float ir2 = ir * ir;
-                float m = (px * (2.0f * (1.0f - r))) * (ir2 * ir2);
-                for (int a = 0; a < 3; ++a) v[a] = k * d[a] + m * x[a];
-            }
-            float se = INFINITY;
-            for (int a = 0; a < 3; ++a) {
-                float lo = (float)ev[a] * vk - B;
-                float hi = lo + vk;
-                float ta = INFINITY;
-                if (v[a] > 0.0f) ta = (hi - y[a]) / v[a];
-                else if (v[a] < 0.0f) ta = (lo - y[a]) / v[a];
-                se = fminf(se, ta);
-            }
-            float s_O = fmaxf(se, 0.0f) + 1e-5f * fmaxf(1.0f, t);
-            step = s_O;
-            /* Eq. 9: read G only when the empty level is coarser than G's grid */
-            /* G is read when the empty level is coarser than G's own resolution */
-            if (op->use_dist && oc->dist && empty_level > g_shift) {
-                int c0[3] = {or_vox(u[0], R_G), or_vox(u[1], R_G), or_vox(u[2], R_G)};
-                int g = oc->dist[(size_t)c0[0] + (size_t)R_G * ((size_t)c0[1] + (size_t)R_G * c0[2])];
-                if (g > 0) {
-                    float sg = or_dist_step(s->bounded, x, d, r, (float)g * vG);
-                    step = op->dist_rule == 1 ? fmaxf(sg, s_O) : sg;
-                }
-            }
+            step = dc.step;
         }
         if (op->lattice_snap && s->bounded) {
+            /* next point on the lattice t_start + k dt0: the next index after a
+             * sample, else the first lattice point at or beyond t + step */
             if (sampled) lat_k += 1;
             else {
-                int kk = (int)floorf(((t + step) - t_start) / dt0);
-                lat_k = kk > lat_k + 1 ? kk : lat_k + 1;
+                double q = (t + step - t_start) / dt0;
+                double kq = floor(q);
+                if (fabs(q - floor(q + 0.5)) <= OR_AMB_LATTICE) res->ambiguous = 1;
+                lat_k = (long)kq > lat_k + 1 ? (long)kq : lat_k + 1;
             }
-            t = t_start + (float)lat_k * dt0;
+            t = t_start + (double)lat_k * dt0;
         } else {
             t = t + step;
         }
+        if (fabs(t - t_out) <= OR_AMB_END * fmax(1.0, fabs(t))) res->ambiguous = 1;
     }
     res->T = T;
 }
 
 /* Pinhole ray of pixel (col, row) of a camera [c2w(3x4) fx fy cx cy] through the
- * pixel centre; OpenCV axes (x right, y down, z forward).  FP32. */
-static void or_camera_ray(const float* cam, int col, int row, float o[3], float d[3]) {
-    float px = (((float)col + 0.5f) - cam[14]) / cam[12];
-    float py = (((float)row + 0.5f) - cam[15]) / cam[13];
+ * pixel centre; OpenCV axes (x right, y down, z forward). */
+static void or_camera_ray(const float* cam, int col, int row, double o[3], double d[3]) {
+    double px = ((double)col + 0.5 - (double)cam[14]) / (double)cam[12];
+    double py = ((double)row + 0.5 - (double)cam[15]) / (double)cam[13];
     for (int r = 0; r < 3; ++r) {
-        d[r] = (cam[4 * r + 0] * px + cam[4 * r + 1] * py) + cam[4 * r + 2];
-        o[r] = cam[4 * r + 3];
+        d[r] = (double)cam[4 * r + 0] * px + (double)cam[4 * r + 1] * py + (double)cam[4 * r + 2];
+        o[r] = (double)cam[4 * r + 3];
     }
 }
 
 /* Ray i of a batch: pixel i (or pix[i]) of the cameras, view-major then row-major,
  * or the i-th explicit ray. */
 static void or_ray_input(const float* cams, int n_cams, int W, int H, const int32_t* pix,
-                         const float* rays_o, const float* rays_d, int i, float o[3], float d[3]) {
+                         const float* rays_o, const float* rays_d, int i, double o[3], double d[3]) {
     if (cams) {
         int64_t id = pix ? pix[i] : i;
         int64_t v = id / ((int64_t)W * H), rem = id % ((int64_t)W * H);
@@ -684,26 +790,20 @@ static void or_ray_input(const float* cams, int n_cams, int W, int H, const int3
 }
 
 void or_camera_rays(const float* cams, int n_cams, int W, int H, const int32_t* pix, int n,
-                    float* o_out, float* d_out) {
-    for (int i = 0; i < n; ++i) {
-        int64_t id = pix ? pix[i] : i;
-        int64_t v = id / ((int64_t)W * H), rem = id % ((int64_t)W * H);
-        if (v >= n_cams) v = n_cams - 1;
-        or_camera_ray(cams + 16 * v, (int)(rem % W), (int)(rem / W), o_out + 3 * i, d_out + 3 * i);
-    }
+                    double* o_out, double* d_out) {
+    for (int i = 0; i < n; ++i) or_ray_input(cams, n_cams, W, H, pix, NULL, NULL, i, o_out + 3 * i, d_out + 3 * i);
 }
 
 /* Final colour: sigmoid(C_d + MLP_psi(C_d, F, SH(d))) (Eq. 5 then the colour
  * sigmoid of Sec. S2.1), composited over the background with the accumulated
  * opacity A (the paper's C when A = 1). */
-static void or_shade(const or_scene* s, const or_opts* op, const or_ray_out* rr, const float d[3],
+static void or_shade(const or_scene* s, const or_opts* op, const or_ray_out* rr, const double d[3],
                      double rgb[3], double x_out[OR_MLP_IN], double acts[256], double z_out[3]) {
     double x[OR_MLP_IN];
     memset(x, 0, sizeof x);
     for (int k = 0; k < 3; ++k) x[k] = rr->C_d[k];
     for (int k = 0; k < 4; ++k) x[3 + k] = rr->F[k];
-    double dd[3] = {d[0], d[1], d[2]};
-    or_sh16(dd, x + 7);
+    or_sh16(d, x + 7);
     double y[3];
     or_mlp_forward(s, x, y, acts);
     for (int k = 0; k < 3; ++k) {
@@ -727,9 +827,9 @@ void or_render(const or_scene* s, const or_occ* oc, const or_opts* op,
     /* rays are independent: one ray per loop iteration, spread over host threads */
     #pragma omp parallel for schedule(dynamic, 16)
     for (int i = 0; i < n; ++i) {
-        float o[3], dv[3], d[3];
+        double o[3], dv[3], d[3];
         or_ray_input(cams, n_cams, W, H, pix, rays_o, rays_d, i, o, dv);
-        float tlo = interval ? interval[2 * i] : -INFINITY, thi = interval ? interval[2 * i + 1] : INFINITY;
+        double tlo = interval ? interval[2 * i] : -INFINITY, thi = interval ? interval[2 * i + 1] : INFINITY;
         or_ray_out rr;
         or_march(s, oc, op, o, dv, tlo, thi, &rr, NULL, d);
         double c[3];
@@ -750,8 +850,9 @@ void or_render(const or_scene* s, const or_occ* oc, const or_opts* op,
 }
 
 /* Per-sample dump of one ray: t, delta, u, sigma, weight (for tests). */
-int or_ray_samples(const or_scene* s, const or_occ* oc, const or_opts* op, const float o[3],
-                   const float d[3], int cap, double* out /* [cap][7] */) {
+int or_ray_samples(const or_scene* s, const or_occ* oc, const or_opts* op, const float of[3],
+                   const float df[3], int cap, double* out /* [cap][7] */) {
+    const double o[3] = {of[0], of[1], of[2]}, d[3] = {df[0], df[1], df[2]};
     or_sample* sm = (or_sample*)malloc(sizeof(or_sample) * (size_t)(op->max_samples > 0 ? op->max_samples : 1));
     or_ray_out rr;
     or_march(s, oc, op, o, d, -INFINITY, INFINITY, &rr, sm, NULL);
@@ -776,7 +877,7 @@ int or_ray_samples(const or_scene* s, const or_occ* oc, const or_opts* op, const
  * gradients of the coarse vertices, the gate logits (coarse channels or the constant
  * logits) or the tiny MLP's weights, and the fine entries.  kink (may be NULL) is set
  * when a hidden unit of the MLP form lies within 1e-5 relative of its ReLU kink. */
-static void or_feature_reverse(const or_scene* s, const or_opts* op, const float u[3], const double g_f[OR_NFEAT],
+static void or_feature_reverse(const or_scene* s, const or_opts* op, const double u[3], const double g_f[OR_NFEAT],
                                double* g_tables, double* g_coarse, double* g_attn_inv, double* g_agg_mlp,
                                int32_t* kink) {
     int nch = or_coarse_channels(s->L, s->aggregation);
@@ -804,33 +905,50 @@ static void or_feature_reverse(const or_scene* s, const or_opts* op, const float
         int nx = OR_NFEAT * s->L;
         const double* w1 = s->agg_mlp;
         const double* w2 = s->agg_mlp + (size_t)OR_AGG_HIDDEN * nx;
-        double xs[OR_NFEAT * OR_MAXL], h[OR_AGG_HIDDEN], gh[OR_AGG_HIDDEN], gx[OR_NFEAT * OR_MAXL];
+        double xs[OR_NFEAT * OR_MAXL], dxs[OR_NFEAT * OR_MAXL], h[OR_AGG_HIDDEN], gh[OR_AGG_HIDDEN];
+        double gx[OR_NFEAT * OR_MAXL];
         uint64_t ents[OR_MAXL][8];
         double ews[OR_MAXL][8];
         memset(xs, 0, sizeof xs);
+        memset(dxs, 0, sizeof dxs);
         for (int l = 0; l < s->L; ++l) {
             int bl[3];
-            double wl[3];
+            double wl[3], gd[3][OR_NFEAT];
+            memset(gd, 0, sizeof gd);
             or_cell(u, s->N[l], bl, wl);
             uint64_t off = or_level_offset(s->N, s->L, s->T_log2, l);
             for (int c = 0; c < 8; ++c) {
                 int xx = bl[0] + (c & 1), yy = bl[1] + ((c >> 1) & 1), zz = bl[2] + ((c >> 2) & 1);
                 ents[l][c] = off + or_level_entry(s->N[l], T, xx, yy, zz);
                 ews[l][c] = or_corner_weight(wl, c);
-                for (int ch = 0; ch < OR_NFEAT; ++ch)
-                    xs[OR_NFEAT * l + ch] += ews[l][c] * s->tables[ents[l][c] * OR_NFEAT + ch];
+                for (int ch = 0; ch < OR_NFEAT; ++ch) {
+                    double v = s->tables[ents[l][c] * OR_NFEAT + ch];
+                    xs[OR_NFEAT * l + ch] += ews[l][c] * v;
+                    /* d/du_a of the corner weight: +-(N-1) times the other two factors */
+                    for (int a = 0; a < 3; ++a) {
+                        double dw = (double)(s->N[l] - 1) * (((c >> a) & 1) ? 1.0 : -1.0);
+                        for (int b = 0; b < 3; ++b)
+                            if (b != a) dw *= ((c >> b) & 1) ? wl[b] : 1.0 - wl[b];
+                        gd[a][ch] += dw * v;
+                    }
+                }
             }
+            for (int ch = 0; ch < OR_NFEAT; ++ch)
+                dxs[OR_NFEAT * l + ch] = (fabs(gd[0][ch]) + fabs(gd[1][ch]) + fabs(gd[2][ch])) * or_kink_pos_err;
         }
         for (int j = 0; j < OR_AGG_HIDDEN; ++j) {
-            double acc = 0.0, mag = 0.0;
+            double acc = 0.0, mag = 0.0, sens = 0.0;
             for (int q = 0; q < nx; ++q) {
                 acc += w1[(size_t)j * nx + q] * xs[q];
                 mag += fabs(w1[(size_t)j * nx + q] * xs[q]);
+                sens += fabs(w1[(size_t)j * nx + q]) * dxs[q];
             }
             h[j] = acc;
-            /* a unit this close to its ReLU kink may switch sides in FP32: the
-             * ray's gradient is then not comparable element by element */
-            if (kink && fabs(acc) <= 1e-5 * mag) *kink = 1;
+            /* a unit this close to its ReLU kink may switch sides in FP32 (its own
+             * rounding, or the FP32 sample position moving the level features by up
+             * to their gradient times the position error): the ray's gradient is then
+             * not comparable element by element */
+            if (kink && fabs(acc) <= 1e-5 * mag + sens) *kink = 1;
         }
         for (int j = 0; j < OR_AGG_HIDDEN; ++j) {
             double ga = 0.0;
@@ -933,7 +1051,7 @@ void or_render_backward(const or_scene* s, const or_occ* oc, const or_opts* op,
     or_sample* sm = (or_sample*)malloc(sizeof(or_sample) * (size_t)cap);
     double* qg = (double*)malloc(sizeof(double) * (size_t)cap);
     for (int i = 0; i < n; ++i) {
-        float o[3], dv[3], d[3];
+        double o[3], dv[3], d[3];
         or_ray_input(cams, n_cams, W, H, pix, rays_o, rays_d, i, o, dv);
         or_ray_out rr;
         or_march(s, oc, op, o, dv, -INFINITY, INFINITY, &rr, sm, d);
@@ -981,7 +1099,7 @@ void or_render_backward(const or_scene* s, const or_occ* oc, const or_opts* op,
         /* per-sample scalar q_i . g (the gradient-weighted quantity composited) */
         int ns = rr.n_samples;
         for (int a = 0; a < ns; ++a) {
-            double q = g_A + g_D * (double)sm[a].t;
+            double q = g_A + g_D * sm[a].t;
             for (int k = 0; k < 3; ++k) q += g_Cd[k] * sm[a].f[1 + k];
             for (int k = 0; k < 4; ++k) q += g_F[k] * sm[a].f[4 + k];
             qg[a] = q;
@@ -992,7 +1110,7 @@ void or_render_backward(const or_scene* s, const or_occ* oc, const or_opts* op,
             double T_next = sp->T_before * (1.0 - sp->alpha);
             double later = 0.0;
             for (int b = a + 1; b < ns; ++b) later += sm[b].T_before * sm[b].alpha * qg[b];
-            double g_sigma = (double)sp->delta * (T_next * qg[a] - later);
+            double g_sigma = sp->delta * (T_next * qg[a] - later);
             double g_f[OR_NFEAT];
             g_f[0] = g_sigma * exp(fmin(sp->sigma_raw, 15.0));
             for (int k = 0; k < 3; ++k) g_f[1 + k] = w * g_Cd[k];
@@ -1194,7 +1312,7 @@ void or_prop_targets(const or_scene* s, const or_occ* oc, const or_opts* op, con
         or_sample* sm = (or_sample*)malloc(sizeof(or_sample) * (size_t)cap);
         #pragma omp for schedule(dynamic, 16)
         for (int i = 0; i < n; ++i) {
-            float o[3], dv[3];
+            double o[3], dv[3];
             or_ray_input(cams, n_cams, W, H, pix, rays_o, rays_d, i, o, dv);
             or_ray_out rr;
             or_march(s, oc, op, o, dv, -INFINITY, INFINITY, &rr, sm, NULL);
@@ -1203,9 +1321,9 @@ void or_prop_targets(const or_scene* s, const or_occ* oc, const or_opts* op, con
             for (int k = 0; k < rr.n_samples; ++k) {
                 cum += sm[k].T_before * sm[k].alpha;
                 if (!got_near && cum > 0.005 * rr.A) { tn = sm[k].t; got_near = 1; }
-                if (!got_far && cum >= 0.995 * rr.A) { tf = (double)sm[k].t + (double)sm[k].delta; got_far = 1; }
+                if (!got_far && cum >= 0.995 * rr.A) { tf = sm[k].t + sm[k].delta; got_far = 1; }
             }
-            if (rr.n_samples > 0 && !got_far) tf = (double)sm[rr.n_samples - 1].t + (double)sm[rr.n_samples - 1].delta;
+            if (rr.n_samples > 0 && !got_far) tf = sm[rr.n_samples - 1].t + sm[rr.n_samples - 1].delta;
             targets[3 * i + 0] = tn;
             targets[3 * i + 1] = tf;
             targets[3 * i + 2] = rr.A;
@@ -1226,7 +1344,7 @@ void or_occupancy_density(const or_scene* s, const or_opts* op, int R, double si
     #pragma omp parallel for schedule(static)
     for (long v = 0; v < n; ++v) {
         int i = (int)(v % R), j = (int)((v / R) % R), k = (int)(v / ((long)R * R));
-        float u[3] = {((float)i + 0.5f) / (float)R, ((float)j + 0.5f) / (float)R, ((float)k + 0.5f) / (float)R};
+        double u[3] = {(i + 0.5) / R, (j + 0.5) / R, (k + 0.5) / R};
         double f[OR_NFEAT];
         or_features(s, op, u, f);
         double sg = exp(f[0]);
@@ -1246,7 +1364,7 @@ void or_occupancy_visibility(const or_scene* s, const or_occ* oc, const or_opts*
                              uint8_t* vis, double* wmax) {
     or_sample* sm = (or_sample*)malloc(sizeof(or_sample) * (size_t)(op->max_samples > 0 ? op->max_samples : 1));
     for (int i = 0; i < n; ++i) {
-        float o[3], dv[3];
+        double o[3], dv[3];
         or_ray_input(cams, n_cams, W, H, pix, rays_o, rays_d, i, o, dv);
         or_ray_out rr;
         or_march(s, oc, op, o, dv, -INFINITY, INFINITY, &rr, sm, NULL);
@@ -1313,18 +1431,18 @@ void or_distortion(const or_scene* s, const or_occ* oc, const or_opts* op,
         or_sample* sm = (or_sample*)malloc(sizeof(or_sample) * (size_t)(op->max_samples > 0 ? op->max_samples : 1));
         #pragma omp for schedule(dynamic, 16)
         for (int r = 0; r < n; ++r) {
-            float o[3], dv[3];
+            double o[3], dv[3];
             or_ray_input(cams, n_cams, W, H, pix, rays_o, rays_d, r, o, dv);
             or_ray_out rr;
             or_march(s, oc, op, o, dv, -INFINITY, INFINITY, &rr, sm, NULL);
             double pair = 0.0, self = 0.0, Ws = 0.0, Ss = 0.0;
             for (int i = 0; i < rr.n_samples; ++i) {
-                double wi = sm[i].T_before * sm[i].alpha, mi = (double)sm[i].t + 0.5 * (double)sm[i].delta;
+                double wi = sm[i].T_before * sm[i].alpha, mi = sm[i].t + 0.5 * sm[i].delta;
                 for (int j = 0; j < rr.n_samples; ++j) {
-                    double wj = sm[j].T_before * sm[j].alpha, mj = (double)sm[j].t + 0.5 * (double)sm[j].delta;
+                    double wj = sm[j].T_before * sm[j].alpha, mj = sm[j].t + 0.5 * sm[j].delta;
                     pair += wi * wj * fabs(mi - mj);
                 }
-                self += wi * wi * (double)sm[i].delta / 3.0;
+                self += wi * wi * sm[i].delta / 3.0;
                 Ws += wi;
                 Ss += wi * mi;
             }
@@ -1349,26 +1467,26 @@ void or_distortion_backward(const or_scene* s, const or_occ* oc, const or_opts* 
     or_sample* sm = (or_sample*)malloc(sizeof(or_sample) * (size_t)(op->max_samples > 0 ? op->max_samples : 1));
     double* g = (double*)malloc(sizeof(double) * (size_t)(op->max_samples > 0 ? op->max_samples : 1));
     for (int r = 0; r < n; ++r) {
-        float o[3], dv[3];
+        double o[3], dv[3];
         or_ray_input(cams, n_cams, W, H, pix, rays_o, rays_d, r, o, dv);
         or_ray_out rr;
         or_march(s, oc, op, o, dv, -INFINITY, INFINITY, &rr, sm, NULL);
         int ns = rr.n_samples;
         for (int j = 0; j < ns; ++j) {
-            double mj = (double)sm[j].t + 0.5 * (double)sm[j].delta;
+            double mj = sm[j].t + 0.5 * sm[j].delta;
             double acc = 0.0;
             for (int k = 0; k < ns; ++k) {
-                double mk = (double)sm[k].t + 0.5 * (double)sm[k].delta;
+                double mk = sm[k].t + 0.5 * sm[k].delta;
                 acc += sm[k].T_before * sm[k].alpha * fabs(mj - mk);
             }
             double wj = sm[j].T_before * sm[j].alpha;
-            g[j] = 2.0 * acc + 2.0 / 3.0 * wj * (double)sm[j].delta;
+            g[j] = 2.0 * acc + 2.0 / 3.0 * wj * sm[j].delta;
         }
         for (int i = 0; i < ns; ++i) {
             const or_sample* sp = sm + i;
             double T_next = sp->T_before * (1.0 - sp->alpha);
-            double d_sigma = (double)sp->delta * T_next * g[i];
-            for (int j = i + 1; j < ns; ++j) d_sigma -= (double)sp->delta * sm[j].T_before * sm[j].alpha * g[j];
+            double d_sigma = sp->delta * T_next * g[i];
+            for (int j = i + 1; j < ns; ++j) d_sigma -= sp->delta * sm[j].T_before * sm[j].alpha * g[j];
             /* the regulariser sees the density only: f's cotangent is [dL/d sigma_raw, 0, ...] */
             double g_f[OR_NFEAT] = {scale * d_sigma * exp(fmin(sp->sigma_raw, 15.0)), 0, 0, 0, 0, 0, 0, 0};
             or_feature_reverse(s, op, sp->u, g_f, g_tables, g_coarse, g_attn_inv, g_agg_mlp, NULL);

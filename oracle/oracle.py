@@ -2,7 +2,7 @@
 
 TEST INFRASTRUCTURE ONLY: the test-suite, the package smoke check and the
 benchmark's CPU-baseline / reference arm call it; the CUDA library never does.
-The arithmetic lives in ``ngprt_oracle.c`` (FP64 values, FP32 march decisions);
+The arithmetic lives in ``ngprt_oracle.c`` (FP64 throughout, the march included);
 this module only builds that file with gcc, marshals numpy arrays and converts
 every table to FP64 before the call.
 """
@@ -88,6 +88,15 @@ def max_threads() -> int:
     return int(lib().or_max_threads())
 
 
+DEFAULT_POSITION_ERROR = 8e-7   # the oracle's OR_AMB_U
+
+
+def set_kink_position_error(e: float) -> None:
+    """Unit-cube position error the tiny-MLP form's kink flag allows for (default: the
+    FP32 march's; 0 for rays whose sample positions are exact in FP32)."""
+    lib().or_set_kink_position_error(C.c_double(e))
+
+
 # ----------------------------------------------------------------- primitives
 
 def hash3(xyz: np.ndarray, T: int) -> np.ndarray:
@@ -156,12 +165,13 @@ def sh16(d: np.ndarray) -> np.ndarray:
 
 
 def camera_rays(cams: np.ndarray, W: int, H: int, pix=None, n=None):
+    """FP64 origins and (unnormalised) directions of pixel-centre rays."""
     cams = _c(cams, np.float32).reshape(-1, 16)
     pix = _c(pix, np.int32)
     if n is None:
         n = len(pix) if pix is not None else len(cams) * W * H
-    o = np.empty((n, 3), np.float32)
-    d = np.empty((n, 3), np.float32)
+    o = np.empty((n, 3), np.float64)
+    d = np.empty((n, 3), np.float64)
     lib().or_camera_rays(_p(cams), C.c_int(len(cams)), C.c_int(W), C.c_int(H), _p(pix), C.c_int(n),
                          _p(o), _p(d))
     return o, d
@@ -445,8 +455,8 @@ def oracle_for_scene(scene, tables=None, coarse=None, use_dist=True, dist_level=
 
 
 def contract(x: np.ndarray, bounded: bool = False):
-    """FP32 contraction y and unit-cube position u of world points x [n, 3]."""
-    x = _c(x, np.float32).reshape(-1, 3)
+    """FP64 contraction y and unit-cube position u of world points x [n, 3]."""
+    x = _c(x, np.float64).reshape(-1, 3)
     y = np.empty_like(x)
     u = np.empty_like(x)
     lib().or_contract_batch(C.c_int(1 if bounded else 0), _p(x), C.c_int(len(x)), _p(y), _p(u))
@@ -544,10 +554,22 @@ Oracle.prop_targets = _prop_targets
 
 def dist_step(x, d, rho, bounded=False):
     """World length of the distance step (Eq. 9) from points x along unit d for
-    contracted radii rho (FP32, as the march takes it)."""
-    x = _c(x, np.float32).reshape(-1, 3)
-    d = _c(d, np.float32).reshape(-1, 3)
-    rho = _c(rho, np.float32).reshape(-1)
-    out = np.empty(len(x), np.float32)
+    contracted radii rho (FP64)."""
+    x = _c(x, np.float64).reshape(-1, 3)
+    d = _c(d, np.float64).reshape(-1, 3)
+    rho = _c(rho, np.float64).reshape(-1)
+    out = np.empty(len(x), np.float64)
     lib().or_dist_step_batch(C.c_int(1 if bounded else 0), _p(x), _p(d), _p(rho), C.c_int(len(x)), _p(out))
+    return out
+
+
+def empty_step(x, d, Rk, R_O=None, bounded=False):
+    """s_O (Sec. 3.3) of world points x along unit d, each in its own voxel of a grid
+    of Rk voxels per axis over the (contracted) domain, with the guard of the finest
+    resolution R_O (default Rk) (FP64)."""
+    x = _c(x, np.float64).reshape(-1, 3)
+    d = _c(d, np.float64).reshape(-1, 3)
+    out = np.empty(len(x), np.float64)
+    lib().or_empty_step_batch(C.c_int(1 if bounded else 0), _p(x), _p(d), C.c_int(Rk), C.c_int(R_O or Rk),
+                              C.c_int(len(x)), _p(out))
     return out

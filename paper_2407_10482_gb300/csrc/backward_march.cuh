@@ -320,9 +320,9 @@ __global__ void __launch_bounds__(128, NGPRT_BWD_MIN_BLOCKS) march_backward_kern
         for (int k = 0; k < NI; ++k) slots[(4 * L + k) * stride] = 0.0f;
     }
     int64_t ray;
-    float o[3], d[3], t, t_out;
+    Ray ry;
     bool hit = false;
-    const bool live = ray_setup(p.m, ray, o, d, t, t_out, hit) && hit;
+    const bool live = ray_setup(p.m, ray, ry, hit) && hit;
     if constexpr (NI == 0) {
         if (!live) return;
     }
@@ -335,14 +335,14 @@ __global__ void __launch_bounds__(128, NGPRT_BWD_MIN_BLOCKS) march_backward_kern
                                               p.g_tables, p.g_coarse, slots, p.records, p.n_records,
                                               p.rec_capacity, 0.0f, 0.0f, 0.0f, ds.y, ds.z, 2.0f * ds.x,
                                               p.dist_scale};
-            march_loop(p.m, o, d, t, t_out, smp, n_march, n_samp);
+            march_loop(p.m, ry, smp, n_march, n_samp);
         } else {
             const float4* c4 = reinterpret_cast<const float4*>(p.cot + ray * kCotFloats);
             const float4 q0 = c4[0], q1 = c4[1], q2 = c4[2];
             BackwardSampler<L, AGG> smp{p.m.g, p.m.opts.attn_mode, p.m.opts.t_term, 1.0f, 0.0f, q2.y,
                                         {q0.x, q0.y, q0.z}, {q0.w, q1.x, q1.y, q1.z}, q1.w, q2.x, p.g_tables,
                                         p.g_coarse, slots, p.records, p.n_records, p.rec_capacity};
-            march_loop(p.m, o, d, t, t_out, smp, n_march, n_samp);
+            march_loop(p.m, ry, smp, n_march, n_samp);
         }
     }
     if constexpr (NI > 0) {

@@ -1,10 +1,12 @@
 // common.cuh -- device helpers shared by the NGP-RT kernels (sm_103a).
 //
-// The march is an FP32 recurrence whose results are integers (which voxel is
-// tested, which point is sampled).  Every operation of it goes through the
-// explicitly rounded intrinsics below, so that no multiply-add is fused and each
-// result is the IEEE round-to-nearest value: the decisions are then a fixed
-// function of the inputs.
+// The march is a recurrence whose results are integers (which voxel is tested,
+// which point is sampled).  It takes its voxel decisions on FP32 unit-cube
+// coordinates; the ray set-up and the running parameter t are carried in
+// double-float, so a position is exact to about the rounding of its last
+// operations.  Its operations go through the explicitly rounded intrinsics below:
+// no multiply-add is fused behind the code's back, which the error-free
+// transformations of the double-float arithmetic rely on.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -75,66 +77,153 @@ __device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b)
 __device__ __forceinline__ float fdiv(float a, float b) { return __fdiv_rn(a, b); }
 __device__ __forceinline__ float fsqrt(float a) { return __fsqrt_rn(a); }
 
-// Pinhole ray through the centre of pixel (col, row); OpenCV axes.
-__device__ __forceinline__ void camera_ray(const ngprt_camera& c, int col, int row, float o[3], float d[3]) {
-    float px = fdiv(fsub(fadd((float)col, 0.5f), c.cx), c.fx);
-    float py = fdiv(fsub(fadd((float)row, 0.5f), c.cy), c.fy);
+// ------------------------------------------------ double-float (hi + lo) values
+// A value held as the unevaluated sum hi + lo of two floats (|lo| <= ulp(hi) / 2)
+// carries about 48 bits.  The error-free transformations below (Knuth's two-sum,
+// Dekker's fast two-sum, the FMA two-product) give the ray set-up and the march's
+// running parameter t that precision, so that a sample position differs from the
+// exact one by little more than the rounding of its final single-precision value.
+struct df {
+    float hi, lo;
+};
+
+__device__ __forceinline__ df df_two_sum(float a, float b) {
+    const float s = fadd(a, b);
+    const float bb = fsub(s, a);
+    return {s, fadd(fsub(a, fsub(s, bb)), fsub(b, bb))};
+}
+// requires |a| >= |b| (or a == 0)
+__device__ __forceinline__ df df_fast_sum(float a, float b) {
+    const float s = fadd(a, b);
+    return {s, fsub(b, fsub(s, a))};
+}
+__device__ __forceinline__ df df_prod(float a, float b) {
+    const float q = fmul(a, b);
+    return {q, __fmaf_rn(a, b, -q)};
+}
+__device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ df df_add(df a, df b) {
+    const df s = df_two_sum(a.hi, b.hi);
+    return df_fast_sum(s.hi, fadd(s.lo, fadd(a.lo, b.lo)));
+}
+__device__ __forceinline__ df df_add_f(df a, float b) {
+    const df s = df_two_sum(a.hi, b);
+    return df_fast_sum(s.hi, fadd(s.lo, a.lo));
+}
+__device__ __forceinline__ df df_mul(df a, df b) {
+    const df q = df_prod(a.hi, b.hi);
+    return df_fast_sum(q.hi, __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, q.lo)));
+}
+__device__ __forceinline__ df df_mul_f(df a, float b) {
+    const df q = df_prod(a.hi, b);
+    return df_fast_sum(q.hi, __fmaf_rn(a.lo, b, q.lo));
+}
+__device__ __forceinline__ df df_div(df a, df b) {
+    const float q1 = fdiv(a.hi, b.hi);
+    const df r = df_add(a, df_neg(df_mul_f(b, q1)));  // a - q1 b
+    return df_fast_sum(q1, fdiv(r.hi, b.hi));
+}
+__device__ __forceinline__ df df_sqrt(df a) {
+    if (!(a.hi > 0.0f)) return {0.0f, 0.0f};
+    const float s = fsqrt(a.hi);
+    const df r = df_add(a, df_neg(df_prod(s, s)));  // a - s^2
+    return df_fast_sum(s, fdiv(r.hi, fmul(2.0f, s)));
+}
+__device__ __forceinline__ bool df_lt(df a, df b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+__device__ __forceinline__ df df_max(df a, df b) { return df_lt(a, b) ? b : a; }
+__device__ __forceinline__ df df_min(df a, df b) { return df_lt(a, b) ? a : b; }
+__device__ __forceinline__ float df_float(df a) { return fadd(a.hi, a.lo); }
+
+// A ray as the march uses it: origin o, unit direction d = dh + dl (double-float),
+// the domain interval [t, t_out) (double-float).
+struct Ray {
+    float o[3], dh[3], dl[3];
+    df t, t_out;
+};
+
+// Pinhole ray direction (unnormalised, double-float) through the centre of pixel
+// (col, row); OpenCV axes (x right, y down, z forward); origin = camera position.
+__device__ __forceinline__ void camera_ray_df(const ngprt_camera& c, int col, int row, float o[3], df d[3]) {
+    const df px = df_div(df_two_sum(fadd((float)col, 0.5f), -c.cx), df{c.fx, 0.0f});
+    const df py = df_div(df_two_sum(fadd((float)row, 0.5f), -c.cy), df{c.fy, 0.0f});
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
-        d[r] = fadd(fadd(fmul(c.c2w[4 * r + 0], px), fmul(c.c2w[4 * r + 1], py)), c.c2w[4 * r + 2]);
+        d[r] = df_add_f(df_add(df_mul_f(px, c.c2w[4 * r + 0]), df_mul_f(py, c.c2w[4 * r + 1])), c.c2w[4 * r + 2]);
         o[r] = c.c2w[4 * r + 3];
     }
+}
+
+// The same ray in plain floats (the learned proposal's input).
+__device__ __forceinline__ void camera_ray(const ngprt_camera& c, int col, int row, float o[3], float d[3]) {
+    df dd[3];
+    camera_ray_df(c, col, row, o, dd);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) d[r] = df_float(dd[r]);
 }
 
 __device__ __forceinline__ float dot3(const float a[3], const float b[3]) {
     return fadd(fadd(fmul(a[0], b[0]), fmul(a[1], b[1])), fmul(a[2], b[2]));
 }
 
-// Normalise d and find the parametric interval [t, t_out) inside the domain
-// (bounded: the box [-1,1]^3; unbounded: the world ball of radius r_far), then
-// clip it to [t_min, inf) and to the optional interval [t_lo, t_hi].
-__device__ __forceinline__ void normalize_dir(float d[3]) {
-    float nn = fsqrt(dot3(d, d));
-    d[0] = fdiv(d[0], nn);
-    d[1] = fdiv(d[1], nn);
-    d[2] = fdiv(d[2], nn);
-}
-
-__device__ __forceinline__ bool ray_interval(int bounded, const float o[3], float d[3], float t_min, float r_far,
-                                             float t_lo, float t_hi, float& t, float& t_out) {
-    normalize_dir(d);
-    float t_in;
+// Normalise the direction and find the parametric interval [t, t_out) inside the
+// domain (bounded: the box [-1,1]^3; unbounded: the world ball of radius r_far),
+// clipped to [t_min, inf) and to the optional interval [t_lo, t_hi]; all in
+// double-float.  False when the interval is empty.
+__device__ __forceinline__ bool ray_interval(int bounded, const float o[3], const df din[3], float t_min, float r_far,
+                                             float t_lo, float t_hi, Ray& ry) {
+    const df n2 = df_add(df_add(df_mul(din[0], din[0]), df_mul(din[1], din[1])), df_mul(din[2], din[2]));
+    const df nn = df_sqrt(n2);
+    df d[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        d[a] = df_div(din[a], nn);
+        ry.o[a] = o[a];
+        ry.dh[a] = d[a].hi;
+        ry.dl[a] = d[a].lo;
+    }
+    df t_in, t_out;
     if (bounded) {
-        float lo[3], hi[3];
+        t_in = df{-INFINITY, 0.0f};
+        t_out = df{INFINITY, 0.0f};
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            float ia = fdiv(1.0f, d[a]);
-            float t0 = fmul(fsub(-1.0f, o[a]), ia), t1 = fmul(fsub(1.0f, o[a]), ia);
-            lo[a] = fminf(t0, t1);
-            hi[a] = fmaxf(t0, t1);
+            if (d[a].hi == 0.0f) {
+                if (!(o[a] >= -1.0f && o[a] <= 1.0f)) return false;
+                continue;
+            }
+            const df t0 = df_div(df_two_sum(-1.0f, -o[a]), d[a]);
+            const df t1 = df_div(df_two_sum(1.0f, -o[a]), d[a]);
+            t_in = df_max(t_in, df_min(t0, t1));
+            t_out = df_min(t_out, df_max(t0, t1));
         }
-        t_in = fmaxf(fmaxf(lo[0], lo[1]), lo[2]);
-        t_out = fminf(fminf(hi[0], hi[1]), hi[2]);
     } else {
-        float b = dot3(o, d);
-        float c = fsub(dot3(o, o), fmul(r_far, r_far));
-        float disc = fsub(fmul(b, b), c);
-        if (!(disc >= 0.0f)) return false;
-        float sq = fsqrt(disc);
-        t_in = fsub(-b, sq);
-        t_out = fadd(-b, sq);
+        // |o + t d| = r_far
+        const df b = df_add(df_add(df_mul_f(d[0], o[0]), df_mul_f(d[1], o[1])), df_mul_f(d[2], o[2]));
+        const df c = df_add(df_add(df_add(df_prod(o[0], o[0]), df_prod(o[1], o[1])), df_prod(o[2], o[2])),
+                            df_neg(df_prod(r_far, r_far)));
+        const df disc = df_add(df_mul(b, b), df_neg(c));
+        if (!(disc.hi >= 0.0f)) return false;
+        const df sq = df_sqrt(disc);
+        t_in = df_add(df_neg(b), df_neg(sq));
+        t_out = df_add(df_neg(b), sq);
     }
-    t = fmaxf(t_in, t_min);
-    t = fmaxf(t, t_lo);
-    t_out = fminf(t_out, t_hi);
-    return t < t_out;
+    ry.t = df_max(df_max(t_in, df{t_min, 0.0f}), df{t_lo, 0.0f});
+    ry.t_out = df_min(t_out, df{t_hi, 0.0f});
+    return df_lt(ry.t, ry.t_out);
 }
 
-// Position at t: world x, contracted y (mip-NeRF 360 when unbounded), unit-cube u.
-__device__ __forceinline__ void march_point(int bounded, const float o[3], const float d[3], float t, float x[3],
-                                            float y[3], float u[3], float& r) {
+// World position x = o + t d at the double-float parameter t (products by
+// two-product, one final rounding of the correction), its radius r, the
+// contracted point y (mip-NeRF 360 when unbounded) and the unit-cube coordinate u.
+__device__ __forceinline__ void march_point(int bounded, const Ray& ry, df t, float x[3], float y[3], float u[3],
+                                            float& r) {
 #pragma unroll
-    for (int a = 0; a < 3; ++a) x[a] = fadd(o[a], fmul(t, d[a]));
+    for (int a = 0; a < 3; ++a) {
+        const df q = df_prod(t.hi, ry.dh[a]);
+        const df s = df_two_sum(ry.o[a], q.hi);
+        const float corr = fadd(s.lo, fadd(q.lo, __fmaf_rn(t.hi, ry.dl[a], fmul(t.lo, ry.dh[a]))));
+        x[a] = fadd(s.hi, corr);
+    }
     r = fsqrt(dot3(x, x));
     if (!bounded && r > 1.0f) {
         const float ir = fdiv(1.0f, r);
@@ -156,16 +245,19 @@ __device__ __forceinline__ int occ_vox(float u, int Rk) {
     return (int)c;
 }
 
-// Grid cell of a vertex grid of N per axis: base chosen in FP32, clamped to
-// [0, N-2]; the weight w = u (N-1) - base carries the product's rounding error
-// back in (an exact FMA residual) so it is accurate to ~1 ulp of w.
+// Grid cell of a vertex grid of N per axis: base = floor(u (N-1)) of the exact
+// product (the rounded product pf and its exact FMA residual e; pf can round up onto
+// an integer only when e < 0), clamped to [0, N-2]; the weight w = u (N-1) - base
+// carries the residual back in, so it is accurate to ~1 ulp of w.
 __device__ __forceinline__ void grid_cell(float u, int N, int& base, float& w) {
     const float nm1 = (float)(N - 1);
-    float pf = fmul(u, nm1);
+    const float pf = fmul(u, nm1);
+    const float e = __fmaf_rn(u, nm1, -pf);
     float bf = floorf(pf);
+    if (bf == pf && e < 0.0f) bf = fsub(bf, 1.0f);
     bf = fminf(fmaxf(bf, 0.0f), (float)(N - 2));
     base = (int)bf;
-    w = fadd(fsub(pf, bf), __fmaf_rn(u, nm1, -pf));
+    w = fadd(fsub(pf, bf), e);
 }
 
 // Row of the coarse vertex at the base corner of cell b and the row strides of

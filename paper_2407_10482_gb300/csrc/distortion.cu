@@ -106,15 +106,15 @@ template <int L>
 __global__ void __launch_bounds__(128) distortion_backward_kernel(const __grid_constant__ DistParams p) {
     extern __shared__ float gate_smem[];
     int64_t ray;
-    float o[3], d[3], t, t_out;
+    Ray ry;
     bool hit;
-    if (!ray_setup(p.m, ray, o, d, t, t_out, hit)) return;
+    if (!ray_setup(p.m, ray, ry, hit)) return;
     if (!hit) return;
     const float4 ds = reinterpret_cast<const float4*>(p.dist_state)[ray];
     DistBwdSampler<L> smp{p.m.g, p.m.opts.attn_mode, p.m.opts.t_term, gate_smem + threadIdx.x, 1.0f, 0.0f, 0.0f,
                           0.0f, ds.y, ds.z, 2.0f * ds.x, p.scale, p.g_tables, p.g_coarse};
     int n_march = 0, n_samp = 0;
-    march_loop(p.m, o, d, t, t_out, smp, n_march, n_samp);
+    march_loop(p.m, ry, smp, n_march, n_samp);
 }
 
 template <int L>

@@ -35,16 +35,16 @@ template <int L, int AGG>
 __global__ void __launch_bounds__(128) distortion_kernel(const __grid_constant__ DistParams p) {
     extern __shared__ float gate_smem[];
     int64_t ray = 0;
-    float o[3], d[3], t, t_out;
+    Ray ry;
     bool hit = false;
-    const bool has_ray = ray_setup(p.m, ray, o, d, t, t_out, hit);
+    const bool has_ray = ray_setup(p.m, ray, ry, hit);
     float Ld = 0.0f;
     if (has_ray) {
         DistSampler<L, AGG> smp{ForwardSampler<L, NGPRT_F32, AGG>(p.m.g, p.m.opts.attn_mode, p.m.opts.t_term,
                                                                   gate_smem + threadIdx.x),
                                 0.0f, 0.0f, 0.0f, 0.0f};
         int n_march = 0, n_samp = 0;
-        if (hit) march_loop(p.m, o, d, t, t_out, smp, n_march, n_samp);
+        if (hit) march_loop(p.m, ry, smp, n_march, n_samp);
         Ld = smp.Lp + smp.Ls;
         reinterpret_cast<float4*>(p.dist_state)[ray] = make_float4(Ld, smp.W, smp.S, 0.0f);
     }

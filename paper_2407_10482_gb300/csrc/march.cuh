@@ -48,8 +48,9 @@ struct MarchParams {
     float fb_thr;           // re-march a ray when a_hat - A(interval) > fb_thr
 };
 
-// Ray of this thread (false if the lane has none).
-__device__ __forceinline__ bool thread_ray(const MarchParams& p, int64_t& ray, float o[3], float d[3]) {
+// Ray of this thread (false if the lane has none): origin and unnormalised
+// double-float direction.
+__device__ __forceinline__ bool thread_ray(const MarchParams& p, int64_t& ray, float o[3], df d[3]) {
     if (p.mode == 0) {
         const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
         const int lane = threadIdx.x & 31;
@@ -60,7 +61,7 @@ __device__ __forceinline__ bool thread_ray(const MarchParams& p, int64_t& ray, f
         const int row = (tile / p.tiles_x) * kTileH + (lane / kTileW);
         if (col >= p.W || row >= p.H) return false;
         ray = view * (int64_t)p.W * p.H + (int64_t)row * p.W + col;
-        camera_ray(p.cams.c[view], col, row, o, d);
+        camera_ray_df(p.cams.c[view], col, row, o, d);
         return true;
     }
     ray = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -72,24 +73,24 @@ __device__ __forceinline__ bool thread_ray(const MarchParams& p, int64_t& ray, f
         int64_t view = id / wh;
         if (view >= p.n_cams) view = p.n_cams - 1;
         const int64_t rem = id - (id / wh) * wh;
-        camera_ray(p.cams.c[view], (int)(rem % p.W), (int)(rem / p.W), o, d);
+        camera_ray_df(p.cams.c[view], (int)(rem % p.W), (int)(rem / p.W), o, d);
     } else {
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             o[a] = p.rays_o[3 * ray + a];
-            d[a] = p.rays_d[3 * ray + a];
+            d[a] = df{p.rays_d[3 * ray + a], 0.0f};
         }
     }
     return true;
 }
 
-// Origin and (unnormalised) direction of ray `ray` of the batch, by its index.
-__device__ __forceinline__ void ray_of(const MarchParams& p, int64_t ray, float o[3], float d[3]) {
+// Origin and (unnormalised) double-float direction of ray `ray` of the batch.
+__device__ __forceinline__ void ray_of(const MarchParams& p, int64_t ray, float o[3], df d[3]) {
     if (p.mode == 2) {
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             o[a] = p.rays_o[3 * ray + a];
-            d[a] = p.rays_d[3 * ray + a];
+            d[a] = df{p.rays_d[3 * ray + a], 0.0f};
         }
         return;
     }
@@ -99,7 +100,7 @@ __device__ __forceinline__ void ray_of(const MarchParams& p, int64_t ray, float 
     int64_t view = id / wh;
     const int64_t rem = id - view * wh;
     if (view >= p.n_cams) view = p.n_cams - 1;
-    camera_ray(p.cams.c[view], (int)(rem % p.W), (int)(rem / p.W), o, d);
+    camera_ray_df(p.cams.c[view], (int)(rem % p.W), (int)(rem / p.W), o, d);
 }
 
 __device__ __forceinline__ float corner_w(const float w[3], int c) {
@@ -261,7 +262,6 @@ __device__ __forceinline__ void sample_features(const Grid& g, const float u[3],
             for (int ch = 0; ch < 4; ++ch) fl[ch] = __half22float2(h[ch]);
         } else {
             float e[8][8];
-#pragma unroll
             // FP32: large levels bypass L1 allocation (16-bit entries share sectors
             // and gain from L1: they keep the default path)
             const bool na = DT == NGPRT_F32 && ((g.na_mask >> l) & 1u);
@@ -373,29 +373,102 @@ __device__ __forceinline__ float dist_step(int bounded, const float x[3], const 
 }
 
 // Position of a ray's march between calls: the current point t, the domain end,
-// the lattice origin and index (lattice_snap), and the counters.
+// the lattice origin (all double-float) and index (lattice_snap), and the counters.
 struct MarchState {
-    float t, t_out, t_start;
+    df t, t_out, t_start;
     int lat_k, n_march, n_samp;
 };
 
-__device__ __forceinline__ MarchState march_state(float t, float t_out) {
+__device__ __forceinline__ MarchState march_state(const Ray& ry) {
     MarchState st;
-    st.t = t;
-    st.t_out = t_out;
-    st.t_start = t;
+    st.t = ry.t;
+    st.t_out = ry.t_out;
+    st.t_start = ry.t;
     st.lat_k = 0;
     st.n_march = 0;
     st.n_samp = 0;
     return st;
 }
 
+// Image speed J(x) d of the contraction along the ray (r = |x| > 1):
+// J d = k d + m x with k = (2 - 1/r)/r and m = (x.d) 2 (1 - r) / r^4.
+__device__ __forceinline__ void contracted_dir(const float x[3], const float d[3], float r, float v[3]) {
+    const float ir = fdiv(1.0f, r);
+    const float kk = fmul(fsub(2.0f, ir), ir);
+    const float px = dot3(x, d);
+    const float ir2 = fmul(ir, ir);
+    const float m = fmul(fmul(px, fmul(2.0f, fsub(1.0f, r))), fmul(ir2, ir2));
+#pragma unroll
+    for (int a = 0; a < 3; ++a) v[a] = fadd(fmul(kk, d[a]), fmul(m, x[a]));
+}
+
+// Fraction of a finest occupancy voxel that an empty-space step carries the image
+// past the exit face of its voxel.
+constexpr float kEmptyGuard = 0.02f;
+
+// s_O (Sec. 3.3): the step that leaves empty voxel ev of resolution Rk.  The image
+// of the ray is aimed at the plane kEmptyGuard finest voxels (side 2B / R_O) beyond
+// the voxel's exit face: along the image's local direction v = J(x) d first, which
+// picks the exit axis; beyond the unit ball the image curves, and one Newton step on
+// that axis, from the image's position and direction at the first estimate (the
+// correction clamped to half of it), corrects the length.
+__device__ __forceinline__ float empty_step(int bounded, const float x[3], const float y[3], const float d[3],
+                                            float r, const int ev[3], int Rk, int R_O) {
+    const float B = bounded ? 1.0f : 2.0f;
+    const bool curved = !bounded && r > 1.0f;
+    float v[3];
+    if (curved) contracted_dir(x, d, r, v);
+    else {
+        v[0] = d[0]; v[1] = d[1]; v[2] = d[2];
+    }
+    const float vk = fdiv(2.0f * B, (float)Rk);
+    const float g = fmul(kEmptyGuard, fdiv(2.0f * B, (float)R_O));
+    float s0 = INFINITY, target = 0.0f;
+    int ax = -1;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float lo = fsub(fmul((float)ev[a], vk), B);
+        float plane;
+        if (v[a] > 0.0f) plane = fadd(fadd(lo, vk), g);
+        else if (v[a] < 0.0f) plane = fsub(lo, g);
+        else continue;
+        const float ta = fdiv(fsub(plane, y[a]), v[a]);
+        if (ta < s0) {
+            s0 = ta;
+            ax = a;
+            target = plane;
+        }
+    }
+    if (ax < 0) return INFINITY;
+    s0 = fmaxf(s0, 0.0f);
+    if (!curved) return s0;
+    float x1[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) x1[a] = fadd(x[a], fmul(s0, d[a]));
+    const float r1 = fsqrt(dot3(x1, x1));
+    float y1, v1;
+    if (r1 > 1.0f) {
+        float vv[3];
+        contracted_dir(x1, d, r1, vv);
+        const float ir = fdiv(1.0f, r1);
+        y1 = fmul(x1[ax], fmul(fsub(2.0f, ir), ir));
+        v1 = vv[ax];
+    } else {
+        y1 = x1[ax];
+        v1 = d[ax];
+    }
+    if (!(fmul(v1, v[ax]) > 0.0f)) return s0;
+    const float c = fdiv(fsub(target, y1), v1);
+    const float h = fmul(0.5f, s0);
+    return fadd(s0, fminf(fmaxf(c, -h), h));
+}
+
 // Advance from st.t through empty space to the next occupied marching point.
 // Returns true with u (unit-cube position), delta (clipped sample step) and dt (the
 // sample step) of the point at st.t, or false when the ray is exhausted (t_out or a
 // cap reached).
-__device__ __forceinline__ bool march_advance(const MarchParams& p, const float o[3], const float d[3],
-                                              MarchState& st, float u[3], float& delta, float& dt) {
+__device__ __forceinline__ bool march_advance(const MarchParams& p, const Ray& ry, MarchState& st, float u[3],
+                                              float& delta, float& dt) {
     const ngprt_render_opts& op = p.opts;
     const int bounded = p.g.bounded;
     const float B = bounded ? 1.0f : 2.0f;
@@ -404,11 +477,10 @@ __device__ __forceinline__ bool march_advance(const MarchParams& p, const float 
     const int R_G = p.occ.R_G;
     const float vG = fdiv(2.0f * B, (float)R_G);
     const bool snap = op.lattice_snap && bounded;
-    float t = st.t;
-    while (t < st.t_out && st.n_march < op.max_march && st.n_samp < op.max_samples) {
+    while (df_lt(st.t, st.t_out) && st.n_march < op.max_march && st.n_samp < op.max_samples) {
         ++st.n_march;
         float x[3], y[3], r;
-        march_point(bounded, o, d, t, x, y, u, r);
+        march_point(bounded, ry, st.t, x, y, u, r);
         int empty_level = -1, ev[3] = {0, 0, 0};
         for (int k = p.occ.n_levels - 1; k >= 0; --k) {
             const int Rk = R_O >> k;
@@ -423,55 +495,29 @@ __device__ __forceinline__ bool march_advance(const MarchParams& p, const float 
         }
         if (empty_level < 0) {
             dt = bounded ? dt0 : fmul(dt0, fmaxf(1.0f, r));
-            delta = fminf(dt, fsub(st.t_out, t));
-            st.t = t;
+            delta = fminf(dt, fadd(fsub(st.t_out.hi, st.t.hi), fsub(st.t_out.lo, st.t.lo)));
             return true;
         }
-        // s_O: leave the empty voxel along the ray's direction in grid space
-        const int Rk = R_O >> empty_level;
-        const float vk = fdiv(2.0f * B, (float)Rk);
-        float v[3];
-        if (bounded || !(r > 1.0f)) {
-            v[0] = d[0]; v[1] = d[1]; v[2] = d[2];
-        } else {
-            // J(x) d = k d + m x, k = (2 - 1/r)/r, m = (x.d) 2 (1 - r) / r^4
-            const float ir = fdiv(1.0f, r);
-            const float kk = fmul(fsub(2.0f, ir), ir);
-            const float px = dot3(x, d);
-            const float ir2 = fmul(ir, ir);
-            const float m = fmul(fmul(px, fmul(2.0f, fsub(1.0f, r))), fmul(ir2, ir2));
-#pragma unroll
-            for (int a = 0; a < 3; ++a) v[a] = fadd(fmul(kk, d[a]), fmul(m, x[a]));
-        }
-        float se = INFINITY;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const float lo = fsub(fmul((float)ev[a], vk), B);
-            const float hi = fadd(lo, vk);
-            float ta = INFINITY;
-            if (v[a] > 0.0f) ta = fdiv(fsub(hi, y[a]), v[a]);
-            else if (v[a] < 0.0f) ta = fdiv(fsub(lo, y[a]), v[a]);
-            se = fminf(se, ta);
-        }
-        const float s_O = fadd(fmaxf(se, 0.0f), fmul(1e-5f, fmaxf(1.0f, t)));
+        const float s_O = empty_step(bounded, x, y, ry.dh, r, ev, R_O >> empty_level, R_O);
         float step = s_O;
         if (op.use_dist && p.occ.dist && empty_level > p.occ.g_shift) {
             const int g0 = occ_vox(u[0], R_G), g1 = occ_vox(u[1], R_G), g2 = occ_vox(u[2], R_G);
             const int gv = __ldg(p.occ.dist + ((size_t)g0 + (size_t)R_G * ((size_t)g1 + (size_t)R_G * g2)));
             if (gv > 0) {
-                const float sg = dist_step(bounded, x, d, r, fmul((float)gv, vG));
+                const float sg = dist_step(bounded, x, ry.dh, r, fmul((float)gv, vG));
                 step = op.dist_rule == 1 ? fmaxf(sg, s_O) : sg;
             }
         }
         if (snap) {
-            const int kk = (int)floorf(fdiv(fsub(fadd(t, step), st.t_start), dt0));
+            // the first lattice point t_start + k dt0 at or beyond t + step
+            const df rel = df_add(df_add_f(st.t, step), df_neg(st.t_start));
+            const int kk = (int)floorf(fdiv(df_float(rel), dt0));
             st.lat_k = kk > st.lat_k + 1 ? kk : st.lat_k + 1;
-            t = fadd(st.t_start, fmul((float)st.lat_k, dt0));
+            st.t = df_add(st.t_start, df_prod((float)st.lat_k, dt0));
         } else {
-            t = fadd(t, step);
+            st.t = df_add_f(st.t, step);
         }
     }
-    st.t = t;
     return false;
 }
 
@@ -480,9 +526,9 @@ __device__ __forceinline__ void march_after_sample(const MarchParams& p, MarchSt
     ++st.n_samp;
     if (p.opts.lattice_snap && p.g.bounded) {
         st.lat_k += 1;
-        st.t = fadd(st.t_start, fmul((float)st.lat_k, fmul(p.opts.step_base, p.opts.step_gamma)));
+        st.t = df_add(st.t_start, df_prod((float)st.lat_k, fmul(p.opts.step_base, p.opts.step_gamma)));
     } else {
-        st.t = fadd(st.t, dt);
+        st.t = df_add_f(st.t, dt);
     }
 }
 
@@ -491,11 +537,10 @@ __device__ __forceinline__ void march_after_sample(const MarchParams& p, MarchSt
 // first advance through empty space each to its own next sample, then sample
 // together.
 template <class Sampler>
-__device__ __forceinline__ void march_loop_from(const MarchParams& p, const float o[3], const float d[3],
-                                                MarchState& st, Sampler& smp) {
+__device__ __forceinline__ void march_loop_from(const MarchParams& p, const Ray& ry, MarchState& st, Sampler& smp) {
     float u[3], delta, dt;
-    while (march_advance(p, o, d, st, u, delta, dt)) {
-        const bool stop = smp.sample(u, st.t, delta);
+    while (march_advance(p, ry, st, u, delta, dt)) {
+        const bool stop = smp.sample(u, df_float(st.t), delta);
         if (stop) {
             ++st.n_samp;
             break;
@@ -505,10 +550,10 @@ __device__ __forceinline__ void march_loop_from(const MarchParams& p, const floa
 }
 
 template <class Sampler>
-__device__ __forceinline__ void march_loop(const MarchParams& p, const float o[3], const float d[3], float t,
-                                           float t_out, Sampler& smp, int& n_march, int& n_samp) {
-    MarchState st = march_state(t, t_out);
-    march_loop_from(p, o, d, st, smp);
+__device__ __forceinline__ void march_loop(const MarchParams& p, const Ray& ry, Sampler& smp, int& n_march,
+                                           int& n_samp) {
+    MarchState st = march_state(ry);
+    march_loop_from(p, ry, st, smp);
     n_march = st.n_march;
     n_samp = st.n_samp;
 }
@@ -565,16 +610,18 @@ struct ForwardSampler {
     }
 };
 
-// Ray set-up shared by both passes: this thread's ray, its domain interval.
-__device__ __forceinline__ bool ray_setup(const MarchParams& p, int64_t& ray, float o[3], float d[3], float& t,
-                                          float& t_out, bool& hit) {
+// Ray set-up shared by every pass: this thread's ray and its domain interval
+// (false if the lane has no ray; hit = the interval is not empty).
+__device__ __forceinline__ bool ray_setup(const MarchParams& p, int64_t& ray, Ray& ry, bool& hit) {
+    float o[3];
+    df d[3];
     if (!thread_ray(p, ray, o, d)) return false;
     float t_lo = -INFINITY, t_hi = INFINITY;
     if (p.t_interval && !p.fb_a_hat) {
         t_lo = p.t_interval[2 * ray];
         t_hi = p.t_interval[2 * ray + 1];
     }
-    hit = ray_interval(p.g.bounded, o, d, p.opts.t_min, p.opts.r_far, t_lo, t_hi, t, t_out);
+    hit = ray_interval(p.g.bounded, o, d, p.opts.t_min, p.opts.r_far, t_lo, t_hi, ry);
     return true;
 }
 
@@ -597,10 +644,10 @@ template <int L, int DT, int AGG>
 __global__ void __launch_bounds__(128, march_min_blocks<L, DT, AGG>())
     march_kernel(const __grid_constant__ MarchParams p) {
     int64_t ray;
-    float o[3], d[3], t, t_out;
+    Ray ry;
     bool hit;
     extern __shared__ float gate_smem[];
-    if (!ray_setup(p, ray, o, d, t, t_out, hit)) return;
+    if (!ray_setup(p, ray, ry, hit)) return;
     float* s = p.state + ray * NGPRT_STATE_FLOATS;
     if (p.fb_a_hat) {
         // fallback pass: keep the interval result unless it missed predicted opacity
@@ -610,10 +657,10 @@ __global__ void __launch_bounds__(128, march_min_blocks<L, DT, AGG>())
     }
     ForwardSampler<L, DT, AGG> smp(p.g, p.opts.attn_mode, p.opts.t_term, gate_smem + threadIdx.x);
     int n_march = 0, n_samp = 0;
-    if (hit) march_loop(p, o, d, t, t_out, smp, n_march, n_samp);
+    if (hit) march_loop(p, ry, smp, n_march, n_samp);
     reinterpret_cast<float4*>(s)[0] = make_float4(smp.Cd[0], smp.Cd[1], smp.Cd[2], smp.F[0]);
     reinterpret_cast<float4*>(s)[1] = make_float4(smp.F[1], smp.F[2], smp.F[3], smp.A);
-    reinterpret_cast<float4*>(s)[2] = make_float4(smp.depth, d[0], d[1], d[2]);
+    reinterpret_cast<float4*>(s)[2] = make_float4(smp.depth, ry.dh[0], ry.dh[1], ry.dh[2]);
     if (p.stats) {
         int2* st = reinterpret_cast<int2*>(p.stats) + ray;
         if (p.fb_a_hat) {

@@ -238,11 +238,19 @@ __global__ void __launch_bounds__(128) mlp_tc_kernel(const __grid_constant__ Mlp
         __syncthreads();
         fence_after();
     }
-    if (!ok && tid == 0) atomicExch(&g_tc_error, 1);
+    // An expired wait leaves the MMA it waited for possibly in flight, still writing
+    // TMEM and reading the operand tiles: wait for that same phase once more (a
+    // second bounded wait) before the tensor memory and shared memory are released.
+    // If the MMA never completes the block keeps its TMEM (the dealloc would race
+    // the MMA) and flags the context as suspect (2): the caller should stop using
+    // the tensor-core forms.
+    bool drained = true;
+    if (!ok) drained = __syncthreads_and(mbar_wait(mbar, phase ^ 1u, 1 << 22)) != 0;
+    if (!ok && tid == 0) atomicMax(&g_tc_error, drained ? 1 : 2);
     fence_before();
     __syncthreads();
     fence_after();
-    if (warp == 0)
+    if (warp == 0 && drained)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
 }
 
@@ -321,7 +329,13 @@ extern "C" int32_t ngprt_sync_status(void* stream) {
     if (v) {
         const int zero = 0;
         cudaMemcpyToSymbol(ngprt::g_tc_error, &zero, sizeof zero);  // reported once
-        ngprt::set_error("ngprt_sync_status: a tensor-core MLP gave up waiting for its MMAs; its rays were not shaded");
+        if (v >= 2)
+            ngprt::set_error("ngprt_sync_status: a tensor-core MLP gave up waiting for its MMAs and they did not "
+                             "complete: its tensor memory was not released, so stop using the tensor-core forms in "
+                             "this context");
+        else
+            ngprt::set_error("ngprt_sync_status: a tensor-core MLP gave up waiting for its MMAs; its rays were not "
+                             "shaded");
         return NGPRT_ERR_TIMEOUT;
     }
     return NGPRT_OK;

@@ -57,14 +57,14 @@ template <int L, int DT, int AGG>
 __global__ void __launch_bounds__(128, march_min_blocks<L, DT, AGG>())
     visibility_kernel(const __grid_constant__ MarchParams p, float w_thr, int32_t R, uint8_t* vis) {
     int64_t ray;
-    float o[3], d[3], t, t_out;
+    Ray ry;
     bool hit;
     extern __shared__ float gate_smem[];
-    if (!ray_setup(p, ray, o, d, t, t_out, hit)) return;
+    if (!ray_setup(p, ray, ry, hit)) return;
     VisibilitySampler<L, DT, AGG> smp{
         ForwardSampler<L, DT, AGG>(p.g, p.opts.attn_mode, p.opts.t_term, gate_smem + threadIdx.x), w_thr, R, vis};
     int n_march = 0, n_samp = 0;
-    if (hit) march_loop(p, o, d, t, t_out, smp, n_march, n_samp);
+    if (hit) march_loop(p, ry, smp, n_march, n_samp);
 }
 
 template <int L, int AGG>

@@ -38,7 +38,10 @@ __device__ __forceinline__ float warp_sum(float v) {
 // e = (o / in_scale, d / |d|) of this thread's ray; false when the lane has none.
 __device__ __forceinline__ bool prop_input(const PropParams& p, int64_t& ray, float e[kPIn]) {
     float o[3], d[3];
-    if (!thread_ray(p.m, ray, o, d)) return false;
+    df dd[3];
+    if (!thread_ray(p.m, ray, o, dd)) return false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) d[a] = df_float(dd[a]);
     const float n = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {

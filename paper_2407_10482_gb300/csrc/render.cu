@@ -42,14 +42,14 @@ __global__ void __launch_bounds__(128, march_min_blocks<L, DT>()) targets_kernel
                                                                                 float* targets) {
     extern __shared__ float gate_smem[];
     int64_t ray;
-    float o[3], d[3], t, t_out;
+    Ray ry;
     bool hit;
-    if (!ray_setup(p, ray, o, d, t, t_out, hit)) return;
+    if (!ray_setup(p, ray, ry, hit)) return;
     const float A = p.state[ray * NGPRT_STATE_FLOATS + 7];
     TargetSampler<L, DT> smp{ForwardSampler<L, DT>(p.g, p.opts.attn_mode, p.opts.t_term, gate_smem + threadIdx.x), A,
                              0.0f, 0.0f, false, false};
     int n_march = 0, n_samp = 0;
-    if (hit) march_loop(p, o, d, t, t_out, smp, n_march, n_samp);
+    if (hit) march_loop(p, ry, smp, n_march, n_samp);
     if (n_samp == 0) smp.t_far = 0.0f;
     targets[3 * ray] = smp.t_near;
     targets[3 * ray + 1] = smp.t_far;
@@ -339,8 +339,6 @@ int32_t check_opts(const ngprt_render_opts* o, const char* fn) {
 using namespace ngprt;
 
 namespace ngprt {
-size_t wavefront_bytes(int64_t n);
-int32_t run_wavefront(int L, int dt, const MarchParams& m, dim3 grid, void* ws, cudaStream_t st);
 static size_t state_bytes(int64_t n) { return ((size_t)n * NGPRT_STATE_FLOATS * sizeof(float) + 255) / 256 * 256; }
 }  // namespace ngprt
 
@@ -348,12 +346,6 @@ extern "C" size_t ngprt_render_workspace_bytes(const ngprt_scene* scene, int64_t
     (void)scene;
     if (n_rays < 0) return 0;
     return state_bytes(n_rays) + 256;
-}
-
-extern "C" size_t ngprt_wavefront_workspace_bytes(const ngprt_scene* scene, int64_t n_rays) {
-    (void)scene;
-    if (n_rays < 0) return 0;
-    return state_bytes(n_rays) + wavefront_bytes(n_rays) + 256;
 }
 
 extern "C" int32_t ngprt_render(const ngprt_scene* scene, const ngprt_occ* occ, const ngprt_camera* cams,
@@ -378,13 +370,10 @@ extern "C" int32_t ngprt_render(const ngprt_scene* scene, const ngprt_occ* occ, 
     dim3 grid;
     if ((rc = setup_rays(p, cams, n_cams, pixel_ids, rays_o, rays_d, n_rays, grid, fn)) != NGPRT_OK) return rc;
     if (n_rays == 0) return NGPRT_OK;
-    // Engine: the wavefront rounds when the workspace holds their scratch, else the
-    // fused march kernel (same results); the state goes to ray_state or the workspace.
+    // the per-ray state goes to ray_state, or else to the workspace
     float* state = ray_state;
     char* ws = static_cast<char*>(workspace);
     const size_t need_state = ray_state ? 0 : state_bytes(n_rays);
-    const bool wavefront = ws && ws_bytes >= need_state + wavefront_bytes(n_rays) &&
-                           scene->aggregation == NGPRT_AGG_SEPARATE_V;
     if (!state) {
         if (!ws || ws_bytes < need_state) {
             set_error("%s: workspace %zu bytes < %zu needed", fn, ws_bytes, ngprt_render_workspace_bytes(scene, n_rays));
@@ -399,12 +388,8 @@ extern "C" int32_t ngprt_render(const ngprt_scene* scene, const ngprt_occ* occ, 
     p.state = state;
     p.stats = ray_stats;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (wavefront) {
-        if ((rc = run_wavefront(scene->L, scene->table_dtype, p, grid, ws + need_state, st)) != NGPRT_OK) return rc;
-    } else {
-        if ((rc = launch_march_any(scene->L, scene->table_dtype, scene->aggregation, p, grid, st)) != NGPRT_OK)
-            return rc;
-    }
+    if ((rc = launch_march_any(scene->L, scene->table_dtype, scene->aggregation, p, grid, st)) != NGPRT_OK)
+        return rc;
     if (!rgb) return cuda_status(fn);
     if ((rc = launch_shade(scene, state, n_rays, opts->bg, rgb, depth, opacity, st, fn)) != NGPRT_OK) return rc;
     return cuda_status(fn);

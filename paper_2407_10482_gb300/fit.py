@@ -118,12 +118,16 @@ def _lr_factor(step: int, fc: FitConfig) -> float:
 
 
 def fit(scene: ng.DeviceScene, occ: ng.DeviceOcc, opts, cams: np.ndarray, W: int, H: int,
-        targets: torch.Tensor, fc: FitConfig = FitConfig(), log_every: int = 0, stream=None):
+        targets: torch.Tensor, fc: FitConfig = FitConfig(), log_every: int = 0, stream=None,
+        refine_at=(), refine=None):
     """Fit ``scene`` (FP32 tables, coarse grid, MLP and the aggregation form's own
     parameters: constant gate logits or the tiny MLP's weights; updated in place) to
     the images ``targets`` [n_views * H * W, 3] of the cameras ``cams``.
+    After each step in ``refine_at`` the occupancy becomes ``refine(step, occ)`` (a
+    DeviceOcc built from the model so far).
     Returns the loss history [(step, loss)] and the wall time in seconds; with
-    ``autotune`` the final gamma is left in ``fit.last_gamma``."""
+    ``autotune`` the final gamma is left in ``fit.last_gamma``, and the occupancy the
+    fit ended with in ``fit.last_occ``."""
     from dataclasses import replace
     dev = scene.tables.device
     rend = ng.Renderer(scene, occ, device=dev)
@@ -195,6 +199,10 @@ def fit(scene: ng.DeviceScene, occ: ng.DeviceOcc, opts, cams: np.ndarray, W: int
             ng.ngprt_adam_step(p, g, m, v, lr * f, fc.beta1, fc.beta2, fc.eps, step, True, stream=stream)
         if logging:
             hist.append((step, float(loss.item())))
+        if refine is not None and step in refine_at:
+            occ = refine(step, occ)
+            rend = ng.Renderer(scene, occ, device=dev)
     torch.cuda.synchronize(dev)
     fit.last_gamma = gamma
+    fit.last_occ = occ
     return hist, time.perf_counter() - t0

@@ -100,30 +100,41 @@ def render_rays(blobs: dict, o: torch.Tensor, d: torch.Tensor, shell: bool, bg=(
     k = min(top_k, mu.shape[0])
     amp_k, idx = torch.topk(amp, k, dim=1)
     tk_k = torch.gather(tk, 1, idx)
-    inv_k = 1.0 / (math.sqrt(2.0) * s[idx])
+    s_k = s[idx]
+    inv_k = 1.0 / (math.sqrt(2.0) * s_k)
     col_k = col[idx]                                         # [n, k, 3]
-    # blob segment: the ball holding every blob out to 6 standard deviations
-    r_b = float(np.max(np.linalg.norm(blobs["mu"], axis=1) + 6.0 * blobs["std"]))
-    ta, tb = _sphere_interval(o, d, r_b)
+    # blob segment: from 6 standard deviations before the first blob the ray meets to
+    # 6 after the last (the optical depth beyond is below 1e-8 of a blob's); rays that
+    # meet no blob skip the quadrature
+    sig = amp_k > 1e-9
+    ta = torch.where(sig, tk_k - 6.0 * s_k, torch.full_like(tk_k, float("inf"))).amin(1)
+    tb = torch.where(sig, tk_k + 6.0 * s_k, torch.full_like(tk_k, float("-inf"))).amax(1)
     if bounded:
         ba, bb = _box_interval(o, d)
         ta, tb = torch.maximum(ta, ba), torch.minimum(tb, bb)
     ta = torch.clamp(ta, min=t_min)
-    tb = torch.maximum(tb, ta)
     T = torch.ones(n, device=dev, dtype=dt)
     C = torch.zeros(n, 3, device=dev, dtype=dt)
-    e_prev = torch.erf((ta.unsqueeze(1) - tk_k) * inv_k)
-    for i in range(1, n_steps + 1):
-        t = ta + (tb - ta) * (i / n_steps)
-        e = torch.erf((t.unsqueeze(1) - tk_k) * inv_k)
-        tau_k = amp_k * (e - e_prev)
-        e_prev = e
-        tau = tau_k.sum(1)
-        w = T * (1.0 - torch.exp(-tau))
-        num = (tau_k.unsqueeze(-1) * col_k).sum(1)
-        C += torch.where((tau > 0).unsqueeze(-1), w.unsqueeze(-1) * num / torch.where(tau > 0, tau, 1.0).unsqueeze(-1),
-                         0.0)
-        T = T * torch.exp(-tau)
+    act = torch.nonzero(tb > ta).squeeze(1)
+    if act.numel():
+        ta_a, tb_a = ta[act], tb[act]
+        tk_a, inv_a, amp_a, col_a = tk_k[act], inv_k[act], amp_k[act], col_k[act]
+        T_a = torch.ones(len(act), device=dev, dtype=dt)
+        C_a = torch.zeros(len(act), 3, device=dev, dtype=dt)
+        e_prev = torch.erf((ta_a.unsqueeze(1) - tk_a) * inv_a)
+        for i in range(1, n_steps + 1):
+            t = ta_a + (tb_a - ta_a) * (i / n_steps)
+            e = torch.erf((t.unsqueeze(1) - tk_a) * inv_a)
+            tau_k = amp_a * (e - e_prev)
+            e_prev = e
+            tau = tau_k.sum(1)
+            w = T_a * (1.0 - torch.exp(-tau))
+            num = torch.bmm(tau_k.unsqueeze(1), col_a).squeeze(1)
+            C_a += torch.where((tau > 0).unsqueeze(-1),
+                               w.unsqueeze(-1) * num / torch.where(tau > 0, tau, 1.0).unsqueeze(-1), 0.0)
+            T_a = T_a * torch.exp(-tau)
+        T[act] = T_a
+        C[act] = C_a
     if shell:
         _, t8 = _sphere_interval(o, d, SHELL_R0)
         _, t10 = _sphere_interval(o, d, SHELL_R1)

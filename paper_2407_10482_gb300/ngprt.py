@@ -16,7 +16,7 @@ import torch
 
 from . import build as _build
 
-ABI_VERSION = 200  # NGPRT_ABI_VERSION of include/ngprt.h that these structs and signatures follow
+ABI_VERSION = 201  # NGPRT_ABI_VERSION of include/ngprt.h that these structs and signatures follow
 MAX_LEVELS = 32
 MAX_CAMERAS = 64
 STATE_FLOATS = 12
@@ -85,7 +85,6 @@ _SIGS = {
     "ngprt_coarse_sparsify_workspace_bytes": (C.c_size_t, [C.c_int32]),
     "ngprt_coarse_sparsify": (C.c_int32, [_P, C.c_int32, C.c_int32, _P, _P, _P, C.c_int64, _P, _P, C.c_size_t,
                                           _P]),
-    "ngprt_wavefront_workspace_bytes": (C.c_size_t, [_P, C.c_int64]),
     "ngprt_render": (C.c_int32, [_P, _P, _P, C.c_int32, _P, _P, _P, C.c_int64, _P, _P, _P, _P, _P, _P, _P,
                                  _P, C.c_size_t, _P]),
     "ngprt_render_backward": (C.c_int32, [_P, _P, _P, C.c_int32, _P, _P, _P, C.c_int64, _P, _P, _P, _P, _P,
@@ -111,8 +110,6 @@ _SIGS = {
     "ngprt_sync_status": (C.c_int32, [_P]),
     "ngprt_test_bounded_wait": (C.c_int32, [C.c_int32, _P]),
     "ngprt_count_nonfinite": (C.c_int32, [_P, C.c_int64, _P, _P]),
-    "ngprt_gather_bench": (C.c_int32, [_P, C.c_int32, C.c_int64, C.c_int64, C.c_int32, C.c_uint32, C.c_int32, _P,
-                                       _P]),
     "ngprt_last_error": (C.c_char_p, []),
     "ngprt_version": (C.c_int32, []),
 }
@@ -263,10 +260,6 @@ def ngprt_render_workspace_bytes(scene: ngprt_scene, n_rays: int) -> int:
     return int(lib().ngprt_render_workspace_bytes(C.byref(scene), n_rays))
 
 
-def ngprt_wavefront_workspace_bytes(scene: ngprt_scene, n_rays: int) -> int:
-    return int(lib().ngprt_wavefront_workspace_bytes(C.byref(scene), n_rays))
-
-
 def cameras_struct(cams: np.ndarray, W: int, H: int):
     """Host array of ngprt_camera from float [V][16] (c2w 3x4, fx, fy, cx, cy)."""
     cams = np.asarray(cams, np.float32).reshape(-1, 16)
@@ -390,11 +383,6 @@ def ngprt_render_noalloc(scene, occ, cams, n_cams, pixel_ids, rays_o, rays_d, n_
     _check("ngprt_render_noalloc", lib().ngprt_render_noalloc(
         C.byref(scene), C.byref(occ), cams, n_cams, _ptr(pixel_ids), _ptr(rays_o), _ptr(rays_d), n_rays,
         _ptr(t_interval), C.byref(opts), _ptr(rgb), _ptr(depth), _ptr(opacity), _ptr(ray_stats), _stream(stream)))
-
-
-def ngprt_gather_bench(table, dtype, n_rows, n_threads, per_thread, seed, sink, stream=None, flags=0) -> None:
-    _check("ngprt_gather_bench", lib().ngprt_gather_bench(_ptr(table), dtype, n_rows, n_threads, per_thread, seed,
-                                                          flags, _ptr(sink), _stream(stream)))
 
 
 def ngprt_grid_indices(scene, u, n, idx_out, stream=None) -> None:

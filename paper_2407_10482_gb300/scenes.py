@@ -19,6 +19,12 @@ evaluates on, §4 and Table 1):
   density channel carries an offset of 3.2 (sigma ~ 25) so that rays stop about
   18 samples into occupied space, the shape of Table 4's "# Occupied" (17-18);
   ``density_bias=0`` gives the stress case without early termination.
+* ``hd_fit`` : the hd model (same levels, grids, MLP, occupancy resolution,
+  orbit and step rule) fitted to ground-truth images of its analytic field: the
+  same law of 64 Gaussian blobs and the shell, with peak densities raised to
+  U[100, 1000] so that the blobs are opaque as the surfaces of a captured scene
+  are.  ``hdfit.fit_hd_scene`` fits it; it is the workload whose PSNR against its
+  targets judges the fast render forms.
 """
 from __future__ import annotations
 
@@ -97,6 +103,13 @@ def hd_config(**kw) -> SceneConfig:
         max_march=1024, max_samples=1024, n_blobs=64, blob_box=1.0, shell=True,
         W=1920, H=1080, fov_y_deg=50.0, orbit_radius=3.0, elevation_deg=20.0, seed=1,
         blob_std=(0.05, 0.15), density_bias=3.2)
+    return replace(c, **kw)
+
+
+def hd_fit_config(**kw) -> SceneConfig:
+    """The fitted hd workload: hd's model shape, opaque blobs (peaks U[100, 1000]),
+    no density offset (the fit starts from its own initial grids)."""
+    c = hd_config(name="hd_fit", blob_peak=(100.0, 1000.0), density_bias=0.0)
     return replace(c, **kw)
 
 
@@ -312,7 +325,7 @@ class RenderOptions:
     use_dist: bool = True
     lattice_snap: bool = False
     attn_mode: int = 0      # 0 separate attention (omega, beta), 1 SUM, 2 shared
-    dist_rule: int = 0      # 0 Eq. 9 as printed, 1 max(v G, s_O)
+    dist_rule: int = 1      # 1 max(v G, s_O) (default), 0 Eq. 9 as printed (v G alone)
 
 
 def default_options(cfg: SceneConfig, **kw) -> RenderOptions:

