@@ -483,6 +483,9 @@ void or_contract_batch(int bounded, const double* x, int n, double* y_out, doubl
 static void or_jacobian_dir(const double x[3], const double d[3], double r, double v[3]) {
     double g = 2.0 / r - 1.0 / (r * r);
     double gp = 2.0 / (r * r * r) - 2.0 / (r * r);
+#ifdef OR_PLANT_JACOBIAN_SIGN
+    gp = -gp;   /* a planted mistake, built only by the pin that must catch it */
+#endif
     double xd = x[0] * d[0] + x[1] * d[1] + x[2] * d[2];
     for (int a = 0; a < 3; ++a) v[a] = g * d[a] + gp * (xd / r) * x[a];
 }

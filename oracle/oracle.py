@@ -21,17 +21,20 @@ _LIB = os.path.join(_LIBDIR, "libngprt_oracle.so")
 MAXL = 32
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (FP contraction off, OpenMP over rays)."""
-    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
-        return _LIB
+def build(force: bool = False, defines: tuple = ()) -> str:
+    """Compile the oracle with gcc (FP contraction off, OpenMP over rays).  `defines`
+    (macro names) build a variant library beside it: the pins use one with a planted
+    mistake to show that they catch it."""
+    lib_path = _LIB if not defines else os.path.join(_LIBDIR, "libngprt_oracle_" + "_".join(defines) + ".so")
+    if not force and os.path.exists(lib_path) and os.path.getmtime(lib_path) >= os.path.getmtime(_SRC):
+        return lib_path
     os.makedirs(_LIBDIR, exist_ok=True)
-    tmp = _LIB + f".{os.getpid()}.tmp"
+    tmp = lib_path + f".{os.getpid()}.tmp"
     cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
-           "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"]
+           "-shared", "-fPIC"] + [f"-D{m}" for m in defines] + ["-o", tmp, _SRC, "-lm"]
     subprocess.check_call(cmd)
-    os.replace(tmp, _LIB)
-    return _LIB
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 class OrScene(C.Structure):
@@ -563,13 +566,13 @@ def dist_step(x, d, rho, bounded=False):
     return out
 
 
-def empty_step(x, d, Rk, R_O=None, bounded=False):
+def empty_step(x, d, Rk, R_O=None, bounded=False, handle=None):
     """s_O (Sec. 3.3) of world points x along unit d, each in its own voxel of a grid
     of Rk voxels per axis over the (contracted) domain, with the guard of the finest
-    resolution R_O (default Rk) (FP64)."""
+    resolution R_O (default Rk) (FP64).  `handle`: another build of the oracle."""
     x = _c(x, np.float64).reshape(-1, 3)
     d = _c(d, np.float64).reshape(-1, 3)
     out = np.empty(len(x), np.float64)
-    lib().or_empty_step_batch(C.c_int(1 if bounded else 0), _p(x), _p(d), C.c_int(Rk), C.c_int(R_O or Rk),
+    (handle or lib()).or_empty_step_batch(C.c_int(1 if bounded else 0), _p(x), _p(d), C.c_int(Rk), C.c_int(R_O or Rk),
                               C.c_int(len(x)), _p(out))
     return out

@@ -423,41 +423,46 @@ __device__ __forceinline__ float empty_step(int bounded, const float x[3], const
     }
     const float vk = fdiv(2.0f * B, (float)Rk);
     const float g = fmul(kEmptyGuard, fdiv(2.0f * B, (float)R_O));
-    float s0 = INFINITY, target = 0.0f;
-    int ax = -1;
+    // the exit axis's values are carried by selection (no array indexed at run time)
+    float s0 = INFINITY, target = 0.0f, v_ax = 0.0f, d_ax = 0.0f, x_ax = 0.0f;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const float lo = fsub(fmul((float)ev[a], vk), B);
-        float plane;
+        float plane = 0.0f;
+        bool moving = true;
         if (v[a] > 0.0f) plane = fadd(fadd(lo, vk), g);
         else if (v[a] < 0.0f) plane = fsub(lo, g);
-        else continue;
-        const float ta = fdiv(fsub(plane, y[a]), v[a]);
+        else moving = false;
+        const float ta = moving ? fdiv(fsub(plane, y[a]), v[a]) : INFINITY;
         if (ta < s0) {
             s0 = ta;
-            ax = a;
             target = plane;
+            v_ax = v[a];
+            d_ax = d[a];
+            x_ax = x[a];
         }
     }
-    if (ax < 0) return INFINITY;
+    if (!(s0 < INFINITY)) return INFINITY;
     s0 = fmaxf(s0, 0.0f);
     if (!curved) return s0;
     float x1[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) x1[a] = fadd(x[a], fmul(s0, d[a]));
+    const float x1_ax = fadd(x_ax, fmul(s0, d_ax));
     const float r1 = fsqrt(dot3(x1, x1));
     float y1, v1;
     if (r1 > 1.0f) {
-        float vv[3];
-        contracted_dir(x1, d, r1, vv);
         const float ir = fdiv(1.0f, r1);
-        y1 = fmul(x1[ax], fmul(fsub(2.0f, ir), ir));
-        v1 = vv[ax];
+        const float kk = fmul(fsub(2.0f, ir), ir);
+        const float ir2 = fmul(ir, ir);
+        const float m = fmul(fmul(dot3(x1, d), fmul(2.0f, fsub(1.0f, r1))), fmul(ir2, ir2));
+        y1 = fmul(x1_ax, kk);
+        v1 = fadd(fmul(kk, d_ax), fmul(m, x1_ax));
     } else {
-        y1 = x1[ax];
-        v1 = d[ax];
+        y1 = x1_ax;
+        v1 = d_ax;
     }
-    if (!(fmul(v1, v[ax]) > 0.0f)) return s0;
+    if (!(fmul(v1, v_ax) > 0.0f)) return s0;
     const float c = fdiv(fsub(target, y1), v1);
     const float h = fmul(0.5f, s0);
     return fadd(s0, fminf(fmaxf(c, -h), h));
@@ -629,15 +634,17 @@ __device__ __forceinline__ bool ray_setup(const MarchParams& p, int64_t& ray, Ra
 // ray id / explicit ray per thread), march + features + compositing, the per-ray
 // composite state written to `state`.  In the fallback pass it re-marches only the
 // rays whose interval result missed the predicted opacity.
-// Blocks per SM the register allocation must allow.  8 (64 registers) hides the
-// gathers' latency best; FP32 tables with 4 or more levels spill enough there that 6
-// (80 registers) is faster (measured: hd L = 16 13.9 against 14.7 ms, L = 4 10.1
-// against 10.3 ms).  The MLP aggregation keeps its 64 hidden units in registers.
+// Blocks per SM the register allocation must allow (measured on the hd scene at
+// L = 16 and the paper shape at L = 4, 1080p): FP32 tables with 4 or more levels
+// are fastest at 5 (102 registers; 12.8 / 9.3 ms against 12.9 / 9.9 at 6), 16-bit
+// tables at 7 (72 registers; 9.0 / 6.3 ms against 9.3 / 6.5 at 8); FP32 with fewer
+// levels keeps 8.  The MLP aggregation keeps its 64 hidden units in registers.
 template <int L, int DT, int AGG = NGPRT_AGG_SEPARATE_V>
 constexpr int march_min_blocks() {
     if (AGG == NGPRT_AGG_MLP) return 3;
     if (NGPRT_MARCH_MIN_BLOCKS > 0) return NGPRT_MARCH_MIN_BLOCKS;
-    return (DT == NGPRT_F32 && L >= 4) ? 6 : 8;
+    if (DT == NGPRT_F32) return L >= 4 ? 5 : 8;
+    return 7;
 }
 
 template <int L, int DT, int AGG>

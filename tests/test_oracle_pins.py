@@ -464,3 +464,108 @@ def test_contracted_distance_step_stays_within_rho():
     # the bound pays off for rays aimed near the centre: much longer than rho
     central = np.abs(np.sum(dirx * d, 1)) > 0.99
     assert np.median(s[central] / rho[central]) > 2.0
+
+
+# ------------------------------------------------------------ empty-space step
+
+def _contract(p):
+    r = np.linalg.norm(p, axis=-1, keepdims=True)
+    return np.where(r > 1, (2 - 1 / np.maximum(r, 1e-300)) * p / np.maximum(r, 1e-300), p)
+
+
+def _image_speed(x, d):
+    """J(x) d of the contraction by central differences (an independent derivative)."""
+    h = 1e-6
+    return (_contract(x + h * d) - _contract(x - h * d)) / (2 * h)
+
+
+def _empty_step_overshoot(handle=None, n=1200, seed=0, R_O=128):
+    """Per pyramid level k: for world points beyond the unit ball and random
+    directions, s_O from the point's voxel of resolution R_O >> k; the segment
+    [x, x + s_O d] sampled densely in FP64 and contracted.  Returns, per level, how
+    far the image gets outside the voxel (over), the bound it must respect, and s_O.
+    The bound: the tangent line to the image, aimed at the plane g past the exit
+    face, leaves the voxel by at most g over the first estimate s0; a longer step
+    (the Newton correction) adds its extra length times the image speed; the image
+    departs from its tangent line by at most s^2 K / 2, K the largest |y''| on the
+    segment (measured here by second differences)."""
+    rng = np.random.default_rng(seed)
+    B = 2.0
+    g = 0.02 * 2 * B / R_O
+    dirs = rng.normal(size=(n, 3))
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    rad = np.exp(rng.uniform(np.log(1.2), np.log(12.0), n))
+    pts = rng.normal(size=(n, 3))
+    pts = pts / np.linalg.norm(pts, axis=1, keepdims=True) * rad[:, None]
+    out = []
+    for k in range(5):
+        Rk = R_O >> k
+        s1 = O.empty_step(pts, dirs, Rk, R_O, handle=handle)
+        side = 2 * B / Rk
+        y0 = _contract(pts)
+        v = _image_speed(pts, dirs)
+        ev = np.clip(np.floor((y0 + B) / side), 0, Rk - 1)
+        lo = -B + ev * side
+        hi = lo + side
+        plane = np.where(v > 0, hi + g, lo - g)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            ta = np.where(v != 0, (plane - y0) / v, np.inf)
+        s0 = np.maximum(ta.min(axis=1), 0.0)
+        tau = np.linspace(0.0, 1.0, 2001)[None, :, None] * s1[:, None, None]
+        ys = _contract(pts[:, None, :] + tau * dirs[:, None, :])
+        outside = np.maximum(lo[:, None, :] - ys, ys - hi[:, None, :]).max(-1)
+        over = outside.max(1)
+        end = outside[:, -1]
+        dt = s1 / 2000
+        K = np.linalg.norm(ys[:, 2:] - 2 * ys[:, 1:-1] + ys[:, :-2], axis=-1).max(1) / np.maximum(dt, 1e-30) ** 2
+        bound = g + np.maximum(s1 - s0, 0.0) * np.linalg.norm(v, axis=1) + 0.5 * s1 ** 2 * K
+        out.append((over, bound, s1, end))
+    return out
+
+
+def test_empty_step_leaves_its_voxel_within_the_overshoot_bound():
+    """s_O in contracted space (Sec. 3.3; beyond the unit ball the image of the ray
+    curves): every step makes progress, its image never gets farther outside the
+    empty voxel than the bound above, and at the finest level the image lands about
+    the guard (2% of a voxel) past the exit face."""
+    res = _empty_step_overshoot()
+    g = 0.02 * 4.0 / 128
+    for k, (over, bound, s1, end) in enumerate(res):
+        assert np.all(s1 > 0), k
+        assert np.all(over <= bound * (1 + 1e-3) + 1e-12), (k, float(np.max(over / bound)))
+        if k < 2:
+            # small voxels, nearly straight images: the step lands at the aimed plane
+            assert np.mean(np.abs(end / g - 1.0) < 0.5) > 0.99, (k, np.mean(np.abs(end / g - 1.0) < 0.5))
+    assert np.median(res[0][0]) == pytest.approx(g, rel=0.05)
+
+
+def test_empty_step_pin_catches_a_sign_error_in_the_jacobian():
+    """The same check on an oracle built with the sign of the radial term of J(x) d
+    flipped (a plausible slip in the image speed) fails on many points."""
+    C = __import__("ctypes")
+    handle = C.CDLL(O.build(defines=("OR_PLANT_JACOBIAN_SIGN",)))
+    handle.or_empty_step_batch.restype = None
+    res = _empty_step_overshoot(handle=handle)
+    g = 0.02 * 4.0 / 128
+    landed = [float(np.mean(np.abs(end / g - 1.0) < 0.5)) for _, _, _, end in res[:2]]
+    assert min(landed) < 0.9, landed
+
+
+def test_empty_step_is_exact_for_straight_images():
+    """Bounded scene and inside the unit ball the image is the ray itself: the step
+    lands exactly the guard past the exit face of the voxel."""
+    rng = np.random.default_rng(3)
+    for bounded, R, B, scale in ((True, 32, 1.0, 0.9), (False, 128, 2.0, 0.6)):
+        x = rng.uniform(-scale, scale, (500, 3))
+        d = rng.normal(size=(500, 3))
+        d /= np.linalg.norm(d, axis=1, keepdims=True)
+        s = O.empty_step(x, d, R, R, bounded=bounded)
+        side = 2 * B / R
+        g = 0.02 * side
+        ev = np.floor((x + B) / side)
+        lo, hi = -B + ev * side, -B + (ev + 1) * side
+        e = x + s[:, None] * d
+        past = np.maximum(lo - e, e - hi).max(1)
+        keep = np.linalg.norm(e, axis=1) < 1.0 if not bounded else np.ones(len(x), bool)
+        assert keep.mean() > 0.5
+        np.testing.assert_allclose(past[keep], g, rtol=1e-9, atol=1e-12)
