@@ -50,7 +50,7 @@ RANDOM_WORKLOAD = ("hd random-weight scene 1920x1080 (same model shape, tables N
 COUNTERS = os.path.join(ROOT, "profiles", "march_kernel_counters.json")
 # sources the march kernel is compiled from: counters taken on other sources are stale
 KERNEL_SOURCES = ("paper_2407_10482_gb300/csrc/common.cuh", "paper_2407_10482_gb300/csrc/march.cuh",
-                  "paper_2407_10482_gb300/csrc/render.cu", "include/ngprt.h")
+                  "paper_2407_10482_gb300/csrc/render.cu")
 
 
 def kernel_source_hash() -> str:
@@ -264,8 +264,28 @@ def fitted_forms(args, fs, opts, dev, stream, flush):
         out.copy_(r16.render(opts, cams=c, W=W, H=H)["rgb"])
     rgb16 = _views(f16_one, fs.cams_test, W, H, dev)
     c1 = fs.cams_test[:1]
-    o16 = r16.render(opts, cams=c1, W=W, H=H)
+    o16 = r16.render(opts, cams=c1, W=W, H=H, stats=True)
+    samples16 = float(o16["stats"][:, 1].float().sum())
     ms_16 = _timed(lambda: r16.render(opts, cams=c1, W=W, H=H, out=o16), stream, flush, reps, warm)
+    # the FP16 march kernel alone: its roofline is instruction issue (4 warp
+    # instructions per SM cycle), with the warp instructions per occupied sample from
+    # the committed ncu counters of this kernel source on this workload
+    cam1, nc1 = ng.cameras_struct(c1, W, H)
+    st16 = torch.empty(n, ng.STATE_FLOATS, device=dev)
+    ro = ng.render_opts(opts)
+    ms_m16 = _timed(lambda: ng.ngprt_render(ds16.struct, fs.occ.struct, cam1, nc1, None, None, None, n, None, ro, None,
+                                            ray_state=st16, stream=stream), stream, flush, reps, warm)
+    cnt16 = load_counters("hd_fit_1080p_fp16")
+    roof16 = {"bound": "issue", "unit": "G warp instructions/s", "kernel": "march_kernel<16,F16>",
+              "march_ms": ms_m16, "source_hash": kernel_source_hash()}
+    if cnt16:
+        ach = cnt16["warp_instructions_per_sample"] * samples16 / (ms_m16 * 1e-3) / 1e9
+        pk = 4 * 152 * args.clock_hz / 1e9
+        roof16.update(achieved=ach, peak=pk, frac=ach / pk,
+                      l1_frac=cnt16["l1_wavefronts_per_sample"] * samples16 / (ms_m16 * 1e-3) / (152 * args.clock_hz),
+                      traffic=cnt16["dram_bytes_per_sample"] * samples16)
+    else:
+        roof16.update(achieved=None, peak=None, frac=None, note="no ncu counters for this kernel source")
     # learned proposal: trained on the plain renderer's weights over 64 orbit views
     # between the held-out ones, every step in the library's kernels
     t0 = time.perf_counter()
@@ -302,7 +322,7 @@ def fitted_forms(args, fs, opts, dev, stream, flush):
                        "marching_per_ray": float(sp[0]), "samples_per_ray": float(sp[1])},
         "fp16_tables_tc_mlp": {"ms_per_frame": ms_16, "frames_per_s": 1000.0 / ms_16,
                                "psnr_vs_targets_db": p16, "psnr_loss_vs_targets_db": p_plain - p16,
-                               "psnr_vs_plain_db": _psnr(rgb16, rgb_plain)},
+                               "psnr_vs_plain_db": _psnr(rgb16, rgb_plain), "roofline_march": roof16},
         "fp16_tc_mlp_proposal": {
             "ms_per_frame": ms_fast, "frames_per_s": 1000.0 / ms_fast, "grays_per_s": n / ms_fast / 1e6,
             "psnr_vs_targets_db": p_fast, "psnr_vs_targets_db_per_view": per_view(rgb_fast),
@@ -654,6 +674,7 @@ def main():
             e2e_ms.append(e0.elapsed_time(e1))
     e2e_fps = world * 1000.0 / max_over_ranks(statistics.mean(e2e_ms), world, dev)
 
+    args.clock_hz = clock_hz = (clk.get("sm_mhz") or 2070.0) * 1e6
     # roofline of the march kernel: the L1 load pipe it runs at.  Wavefronts per
     # occupied sample come from the committed ncu counters of this kernel source on
     # this workload; times this frame's samples, over the kernel's event time,
@@ -662,7 +683,6 @@ def main():
     peaks = _peaks()
     t_march_avg = statistics.mean(t_march)
     cnt = load_counters("hd_fit_1080p_fp32")
-    clock_hz = (clk.get("sm_mhz") or 2070.0) * 1e6
     roof = {"bound": "l1", "unit": "Gwavefronts/s",
             "kernel": "march_kernel<16,F32> (fused march: occupancy, coarse fetch, 16-level gathers, attention, "
                       "compositing)",

@@ -476,7 +476,10 @@ int32_t ngprt_adam_step(float* param, float* grad, float* m, float* v, int64_t n
  *     larger batches in chunks.
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call before
- *     any stream capture.
+ *     any stream capture.  The address is kept for the life of the process: it
+ *     assumes the device's context is never reset.  After cudaDeviceReset (or a
+ *     primary context released and created again) the kept address is stale, so do
+ *     not call this entry point on that device again in the same process.
  *   - Every call on a device shares the one array, which keeps the last call's
  *     contents (each call overwrites the state of the rays it renders before reading
  *     it).  Calls that overlap on the GPU (other streams, other host threads) race

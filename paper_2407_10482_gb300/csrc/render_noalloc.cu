@@ -27,7 +27,9 @@ float* g_state_ptr[kMaxDevices] = {nullptr};
 
 // Device address of the static array on the current device.  In host code the
 // array's name is only a host-side stand-in, so the address must come from
-// cudaGetSymbolAddress, once per device, with that device current.
+// cudaGetSymbolAddress, once per device, with that device current.  It is kept for
+// the life of the process, which assumes the device's context is never reset (the
+// header tells callers so).
 int32_t device_scratch(float** out, const char* fn) {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
