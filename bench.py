@@ -263,6 +263,13 @@ def fitted_forms(args, fs, opts, dev, stream, flush):
     def f16_one(c, out):
         out.copy_(r16.render(opts, cams=c, W=W, H=H)["rgb"])
     rgb16 = _views(f16_one, fs.cams_test, W, H, dev)
+    # BF16 tables with the same tensor-core MLP
+    dsb = ng.DeviceScene(cfg, ds.tables, ds.coarse, ds.mlp_w, table_dtype=ng.BF16, mlp_dtype=ng.F16, device=dev)
+    rb = ng.Renderer(dsb, fs.occ, device=dev)
+    rgbb = _views(lambda c, out: out.copy_(rb.render(opts, cams=c, W=W, H=H)["rgb"]), fs.cams_test, W, H, dev)
+    ob = rb.render(opts, cams=fs.cams_test[:1], W=W, H=H)
+    ms_b = _timed(lambda: rb.render(opts, cams=fs.cams_test[:1], W=W, H=H, out=ob), stream, flush, reps, warm)
+    del rb, ob
     c1 = fs.cams_test[:1]
     o16 = r16.render(opts, cams=c1, W=W, H=H, stats=True)
     samples16 = float(o16["stats"][:, 1].float().sum())
@@ -323,6 +330,9 @@ def fitted_forms(args, fs, opts, dev, stream, flush):
         "fp16_tables_tc_mlp": {"ms_per_frame": ms_16, "frames_per_s": 1000.0 / ms_16,
                                "psnr_vs_targets_db": p16, "psnr_loss_vs_targets_db": p_plain - p16,
                                "psnr_vs_plain_db": _psnr(rgb16, rgb_plain), "roofline_march": roof16},
+        "bf16_tables_tc_mlp": {"ms_per_frame": ms_b, "frames_per_s": 1000.0 / ms_b,
+                               "psnr_vs_targets_db": _psnr(rgbb, tg), "psnr_loss_vs_targets_db": p_plain - _psnr(rgbb, tg),
+                               "psnr_vs_plain_db": _psnr(rgbb, rgb_plain)},
         "fp16_tc_mlp_proposal": {
             "ms_per_frame": ms_fast, "frames_per_s": 1000.0 / ms_fast, "grays_per_s": n / ms_fast / 1e6,
             "psnr_vs_targets_db": p_fast, "psnr_vs_targets_db_per_view": per_view(rgb_fast),
@@ -376,8 +386,9 @@ def random_scene(args, dev, stream, flush):
     opts = S.default_options(cfg)
     docc = ng.DeviceOcc(sc.occ, cfg.R_O, cfg.n_occ_levels, device=dev)
     out = {"workload": RANDOM_WORKLOAD}
-    for dt, key in ((ng.F32, "fp32"), (ng.F16, "fp16_tc")):
-        ds = ng.DeviceScene(cfg, sc.tables, sc.coarse, sc.mlp_w, table_dtype=dt, mlp_dtype=dt, device=dev)
+    for dt, key in ((ng.F32, "fp32"), (ng.F16, "fp16_tc"), (ng.BF16, "bf16_tc")):
+        ds = ng.DeviceScene(cfg, sc.tables, sc.coarse, sc.mlp_w, table_dtype=dt,
+                            mlp_dtype=ng.F32 if dt == ng.F32 else ng.F16, device=dev)
         rend = ng.Renderer(ds, docc, device=dev)
         o = rend.render(opts, cams=cams, W=cfg.W, H=cfg.H)
         ms = _timed(lambda: rend.render(opts, cams=cams, W=cfg.W, H=cfg.H, out=o), stream, flush, 5, 3)

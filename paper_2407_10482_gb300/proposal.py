@@ -27,10 +27,13 @@ class ProposalConfig:
     t_scale: float = 16.0      # t_near, t_far = t_scale * sigmoid(.)
     # world units the march starts before t_near.  The rays the proposal gets wrong
     # are opaque ones started behind their surface, which the opacity fallback cannot
-    # see; on the hd scene a margin of 1.0 against 0.5 lifts the worst of 8 views
-    # from 45.9 to 48.4 dB against the plain render for 1% more frame time
+    # see.  On the fitted hd scene (8 held-out views) 1.0 keeps the PSNR loss against
+    # the ground truth at 0.06 dB; 0.5 and 0.25 lose 0.3 and 0.8 dB for 1.5% and 3.6%
+    # less frame time
     margin_near: float = 1.0
-    margin_far: float = float("inf")  # after t_far (inf: no far clip, termination ends the ray)
+    # after t_far (inf: no far clip, termination ends the ray); a clip at 2.0 or 0.5
+    # measured 11-19% slower there, with no PSNR gain
+    margin_far: float = float("inf")
     a_min: float = 0.01        # predicted opacity below which nothing is marched
     fallback: float = 0.01     # re-march when a_hat - A(interval) exceeds this
     steps: int = 6000
