@@ -260,6 +260,40 @@ __device__ __forceinline__ void grid_cell(float u, int N, int& base, float& w) {
     w = fadd(fsub(pf, bf), e);
 }
 
+// The cell for the 16-bit table forms, without conversion instructions: u (N-1) +
+// 2^23 added with rounding toward minus infinity holds floor(u (N-1)) in its low
+// mantissa bits (for 0 <= u (N-1) < 2^23), clamped in that form to [0, N-2] (a NaN
+// clamps to 0).  It floors the rounded product, which differs from the exact
+// product's floor only where u (N-1) rounds onto a vertex; there both cells
+// interpolate to the same value up to rounding (trilinear interpolation is
+// continuous across the vertex).
+__device__ __forceinline__ void grid_cell_fast(float u, int N, int& base, float& w) {
+    constexpr float kM = 8388608.0f;  // 2^23, bit pattern 0x4B000000
+    const float pf = fmul(u, (float)(N - 1));
+    const float t = fminf(fmaxf(__fadd_rd(pf, kM), kM), fadd(kM, (float)(N - 2)));
+    base = __float_as_int(t) - 0x4B000000;
+    w = fsub(pf, fsub(t, kM));
+}
+
+// Trilinear weights of a cell's 8 corners for FP16 interpolation as 4 packed pairs:
+// cw[j] holds corners 2j and 2j+1 (x = 0 and x = 1 at y = j & 1, z = j >> 1), the
+// FP16 products of the per-axis pairs (1 - w, w).
+__device__ __forceinline__ void corner_w_h2(const float w[3], __half2 cw[4]) {
+    const __half2 hx = __floats2half2_rn(fsub(1.0f, w[0]), w[0]);
+    const __half2 hy = __floats2half2_rn(fsub(1.0f, w[1]), w[1]);
+    const __half2 hz = __floats2half2_rn(fsub(1.0f, w[2]), w[2]);
+    const __half2 xy0 = __hmul2(hx, __low2half2(hy)), xy1 = __hmul2(hx, __high2half2(hy));
+    cw[0] = __hmul2(xy0, __low2half2(hz));
+    cw[1] = __hmul2(xy1, __low2half2(hz));
+    cw[2] = __hmul2(xy0, __high2half2(hz));
+    cw[3] = __hmul2(xy1, __high2half2(hz));
+}
+
+// Weight of corner c (bit 0: x, bit 1: y, bit 2: z) in both halves.
+__device__ __forceinline__ __half2 corner_h2(const __half2 cw[4], int c) {
+    return (c & 1) ? __high2half2(cw[c >> 1]) : __low2half2(cw[c >> 1]);
+}
+
 // Row of the coarse vertex at the base corner of cell b and the row strides of
 // its y and z neighbours: dense [R_C^3] rows, or the 9^3-vertex block of the cell's
 // 8^3-cell block in the sparse grid (one index lookup for all 8 corners).
@@ -281,17 +315,18 @@ __device__ __forceinline__ void coarse_base(const Grid& g, const int b[3], uint3
     }
 }
 
-// Absolute table row of vertex (x, y, z) of level l: dense row-major or the
-// Instant-NGP spatial hash.
-__device__ __forceinline__ uint32_t level_row(const Grid& g, int l, uint32_t x, uint32_t y, uint32_t z) {
-    uint32_t idx;
+// Row of vertex (x, y, z) within level l (dense row-major or the Instant-NGP
+// spatial hash), and its absolute table row.
+__device__ __forceinline__ uint32_t level_index(const Grid& g, int l, uint32_t x, uint32_t y, uint32_t z) {
     if ((g.dense_mask >> l) & 1u) {
         const uint32_t n = (uint32_t)g.N[l];
-        idx = x + n * (y + n * z);
-    } else {
-        idx = (x ^ (y * 2654435761u) ^ (z * 805459861u)) & g.T_mask;
+        return x + n * (y + n * z);
     }
-    return g.level_off[l] + idx;
+    return (x ^ (y * 2654435761u) ^ (z * 805459861u)) & g.T_mask;
+}
+
+__device__ __forceinline__ uint32_t level_row(const Grid& g, int l, uint32_t x, uint32_t y, uint32_t z) {
+    return g.level_off[l] + level_index(g, l, x, y, z);
 }
 
 // ------------------------------------------------------------ vector loads
@@ -418,6 +453,24 @@ __device__ __forceinline__ float sigmoidf_(float x) { return 1.0f / (1.0f + expf
 // Attention gate sigma(x) = 1 / (1 + e^-x) with the hardware exponential and
 // reciprocal (relative error ~1e-6; the gates only scale feature values).
 __device__ __forceinline__ float gate_sigmoid(float x) { return __fdividef(1.0f, 1.0f + __expf(-x)); }
+
+// The same gate for a pair of FP16 logits, sigma(x) = (1 + tanh(x / 2)) / 2, with the
+// hardware's packed FP16 tanh (absolute error of the gate about 5e-4, the size of
+// the FP16 logit's own rounding).
+__device__ __forceinline__ __half2 gate_sigmoid_h2(__half2 x) {
+    const __half2 half = __float2half2_rn(0.5f);
+    const __half2 a = __hmul2(x, half);
+    uint32_t t;
+    asm("tanh.approx.f16x2 %0, %1;" : "=r"(t) : "r"(*reinterpret_cast<const uint32_t*>(&a)));
+    return __hfma2(*reinterpret_cast<const __half2*>(&t), half, half);
+}
+
+// c + a b with FP16 factors and an FP32 addend and result (one rounding, to FP32).
+__device__ __forceinline__ float fma_f16_f32(__half a, __half b, float c) {
+    float d;
+    asm("fma.rn.f32.f16 %0, %1, %2, %3;" : "=f"(d) : "h"(__half_as_ushort(a)), "h"(__half_as_ushort(b)), "f"(c));
+    return d;
+}
 
 // Real spherical harmonics, bands 0..3, order l^2 + l + m, no Condon-Shortley
 // phase, orthonormal on the sphere (Cartesian polynomial form).

@@ -103,6 +103,14 @@ __device__ __forceinline__ void ray_of(const MarchParams& p, int64_t ray, float 
     camera_ray_df(p.cams.c[view], (int)(rem % p.W), (int)(rem / p.W), o, d);
 }
 
+// Trilinear cell of a table lattice: exact for FP32 tables (the parity form), the
+// conversion-free floor for the 16-bit forms.
+template <int DT>
+__device__ __forceinline__ void table_cell(float u, int N, int& b, float& w) {
+    if constexpr (DT == NGPRT_F32) grid_cell(u, N, b, w);
+    else grid_cell_fast(u, N, b, w);
+}
+
 __device__ __forceinline__ float corner_w(const float w[3], int c) {
     const float wx = (c & 1) ? w[0] : 1.0f - w[0];
     const float wy = (c & 2) ? w[1] : 1.0f - w[1];
@@ -139,8 +147,9 @@ constexpr int kLevelUnroll = NGPRT_LEVEL_UNROLL;
 // the attention logits); the 2L gates (sigmoid of the interpolated or constant
 // logits) are parked in shared memory, gates[k*stride], so that the level loop need
 // not be unrolled.  FP32 and BF16 tables interpolate in FP32; FP16 tables
-// interpolate in packed half2 FMAs (FP16 products and sums, one conversion per
-// channel), the rest of the sample in FP32.  The MLP form accumulates its 64 hidden
+// interpolate in packed half2 FMAs with FP16 corner weights (FP16 products and
+// sums, one conversion per channel), the rest of the sample in FP32.  The 16-bit
+// forms take their cells with the conversion-free floor (grid_cell_fast).  The MLP form accumulates its 64 hidden
 // units level by level (W1 columns of level l against f^l), then applies W2.
 // With kKeep (reverse pass), level l also leaves sigma^l and q^l = sum over the
 // colour channels of f^l times gq (the ray's colour cotangents) in the slots
@@ -152,16 +161,21 @@ __device__ __forceinline__ void sample_features(const Grid& g, const float u[3],
     constexpr int NC = coarse_channels(L, AGG);
     static_assert(NC % 2 == 0, "coarse channels are fetched in pairs");
     constexpr bool kGated = AGG != NGPRT_AGG_SUM && AGG != NGPRT_AGG_MLP;
+    // FP16 tables with per-level gate pairs: the gates stay in FP16 (one word per
+    // level) and each level's gated sum is taken in mixed precision (FP16 factors,
+    // FP32 sum), without converting the level's features
+    constexpr bool kHalfGates = DT == NGPRT_F16 && AGG == NGPRT_AGG_SEPARATE_V && !kKeep;
     int b[3];
     float w[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) grid_cell(u[a], g.R_C, b[a], w[a]);
+    for (int a = 0; a < 3; ++a) table_cell<DT>(u[a], g.R_C, b[a], w[a]);
     float2 acc[NC / 2];
     uint32_t cb, sy, sz;
     coarse_base(g, b, cb, sy, sz);
     if constexpr (DT == NGPRT_F16) {
         // FP16 tables: trilinear sums in packed half2 FMAs, converted once
-        __half2 hacc[NC / 2];
+        __half2 hacc[NC / 2], cw[4];
+        corner_w_h2(w, cw);
 #pragma unroll
         for (int ch = 0; ch < NC / 2; ++ch) hacc[ch] = __float2half2_rn(0.0f);
 #pragma unroll
@@ -169,13 +183,22 @@ __device__ __forceinline__ void sample_features(const Grid& g, const float u[3],
             const uint32_t v = cb + (uint32_t)(c & 1) + sy * (uint32_t)((c >> 1) & 1) + sz * (uint32_t)((c >> 2) & 1);
             uint32_t q[NC / 2];
             load_pairs<NC>(static_cast<const uint16_t*>(g.coarse) + (size_t)v * NC, q);
-            const __half2 cw2 = __float2half2_rn(corner_w(w, c));
+            const __half2 cw2 = corner_h2(cw, c);
 #pragma unroll
             for (int ch = 0; ch < NC / 2; ++ch)
                 hacc[ch] = __hfma2(cw2, *reinterpret_cast<const __half2*>(&q[ch]), hacc[ch]);
         }
 #pragma unroll
-        for (int ch = 0; ch < NC / 2; ++ch) acc[ch] = __half22float2(hacc[ch]);
+        for (int ch = 0; ch < (kHalfGates ? kNFeat / 2 : NC / 2); ++ch) acc[ch] = __half22float2(hacc[ch]);
+        if constexpr (kHalfGates) {
+#pragma unroll
+            for (int l = 0; l < L; ++l) {
+                const __half2 lg = hacc[kNFeat / 2 + l];
+                const __half2 gp = attn_mode == 1 ? __float2half2_rn(1.0f)
+                                                  : gate_sigmoid_h2(attn_mode == 2 ? __low2half2(lg) : lg);
+                reinterpret_cast<__half2*>(gates)[l * stride] = gp;
+            }
+        }
     } else {
 #pragma unroll
         for (int ch = 0; ch < NC / 2; ++ch) acc[ch] = make_float2(0.0f, 0.0f);
@@ -195,7 +218,7 @@ __device__ __forceinline__ void sample_features(const Grid& g, const float u[3],
         f[2 * ch] = acc[ch].x;
         f[2 * ch + 1] = acc[ch].y;
     }
-    if constexpr (kGated) {
+    if constexpr (kGated && !kHalfGates) {
 #pragma unroll
         for (int l = 0; l < L; ++l) {
             float om, be;
@@ -237,29 +260,44 @@ __device__ __forceinline__ void sample_features(const Grid& g, const float u[3],
         int bl[3];
         float wl[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) grid_cell(u[a], g.N[l], bl[a], wl[a]);
+        for (int a = 0; a < 3; ++a) table_cell<DT>(u[a], g.N[l], bl[a], wl[a]);
+        // rows within the level, against the level's first entry
         uint32_t rows[8];
 #pragma unroll
         for (int c = 0; c < 8; ++c)
-            rows[c] = level_row(g, l, (uint32_t)(bl[0] + (c & 1)), (uint32_t)(bl[1] + ((c >> 1) & 1)),
-                                (uint32_t)(bl[2] + ((c >> 2) & 1)));
+            rows[c] = level_index(g, l, (uint32_t)(bl[0] + (c & 1)), (uint32_t)(bl[1] + ((c >> 1) & 1)),
+                                  (uint32_t)(bl[2] + ((c >> 2) & 1)));
+        const void* tl = static_cast<const char*>(g.tables) + (size_t)g.level_off[l] * (DT == NGPRT_F32 ? 32 : 16);
         float2 fl[4];
         if constexpr (DT == NGPRT_F16) {
             uint4 q[8];
 #pragma unroll
-            for (int c = 0; c < 8; ++c) q[c] = __ldg(static_cast<const uint4*>(g.tables) + rows[c]);
-            __half2 h[4];
+            for (int c = 0; c < 8; ++c) q[c] = __ldg(static_cast<const uint4*>(tl) + rows[c]);
+            __half2 h[4], cw[4];
+            corner_w_h2(wl, cw);
 #pragma unroll
             for (int ch = 0; ch < 4; ++ch) h[ch] = __float2half2_rn(0.0f);
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
-                const __half2 cw2 = __float2half2_rn(corner_w(wl, c));
+                const __half2 cw2 = corner_h2(cw, c);
                 const __half2* e2 = reinterpret_cast<const __half2*>(&q[c]);
 #pragma unroll
                 for (int ch = 0; ch < 4; ++ch) h[ch] = __hfma2(cw2, e2[ch], h[ch]);
             }
+            if constexpr (kHalfGates) {
+                const __half2 gp = reinterpret_cast<const __half2*>(gates)[l * stride];
+                const __half om = __low2half(gp), be = __high2half(gp);
+                f[0] = fma_f16_f32(om, __low2half(h[0]), f[0]);
+                f[1] = fma_f16_f32(be, __high2half(h[0]), f[1]);
 #pragma unroll
-            for (int ch = 0; ch < 4; ++ch) fl[ch] = __half22float2(h[ch]);
+                for (int ch = 1; ch < 4; ++ch) {
+                    f[2 * ch] = fma_f16_f32(be, __low2half(h[ch]), f[2 * ch]);
+                    f[2 * ch + 1] = fma_f16_f32(be, __high2half(h[ch]), f[2 * ch + 1]);
+                }
+            } else {
+#pragma unroll
+                for (int ch = 0; ch < 4; ++ch) fl[ch] = __half22float2(h[ch]);
+            }
         } else {
             float e[8][8];
             // FP32: large levels bypass L1 allocation (16-bit entries share sectors
@@ -267,8 +305,8 @@ __device__ __forceinline__ void sample_features(const Grid& g, const float u[3],
             const bool na = DT == NGPRT_F32 && ((g.na_mask >> l) & 1u);
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
-                if (na) load_entry_f32_na(g.tables, rows[c], e[c]);
-                else load_entry<DT>(g.tables, rows[c], e[c]);
+                if (na) load_entry_f32_na(tl, rows[c], e[c]);
+                else load_entry<DT>(tl, rows[c], e[c]);
             }
 #pragma unroll
             for (int ch = 0; ch < 4; ++ch) fl[ch] = make_float2(0.0f, 0.0f);
@@ -320,14 +358,14 @@ __device__ __forceinline__ void sample_features(const Grid& g, const float u[3],
                 h = fmaf(c.w, fl[3].y, h);
                 hid[j] = h;
             }
-        } else {
+        } else if constexpr (!kHalfGates) {
+            // packed pairs: each half is the scalar fmaf, bit for bit
             const float om = gates[(2 * l) * stride], be = gates[(2 * l + 1) * stride];
-            f[0] = fmaf(om, fl[0].x, f[0]);
-            f[1] = fmaf(be, fl[0].y, f[1]);
 #pragma unroll
-            for (int ch = 1; ch < 4; ++ch) {
-                f[2 * ch] = fmaf(be, fl[ch].x, f[2 * ch]);
-                f[2 * ch + 1] = fmaf(be, fl[ch].y, f[2 * ch + 1]);
+            for (int ch = 0; ch < 4; ++ch) {
+                const float2 r = ffma2(make_float2(ch == 0 ? om : be, be), fl[ch], make_float2(f[2 * ch], f[2 * ch + 1]));
+                f[2 * ch] = r.x;
+                f[2 * ch + 1] = r.y;
             }
         }
     }
@@ -487,9 +525,12 @@ __device__ __forceinline__ bool march_advance(const MarchParams& p, const Ray& r
         float x[3], y[3], r;
         march_point(bounded, ry, st.t, x, y, u, r);
         int empty_level = -1, ev[3] = {0, 0, 0};
+        // the finest level's voxel, once: R_O is a power of two, so u R_k = u R_O / 2^k
+        // exactly and a coarser level's voxel is the finest one's shifted right by k
+        const int f0 = occ_vox(u[0], R_O), f1 = occ_vox(u[1], R_O), f2 = occ_vox(u[2], R_O);
         for (int k = p.occ.n_levels - 1; k >= 0; --k) {
             const int Rk = R_O >> k;
-            const int c0 = occ_vox(u[0], Rk), c1 = occ_vox(u[1], Rk), c2 = occ_vox(u[2], Rk);
+            const int c0 = f0 >> k, c1 = f1 >> k, c2 = f2 >> k;
             const uint32_t bi = (uint32_t)c0 + (uint32_t)Rk * ((uint32_t)c1 + (uint32_t)Rk * (uint32_t)c2);
             const uint32_t word = __ldg(p.occ.bits + p.occ.word_off[k] + (bi >> 5));
             if (!((word >> (bi & 31)) & 1u)) {
@@ -506,7 +547,8 @@ __device__ __forceinline__ bool march_advance(const MarchParams& p, const Ray& r
         const float s_O = empty_step(bounded, x, y, ry.dh, r, ev, R_O >> empty_level, R_O);
         float step = s_O;
         if (op.use_dist && p.occ.dist && empty_level > p.occ.g_shift) {
-            const int g0 = occ_vox(u[0], R_G), g1 = occ_vox(u[1], R_G), g2 = occ_vox(u[2], R_G);
+            const int gs = p.occ.g_shift;
+            const int g0 = f0 >> gs, g1 = f1 >> gs, g2 = f2 >> gs;
             const int gv = __ldg(p.occ.dist + ((size_t)g0 + (size_t)R_G * ((size_t)g1 + (size_t)R_G * g2)));
             if (gv > 0) {
                 const float sg = dist_step(bounded, x, ry.dh, r, fmul((float)gv, vG));
