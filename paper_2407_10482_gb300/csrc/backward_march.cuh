@@ -148,7 +148,7 @@ __device__ __forceinline__ void scatter_features(const Grid& g, const float u[3]
         const float gf[8] = {gs, gw[0], gw[1], gw[2], gw[3], gw[4], gw[5], gw[6]};
         scatter_mlp_levels<L>(g, u, gf, slots, stride, g_tables);
     }
-#pragma unroll kLevelUnroll
+#pragma unroll kScatterUnroll
     for (int l = 0; l < (AGG == NGPRT_AGG_MLP ? 0 : L); ++l) {
         float om = 1.0f, be = 1.0f;
         if constexpr (AGG != NGPRT_AGG_SUM) {

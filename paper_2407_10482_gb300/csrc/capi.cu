@@ -99,6 +99,8 @@ int32_t make_grid(const ngprt_scene* s, Grid& g, const char* fn) {
         if ((e < T ? e : T) >= (uint64_t)NGPRT_NA_MIN_ENTRIES) g.na_mask |= 1u << l;
         off += e < T ? e : T;
     }
+    const int nd = __builtin_popcount(g.dense_mask);
+    g.n_dense = g.dense_mask == (nd >= 32 ? 0xFFFFFFFFu : (1u << nd) - 1u) ? nd : -1;
     return NGPRT_OK;
 }
 

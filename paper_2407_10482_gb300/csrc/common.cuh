@@ -42,6 +42,7 @@ struct Grid {
     uint32_t level_off[kMaxL];   // first row of each level
     int32_t N[kMaxL];
     uint32_t dense_mask;         // bit l: level l is dense
+    int32_t n_dense;             // the dense levels are levels 0 .. n_dense-1 (-1: not a prefix)
     uint32_t na_mask;            // bit l: level l's FP32 entries are read without L1 allocation
     uint32_t T_mask;             // 2^T_log2 - 1
     int32_t L;
@@ -260,19 +261,21 @@ __device__ __forceinline__ void grid_cell(float u, int N, int& base, float& w) {
     w = fadd(fsub(pf, bf), e);
 }
 
-// The cell for the 16-bit table forms, without conversion instructions: u (N-1) +
-// 2^23 added with rounding toward minus infinity holds floor(u (N-1)) in its low
-// mantissa bits (for 0 <= u (N-1) < 2^23), clamped in that form to [0, N-2] (a NaN
-// clamps to 0).  It floors the rounded product, which differs from the exact
-// product's floor only where u (N-1) rounds onto a vertex; there both cells
-// interpolate to the same value up to rounding (trilinear interpolation is
-// continuous across the vertex).
-__device__ __forceinline__ void grid_cell_fast(float u, int N, int& base, float& w) {
-    constexpr float kM = 8388608.0f;  // 2^23, bit pattern 0x4B000000
-    const float pf = fmul(u, (float)(N - 1));
-    const float t = fminf(fmaxf(__fadd_rd(pf, kM), kM), fadd(kM, (float)(N - 2)));
-    base = __float_as_int(t) - 0x4B000000;
-    w = fsub(pf, fsub(t, kM));
+// Unit-cube coordinate in 0.32 fixed point, floor(u 2^32), saturated to
+// [0, 2^32 - 1] (the conversion saturates; a NaN converts to 0).
+__device__ __forceinline__ uint32_t unit_fx(float u) { return __float2uint_rz(fmul(u, 4294967296.0f)); }
+
+// The cell for the 16-bit table forms from the fixed-point coordinate U: the 64-bit
+// product U (N-1) holds the cell in its high word (at most N-2, since U < 2^32, so
+// no clamp) and the position within the cell in its low word, whose top 23 bits
+// give the weight exactly as a float in [0, 1).  It floors u (N-1) to within 2^-32
+// of u; where that differs from the FP32 floor the point lies on a vertex, where
+// both cells interpolate to the same value up to rounding (trilinear
+// interpolation is continuous across the vertex).
+__device__ __forceinline__ void grid_cell_fx(uint32_t U, int N, int& base, float& w) {
+    const uint64_t p = (uint64_t)U * (uint32_t)(N - 1);
+    base = (int)(uint32_t)(p >> 32);
+    w = fsub(__uint_as_float(0x3F800000u | ((uint32_t)p >> 9)), 1.0f);
 }
 
 // Trilinear weights of a cell's 8 corners for FP16 interpolation as 4 packed pairs:
@@ -323,6 +326,20 @@ __device__ __forceinline__ uint32_t level_index(const Grid& g, int l, uint32_t x
         return x + n * (y + n * z);
     }
     return (x ^ (y * 2654435761u) ^ (z * 805459861u)) & g.T_mask;
+}
+
+// The same with the level's kind fixed at compile time: 1 dense, 2 hashed (0: by
+// the mask).
+template <int kKind>
+__device__ __forceinline__ uint32_t level_index_k(const Grid& g, int l, uint32_t x, uint32_t y, uint32_t z) {
+    if constexpr (kKind == 1) {
+        const uint32_t n = (uint32_t)g.N[l];
+        return x + n * (y + n * z);
+    } else if constexpr (kKind == 2) {
+        return (x ^ (y * 2654435761u) ^ (z * 805459861u)) & g.T_mask;
+    } else {
+        return level_index(g, l, x, y, z);
+    }
 }
 
 __device__ __forceinline__ uint32_t level_row(const Grid& g, int l, uint32_t x, uint32_t y, uint32_t z) {

@@ -9,6 +9,8 @@
 
 #include <math.h>
 
+#include <type_traits>
+
 #include "common.cuh"
 
 // Occupancy hint for the march kernels (blocks of 128 threads per SM the register
@@ -103,12 +105,12 @@ __device__ __forceinline__ void ray_of(const MarchParams& p, int64_t ray, float 
     camera_ray_df(p.cams.c[view], (int)(rem % p.W), (int)(rem / p.W), o, d);
 }
 
-// Trilinear cell of a table lattice: exact for FP32 tables (the parity form), the
-// conversion-free floor for the 16-bit forms.
+// Trilinear cell of a table lattice: the exact FP32 floor for FP32 tables (the
+// parity form), the fixed-point cell (ufx = unit_fx(u)) for the 16-bit forms.
 template <int DT>
-__device__ __forceinline__ void table_cell(float u, int N, int& b, float& w) {
+__device__ __forceinline__ void table_cell(float u, uint32_t ufx, int N, int& b, float& w) {
     if constexpr (DT == NGPRT_F32) grid_cell(u, N, b, w);
-    else grid_cell_fast(u, N, b, w);
+    else grid_cell_fx(ufx, N, b, w);
 }
 
 __device__ __forceinline__ float corner_w(const float w[3], int c) {
@@ -136,10 +138,17 @@ __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
     return *reinterpret_cast<float2*>(&D);
 }
 
+// Unroll of the level loops: the forward's gathers (1: measured fastest on the
+// fitted hd scene at 1080p, FP16 9.5 ms against 10.9 at 2) and the reverse pass's
+// scatter.
 #ifndef NGPRT_LEVEL_UNROLL
-#define NGPRT_LEVEL_UNROLL 2
+#define NGPRT_LEVEL_UNROLL 1
+#endif
+#ifndef NGPRT_SCATTER_UNROLL
+#define NGPRT_SCATTER_UNROLL 2
 #endif
 constexpr int kLevelUnroll = NGPRT_LEVEL_UNROLL;
+constexpr int kScatterUnroll = NGPRT_SCATTER_UNROLL;
 
 // Eq. 6-8 at unit-cube position u: f = f~ + Att(f^1..f^L; a), or one of the
 // aggregations of Table 3 (AGG, an ngprt_aggregation).  The coarse fetch
@@ -165,10 +174,15 @@ __device__ __forceinline__ void sample_features(const Grid& g, const float u[3],
     // level) and each level's gated sum is taken in mixed precision (FP16 factors,
     // FP32 sum), without converting the level's features
     constexpr bool kHalfGates = DT == NGPRT_F16 && AGG == NGPRT_AGG_SEPARATE_V && !kKeep;
+    uint32_t ufx[3] = {0u, 0u, 0u};
+    if constexpr (DT != NGPRT_F32) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) ufx[a] = unit_fx(u[a]);
+    }
     int b[3];
     float w[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) table_cell<DT>(u[a], g.R_C, b[a], w[a]);
+    for (int a = 0; a < 3; ++a) table_cell<DT>(u[a], ufx[a], g.R_C, b[a], w[a]);
     float2 acc[NC / 2];
     uint32_t cb, sy, sz;
     coarse_base(g, b, cb, sy, sz);
@@ -255,20 +269,21 @@ __device__ __forceinline__ void sample_features(const Grid& g, const float u[3],
 #pragma unroll
         for (int j = 0; j < kHid; ++j) hid[j] = 0.0f;
     }
-#pragma unroll kLevelUnroll
-    for (int l = 0; l < L; ++l) {
+    // one level's gathers and sums; kind: 1 dense, 2 hashed, 0 by the mask
+    auto level = [&](const int l, auto kind) {
+        constexpr int kKind = decltype(kind)::value;
         int bl[3];
         float wl[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) table_cell<DT>(u[a], g.N[l], bl[a], wl[a]);
+        for (int a = 0; a < 3; ++a) table_cell<DT>(u[a], ufx[a], g.N[l], bl[a], wl[a]);
         // rows within the level, against the level's first entry
         uint32_t rows[8];
 #pragma unroll
         for (int c = 0; c < 8; ++c)
-            rows[c] = level_index(g, l, (uint32_t)(bl[0] + (c & 1)), (uint32_t)(bl[1] + ((c >> 1) & 1)),
-                                  (uint32_t)(bl[2] + ((c >> 2) & 1)));
+            rows[c] = level_index_k<kKind>(g, l, (uint32_t)(bl[0] + (c & 1)), (uint32_t)(bl[1] + ((c >> 1) & 1)),
+                                           (uint32_t)(bl[2] + ((c >> 2) & 1)));
         const void* tl = static_cast<const char*>(g.tables) + (size_t)g.level_off[l] * (DT == NGPRT_F32 ? 32 : 16);
-        float2 fl[4];
+        [[maybe_unused]] float2 fl[4];
         if constexpr (DT == NGPRT_F16) {
             uint4 q[8];
 #pragma unroll
@@ -368,6 +383,17 @@ __device__ __forceinline__ void sample_features(const Grid& g, const float u[3],
                 f[2 * ch + 1] = r.y;
             }
         }
+    };
+    // the dense levels first when they are a prefix (each loop's kind fixed)
+    if (g.n_dense >= 0) {
+        const int nd = min(g.n_dense, L);
+#pragma unroll kLevelUnroll
+        for (int l = 0; l < nd; ++l) level(l, std::integral_constant<int, 1>{});
+#pragma unroll kLevelUnroll
+        for (int l = nd; l < L; ++l) level(l, std::integral_constant<int, 2>{});
+    } else {
+#pragma unroll kLevelUnroll
+        for (int l = 0; l < L; ++l) level(l, std::integral_constant<int, 0>{});
     }
     if constexpr (AGG == NGPRT_AGG_MLP) {
         if constexpr (kKeep) {
@@ -676,17 +702,18 @@ __device__ __forceinline__ bool ray_setup(const MarchParams& p, int64_t& ray, Ra
 // ray id / explicit ray per thread), march + features + compositing, the per-ray
 // composite state written to `state`.  In the fallback pass it re-marches only the
 // rays whose interval result missed the predicted opacity.
-// Blocks per SM the register allocation must allow (measured on the hd scene at
-// L = 16 and the paper shape at L = 4, 1080p): FP32 tables with 4 or more levels
-// are fastest at 5 (102 registers; 12.8 / 9.3 ms against 12.9 / 9.9 at 6), 16-bit
-// tables at 7 (72 registers; 9.0 / 6.3 ms against 9.3 / 6.5 at 8); FP32 with fewer
-// levels keeps 8.  The MLP aggregation keeps its 64 hidden units in registers.
+// Blocks per SM the register allocation must allow (measured at 1080p on the
+// fitted hd scene, L = 16, and earlier on the paper shape, L = 4): FP32 tables with
+// 4 or more levels are fastest at 5 (102 registers; 16.1 ms against 16.2 at 6 and
+// 18.0 at 8), FP16 tables at 8 (64 registers; 9.5 ms against 9.6 at 7 and 9.9 at
+// 6), BF16 tables (interpolated in FP32) at 7; FP32 with fewer levels keeps 8.  The MLP aggregation keeps its 64 hidden
+// units in registers.
 template <int L, int DT, int AGG = NGPRT_AGG_SEPARATE_V>
 constexpr int march_min_blocks() {
     if (AGG == NGPRT_AGG_MLP) return 3;
     if (NGPRT_MARCH_MIN_BLOCKS > 0) return NGPRT_MARCH_MIN_BLOCKS;
     if (DT == NGPRT_F32) return L >= 4 ? 5 : 8;
-    return 7;
+    return DT == NGPRT_F16 ? 8 : 7;
 }
 
 template <int L, int DT, int AGG>
