@@ -274,22 +274,25 @@ def fitted_forms(args, fs, opts, dev, stream, flush):
     o16 = r16.render(opts, cams=c1, W=W, H=H, stats=True)
     samples16 = float(o16["stats"][:, 1].float().sum())
     ms_16 = _timed(lambda: r16.render(opts, cams=c1, W=W, H=H, out=o16), stream, flush, reps, warm)
-    # the FP16 march kernel alone: its roofline is instruction issue (4 warp
-    # instructions per SM cycle), with the warp instructions per occupied sample from
-    # the committed ncu counters of this kernel source on this workload
+    # the FP16 march kernel alone: bound by the L1 data pipe (one wavefront per SM
+    # cycle), with instruction issue (4 warp instructions per SM cycle) the next
+    # limit; wavefronts and warp instructions per occupied sample from the committed
+    # ncu counters of this kernel source on this workload
     cam1, nc1 = ng.cameras_struct(c1, W, H)
     st16 = torch.empty(n, ng.STATE_FLOATS, device=dev)
     ro = ng.render_opts(opts)
     ms_m16 = _timed(lambda: ng.ngprt_render(ds16.struct, fs.occ.struct, cam1, nc1, None, None, None, n, None, ro, None,
                                             ray_state=st16, stream=stream), stream, flush, reps, warm)
     cnt16 = load_counters("hd_fit_1080p_fp16")
-    roof16 = {"bound": "issue", "unit": "G warp instructions/s", "kernel": "march_kernel<16,F16>",
+    roof16 = {"bound": "l1", "unit": "Gwavefronts/s", "kernel": "march_kernel<16,F16>",
               "march_ms": ms_m16, "source_hash": kernel_source_hash()}
     if cnt16:
-        ach = cnt16["warp_instructions_per_sample"] * samples16 / (ms_m16 * 1e-3) / 1e9
-        pk = 4 * 152 * args.clock_hz / 1e9
+        ach = cnt16["l1_wavefronts_per_sample"] * samples16 / (ms_m16 * 1e-3) / 1e9
+        pk = cnt16["l1_wavefronts_peak_per_cycle_per_sm"] * cnt16["sms"] * args.clock_hz / 1e9
+        iss = cnt16["warp_instructions_per_sample"] * samples16 / (ms_m16 * 1e-3) / 1e9
         roof16.update(achieved=ach, peak=pk, frac=ach / pk,
-                      l1_frac=cnt16["l1_wavefronts_per_sample"] * samples16 / (ms_m16 * 1e-3) / (152 * args.clock_hz),
+                      issue={"achieved_G_warp_inst_per_s": iss, "peak": 4 * 152 * args.clock_hz / 1e9,
+                             "frac": iss / (4 * 152 * args.clock_hz / 1e9)},
                       traffic=cnt16["dram_bytes_per_sample"] * samples16)
     else:
         roof16.update(achieved=None, peak=None, frac=None, note="no ncu counters for this kernel source")
