@@ -302,11 +302,12 @@ struct BackwardSampler {
     }
 };
 
-// Resident blocks the reverse march's register allocation must allow.  1 lets it
-// take 255 registers (about 7 warps per SM) and was the fastest measured: 4..8
-// blocks (fewer registers, more warps) made a 2^18-ray training step 5-10% slower.
+// Resident blocks the reverse march's register allocation must allow: 3 (168
+// registers, no spills) was the fastest measured on a 2^18-ray training step of
+// the fitted hd scene (33.4 ms against 34.5 at 1, 255 registers; 34.4 at 4; 35.6 at
+// 5 and 37.7 at 6, where it spills).
 #ifndef NGPRT_BWD_MIN_BLOCKS
-#define NGPRT_BWD_MIN_BLOCKS 1
+#define NGPRT_BWD_MIN_BLOCKS 3
 #endif
 
 template <int L, int AGG, bool kDist = false>

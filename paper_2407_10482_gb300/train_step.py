@@ -4,7 +4,12 @@ L2 loss, reverse pass (rays in the drawn order), Adam on the tables, coarse grid
 and MLP.  Render, loss, reverse pass and Adam run in the library's kernels; torch
 permutes the rays between the two orders.
 
-    python -m paper_2407_10482_gb300.train_step --rays 65536 --steps 5
+    python -m paper_2407_10482_gb300.train_step --rays 65536 --steps 5 [--scene FILE]
+
+Without --scene: the random-weight hd scene and 8 orbit views; with it, a scene
+written by ``checkpoint.save_scene`` (for instance the fitted hd scene of
+``bench.py --save-scene``) and its 8 held-out views.  Targets are uniform random
+colours (the work of a step does not depend on them).
 """
 from __future__ import annotations
 
@@ -54,13 +59,21 @@ def main():
     ap.add_argument("--rays", type=int, default=1 << 18)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--scene", default="", help="a saved scene (checkpoint.save_scene) instead of the random hd scene")
     args = ap.parse_args()
     ng.lib()
-    cfg = S.hd_config()
-    sc = S.make_scene(cfg)
+    if args.scene:
+        from . import checkpoint as CK
+        from . import hdfit as HF
+        sc = CK.load_scene(args.scene)
+        cfg = sc.cfg
+        cams = HF.test_cameras(cfg, 8)
+    else:
+        cfg = S.hd_config()
+        sc = S.make_scene(cfg)
+        cams = S.orbit_cameras(cfg, 8)
     ds = ng.DeviceScene(cfg, sc.tables, sc.coarse, sc.mlp_w)
     docc = ng.DeviceOcc(sc.occ, cfg.R_O, cfg.n_occ_levels)
-    cams = S.orbit_cameras(cfg, 8)
     pix = torch.as_tensor(S.random_pixels(args.rays, 8, cfg.W, cfg.H, 3)).cuda()
     targets = torch.rand(args.rays, 3, generator=torch.Generator().manual_seed(3)).cuda()
     step, loss = make_step(cfg, ds, docc, cams, targets, pix)
