@@ -280,9 +280,10 @@ def fitted_forms(args, fs, opts, dev, stream, flush):
     # ncu counters of this kernel source on this workload
     cam1, nc1 = ng.cameras_struct(c1, W, H)
     st16 = torch.empty(n, ng.STATE_FLOATS, device=dev)
+    ws16 = torch.empty(ng.ngprt_render_workspace_bytes(ds16.struct, n), dtype=torch.uint8, device=dev)
     ro = ng.render_opts(opts)
     ms_m16 = _timed(lambda: ng.ngprt_render(ds16.struct, fs.occ.struct, cam1, nc1, None, None, None, n, None, ro, None,
-                                            ray_state=st16, stream=stream), stream, flush, reps, warm)
+                                            ray_state=st16, workspace=ws16, stream=stream), stream, flush, reps, warm)
     cnt16 = load_counters("hd_fit_1080p_fp16")
     roof16 = {"bound": "l1", "unit": "Gwavefronts/s", "kernel": "march_kernel<16,F16>",
               "march_ms": ms_m16, "source_hash": kernel_source_hash()}
@@ -611,13 +612,14 @@ def main():
     cam_arr, n_cams = ng.cameras_struct(cams, cfg.W, cfg.H)
     ro = ng.render_opts(opts)
     state = torch.empty(n, ng.STATE_FLOATS, device=dev)
+    ws = torch.empty(ng.ngprt_render_workspace_bytes(ds.struct, n), dtype=torch.uint8, device=dev)
     rgb = torch.empty(n, 3, device=dev)
     depth = torch.empty(n, device=dev)
     opac = torch.empty(n, device=dev)
 
     def march():
         ng.ngprt_render(ds.struct, docc.struct, cam_arr, n_cams, None, None, None, n, None, ro, None,
-                        ray_state=state, stream=stream)
+                        ray_state=state, workspace=ws, stream=stream)
 
     def shade():
         ng.ngprt_shade(ds.struct, state, n, opts.bg, rgb, depth, opac, stream=stream)
@@ -678,7 +680,7 @@ def main():
         e0.record(stream)
         cam_arr_k, _ = ng.cameras_struct(cams, cfg.W, cfg.H)
         ng.ngprt_render(ds.struct, docc.struct, cam_arr_k, n_cams, None, None, None, n, None, ro, rgb, depth, opac,
-                        None, state, None, stream=stream)
+                        None, state, ws, stream=stream)
         host["rgb"].copy_(rgb, non_blocking=True)
         host["depth"].copy_(depth, non_blocking=True)
         host["opacity"].copy_(opac, non_blocking=True)

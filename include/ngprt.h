@@ -299,7 +299,14 @@ size_t ngprt_render_workspace_bytes(const ngprt_scene* scene, int64_t n_rays);
  *                ngprt_render_backward consumes.
  *   workspace  : 256-byte aligned, at least ngprt_render_workspace_bytes(n) bytes
  *                (the per-ray state when ray_state is NULL); NULL allowed with
- *                ray_state.  One fused march kernel runs either way.
+ *                ray_state.  One fused march kernel runs either way.  The 8 bytes
+ *                after the state's rounded size (ngprt_render_workspace_bytes(n) -
+ *                256) hold a counter from which the kernel's warps take image tiles
+ *                (runs of 32 rays for pixel_ids or explicit rays) at run time, zeroed
+ *                on `stream` before the launch.  Without a workspace of that size,
+ *                each warp renders the tile of its own index.  The counter makes
+ *                concurrent calls that share one workspace race, as the state
+ *                already does.
  */
 int32_t ngprt_render(const ngprt_scene* scene, const ngprt_occ* occ, const ngprt_camera* cams, int32_t n_cams,
                      const int32_t* pixel_ids, const float* rays_o, const float* rays_d, int64_t n_rays,

@@ -388,6 +388,12 @@ extern "C" int32_t ngprt_render(const ngprt_scene* scene, const ngprt_occ* occ, 
     p.state = state;
     p.stats = ray_stats;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // tiles (runs of 32 rays for ray lists) are handed out at run time from a counter
+    // in the workspace's bytes past the state (the static tile-per-warp grid without)
+    if (ws && ws_bytes >= state_bytes(n_rays) + sizeof(unsigned long long)) {
+        p.tile_counter = reinterpret_cast<unsigned long long*>(ws + state_bytes(n_rays));
+        cudaMemsetAsync(p.tile_counter, 0, sizeof(unsigned long long), st);
+    }
     if ((rc = launch_march_any(scene->L, scene->table_dtype, scene->aggregation, p, grid, st)) != NGPRT_OK)
         return rc;
     if (!rgb) return cuda_status(fn);

@@ -114,6 +114,8 @@ class FastRenderer:
             self.a_hat = torch.empty(n, device=d)
             self.state = torch.empty(n, ng.STATE_FLOATS, device=d)
             self.stats = torch.empty(n, 2, dtype=torch.int32, device=d)
+            # the render's workspace (the march's tile counter past the state's bytes)
+            self.ws = torch.empty(ng.ngprt_render_workspace_bytes(self.scene.struct, n), dtype=torch.uint8, device=d)
             self._n = n
 
     def render(self, opts, cams: np.ndarray, W: int, H: int, rgb, depth=None, opacity=None, stats=False,
@@ -127,7 +129,7 @@ class FastRenderer:
         ng.ngprt_propose(self.w, cam_arr, n_cams, None, None, None, n, c.in_scale, c.t_scale, c.margin_near,
                          c.margin_far, c.a_min, self.interval, self.a_hat, stream=stream)
         ng.ngprt_render(self.scene.struct, self.occ.struct, cam_arr, n_cams, None, None, None, n, self.interval, ro,
-                        None, ray_stats=st, ray_state=self.state, stream=stream)
+                        None, ray_stats=st, ray_state=self.state, workspace=self.ws, stream=stream)
         ng.ngprt_render_fallback(self.scene.struct, self.occ.struct, cam_arr, n_cams, None, None, None, n,
                                  self.interval, self.a_hat, c.fallback, ro, self.state, st, stream=stream)
         ng.ngprt_shade(self.scene.struct, self.state, n, opts.bg, rgb, depth, opacity, stream=stream)
