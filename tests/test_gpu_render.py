@@ -364,3 +364,44 @@ def test_maximum_view_batch(ng):
     _compare(sub, orc.render(opts, cams=cams, pix=pix))
     with pytest.raises(ng.NgprtError, match="n_cams"):
         rend.render(opts, cams=S.orbit_cameras(cfg, 65), W=cfg.W, H=cfg.H)
+
+
+@pytest.mark.parametrize("mode", ["tiles", "pixel_ids", "rays"])
+@pytest.mark.parametrize("table_dtype", [0, 1])
+def test_run_time_tile_scheduling_matches_the_static_grid(ng, mode, table_dtype):
+    """With a workspace the march kernel's warps take tiles (runs of 32 listed rays)
+    from a counter; without one each warp renders the tile of its own index.  Every
+    ray's arithmetic is the same either way, so the per-ray state and counts must be
+    bit-identical.  Ragged tiles and several views included; the hd scene's FP16 form
+    runs at its own block count."""
+    cfg = S.hd_config(W=203, H=117)
+    sc = S.make_scene(cfg)
+    ds = ng.DeviceScene(cfg, sc.tables, sc.coarse, sc.mlp_w, table_dtype=table_dtype, mlp_dtype=table_dtype)
+    docc = ng.DeviceOcc(sc.occ, cfg.R_O, cfg.n_occ_levels)
+    ro = ng.render_opts(S.default_options(cfg))
+    cams = S.orbit_cameras(cfg, 3, azimuth0=7.0, step_deg=120.0)
+    cam_arr, n_cams = ng.cameras_struct(cams, cfg.W, cfg.H)
+    pix = rays_o = rays_d = None
+    if mode == "tiles":
+        n = n_cams * cfg.W * cfg.H
+    elif mode == "pixel_ids":
+        n = 20011
+        pix = torch.as_tensor(S.random_pixels(n, 3, cfg.W, cfg.H, 5)).cuda()
+    else:
+        n = 20011
+        o, d = S.random_rays(n, 9, False)
+        rays_o, rays_d = torch.as_tensor(o).cuda(), torch.as_tensor(d).cuda()
+        cam_arr, n_cams = None, 0
+    out = {}
+    for name, ws_bytes in (("static", 0), ("counter", ng.ngprt_render_workspace_bytes(ds.struct, n))):
+        state = torch.full((n, ng.STATE_FLOATS), float("nan"), device="cuda")
+        stats = torch.full((n, 2), -1, dtype=torch.int32, device="cuda")
+        ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda") if ws_bytes else None
+        for _ in range(2):   # the counter is zeroed again before every launch
+            ng.ngprt_render(ds.struct, docc.struct, cam_arr, n_cams, pix, rays_o, rays_d, n, None, ro, None,
+                            ray_stats=stats, ray_state=state, workspace=ws)
+        torch.cuda.synchronize()
+        out[name] = (state.cpu().numpy().view(np.uint32), stats.cpu().numpy())
+    assert (out["static"][1] >= 0).all()
+    assert np.array_equal(out["static"][0], out["counter"][0])
+    assert np.array_equal(out["static"][1], out["counter"][1])
